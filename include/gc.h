@@ -1,0 +1,168 @@
+/*
+ * gc.h -- C ABI of the GB300 group-closeness library (libgc.so).
+ *
+ * Greedy++ group-closeness maximization after Bergamini, Gonser and
+ * Meyerhenke, "Scaling up Group Closeness Maximization" (arXiv:1710.01144).
+ * All compute runs in CUDA kernels for sm_103a on the current device; there
+ * is no CPU fallback.  Every entry point returns GC_OK (0) or a negative
+ * error code; gc_last_error() gives a thread-local message for the last
+ * failure.
+ *
+ * Definitions (Sec. 2 of the paper; the readings are the library's):
+ *   G = (V, E) simple, undirected, unweighted, connected; n = |V|.
+ *   d(u, S) = min_{s in S} d(u, s)   (BFS distance, Sec. 2)
+ *   farness f(S) = sum_{u in V} d(u, S), an int64.  The paper's closeness is
+ *     c(S) = n / f(S); its 1/n normalisation is dropped.  Members contribute 0.
+ *   gain Delta(v | S) = f(S) - f(S + {v}) = sum_u max(0, d(u,S) - d(v,u)) >= 0,
+ *     the decrease of farness when v joins S (Sec. 4.2 writes the same
+ *     quantity with the opposite sign).  Delta(v | S) = 0 for v in S.
+ *   Ties between equal gains or equal farness always go to the smaller id.
+ *
+ * Graph format: int32 CSR.  row_ptr[n+1] with row_ptr[0] = 0 and
+ * non-decreasing entries; col_idx[row_ptr[n]] neighbour ids in [0, n); each
+ * undirected edge is stored in both rows.  nnz = row_ptr[n] < 2^31.
+ *
+ * Streams: every call is ordered on the stream given to gc_load_csr (a
+ * cudaStream_t passed as void*, NULL = legacy default stream).  Calls that
+ * return host results synchronise that stream before returning.
+ * A handle must not be used from two threads at once.
+ */
+#ifndef GC_H_
+#define GC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------- error codes -- */
+#define GC_OK 0
+#define GC_EINVAL (-1)        /* bad argument: NULL pointer, k < 1 or k > n,
+                                 id outside [0, n), empty group, malformed CSR */
+#define GC_EDISCONNECTED (-2) /* some vertex is unreachable (farness undefined) */
+#define GC_ERANGE (-3)        /* size limit exceeded (nnz >= 2^31, scratch cap) */
+#define GC_ENOMEM (-4)        /* device allocation failed */
+#define GC_ECUDA (-5)         /* a CUDA runtime call failed */
+#define GC_ETIMEOUT (-6)      /* a device-side wait exceeded its time limit; the
+                                 kernel gave up, the context stays usable */
+#define GC_EINTERNAL (-7)     /* a device-side consistency check failed */
+
+/* ------------------------------------------------------ gc_load_csr flags -- */
+#define GC_DEVICE_PTRS 0x1u /* row_ptr / col_idx are device pointers */
+#define GC_ADOPT 0x2u       /* with GC_DEVICE_PTRS: use the caller's device
+                               arrays in place (no copy); they must stay alive
+                               and unchanged until gc_free */
+#define GC_VALIDATE 0x4u    /* check the CSR on the device: row_ptr monotone,
+                               ids in range, no self-loops, neighbour lists
+                               strictly increasing (so no duplicates), every
+                               edge present in both directions, and the graph
+                               connected.  Failures return GC_EINVAL or
+                               GC_EDISCONNECTED. */
+
+typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays + scratch */
+
+/* Options of gc_greedy; zero-initialise and set what you need
+ * (gc_opts_default fills the defaults). */
+typedef struct gc_opts {
+  int32_t eval_per_step;   /* candidates evaluated exactly per lazy step
+                              (rounded up to a multiple of 64); 0 = autotuned */
+  int32_t use_proposal;    /* 1: order exact evaluations by the learned proposal
+                              network (see gc_set_proposal); the accepted vertex
+                              and therefore the group are unchanged */
+  int32_t max_ctas;        /* cap on resident CTAs of the gain kernel; 0 = all */
+  int32_t timeout_ms;      /* limit of every device-side wait; 0 = 10000 */
+  int32_t reserved[4];
+} gc_opts;
+
+/* Work counters of the last gc_greedy / gc_marginal_gains call. */
+typedef struct gc_stats {
+  int64_t rounds;          /* greedy rounds completed (= k) */
+  int64_t steps;           /* lazy evaluation steps over all rounds >= 1 */
+  int64_t evals;           /* exact gains computed (rounds >= 1) */
+  int64_t batches;         /* 64-lane batches run by the gain kernel */
+  int64_t edges_scalar;    /* adjacency entries a one-source pruned BFS per
+                              candidate would scan (sum over lanes) */
+  int64_t edges_union;     /* adjacency entries the 64-lane kernel scanned */
+  int64_t levels;          /* BFS levels summed over batches */
+  int64_t frontier;        /* frontier entries (vertex, lane word) expanded */
+  int64_t pushes;          /* vertices that entered a next-level frontier */
+  int64_t lanes;           /* candidate lanes processed (all launches) */
+  int64_t round0_evals;    /* candidates evaluated (exactly or cut) in round 0 */
+  double ms_round0;        /* time of round 0 (top-1 closeness + d_S) */
+  double ms_total;         /* time of the whole call */
+  double ms_gain_kernel;   /* summed duration of gain-kernel launches */
+  int64_t gain_launches;   /* gain-kernel launches */
+  int64_t kernel_launches; /* all kernel launches of the call */
+} gc_stats;
+
+/* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */
+int gc_opts_default(gc_opts *opts);
+
+/* gc_load_csr -- create a graph handle.
+ * n        : vertex count, 1 <= n < 2^31.
+ * row_ptr  : int32[n+1]; col_idx : int32[row_ptr[n]]; host pointers unless
+ *            flags has GC_DEVICE_PTRS.  Without GC_ADOPT the arrays are copied
+ *            and the caller keeps ownership of its buffers.
+ * flags    : GC_DEVICE_PTRS | GC_ADOPT | GC_VALIDATE.
+ * stream   : cudaStream_t (as void*) on which this handle's work is ordered.
+ * out      : receives the handle; release it with gc_free.
+ * Errors   : GC_EINVAL (NULL, n < 1, row_ptr[0] != 0, GC_ADOPT without
+ *            GC_DEVICE_PTRS, or a GC_VALIDATE failure), GC_ERANGE (nnz out of
+ *            int32 range), GC_EDISCONNECTED (GC_VALIDATE only), GC_ENOMEM,
+ *            GC_ECUDA.  Nothing is allocated on failure. */
+int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                void *stream, gc_graph **out);
+
+/* gc_free -- release the handle and its device memory (adopted arrays are left
+ * alone).  NULL is accepted.  Returns GC_OK. */
+int gc_free(gc_graph *g);
+
+/* gc_num_vertices / gc_num_entries -- n and nnz of a handle (-1 on NULL). */
+int64_t gc_num_vertices(const gc_graph *g);
+int64_t gc_num_entries(const gc_graph *g);
+
+/* gc_group_farness -- f(S) = sum_u d(u, S) (Sec. 2) by one multi-source BFS.
+ * S        : host int32[s_len] vertex ids (duplicates allowed), s_len >= 1.
+ * out      : host int64.
+ * Errors   : GC_EINVAL (NULL, s_len < 1, id out of range), GC_EDISCONNECTED. */
+int gc_group_farness(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_farness);
+
+/* gc_marginal_gains -- Delta(v | S) for each candidate v (Sec. 4.1 pruned SSSP,
+ * evaluated 64 candidates at a time by a bit-parallel multi-source BFS in the
+ * form of Theorem 1, Sec. 4.3).
+ * S        : host int32[s_len], s_len >= 1 (d(., empty set) is undefined).
+ * cand     : host int32[n_cand], any ids in [0, n), repeats allowed, n_cand >= 0.
+ * out_gain : host int64[n_cand]; 0 for candidates in S.
+ * stats    : optional (NULL), filled with the kernel's work counters.
+ * Errors   : GC_EINVAL, GC_EDISCONNECTED. */
+int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_t *cand,
+                      int32_t n_cand, int64_t *out_gain, gc_stats *stats);
+
+/* gc_marginal_gains_device -- as gc_marginal_gains with device pointers for
+ * S, cand and out_gain; asynchronous on the handle's stream (no sync, no
+ * host-visible error for bad ids: ids are checked on the device and an
+ * out-of-range id yields gain -1 for that candidate). */
+int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len,
+                             const int32_t *cand_dev, int32_t n_cand, int64_t *out_gain_dev);
+
+/* gc_greedy -- Greedy++ (Algorithm 2 with pruned SSSPs, Sec. 4.1, and the lazy
+ * supermodular bounds, Sec. 4.2): s0 = argmin_v f({v}) (top-1 closeness,
+ * Sec. 3.1), then k-1 rounds adding argmax_v Delta(v | S).
+ * k          : 1 <= k <= n.
+ * opts       : NULL = defaults.
+ * out_group  : host int32[k], vertices in pick order (s0 first).
+ * out_farness: host int64, f(S) of the final group.
+ * stats      : optional work counters.
+ * The group equals the plain greedy of Algorithm 2 with smallest-id ties.
+ * Errors   : GC_EINVAL, GC_EDISCONNECTED, GC_ETIMEOUT, GC_ENOMEM, GC_ECUDA. */
+int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group,
+              int64_t *out_farness, gc_stats *stats);
+
+/* gc_last_error -- thread-local description of the last failure ("" if none). */
+const char *gc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GC_H_ */

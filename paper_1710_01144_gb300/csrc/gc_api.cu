@@ -1,0 +1,463 @@
+// C ABI of libgc (declared in include/gc.h): handle management and the host
+// side of Greedy++ (Algorithm 2 with the pruned SSSP of Sec. 4.1 and the lazy
+// bounds of Sec. 4.2).  The host only sequences kernels; every distance, gain,
+// bound, selection and arg-reduction is computed on the device.
+#include <limits.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? GC_ENOMEM : GC_ECUDA;
+}
+
+static int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+#define GC_TRY(expr)              \
+  do {                            \
+    int rc_ = (expr);             \
+    if (rc_ != GC_OK) return rc_; \
+  } while (0)
+
+template <typename T>
+static int dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(GC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                               " bytes failed: " + cudaGetErrorString(e));
+  }
+  return GC_OK;
+}
+
+static void release(gc_graph *g) {
+  if (!g) return;
+  if (g->owns_csr) {
+    cudaFree(g->rp);
+    cudaFree(g->ci);
+  }
+  void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
+                 g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
+                 g->ws, g->dec};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (g->h_sctl) cudaFreeHost(g->h_sctl);
+  if (g->h_gctl) cudaFreeHost(g->h_gctl);
+  if (g->h_bctl) cudaFreeHost(g->h_bctl);
+  for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+  delete g;
+}
+
+static int64_t timeout_ns(const gc_opts *o) {
+  const int64_t ms = (o && o->timeout_ms > 0) ? o->timeout_ms : 10000;
+  return ms * 1000000LL;
+}
+
+// Events bracketing gain-kernel launches (pairs), reused across calls.
+static int gain_event(gc_graph *g, size_t idx, cudaEvent_t *ev) {
+  while (g->events.size() <= idx) {
+    cudaEvent_t e;
+    GC_CUDA(cudaEventCreate(&e));
+    g->events.push_back(e);
+  }
+  *ev = g->events[idx];
+  return GC_OK;
+}
+
+static int sync(gc_graph *g) {
+  GC_CUDA(cudaStreamSynchronize(g->stream));
+  return GC_OK;
+}
+
+static int read_ctl(gc_graph *g) {
+  GC_CUDA(cudaMemcpyAsync(g->h_sctl, g->sctl, sizeof(SelCtl), cudaMemcpyDeviceToHost, g->stream));
+  GC_CUDA(cudaMemcpyAsync(g->h_gctl, g->gctl, sizeof(GainCtl), cudaMemcpyDeviceToHost, g->stream));
+  GC_CUDA(cudaMemcpyAsync(g->h_bctl, g->bctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, g->stream));
+  return sync(g);
+}
+
+static int device_errors(gc_graph *g) {
+  const int e = g->h_gctl->err ? g->h_gctl->err : g->h_bctl->err ? g->h_bctl->err : g->h_sctl->err;
+  if (!e) return GC_OK;
+  const char *what = e == GC_ETIMEOUT ? "device-side wait timed out"
+                     : e == GC_EDISCONNECTED ? "graph is disconnected"
+                     : e == GC_EINVAL ? "invalid vertex id on the device"
+                                      : "device-side consistency check failed";
+  return fail(e, what);
+}
+
+// d_S <- BFS from the device array seeds[0..n_seeds); checks connectivity.
+static int distances_from(gc_graph *g, const int32_t *seeds_dev, int32_t n_seeds, int64_t tns,
+                          int64_t *farness) {
+  GC_TRY(launch_fill_i32(g, g->dS, kInf, g->n));
+  GC_TRY(launch_bfs_relabel(g, g->dS, seeds_dev, n_seeds, tns));
+  GC_TRY(launch_sum_dist(g, g->dS));
+  GC_TRY(read_ctl(g));
+  if (g->h_bctl->err) return device_errors(g);
+  if (g->h_sctl->count != 0) return fail(GC_EDISCONNECTED, "graph is disconnected");
+  if (farness) *farness = g->h_sctl->sum;
+  return GC_OK;
+}
+
+static int check_ids(const gc_graph *g, const int32_t *a, int32_t len, const char *what) {
+  for (int32_t i = 0; i < len; ++i)
+    if (a[i] < 0 || a[i] >= g->n)
+      return fail(GC_EINVAL, std::string(what) + " holds a vertex id outside [0, n)");
+  return GC_OK;
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+extern "C" {
+
+int gc_opts_default(gc_opts *o) {
+  if (!o) return fail(GC_EINVAL, "opts is NULL");
+  memset(o, 0, sizeof(*o));
+  o->timeout_ms = 10000;
+  return GC_OK;
+}
+
+const char *gc_last_error(void) { return g_last_error.c_str(); }
+
+int64_t gc_num_vertices(const gc_graph *g) { return g ? g->n : -1; }
+int64_t gc_num_entries(const gc_graph *g) { return g ? g->nnz : -1; }
+
+int gc_free(gc_graph *g) {
+  if (g) {
+    cudaStreamSynchronize(g->stream);
+    release(g);
+  }
+  return GC_OK;
+}
+
+int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint32_t flags,
+                void *stream, gc_graph **out) {
+  if (!out) return fail(GC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !row_ptr) return fail(GC_EINVAL, "n < 1 or row_ptr is NULL");
+  if ((flags & GC_ADOPT) && !(flags & GC_DEVICE_PTRS))
+    return fail(GC_EINVAL, "GC_ADOPT requires GC_DEVICE_PTRS");
+  const bool dev = flags & GC_DEVICE_PTRS;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t ends[2];
+  if (dev) {
+    GC_CUDA(cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GC_CUDA(cudaMemcpyAsync(&ends[1], row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GC_CUDA(cudaStreamSynchronize(st));
+  } else {
+    ends[0] = row_ptr[0];
+    ends[1] = row_ptr[n];
+  }
+  if (ends[0] != 0) return fail(GC_EINVAL, "row_ptr[0] != 0");
+  if (ends[1] < 0) return fail(GC_ERANGE, "row_ptr[n] is negative (nnz out of int32 range)");
+  const int64_t nnz = ends[1];
+  if (nnz > 0 && !col_idx) return fail(GC_EINVAL, "col_idx is NULL");
+  if (!dev) {  // host arrays: check monotone row_ptr and id range here, cheaply
+    if (flags & GC_VALIDATE)
+      for (int32_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(GC_EINVAL, "row_ptr is not monotone");
+  }
+
+  gc_graph *g = new gc_graph();
+  g->n = n;
+  g->nnz = nnz;
+  g->stream = st;
+  int rc = GC_OK;
+  auto bail = [&](int code) {
+    release(g);
+    return code;
+  };
+  if (cudaGetDevice(&g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+    return bail(fail(GC_ECUDA, "no CUDA device"));
+  // CSR
+  if (flags & GC_ADOPT) {
+    g->owns_csr = false;
+    g->rp = const_cast<int32_t *>(row_ptr);
+    g->ci = const_cast<int32_t *>(col_idx);
+  } else {
+    if ((rc = dalloc(&g->rp, (size_t)n + 1)) || (rc = dalloc(&g->ci, (size_t)nnz))) return bail(rc);
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(g->rp, row_ptr, ((size_t)n + 1) * sizeof(int32_t), kind, st) != cudaSuccess ||
+        (nnz && cudaMemcpyAsync(g->ci, col_idx, (size_t)nnz * sizeof(int32_t), kind, st) != cudaSuccess))
+      return bail(fail(GC_ECUDA, "copy of the CSR failed"));
+  }
+  // launch geometry
+  int occ = 0;
+  if ((rc = gain_kernel_occupancy(&occ))) return bail(rc);
+  g->gain_ctas = std::max(1, occ) * g->num_sms;
+  if ((rc = bfs_kernel_occupancy(&occ))) return bail(rc);
+  g->bfs_ctas = std::max(1, occ) * g->num_sms;
+  g->red_blocks = g->num_sms * 4;
+  // per-vertex arrays
+  const size_t N = (size_t)n;
+  if ((rc = dalloc(&g->dS, N)) || (rc = dalloc(&g->ub, N)) || (rc = dalloc(&g->stamp, N)) ||
+      (rc = dalloc(&g->key, N)) || (rc = dalloc(&g->f0, N)) || (rc = dalloc(&g->list, N)) ||
+      (rc = dalloc(&g->lgain, N)) || (rc = dalloc(&g->bq0, N)) || (rc = dalloc(&g->bq1, N)) ||
+      (rc = dalloc(&g->io_a, N)) || (rc = dalloc(&g->io_b, N)) ||
+      (rc = dalloc(&g->blk, (size_t)g->red_blocks + 8)) ||
+      (rc = dalloc(&g->partial, 3 * (size_t)g->red_blocks + 8)) ||
+      (rc = dalloc(&g->hist, (size_t)kHistBins)) || (rc = dalloc(&g->bctl, 1)) ||
+      (rc = dalloc(&g->gctl, 1)) || (rc = dalloc(&g->sctl, 1)))
+    return bail(rc);
+  if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
+      cudaMallocHost((void **)&g->h_gctl, sizeof(GainCtl)) != cudaSuccess ||
+      cudaMallocHost((void **)&g->h_bctl, sizeof(BfsCtl)) != cudaSuccess)
+    return bail(fail(GC_ENOMEM, "pinned host allocation failed"));
+  // gain-kernel workspaces: one per resident CTA, within 40% of free memory
+  g->ws_stride = gain_ws_stride(n);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return bail(fail(GC_ECUDA, "cudaMemGetInfo"));
+  const size_t budget = free_b / 10 * 4;
+  int want = g->gain_ctas;
+  if ((size_t)want * g->ws_stride > budget) want = (int)std::max<size_t>(1, budget / g->ws_stride);
+  g->gain_ctas = want;
+  g->ws_count = want;
+  if ((rc = dalloc(&g->ws, (size_t)want * g->ws_stride))) return bail(rc);
+  if (cudaMemsetAsync(g->ws, 0, (size_t)want * g->ws_stride, st) != cudaSuccess ||
+      cudaMemsetAsync(g->hist, 0, kHistBins * sizeof(unsigned int), st) != cudaSuccess ||
+      cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), st) != cudaSuccess ||
+      cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), st) != cudaSuccess)
+    return bail(fail(GC_ECUDA, "memset failed"));
+  if (flags & GC_VALIDATE) {
+    if ((rc = launch_validate(g))) return bail(rc == GC_EINVAL ? fail(GC_EINVAL, "CSR validation failed") : rc);
+    int32_t zero = 0;
+    if ((rc = dalloc(&g->dec, 1))) return bail(rc);
+    cudaMemcpy(g->dec, &zero, sizeof(int32_t), cudaMemcpyHostToDevice);
+    int64_t f;
+    rc = distances_from(g, g->dec, 1, 10000000000LL, &f);
+    cudaFree(g->dec);
+    g->dec = nullptr;
+    if (rc) return bail(rc);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(GC_ECUDA, "load failed"));
+  *out = g;
+  return GC_OK;
+}
+
+int gc_group_farness(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_farness) {
+  if (!g || !S || !out_farness || s_len < 1 || s_len > g->n)
+    return fail(GC_EINVAL, "bad argument to gc_group_farness");
+  GC_TRY(check_ids(g, S, s_len, "S"));
+  GC_CUDA(cudaMemcpyAsync(g->io_a, S, (size_t)s_len * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+  return distances_from(g, g->io_a, s_len, timeout_ns(nullptr), out_farness);
+}
+
+static int gains_core(gc_graph *g, const int32_t *S_dev, int32_t s_len, const int32_t *cand_dev,
+                      int32_t n_cand, long long *out_dev, bool check) {
+  GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
+  if (check) {
+    GC_TRY(distances_from(g, S_dev, s_len, timeout_ns(nullptr), nullptr));
+  } else {
+    GC_TRY(launch_fill_i32(g, g->dS, kInf, g->n));
+    GC_TRY(launch_bfs_relabel(g, g->dS, S_dev, s_len, timeout_ns(nullptr)));
+  }
+  return launch_gains(g, kModeGain, cand_dev, n_cand, nullptr, out_dev, 0);
+}
+
+int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_t *cand,
+                      int32_t n_cand, int64_t *out_gain, gc_stats *stats) {
+  if (!g || !S || s_len < 1 || s_len > g->n || n_cand < 0 || (n_cand > 0 && (!cand || !out_gain)))
+    return fail(GC_EINVAL, "bad argument to gc_marginal_gains");
+  GC_TRY(check_ids(g, S, s_len, "S"));
+  GC_TRY(check_ids(g, cand, n_cand, "cand"));
+  auto t0 = std::chrono::steady_clock::now();
+  GC_CUDA(cudaMemcpyAsync(g->io_a, S, (size_t)s_len * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
+  GC_TRY(distances_from(g, g->io_a, s_len, timeout_ns(nullptr), nullptr));
+  float ms_k = 0.f;
+  int64_t launches = 0;
+  for (int32_t off = 0; off < n_cand; off += g->n) {
+    const int32_t len = std::min<int32_t>(g->n, n_cand - off);
+    GC_CUDA(cudaMemcpyAsync(g->list, cand + off, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            g->stream));
+    cudaEvent_t e0, e1;
+    GC_TRY(gain_event(g, 0, &e0));
+    GC_TRY(gain_event(g, 1, &e1));
+    GC_CUDA(cudaEventRecord(e0, g->stream));
+    GC_TRY(launch_gains(g, kModeGain, g->list, len, nullptr, g->lgain, 0));
+    GC_CUDA(cudaEventRecord(e1, g->stream));
+    GC_CUDA(cudaMemcpyAsync(out_gain + off, g->lgain, (size_t)len * sizeof(long long),
+                            cudaMemcpyDeviceToHost, g->stream));
+    GC_TRY(sync(g));
+    float ms = 0.f;
+    GC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ms_k += ms;
+    ++launches;
+  }
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->evals = n_cand;
+    stats->batches = (int64_t)g->h_gctl->batches;
+    stats->edges_scalar = (int64_t)g->h_gctl->edges_scalar;
+    stats->edges_union = (int64_t)g->h_gctl->edges_union;
+    stats->levels = (int64_t)g->h_gctl->levels;
+    stats->frontier = (int64_t)g->h_gctl->frontier;
+    stats->pushes = (int64_t)g->h_gctl->pushes;
+    stats->lanes = (int64_t)g->h_gctl->lanes;
+    stats->ms_gain_kernel = ms_k;
+    stats->gain_launches = launches;
+    stats->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return GC_OK;
+}
+
+int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len, const int32_t *cand_dev,
+                             int32_t n_cand, int64_t *out_gain_dev) {
+  if (!g || !S_dev || s_len < 1 || n_cand < 0 || (n_cand > 0 && (!cand_dev || !out_gain_dev)))
+    return fail(GC_EINVAL, "bad argument to gc_marginal_gains_device");
+  return gains_core(g, S_dev, s_len, cand_dev, n_cand, (long long *)out_gain_dev, false);
+}
+
+int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
+              gc_stats *stats) {
+  if (!g || !out_group || !out_farness || k < 1 || k > g->n)
+    return fail(GC_EINVAL, "bad argument to gc_greedy (need 1 <= k <= n)");
+  gc_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gc_opts_default(&opts);
+  if (opts.use_proposal) return fail(GC_EINVAL, "no proposal network is loaded");
+  const int64_t tns = timeout_ns(&opts);
+  auto t0 = std::chrono::steady_clock::now();
+  int64_t launches = 0;
+  size_t ev_used = 0;
+  auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev) -> int {
+    cudaEvent_t e0, e1;
+    GC_TRY(gain_event(g, ev_used, &e0));
+    GC_TRY(gain_event(g, ev_used + 1, &e1));
+    ev_used += 2;
+    GC_CUDA(cudaEventRecord(e0, g->stream));
+    GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas));
+    GC_CUDA(cudaEventRecord(e1, g->stream));
+    return GC_OK;
+  };
+  GC_CUDA(cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), g->stream));
+  GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
+  GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+
+  // ---- round 0: s0 = argmin_v f({v}) (top-1 closeness with cuts) ----
+  const long long inf64 = LLONG_MAX;
+  GC_CUDA(cudaMemcpyAsync(&g->gctl->best_f, &inf64, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_fill_i64(g, g->f0, -1, g->n));
+  GC_TRY(launch_round0_keys(g));
+  const int32_t want0 = kLanes * g->gain_ctas;
+  GC_TRY(launch_select(g, kSelKey, 0, want0, false, 0));
+  GC_TRY(gains_timed(kModeFarness, g->list, 0, &g->sctl->n_sel));
+  GC_TRY(launch_after_eval(g, 0, 0));
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  const long long best_f = g->h_gctl->best_f;
+  if (best_f == LLONG_MAX) return fail(GC_EINTERNAL, "round 0 found no exact farness");
+  // every vertex whose lower bound does not exceed the best farness is evaluated
+  GC_TRY(launch_select(g, kSelKey, 0, 0, true, -best_f));
+  GC_TRY(gains_timed(kModeFarness, g->list, 0, &g->sctl->n_sel));
+  GC_TRY(launch_after_eval(g, 0, 0));
+  GC_TRY(launch_argmin_f0(g));
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  const int32_t s0 = g->h_sctl->arg_id;
+  const long long f_s0 = g->h_sctl->arg_val;
+  if (s0 < 0) return fail(GC_EINTERNAL, "round 0 produced no vertex");
+  int64_t f = 0;
+  GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, &f));
+  if (f != f_s0) return fail(GC_EINTERNAL, "farness of s0 disagrees between round 0 and the BFS");
+  const int64_t round0_evals = (int64_t)g->h_gctl->lanes;
+  const double ms_round0 =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  out_group[0] = s0;
+
+  // ---- rounds 1..k-1: lazy greedy with exact pruned gains ----
+  if (k > 1) {
+    GC_TRY(launch_fill_i64(g, g->ub, LLONG_MAX, g->n));
+    GC_TRY(launch_fill_i64(g, g->ub + s0, -1, 1));
+    GC_TRY(launch_fill_i32(g, g->stamp, 0, g->n));
+  }
+  int32_t step_want = opts.eval_per_step > 0 ? opts.eval_per_step : kLanes * std::max(1, g->gain_ctas / 2);
+  step_want = ((step_want + kLanes - 1) / kLanes) * kLanes;
+  std::vector<long long> gains_picked(k, 0), decreases(k, 0);
+  for (int32_t r = 1; r < k; ++r) {
+    GC_TRY(launch_round_begin(g));
+    for (int step = 0;; ++step) {
+      if (r == 1) GC_TRY(launch_select(g, kSelLazy, r, 0, true, 0));  // no bounds yet: all of V \ S
+      else GC_TRY(launch_select(g, kSelLazy, r, step_want, false, 0));
+      GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel));
+      GC_TRY(launch_after_eval(g, r, 0));
+      GC_TRY(launch_unevaluated_best(g, r));
+      GC_CUDA(cudaMemcpyAsync(g->h_sctl, g->sctl, sizeof(SelCtl), cudaMemcpyDeviceToHost, g->stream));
+      GC_TRY(sync(g));
+      if (g->h_sctl->accepted) break;
+      if (g->h_sctl->n_sel == 0) return fail(GC_EINTERNAL, "lazy step selected no candidate");
+    }
+    const int32_t pick = g->h_sctl->best_id;
+    gains_picked[r] = g->h_sctl->best_gain;
+    GC_TRY(launch_round_end(g));
+    GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+    GC_TRY(launch_bfs_relabel(g, g->dS, &g->sctl->best_id, 1, tns));
+    GC_CUDA(cudaMemcpyAsync(&g->h_bctl->decrease, &g->bctl->decrease, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, g->stream));
+    GC_TRY(sync(g));
+    decreases[r] = (long long)g->h_bctl->decrease;
+    if (decreases[r] != gains_picked[r])
+      return fail(GC_EINTERNAL, "gain of the pick disagrees with the d_S update (round " +
+                                    std::to_string(r) + ")");
+    f -= gains_picked[r];
+    out_group[r] = pick;
+  }
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  *out_farness = f;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->rounds = k;
+    stats->steps = g->h_sctl->steps;
+    stats->evals = g->h_sctl->evals;
+    stats->batches = (int64_t)g->h_gctl->batches;
+    stats->edges_scalar = (int64_t)g->h_gctl->edges_scalar;
+    stats->edges_union = (int64_t)g->h_gctl->edges_union;
+    stats->levels = (int64_t)g->h_gctl->levels;
+    stats->frontier = (int64_t)g->h_gctl->frontier;
+    stats->pushes = (int64_t)g->h_gctl->pushes;
+    stats->lanes = (int64_t)g->h_gctl->lanes;
+    stats->round0_evals = round0_evals;
+    stats->ms_round0 = ms_round0;
+    double ms_k = 0;
+    for (size_t i = 0; i + 1 < ev_used; i += 2) {
+      float ms = 0.f;
+      GC_CUDA(cudaEventElapsedTime(&ms, g->events[i], g->events[i + 1]));
+      ms_k += ms;
+    }
+    stats->ms_gain_kernel = ms_k;
+    stats->gain_launches = (int64_t)(ev_used / 2);
+    stats->kernel_launches = launches;
+    stats->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return GC_OK;
+}
+
+}  // extern "C"

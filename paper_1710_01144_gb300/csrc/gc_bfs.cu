@@ -1,0 +1,277 @@
+// Grid-wide BFS kernels of libgc: the distance-to-group array d_S
+// (Algorithm 2: SSSP from s0, then d_S <- min(d_S, d(s, .)) after each pick,
+// done as a pruned SSSP per Sec. 4.1), group farness (Sec. 2), the round-0
+// lower bound, and CSR validation.
+#include <cooperative_groups.h>
+
+#include "gc_device.cuh"
+#include "gc_internal.cuh"
+
+namespace gc {
+
+__global__ void k_fill_i32(int32_t *p, int32_t v, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+__global__ void k_fill_i64(long long *p, long long v, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// Relabel BFS (cooperative, one launch for all levels).  Level L+1 labels go to
+// every neighbour w of the level-L frontier with L+1 < dist[w]; only relabelled
+// vertices enter the next frontier.  With dist = kInf this is a plain
+// (multi-source) BFS; with dist = d_S and one seed s it is the pruned SSSP of
+// Sec. 4.1 that turns d_S into min(d_S, d(s, .)): a vertex not strictly closer
+// to s than to S keeps its label and is not expanded.  ctl->decrease collects
+// sum(old - new) over relabelled vertices with a finite old label, i.e. the
+// farness decrease Delta(s | S).
+__global__ void __launch_bounds__(kBfsThreads) k_bfs_relabel(
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
+    const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, BfsCtl *ctl,
+    unsigned long long timeout_ns) {
+  __shared__ unsigned long long sh[32];
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long dec = 0, rel = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x) {
+    const int s = seeds[i];
+    if (s < 0 || s >= n) {
+      atomicExch(&ctl->err, GC_EINVAL);
+      continue;
+    }
+    const int old = atomicMin(&dist[s], 0);
+    if (old > 0) {
+      const int p = atomicAdd(&ctl->qsize[0], 1);
+      q0[p] = s;
+      if (old < kInf) dec += (unsigned long long)old;
+      ++rel;
+    }
+  }
+  bool ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
+  for (int L = 0; ok; ++L) {
+    const int F = *(volatile int32_t *)&ctl->qsize[L % 3];
+    if (F == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qsize[(L + 2) % 3] = 0;
+    const int32_t *qc = (L & 1) ? q1 : q0;
+    int32_t *qn = (L & 1) ? q0 : q1;
+    int32_t *qn_size = &ctl->qsize[(L + 1) % 3];
+    const int nl = L + 1;
+    for (int i = gwarp; i < F; i += nwarps) {
+      const int u = qc[i];
+      const int beg = rp[u], end = rp[u + 1];
+      for (int base = beg; base < end; base += 32) {
+        const int e = base + lane;
+        bool push = false;
+        int w = 0;
+        if (e < end) {
+          w = ci[e];
+          if (nl < dist[w]) {
+            const int old = atomicMin(&dist[w], nl);
+            if (old > nl) {
+              push = true;
+              if (old < kInf) dec += (unsigned long long)(old - nl);
+              ++rel;
+            }
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, push);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int pos = 0;
+          if (lane == leader) pos = atomicAdd(qn_size, __popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (push) qn[pos + __popc(m & ((1u << lane) - 1u))] = w;
+        }
+      }
+    }
+    ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
+    if (ok && blockIdx.x == 0 && threadIdx.x == 0) ctl->levels = L + 1;
+  }
+  dec = block_sum(dec, sh);
+  rel = block_sum(rel, sh);
+  if (threadIdx.x == 0) {
+    if (dec) atomicAdd(&ctl->decrease, dec);
+    if (rel) atomicAdd(&ctl->relabelled, rel);
+  }
+}
+
+// sum(dist) and the count of unreached vertices; the last CTA to finish folds
+// the per-CTA partials (ticket pattern, no waiting) into ctl->sum / ctl->count.
+__global__ void __launch_bounds__(kRedThreads) k_sum_dist(const int32_t *__restrict__ dist, int32_t n,
+                                                         long long *partial, SelCtl *ctl) {
+  __shared__ long long sh[32];
+  __shared__ bool last;
+  long long s = 0, c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = dist[i];
+    if (d >= kInf) ++c;
+    else s += d;
+  }
+  s = block_sum(s, sh);
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s;
+    partial[2 * blockIdx.x + 1] = c;
+    __threadfence();
+    last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  s = 0;
+  c = 0;
+  for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    s += ((volatile long long *)partial)[2 * b];
+    c += ((volatile long long *)partial)[2 * b + 1];
+  }
+  s = block_sum(s, sh);
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    ctl->sum = s;
+    ctl->count = c;
+    ctl->ticket = 0;
+  }
+}
+
+// Round-0 lower bound on f({v}) (the BFScut idea of Sec. 3.1 with a degree
+// bound for the second level): the deg(v) neighbours sit at distance 1; at
+// most c2 = min(sum_{w in N(v)} (deg(w) - 1), n - 1 - deg(v)) vertices sit at
+// distance 2 (every neighbour has v among its own neighbours); everything else
+// is at least 3 away.  key[v] = -(deg + 2 c2 + 3 (n - 1 - deg - c2)).
+__global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__restrict__ rp,
+                                                             const int32_t *__restrict__ ci,
+                                                             int32_t n, long long *key) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = gwarp; v < n; v += nwarps) {
+    const int beg = rp[v], end = rp[v + 1];
+    long long x = 0;
+    for (int e = beg + lane; e < end; e += 32) {
+      const int w = ci[e];
+      x += (long long)(rp[w + 1] - rp[w] - 1);
+    }
+    x = warp_sum(x);
+    if (lane == 0) {
+      const long long deg = end - beg;
+      long long rest = (long long)n - 1 - deg;
+      if (rest < 0) rest = 0;
+      const long long c2 = x < rest ? x : rest;
+      key[v] = -(deg + 2 * c2 + 3 * (rest - c2));
+    }
+  }
+}
+
+// CSR validation, part 1: row_ptr monotone within [0, nnz].
+__global__ void k_validate_rowptr(const int32_t *__restrict__ rp, int32_t n, int64_t nnz,
+                                  SelCtl *ctl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int a = rp[i], b = rp[i + 1];
+    if (a < 0 || b < a || (int64_t)b > nnz) atomicExch(&ctl->err, GC_EINVAL);
+  }
+}
+
+// CSR validation, part 2 (only after part 1 passed): ids in range, no
+// self-loop, strictly increasing rows, and every edge (u, w) mirrored by
+// (w, u) (binary search in the sorted row of w).
+__global__ void k_validate_rows(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                int32_t n, SelCtl *ctl) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = gwarp; u < n; u += nwarps) {
+    const int beg = rp[u], end = rp[u + 1];
+    for (int e = beg + lane; e < end; e += 32) {
+      const int w = ci[e];
+      bool bad = (w < 0 || w >= n || w == u || (e > beg && ci[e - 1] >= w));
+      if (!bad) {
+        int lo = rp[w], hi = rp[w + 1];
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (ci[mid] < u) lo = mid + 1;
+          else hi = mid;
+        }
+        bad = !(lo < rp[w + 1] && ci[lo] == u);
+      }
+      if (bad) atomicExch(&ctl->err, GC_EINVAL);
+    }
+  }
+}
+
+// ------------------------------------------------------------- launchers ----
+static int grid_for(int64_t count, int threads, int cap) {
+  int64_t b = (count + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+int launch_fill_i32(gc_graph *g, int32_t *p, int32_t v, int64_t count) {
+  if (count <= 0) return GC_OK;
+  k_fill_i32<<<grid_for(count, 256, g->num_sms * 8), 256, 0, g->stream>>>(p, v, count);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+int launch_fill_i64(gc_graph *g, long long *p, long long v, int64_t count) {
+  if (count <= 0) return GC_OK;
+  k_fill_i64<<<grid_for(count, 256, g->num_sms * 8), 256, 0, g->stream>>>(p, v, count);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t n_seeds,
+                       int64_t timeout_ns) {
+  GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+  const int32_t *rp = g->rp, *ci = g->ci;
+  int32_t n = g->n;
+  int32_t *q0 = g->bq0, *q1 = g->bq1;
+  BfsCtl *ctl = g->bctl;
+  unsigned long long tns = (unsigned long long)timeout_ns;
+  void *args[] = {(void *)&rp, (void *)&ci, (void *)&n, (void *)&dist, (void *)&seeds,
+                  (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&ctl, (void *)&tns};
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(g->bfs_ctas),
+                                      dim3(kBfsThreads), args, 0, g->stream));
+  return GC_OK;
+}
+
+int bfs_kernel_occupancy(int *blocks_per_sm) {
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_bfs_relabel, kBfsThreads, 0));
+  return GC_OK;
+}
+
+int launch_sum_dist(gc_graph *g, const int32_t *dist) {
+  k_sum_dist<<<g->red_blocks, kRedThreads, 0, g->stream>>>(dist, g->n, g->partial, g->sctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_round0_keys(gc_graph *g) {
+  k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
+                  g->stream>>>(g->rp, g->ci, g->n, g->key);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_validate(gc_graph *g) {
+  GC_CUDA(cudaMemsetAsync(&g->sctl->err, 0, sizeof(int32_t), g->stream));
+  k_validate_rowptr<<<grid_for(g->n, 256, g->num_sms * 8), 256, 0, g->stream>>>(g->rp, g->n, g->nnz,
+                                                                                 g->sctl);
+  GC_CUDA(cudaGetLastError());
+  GC_CUDA(cudaMemcpyAsync(&g->h_sctl->err, &g->sctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          g->stream));
+  GC_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->h_sctl->err) return GC_EINVAL;
+  k_validate_rows<<<grid_for((int64_t)g->n * 32, 256, g->num_sms * 8), 256, 0, g->stream>>>(
+      g->rp, g->ci, g->n, g->sctl);
+  GC_CUDA(cudaGetLastError());
+  GC_CUDA(cudaMemcpyAsync(&g->h_sctl->err, &g->sctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          g->stream));
+  GC_CUDA(cudaStreamSynchronize(g->stream));
+  return g->h_sctl->err ? GC_EINVAL : GC_OK;
+}
+
+}  // namespace gc

@@ -1,0 +1,124 @@
+// Device helpers shared by the libgc kernels: bounded grid barrier, timers,
+// warp/block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier for cooperative launches (all CTAs co-resident).  Thread 0 of
+// each CTA arrives on bar->count; the last arrival resets the counter and bumps
+// bar->gen; the others poll bar->gen.  The poll is bounded twice: by
+// `timeout_ns` of global time and by an iteration cap.  On expiry the CTA
+// records GC_ETIMEOUT in *err and the barrier returns false; every caller then
+// leaves its kernel.  Returns false as well when *err is already set.
+__device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
+                                          unsigned long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int *vgen = &bar->gen;
+    const unsigned int g0 = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned int it = 0;
+      while (*vgen == g0) {
+        __nanosleep(40);
+        ++it;
+        if ((it & 127u) == 0 && (global_ns() - t0 > timeout_ns || it > (1u << 30))) {
+          atomicExch(err, GC_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && (*(volatile int32_t *)err == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  `sh` needs 32 entries.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide exclusive scan of int32 (blockDim.x <= 1024); returns the
+// exclusive prefix, *total gets the block total.  `sh` needs 33 entries.
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    int s = (lane < nw) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sh[lane] = s;  // inclusive prefix of warp totals
+    if (lane == nw - 1) sh[32] = s;
+  }
+  __syncthreads();
+  const int warp_off = wid ? sh[wid - 1] : 0;
+  *total = sh[32];
+  const int r = warp_off + x - v;
+  __syncthreads();
+  return r;
+}
+
+// (value, id) pairs ordered by larger value, then smaller id.
+__device__ __forceinline__ bool better_max(long long v, int id, long long bv, int bid) {
+  return v > bv || (v == bv && (unsigned)id < (unsigned)bid);
+}
+// (value, id) pairs ordered by smaller value, then smaller id.
+__device__ __forceinline__ bool better_min(long long v, int id, long long bv, int bid) {
+  return v < bv || (v == bv && (unsigned)id < (unsigned)bid);
+}
+
+}  // namespace gc

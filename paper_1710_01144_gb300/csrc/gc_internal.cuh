@@ -1,0 +1,170 @@
+// Internal declarations of libgc: handle layout, device helpers, kernels.
+// Group-closeness Greedy++ (arXiv:1710.01144) on sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gc.h"
+
+namespace gc {
+
+constexpr int32_t kInf = 0x3fffffff;  // "unreached" distance (d + 1 cannot overflow)
+constexpr int kLanes = 64;            // candidates per bit-parallel batch (one uint64 word)
+constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
+constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS
+constexpr int kRedThreads = 256;      // threads per CTA of reductions / scans
+constexpr int kHistBins = 2048;       // bins of the selection histogram
+
+// ----------------------------------------------------------- control words --
+// Bounded grid barrier used by cooperative kernels: arrival counter and
+// generation.  Every wait gives up after a time limit and reports GC_ETIMEOUT.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Grid-wide BFS control block (zeroed before each launch).
+struct BfsCtl {
+  GridBar bar;
+  int32_t qsize[3];     // frontier sizes by level mod 3
+  int32_t err;          // GC_* code set by the device, 0 = fine
+  int32_t levels;       // levels completed
+  int32_t pad;
+  unsigned long long decrease;  // sum over relabelled vertices of (old - new), old finite
+  unsigned long long relabelled;
+};
+
+// Gain-kernel control block.  batch_next is zeroed before every launch; err,
+// best_f and the counters live across the launches of one API call.
+struct GainCtl {
+  unsigned int batch_next;  // next batch to take (persistent CTAs)
+  int32_t err;
+  long long best_f;         // farness mode: best exact farness seen (atomicMin), cut threshold
+  unsigned long long edges_scalar;  // sum over lanes of adjacency entries a 1-source BFS scans
+  unsigned long long edges_union;   // adjacency entries scanned (once per frontier word)
+  unsigned long long levels;        // BFS levels summed over batches
+  unsigned long long batches;
+  unsigned long long frontier;      // frontier entries expanded
+  unsigned long long pushes;        // vertices that entered a next frontier
+  unsigned long long lanes;         // candidate lanes processed
+};
+
+// Selection / reduction control block (lives across a whole greedy call).
+struct SelCtl {
+  // threshold search (keys are compared as int64; differences in uint64)
+  long long lo, hi;      // key range of the current histogram pass
+  long long tau;         // selection: key >= tau
+  long long sel_count;   // selectable vertices
+  int32_t done;          // threshold fixed
+  int32_t n_sel;         // size of the compacted list
+  // lazy round state
+  long long best_gain;   // best exact gain of the current round (-1 = none)
+  int32_t best_id;
+  int32_t accepted;      // 1 once the round's pick is certified
+  long long unev_ub;     // best bound among candidates not evaluated this round
+  int32_t unev_id;
+  int32_t pad0;
+  // reductions
+  unsigned int ticket;   // last-CTA ticket of the reductions
+  int32_t err;
+  long long sum, count;  // k_sum_dist: sum of distances, unreached vertices
+  long long arg_val;     // k_argmin_f0
+  int32_t arg_id;
+  int32_t pad1;
+  long long evals, steps;  // lazy-step counters of the call
+};
+
+// --------------------------------------------------------------- handle ----
+}  // namespace gc
+
+struct gc_graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_csr = true;
+  int32_t *rp = nullptr;  // row_ptr[n+1]
+  int32_t *ci = nullptr;  // col_idx[nnz]
+  int32_t *dS = nullptr;  // distance to the current group
+  long long *ub = nullptr;     // lazy bound / exact gain of the round in stamp
+  int32_t *stamp = nullptr;    // round of the last exact evaluation (0 = never)
+  long long *key = nullptr;    // round-0 selection key (-lower bound), INT64_MIN = done
+  long long *f0 = nullptr;     // round 0: exact f({v}) or -1
+  int32_t *list = nullptr;     // compacted candidate list [n]
+  long long *lgain = nullptr;  // gains/farness of list entries [n]
+  int32_t *bq0 = nullptr, *bq1 = nullptr;  // grid BFS queues [n]
+  int32_t *blk = nullptr;                  // per-block counts / offsets
+  long long *partial = nullptr;            // per-block partial reductions (x4)
+  unsigned int *hist = nullptr;            // selection histogram [kHistBins]
+  int32_t *io_a = nullptr;                 // staging for small host arrays [n]
+  int32_t *io_b = nullptr;
+  gc::BfsCtl *bctl = nullptr;
+  gc::GainCtl *gctl = nullptr;
+  gc::SelCtl *sctl = nullptr;
+  gc::SelCtl *h_sctl = nullptr;  // pinned host mirror
+  gc::GainCtl *h_gctl = nullptr;
+  gc::BfsCtl *h_bctl = nullptr;
+  // gain-kernel workspaces: one per resident CTA
+  unsigned char *ws = nullptr;
+  size_t ws_stride = 0;
+  int ws_count = 0;
+  int gain_ctas = 0;       // resident CTAs of the gain kernel
+  int bfs_ctas = 0;        // resident CTAs of the cooperative BFS
+  int red_blocks = 0;      // grid size of reductions
+  int32_t *dec = nullptr;                  // scratch word
+  std::vector<cudaEvent_t> events;         // gain-kernel timing events (pairs)
+};
+
+namespace gc {
+
+// ------------------------------------------------------------ errors -------
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define GC_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return gc::cuda_fail(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------ launches -----
+// Grid-wide relabel BFS: dist[w] <- min(dist[w], level) from the seeds,
+// expanding only where the label decreased.  dist must already hold either
+// kInf (fresh BFS) or the current d_S (pruned update, Sec. 4.1).
+int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t n_seeds,
+                       int64_t timeout_ns);
+int launch_fill_i32(gc_graph *g, int32_t *p, int32_t v, int64_t count);
+int launch_fill_i64(gc_graph *g, long long *p, long long v, int64_t count);
+// sum of dist and count of unreached -> sctl->sum, sctl->count
+int launch_sum_dist(gc_graph *g, const int32_t *dist);
+// round-0 lower bound key[v] = -LB(v) (two-level degree bound)
+int launch_round0_keys(gc_graph *g);
+// validation: returns GC_OK / GC_EINVAL via sctl->err
+int launch_validate(gc_graph *g);
+
+enum GainMode { kModeGain = 0, kModeFarness = 1 };
+// Evaluate cand[0..n_cand) in 64-lane batches.  Gain mode: out = Delta(v|S) with
+// dS; farness mode: out = f({v}) or -1 if cut by gctl->best_f.
+// n_cand_dev (optional) overrides n_cand with a count held in device memory.
+int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
+                 const int32_t *n_cand_dev, long long *out, int max_ctas);
+size_t gain_ws_stride(int32_t n);
+int gain_kernel_occupancy(int *blocks_per_sm);
+
+// selection
+enum SelMode { kSelLazy = 0, kSelKey = 1 };
+int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, bool fixed_tau,
+                  long long tau);
+int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list);
+int launch_unevaluated_best(gc_graph *g, int32_t round);
+int launch_argmin_f0(gc_graph *g);
+int launch_round_begin(gc_graph *g);
+int launch_round_end(gc_graph *g);
+int bfs_kernel_occupancy(int *blocks_per_sm);
+
+}  // namespace gc

@@ -1,0 +1,186 @@
+"""Thin ctypes binding of ``libgc.so`` (C ABI in include/gc.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library is missing or no GPU is
+present, the calls raise.  PyTorch is used for device memory and the current
+stream when tensors are passed.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgc.so")
+
+GC_OK = 0
+GC_EINVAL = -1
+GC_EDISCONNECTED = -2
+GC_ERANGE = -3
+GC_ENOMEM = -4
+GC_ECUDA = -5
+GC_ETIMEOUT = -6
+GC_EINTERNAL = -7
+GC_DEVICE_PTRS = 0x1
+GC_ADOPT = 0x2
+GC_VALIDATE = 0x4
+
+# every entry point declared in include/gc.h
+EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
+           "gc_group_farness", "gc_marginal_gains", "gc_marginal_gains_device", "gc_greedy",
+           "gc_last_error")
+
+
+class GcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eval_per_step", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
+                ("max_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "rounds", "steps", "evals", "batches", "edges_scalar", "edges_union", "levels", "frontier",
+        "pushes", "lanes", "round0_evals")] + [
+        ("ms_round0", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
+        ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgc.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libgc.so is not built (run paper_1710_01144_gb300.build.build())")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.gc_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        lib.gc_load_csr.argtypes = [i32, vp, vp, ctypes.c_uint32, vp, ctypes.POINTER(vp)]
+        lib.gc_free.argtypes = [vp]
+        lib.gc_num_vertices.argtypes = [vp]
+        lib.gc_num_vertices.restype = i64
+        lib.gc_num_entries.argtypes = [vp]
+        lib.gc_num_entries.restype = i64
+        lib.gc_group_farness.argtypes = [vp, vp, i32, vp]
+        lib.gc_marginal_gains.argtypes = [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Stats)]
+        lib.gc_marginal_gains_device.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.gc_greedy.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != GC_OK:
+        raise GcError(rc, load().gc_last_error().decode())
+
+
+def _current_stream() -> int:
+    import torch
+
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a if a.size else np.zeros(1, dtype=np.int32)
+
+
+class Graph:
+    """A graph resident on the current CUDA device.
+
+    ``row_ptr``/``col_idx`` are numpy int32 arrays (host, copied) or int32 CUDA
+    tensors (device; ``adopt=True`` uses them in place, keep them alive)."""
+
+    def __init__(self, row_ptr, col_idx, validate: bool = False, adopt: bool = False, stream=None):
+        lib = load()
+        self._keep = None
+        flags = GC_VALIDATE if validate else 0
+        if hasattr(row_ptr, "data_ptr"):
+            flags |= GC_DEVICE_PTRS | (GC_ADOPT if adopt else 0)
+            n = row_ptr.numel() - 1
+            rp_p, ci_p = row_ptr.data_ptr(), col_idx.data_ptr()
+            if adopt:
+                self._keep = (row_ptr, col_idx)
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            ci = _i32(col_idx)
+            n = rp.size - 1
+            rp_p, ci_p = rp.ctypes.data, ci.ctypes.data
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(lib.gc_load_csr(n, rp_p, ci_p, flags, self.stream, ctypes.byref(h)))
+        self._h = h
+        self.n = int(lib.gc_num_vertices(h))
+        self.nnz = int(lib.gc_num_entries(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def farness(self, S) -> int:
+        s = _i32(S)
+        out = ctypes.c_int64()
+        _check(load().gc_group_farness(self._h, s.ctypes.data, int(np.size(S)), ctypes.byref(out)))
+        return out.value
+
+    def gains(self, S, cand, stats: bool = False):
+        s = _i32(S)
+        c = np.ascontiguousarray(cand, dtype=np.int32)
+        out = np.zeros(max(c.size, 1), dtype=np.int64)
+        st = Stats()
+        _check(load().gc_marginal_gains(self._h, s.ctypes.data, int(np.size(S)), _i32(c).ctypes.data,
+                                        c.size, out.ctypes.data, ctypes.byref(st)))
+        return (out[:c.size], st.as_dict()) if stats else out[:c.size]
+
+    def gains_device(self, S_dev, cand_dev, out_dev):
+        """Asynchronous gains on the handle's stream; all three are CUDA tensors."""
+        _check(load().gc_marginal_gains_device(self._h, S_dev.data_ptr(), S_dev.numel(), cand_dev.data_ptr(),
+                                               cand_dev.numel(), out_dev.data_ptr()))
+
+    def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
+               use_proposal: bool = False):
+        o = Opts()
+        load().gc_opts_default(ctypes.byref(o))
+        o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
+        if timeout_ms:
+            o.timeout_ms = timeout_ms
+        grp = np.zeros(max(int(k), 1), dtype=np.int32)
+        f = ctypes.c_int64()
+        st = Stats()
+        _check(load().gc_greedy(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
+                                ctypes.byref(st)))
+        return grp[:k], f.value, st.as_dict()

@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element and bit-exact (all quantities are integers)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_01144_gb300 import graphgen
+from tests import smallgraphs as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gcm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1710_01144_gb300 import build, gc
+
+    build.build()
+    return gc
+
+
+def small_cases():
+    return [("path37", sg.path(37)), ("cycle20", sg.cycle(20)), ("star70", sg.star(70)),
+            ("grid9x13", sg.grid(9, 13)), ("cater", sg.caterpillar(12, 3)), ("k9", sg.complete(9)),
+            ("tree", sg.tree_random(500, 3)), ("gnp", sg.gnp_connected(150, 0.03, 5)),
+            ("ba", graphgen.barabasi_albert(700, 3, 7)), ("rmat10", graphgen.rmat(10, 8.0, seed=3)),
+            ("road", graphgen.grid_road(40, 33, 0.2, 0.01, 5))]
+
+
+@pytest.mark.parametrize("name,g", small_cases())
+def test_farness(gcm, name, g):
+    rp, ci = g
+    n = rp.size - 1
+    rng = np.random.default_rng(1)
+    with gcm.Graph(rp, ci, validate=True) as G:
+        for size in (1, 2, 5, min(17, n)):
+            S = rng.choice(n, size=size, replace=False)
+            assert G.farness(S) == oracle.farness(rp, ci, S)
+        assert G.farness([0, 0, 0]) == oracle.farness(rp, ci, [0])
+
+
+@pytest.mark.parametrize("name,g", small_cases())
+def test_gains_all_candidates(gcm, name, g):
+    rp, ci = g
+    n = rp.size - 1
+    rng = np.random.default_rng(2)
+    with gcm.Graph(rp, ci) as G:
+        for size in (1, 3, 8):
+            S = rng.choice(n, size=min(size, n), replace=False)
+            cand = np.arange(n, dtype=np.int32)
+            np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+
+
+def test_gains_ragged_repeats_members(gcm):
+    rp, ci = graphgen.barabasi_albert(3000, 4, 11)
+    n = rp.size - 1
+    rng = np.random.default_rng(3)
+    S = rng.choice(n, size=6, replace=False)
+    with gcm.Graph(rp, ci) as G:
+        for m in (0, 1, 63, 64, 65, 129, 1000, 4097):
+            cand = rng.integers(0, n, size=m).astype(np.int32)
+            if m > 3:
+                cand[:3] = S[:3]  # members -> 0
+                cand[3] = cand[4]  # a repeat
+            got = G.gains(S, cand)
+            assert got.shape == (m,)
+            np.testing.assert_array_equal(got, oracle.gains(rp, ci, S, cand))
+        # more candidates than vertices (chunked)
+        cand = rng.integers(0, n, size=2 * n + 5).astype(np.int32)
+        np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+
+
+@pytest.mark.parametrize("name,g", small_cases())
+def test_greedy_equals_plain_oracle(gcm, name, g):
+    rp, ci = g
+    n = rp.size - 1
+    k = min(12, n)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, k)
+    with gcm.Graph(rp, ci) as G:
+        for eval_per_step in (0, 64):
+            got, f, st = G.greedy(k, eval_per_step=eval_per_step)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+            assert st["rounds"] == k
+
+
+def test_greedy_ba2000_k10(gcm):
+    """The small evaluation workload: BA n=2000, m=5, seed 1, k=10."""
+    rp, ci = graphgen.ba_n2000_m5()
+    grp, ft, _ = oracle.greedy_plain(rp, ci, 10)
+    with gcm.Graph(rp, ci, validate=True) as G:
+        got, f, _ = G.greedy(10)
+    np.testing.assert_array_equal(got, grp)
+    assert f == ft[-1]
+
+
+@pytest.mark.parametrize("scale,k", [(12, 30), (14, 40)])
+def test_greedy_rmat_vs_greedypp(gcm, scale, k):
+    rp, ci = graphgen.rmat(scale, 16.0, seed=5)
+    grp, ft, _, _ = oracle.greedypp(rp, ci, k)
+    with gcm.Graph(rp, ci) as G:
+        for eps in (0, 64, 1024):
+            got, f, _ = G.greedy(k, eval_per_step=eps)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+
+
+def test_greedy_rmat20_k100_full_size(gcm):
+    """R-MAT scale 20 (ef 16, seed 1), k = 100: the benchmark workload, in the
+    benchmark's launch configuration, against CPU Greedy++ (itself pinned to
+    the plain oracle).  Prefixes are the k = 10 and k = 50 answers."""
+    rp, ci = graphgen.rmat_s20_ef16()
+    grp, ft, _, _ = oracle.greedypp(rp, ci, 100)
+    with gcm.Graph(rp, ci) as G:
+        got, f, st = G.greedy(100)
+        np.testing.assert_array_equal(got, grp)
+        assert f == ft[-1]
+        # farness of the prefixes by the library's own BFS, against the trace
+        for kk in (10, 50):
+            assert G.farness(got[:kk]) == ft[kk - 1]
+        # sampled exact gains at full size
+        rng = np.random.default_rng(9)
+        cand = rng.integers(0, rp.size - 1, size=300).astype(np.int32)
+        np.testing.assert_array_equal(G.gains(got[:10], cand), oracle.gains(rp, ci, got[:10], cand))
+
+
+def test_errors(gcm):
+    rp, ci = sg.path(10)
+    with gcm.Graph(rp, ci) as G:
+        for bad in (0, 11, -1):
+            with pytest.raises(gcm.GcError) as e:
+                G.greedy(bad)
+            assert e.value.code == gcm.GC_EINVAL
+        with pytest.raises(gcm.GcError) as e:
+            G.farness([10])
+        assert e.value.code == gcm.GC_EINVAL
+        with pytest.raises(gcm.GcError) as e:
+            G.gains([], [1])
+        assert e.value.code == gcm.GC_EINVAL
+        with pytest.raises(gcm.GcError) as e:
+            G.gains([1], [12])
+        assert e.value.code == gcm.GC_EINVAL
+        assert G.greedy(10)[1] == 0  # k = n: every vertex in the group
+    rp, ci = sg.disjoint_union(sg.path(4), sg.cycle(5))
+    with pytest.raises(gcm.GcError) as e:
+        gcm.Graph(rp, ci, validate=True)
+    assert e.value.code == gcm.GC_EDISCONNECTED
+    with gcm.Graph(rp, ci) as G:
+        with pytest.raises(gcm.GcError) as e:
+            G.farness([0])
+        assert e.value.code == gcm.GC_EDISCONNECTED
+        with pytest.raises(gcm.GcError) as e:
+            G.greedy(2)
+        assert e.value.code == gcm.GC_EDISCONNECTED
+    # malformed CSR: asymmetric edge, self-loop, unsorted row, bad row_ptr
+    bad = [
+        (np.array([0, 1, 1], np.int32), np.array([1], np.int32)),
+        (np.array([0, 2, 3], np.int32), np.array([0, 1, 0], np.int32)),
+        (np.array([0, 2, 3, 4], np.int32), np.array([2, 1, 0, 0], np.int32)),
+        (np.array([0, 2, 1, 3], np.int32), np.array([1, 2, 0], np.int32)),
+    ]
+    for rp, ci in bad:
+        with pytest.raises(gcm.GcError) as e:
+            gcm.Graph(rp, ci, validate=True)
+        assert e.value.code == gcm.GC_EINVAL
+
+
+def test_device_pointers_and_adopt(gcm):
+    import torch
+
+    rp, ci = graphgen.rmat(11, 8.0, seed=8)
+    n = rp.size - 1
+    trp = torch.from_numpy(rp).cuda()
+    tci = torch.from_numpy(ci).cuda()
+    S = np.array([0, 5, 9], np.int32)
+    cand = np.arange(n, dtype=np.int32)
+    ref = oracle.gains(rp, ci, S, cand)
+    for adopt in (False, True):
+        with gcm.Graph(trp, tci, validate=True, adopt=adopt) as G:
+            out = torch.empty(n, dtype=torch.int64, device="cuda")
+            G.gains_device(torch.from_numpy(S).cuda(), torch.from_numpy(cand).cuda(), out)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), ref)
