@@ -1,0 +1,373 @@
+"""Benchmark: time to a size-k Greedy++ group on the GPU (plus pruned-BFS GTEPS).
+
+Workload (one step): the whole hot path -- round 0 (top-1 closeness), d_S,
+and k-1 lazy rounds of exact pruned-BFS gains -- on a seeded R-MAT graph of
+scale 20 (edge factor 16, a=.57 b=.19 c=.19, seed 1, largest connected
+component), k = 100 (its prefixes are the k = 10 and k = 50 groups).
+
+value = size-k groups per second over all ranks (each rank solves its own
+replica; no collective on the data path), with the CSR resident in HBM.
+e2e   = the same through the public API from pinned host buffers: load the
+        CSR (H2D), run, read the group back (D2H), free.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gc|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to size-k group and pruned-BFS GTEPS, learned+batched vs plain GPU greedy"
+WORKLOAD = "rmat_s20_ef16_lcc_k100"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gc", choices=["gc", "reference"])
+    p.add_argument("--k", type=int, default=100)
+    p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def workload_graph(scale: int):
+    from paper_1710_01144_gb300 import graphgen
+
+    return graphgen.rmat(scale, 16.0, 0.57, 0.19, 0.19, seed=1)
+
+
+def config_dict(args, n, nnz, l2_note):
+    return {"workload": WORKLOAD if args.scale == 20 and args.k == 100 else
+            "rmat_s%d_ef16_lcc_k%d" % (args.scale, args.k),
+            "graph": "R-MAT scale %d, edge factor 16, (a,b,c)=(.57,.19,.19), seed 1, "
+                     "symmetrised, deduplicated, largest component" % args.scale,
+            "n": int(n), "nnz": int(nnz), "k": args.k, "l2": l2_note,
+            "parallelism": "replicas (one independent solve per GPU)"}
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def gain_kernel_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1710_01144_gb300", "csrc", "gc_gain.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per gain-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "gain_kernel_rmat_s20_dram.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            a, b = line.split("=", 1)
+            kv[a.strip()] = b.strip()
+    if kv.get("kernel_source_sha256_16") != gain_kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_bytes(st) -> float:
+    """Bytes the 64-lane pruned BFS must move: per frontier entry the row
+    pointers (8 B) and its lane word (8 B); 4 B per adjacency entry scanned;
+    per vertex entering a next frontier its d_S value (4 B) and a visited and a
+    next-level lane word (2 x 8 B); 8 B per candidate gain written."""
+    return 16.0 * st["frontier"] + 4.0 * st["edges_union"] + 20.0 * st["pushes"] + 8.0 * st["lanes"]
+
+
+# --------------------------------------------------------------- gc arm ----
+def run_gc(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1710_01144_gb300 import build as gcbuild
+    from paper_1710_01144_gb300 import gc
+
+    gcbuild.build()
+    rp, ci = workload_graph(args.scale)
+    n, nnz = rp.size - 1, ci.size
+    G = gc.Graph(rp, ci, validate=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        grp0, f0, _ = G.greedy(args.k)
+    barrier()
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    clk = ClockSampler(("GPU-" + str(uuid)) if uuid is not None else None)
+    clk.start()
+    times, stats = [], []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between steps (outside the timed window)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grp, f, st = G.greedy(args.k)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+        assert np.array_equal(grp, grp0) and f == f0, "non-deterministic group"
+    barrier()
+    clocks = clk.stop()
+    t_step = sum(times) / len(times)
+    if ws > 1:
+        t = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # e2e: public API from pinned host buffers, copies inside the timed region
+    trp = torch.from_numpy(rp).pin_memory()
+    tci = torch.from_numpy(ci).pin_memory()
+    hrp, hci = trp.numpy(), tci.numpy()
+    e2e_steps = args.e2e_steps or args.steps
+    G.close()
+    with gc.Graph(hrp, hci) as Gw:  # warm the allocator path once
+        Gw.greedy(args.k)
+    barrier()
+    e2e_t = []
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with gc.Graph(hrp, hci) as Ge:
+            g_e, f_e, _ = Ge.greedy(args.k)
+        e2e_t.append((time.perf_counter() - t0) * 1e3)
+        assert np.array_equal(g_e, grp0) and f_e == f0
+    barrier()
+    t_e2e = sum(e2e_t) / len(e2e_t)
+    if ws > 1:
+        t = torch.tensor([t_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    if rank == 0:
+        tot = {k: sum(s[k] for s in stats) for k in stats[0]}
+        kern_ms = tot["ms_gain_kernel"]
+        launches = tot["gain_launches"]
+        bytes_alg = algorithmic_bytes(tot)
+        achieved = bytes_alg / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0
+        peak, peak_kind = measured_peaks()
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC,
+            "value": ws * 1000.0 / t_step,
+            "unit": "size-%d groups/s" % args.k,
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_step,
+            "time_to_group_ms": t_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int64",
+            "data": "synthetic (seeded R-MAT generator)",
+            "config": config_dict(args, n, nnz, "flushed between steps (512 MiB write outside the timed window)"),
+            "gteps_scalar": tot["edges_scalar"] / (sum(times) * 1e-3) / 1e9,
+            "gteps_union": tot["edges_union"] / (sum(times) * 1e-3) / 1e9,
+            "work_per_step": {k: tot[k] // args.steps for k in
+                              ("evals", "steps", "batches", "edges_scalar", "edges_union", "levels",
+                               "round0_evals", "gain_launches", "kernel_launches")},
+            "ms_round0": tot["ms_round0"] / args.steps,
+            "ms_round1": tot["ms_round1"] / args.steps,
+            "group_farness": int(f0),
+            "group_prefix": [int(x) for x in grp0[:10]],
+            "roofline": {
+                "kernel": "k_gains64 (64-lane pruned multi-source BFS)",
+                "bound": "hbm",
+                "achieved": achieved,
+                "peak": peak,
+                "peak_kind": peak_kind,
+                "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": bytes_alg / max(launches, 1),
+                "avg_launch_ms": kern_ms / max(launches, 1),
+                "launches": launches,
+                "share_of_step": kern_ms / sum(times),
+            },
+            "e2e": {"value": ws * 1000.0 / t_e2e, "unit": "size-%d groups/s" % args.k,
+                    "ms_per_step": t_e2e,
+                    "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
+                    "d2h_bytes_per_step": int(4 * args.k + 8)},
+            "gpu_launches": int(tot["kernel_launches"]),
+            "clocks": clocks,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(rp, ci, args.k, grp0, f0)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(rp, ci, k, grp_gpu, f_gpu):
+    """CPU Greedy++ of the oracle, as it stands, on the host cores: one run of
+    the full workload (seconds)."""
+    import oracle
+
+    cores = host_cores()
+    t0 = time.perf_counter()
+    grp, ft, _, st = oracle.greedypp(rp, ci, k, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "size-%d groups/s" % k, "cores": cores, "kind": "oracle",
+            "sample": "full workload, one run: CPU Greedy++ (BFScut top-1 closeness, pruned SSSP, "
+                      "lazy bounds; OpenMP) k=%d on the same graph" % k,
+            "seconds": dt, "gteps": st["edges"] / dt / 1e9,
+            "same_group_as_gpu": bool(np.array_equal(grp, grp_gpu) and ft[-1] == f_gpu)}
+
+
+# -------------------------------------------------------- reference arm ----
+def run_reference(args):
+    """The CPU oracle (CPU Greedy++) timed on the host cores on the same
+    workload; under torchrun only rank 0 runs."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    rp, ci = workload_graph(args.scale)
+    cores = host_cores()
+    for _ in range(args.warmup):
+        oracle.greedypp(rp, ci, args.k, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        grp, ft, _, st = oracle.greedypp(rp, ci, args.k, threads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = 1.0 / dt
+    unit = "size-%d groups/s" % args.k
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "time_to_group_ms": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded R-MAT generator)",
+        "config": config_dict(args, rp.size - 1, ci.size, "n/a (CPU)"),
+        "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": "full workload per step: CPU Greedy++ k=%d" % args.k},
+        "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "group_farness": int(ft[-1]),
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -72,7 +72,12 @@ typedef struct gc_opts {
                               and therefore the group are unchanged */
   int32_t max_ctas;        /* cap on resident CTAs of the gain kernel; 0 = all */
   int32_t timeout_ms;      /* limit of every device-side wait; 0 = 10000 */
-  int32_t reserved[4];
+  int32_t step_lanes;      /* candidates per 64-lane batch in rounds >= 2 (1..64);
+                              fewer lanes spread a step over more CTAs; 0 = 8 */
+  int32_t step_mode;       /* rounds >= 2: 0 = default, 1 = CTA-per-batch steps of
+                              eval_per_step candidates, 2 = one grid-wide batch of
+                              the 64 largest bounds per step */
+  int32_t reserved[2];
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */
@@ -90,6 +95,7 @@ typedef struct gc_stats {
   int64_t lanes;           /* candidate lanes processed (all launches) */
   int64_t round0_evals;    /* candidates evaluated (exactly or cut) in round 0 */
   double ms_round0;        /* time of round 0 (top-1 closeness + d_S) */
+  double ms_round1;        /* time of round 1 (every vertex evaluated) */
   double ms_total;         /* time of the whole call */
   double ms_gain_kernel;   /* summed duration of gain-kernel launches */
   int64_t gain_launches;   /* gain-kernel launches */

@@ -29,6 +29,8 @@ static int fail(int code, const std::string &msg) {
   return code;
 }
 
+constexpr int32_t kRound0GridMax = 256;  // round-0 survivors handled by grid-wide batches
+
 #define GC_TRY(expr)              \
   do {                            \
     int rc_ = (expr);             \
@@ -57,7 +59,7 @@ static void release(gc_graph *g) {
   }
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
-                 g->ws, g->dec};
+                 g->ws, g->dec, g->ggctl, g->goff};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -98,6 +100,10 @@ static int read_ctl(gc_graph *g) {
 static int device_errors(gc_graph *g) {
   const int e = g->h_gctl->err ? g->h_gctl->err : g->h_bctl->err ? g->h_bctl->err : g->h_sctl->err;
   if (!e) return GC_OK;
+  // a kernel that gave up may have left lane words behind: clear the scratch
+  cudaMemsetAsync(g->ws, 0, (size_t)g->ws_count * g->ws_stride, g->stream);
+  cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream);
+  cudaStreamSynchronize(g->stream);
   const char *what = e == GC_ETIMEOUT ? "device-side wait timed out"
                      : e == GC_EDISCONNECTED ? "graph is disconnected"
                      : e == GC_EINVAL ? "invalid vertex id on the device"
@@ -209,6 +215,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   g->gain_ctas = std::max(1, occ) * g->num_sms;
   if ((rc = bfs_kernel_occupancy(&occ))) return bail(rc);
   g->bfs_ctas = std::max(1, occ) * g->num_sms;
+  if ((rc = grid_gain_occupancy(&occ))) return bail(rc);
+  g->grid_ctas = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
   g->red_blocks = g->num_sms * 4;
   // per-vertex arrays
   const size_t N = (size_t)n;
@@ -219,7 +227,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->blk, (size_t)g->red_blocks + 8)) ||
       (rc = dalloc(&g->partial, 3 * (size_t)g->red_blocks + 8)) ||
       (rc = dalloc(&g->hist, (size_t)kHistBins)) || (rc = dalloc(&g->bctl, 1)) ||
-      (rc = dalloc(&g->gctl, 1)) || (rc = dalloc(&g->sctl, 1)))
+      (rc = dalloc(&g->gctl, 1)) || (rc = dalloc(&g->sctl, 1)) || (rc = dalloc(&g->ggctl, 1)) ||
+      (rc = dalloc(&g->goff, N + 1)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_gctl, sizeof(GainCtl)) != cudaSuccess ||
@@ -284,6 +293,7 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
   GC_TRY(check_ids(g, S, s_len, "S"));
   GC_TRY(check_ids(g, cand, n_cand, "cand"));
   auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = g->launches;
   GC_CUDA(cudaMemcpyAsync(g->io_a, S, (size_t)s_len * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
   GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
   GC_TRY(distances_from(g, g->io_a, s_len, timeout_ns(nullptr), nullptr));
@@ -321,6 +331,7 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
     stats->lanes = (int64_t)g->h_gctl->lanes;
     stats->ms_gain_kernel = ms_k;
     stats->gain_launches = launches;
+    stats->kernel_launches = g->launches - launches0;
     stats->ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -344,15 +355,27 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   if (opts.use_proposal) return fail(GC_EINVAL, "no proposal network is loaded");
   const int64_t tns = timeout_ns(&opts);
   auto t0 = std::chrono::steady_clock::now();
-  int64_t launches = 0;
+  const int64_t launches0 = g->launches;
   size_t ev_used = 0;
-  auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev) -> int {
+  auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
+                         int lanes) -> int {
     cudaEvent_t e0, e1;
     GC_TRY(gain_event(g, ev_used, &e0));
     GC_TRY(gain_event(g, ev_used + 1, &e1));
     ev_used += 2;
     GC_CUDA(cudaEventRecord(e0, g->stream));
-    GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas));
+    GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas, lanes));
+    GC_CUDA(cudaEventRecord(e1, g->stream));
+    return GC_OK;
+  };
+  auto grid_timed = [&](int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,
+                        long long *out) -> int {
+    cudaEvent_t e0, e1;
+    GC_TRY(gain_event(g, ev_used, &e0));
+    GC_TRY(gain_event(g, ev_used + 1, &e1));
+    ev_used += 2;
+    GC_CUDA(cudaEventRecord(e0, g->stream));
+    GC_TRY(launch_gains_grid(g, mode, cand, nl, nl_dev, out, tns));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     return GC_OK;
   };
@@ -360,35 +383,42 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
   GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
 
-  // ---- round 0: s0 = argmin_v f({v}) (top-1 closeness with cuts) ----
-  const long long inf64 = LLONG_MAX;
-  GC_CUDA(cudaMemcpyAsync(&g->gctl->best_f, &inf64, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
+  // ---- round 0: s0 = argmin_v f({v}) (top-1 closeness, Sec. 3.1) ----
+  // A lower bound LB(v) for every vertex; one grid-wide BFS from the vertex
+  // with the smallest bound gives an exact farness f_a that serves as the cut
+  // threshold; then every vertex with LB(v) <= f_a is evaluated by the
+  // bit-parallel BFS with per-level cuts (BFScut).  Vertices above the bound
+  // cannot beat f_a and are never searched.
   GC_TRY(launch_fill_i64(g, g->f0, -1, g->n));
   GC_TRY(launch_round0_keys(g));
-  const int32_t want0 = kLanes * g->gain_ctas;
-  GC_TRY(launch_select(g, kSelKey, 0, want0, false, 0));
-  GC_TRY(gains_timed(kModeFarness, g->list, 0, &g->sctl->n_sel));
-  GC_TRY(launch_after_eval(g, 0, 0));
+  GC_TRY(launch_argmin_lb(g));
+  GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
+  GC_TRY(launch_round0_seed(g));
+  GC_TRY(launch_select(g, kSelKey, 0, 0, kTauDevice, 0));
   GC_TRY(read_ctl(g));
-  GC_TRY(device_errors(g));
-  const long long best_f = g->h_gctl->best_f;
-  if (best_f == LLONG_MAX) return fail(GC_EINTERNAL, "round 0 found no exact farness");
-  // every vertex whose lower bound does not exceed the best farness is evaluated
-  GC_TRY(launch_select(g, kSelKey, 0, 0, true, -best_f));
-  GC_TRY(gains_timed(kModeFarness, g->list, 0, &g->sctl->n_sel));
+  const int32_t n_surv = g->h_sctl->n_sel;
+  if (n_surv <= kRound0GridMax) {
+    // few survivors (hubs with large searches): one grid-wide batch per 64
+    for (int32_t off = 0; off < n_surv; off += kLanes)
+      GC_TRY(grid_timed(kModeFarness, g->list + off, std::min<int32_t>(kLanes, n_surv - off), nullptr,
+                        g->lgain + off));
+  } else {
+    GC_TRY(gains_timed(kModeFarness, g->list, n_surv, nullptr, kLanes));
+  }
   GC_TRY(launch_after_eval(g, 0, 0));
   GC_TRY(launch_argmin_f0(g));
   GC_TRY(read_ctl(g));
   GC_TRY(device_errors(g));
   const int32_t s0 = g->h_sctl->arg_id;
   const long long f_s0 = g->h_sctl->arg_val;
+  const int64_t round0_evals = (int64_t)g->h_gctl->lanes + 1;
   if (s0 < 0) return fail(GC_EINTERNAL, "round 0 produced no vertex");
   int64_t f = 0;
   GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, &f));
   if (f != f_s0) return fail(GC_EINTERNAL, "farness of s0 disagrees between round 0 and the BFS");
-  const int64_t round0_evals = (int64_t)g->h_gctl->lanes;
   const double ms_round0 =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  double ms_round1 = 0;
   out_group[0] = s0;
 
   // ---- rounds 1..k-1: lazy greedy with exact pruned gains ----
@@ -397,15 +427,25 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(launch_fill_i64(g, g->ub + s0, -1, 1));
     GC_TRY(launch_fill_i32(g, g->stamp, 0, g->n));
   }
-  int32_t step_want = opts.eval_per_step > 0 ? opts.eval_per_step : kLanes * std::max(1, g->gain_ctas / 2);
-  step_want = ((step_want + kLanes - 1) / kLanes) * kLanes;
+  // later rounds: few candidates per step, spread over CTAs in small batches
+  const int32_t step_want = opts.eval_per_step > 0 ? opts.eval_per_step : 128;
+  const int step_lanes = (opts.step_lanes > 0 && opts.step_lanes <= kLanes) ? opts.step_lanes : 8;
+  const bool grid_steps = opts.step_mode == 2;
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
   for (int32_t r = 1; r < k; ++r) {
     GC_TRY(launch_round_begin(g));
     for (int step = 0;; ++step) {
-      if (r == 1) GC_TRY(launch_select(g, kSelLazy, r, 0, true, 0));  // no bounds yet: all of V \ S
-      else GC_TRY(launch_select(g, kSelLazy, r, step_want, false, 0));
-      GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel));
+      if (r == 1) {  // no bounds yet: all of V \ S, 64-lane batches over all CTAs
+        GC_TRY(launch_select(g, kSelLazy, r, 0, kTauHost, 0));
+        GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel, kLanes));
+      } else if (grid_steps) {  // the top-64 bounds as one grid-wide batch
+        GC_TRY(launch_select(g, kSelLazy, r, kLanes, kTauHistogram, 0));
+        GC_TRY(launch_clamp_nsel(g, kLanes));
+        GC_TRY(grid_timed(kModeGain, g->list, 0, &g->sctl->n_sel, g->lgain));
+      } else {
+        GC_TRY(launch_select(g, kSelLazy, r, step_want, kTauHistogram, 0));
+        GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel, step_lanes));
+      }
       GC_TRY(launch_after_eval(g, r, 0));
       GC_TRY(launch_unevaluated_best(g, r));
       GC_CUDA(cudaMemcpyAsync(g->h_sctl, g->sctl, sizeof(SelCtl), cudaMemcpyDeviceToHost, g->stream));
@@ -427,6 +467,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
                                     std::to_string(r) + ")");
     f -= gains_picked[r];
     out_group[r] = pick;
+    if (r == 1)
+      ms_round1 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() -
+                  ms_round0;
   }
   GC_TRY(read_ctl(g));
   GC_TRY(device_errors(g));
@@ -445,6 +488,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lanes = (int64_t)g->h_gctl->lanes;
     stats->round0_evals = round0_evals;
     stats->ms_round0 = ms_round0;
+    stats->ms_round1 = ms_round1;
     double ms_k = 0;
     for (size_t i = 0; i + 1 < ev_used; i += 2) {
       float ms = 0.f;
@@ -453,7 +497,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     }
     stats->ms_gain_kernel = ms_k;
     stats->gain_launches = (int64_t)(ev_used / 2);
-    stats->kernel_launches = launches;
+    stats->kernel_launches = g->launches - launches0;
     stats->ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }

@@ -212,12 +212,14 @@ static int grid_for(int64_t count, int threads, int cap) {
 
 int launch_fill_i32(gc_graph *g, int32_t *p, int32_t v, int64_t count) {
   if (count <= 0) return GC_OK;
+  ++g->launches;
   k_fill_i32<<<grid_for(count, 256, g->num_sms * 8), 256, 0, g->stream>>>(p, v, count);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
 int launch_fill_i64(gc_graph *g, long long *p, long long v, int64_t count) {
   if (count <= 0) return GC_OK;
+  ++g->launches;
   k_fill_i64<<<grid_for(count, 256, g->num_sms * 8), 256, 0, g->stream>>>(p, v, count);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
@@ -233,6 +235,7 @@ int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t
   unsigned long long tns = (unsigned long long)timeout_ns;
   void *args[] = {(void *)&rp, (void *)&ci, (void *)&n, (void *)&dist, (void *)&seeds,
                   (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&ctl, (void *)&tns};
+  ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(g->bfs_ctas),
                                       dim3(kBfsThreads), args, 0, g->stream));
   return GC_OK;
@@ -244,12 +247,14 @@ int bfs_kernel_occupancy(int *blocks_per_sm) {
 }
 
 int launch_sum_dist(gc_graph *g, const int32_t *dist) {
+  ++g->launches;
   k_sum_dist<<<g->red_blocks, kRedThreads, 0, g->stream>>>(dist, g->n, g->partial, g->sctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
 
 int launch_round0_keys(gc_graph *g) {
+  ++g->launches;
   k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
                   g->stream>>>(g->rp, g->ci, g->n, g->key);
   GC_CUDA(cudaGetLastError());
@@ -258,6 +263,7 @@ int launch_round0_keys(gc_graph *g) {
 
 int launch_validate(gc_graph *g) {
   GC_CUDA(cudaMemsetAsync(&g->sctl->err, 0, sizeof(int32_t), g->stream));
+  ++g->launches;
   k_validate_rowptr<<<grid_for(g->n, 256, g->num_sms * 8), 256, 0, g->stream>>>(g->rp, g->n, g->nnz,
                                                                                  g->sctl);
   GC_CUDA(cudaGetLastError());
@@ -265,6 +271,7 @@ int launch_validate(gc_graph *g) {
                           g->stream));
   GC_CUDA(cudaStreamSynchronize(g->stream));
   if (g->h_sctl->err) return GC_EINVAL;
+  ++g->launches;
   k_validate_rows<<<grid_for((int64_t)g->n * 32, 256, g->num_sms * 8), 256, 0, g->stream>>>(
       g->rp, g->ci, g->n, g->sctl);
   GC_CUDA(cudaGetLastError());

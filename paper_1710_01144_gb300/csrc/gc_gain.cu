@@ -64,7 +64,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kGainThreads, 2)
     k_gains64(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
               const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t n_cand_arg,
-              const int32_t *__restrict__ n_cand_dev, long long *__restrict__ out, unsigned char *ws_base, size_t ws_stride, GainCtl *ctl) {
+              const int32_t *__restrict__ n_cand_dev, long long *__restrict__ out,
+              unsigned char *ws_base, size_t ws_stride, GainCtl *ctl, int lanes) {
   constexpr int T = kGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ int s_cnt[kLanes];
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kGainThreads, 2)
   const int tid = threadIdx.x;
   const GainWs ws = gain_ws(ws_base, ws_stride, n, blockIdx.x);
   const int n_cand = n_cand_dev ? *n_cand_dev : n_cand_arg;
-  const int n_batches = (n_cand + kLanes - 1) / kLanes;
+  const int n_batches = (n_cand + lanes - 1) / lanes;
   u64 c_scalar = 0, c_union = 0, c_levels = 0, c_batches = 0, c_front = 0, c_push = 0, c_lanes = 0;
 
   for (;;) {
@@ -88,8 +89,8 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     __syncthreads();
     const int b = s_batch;
     if (b >= n_batches) break;
-    const int base = b * kLanes;
-    const int nl = min(kLanes, n_cand - base);
+    const int base = b * lanes;
+    const int nl = min(lanes, n_cand - base);
     if (tid < kLanes) {
       s_gain[tid] = 0;
       s_cnt[tid] = 0;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     if (tid == 0) {
       s_qn = 0;
       s_touched = 0;
-      s_alive = nl == kLanes ? ~0ull : ((1ull << nl) - 1ull);
+      s_alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
     }
     __syncthreads();
     int32_t *qcur_v = ws.qv0, *qnxt_v = ws.qv1;
@@ -281,21 +282,23 @@ int gain_kernel_occupancy(int *blocks_per_sm) {
 }
 
 int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
-                 const int32_t *n_cand_dev, long long *out, int max_ctas) {
+                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes) {
   if (!n_cand_dev && n_cand <= 0) return GC_OK;
+  if (lanes < 1 || lanes > kLanes) lanes = kLanes;
   GC_CUDA(cudaMemsetAsync(&g->gctl->batch_next, 0, sizeof(unsigned int), g->stream));
   int ctas = g->gain_ctas;
   if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
   if (!n_cand_dev) {
-    const int n_batches = (n_cand + kLanes - 1) / kLanes;
+    const int n_batches = (n_cand + lanes - 1) / lanes;
     if (ctas > n_batches) ctas = n_batches;
   }
+  ++g->launches;
   if (mode == kModeGain)
     k_gains64<kModeGain><<<ctas, kGainThreads, 0, g->stream>>>(
-        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl);
+        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes);
   else
     k_gains64<kModeFarness><<<ctas, kGainThreads, 0, g->stream>>>(
-        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl);
+        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

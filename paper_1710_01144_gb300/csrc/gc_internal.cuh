@@ -18,6 +18,8 @@ constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
 constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS
 constexpr int kRedThreads = 256;      // threads per CTA of reductions / scans
 constexpr int kHistBins = 2048;       // bins of the selection histogram
+constexpr int kGridGainThreads = 512; // threads per CTA of the grid-wide gain kernel
+constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
 
 // ----------------------------------------------------------- control words --
 // Bounded grid barrier used by cooperative kernels: arrival counter and
@@ -51,6 +53,19 @@ struct GainCtl {
   unsigned long long frontier;      // frontier entries expanded
   unsigned long long pushes;        // vertices that entered a next frontier
   unsigned long long lanes;         // candidate lanes processed
+};
+
+// Grid-wide gain kernel control block (zeroed before each launch).
+struct GridGainCtl {
+  GridBar bar;
+  int32_t err;
+  int32_t F;          // current frontier size
+  int32_t qn[2];      // next-frontier counters by level parity
+  int32_t touched;    // vertices with a non-zero visited word
+  int32_t pad;
+  unsigned long long gain[kLanes];  // per-lane gain (gain mode) / distance sum (farness)
+  unsigned long long cnt[kLanes];   // farness mode: per-lane visited count
+  int32_t blk_tot[kMaxGridCtas];    // per-CTA adjacency totals of the level
 };
 
 // Selection / reduction control block (lives across a whole greedy call).
@@ -104,6 +119,8 @@ struct gc_graph {
   int32_t *io_a = nullptr;                 // staging for small host arrays [n]
   int32_t *io_b = nullptr;
   gc::BfsCtl *bctl = nullptr;
+  gc::GridGainCtl *ggctl = nullptr;
+  int32_t *goff = nullptr;                 // grid gain kernel: frontier offsets [n+1]
   gc::GainCtl *gctl = nullptr;
   gc::SelCtl *sctl = nullptr;
   gc::SelCtl *h_sctl = nullptr;  // pinned host mirror
@@ -115,8 +132,10 @@ struct gc_graph {
   int ws_count = 0;
   int gain_ctas = 0;       // resident CTAs of the gain kernel
   int bfs_ctas = 0;        // resident CTAs of the cooperative BFS
+  int grid_ctas = 0;       // resident CTAs of the grid-wide gain kernel
   int red_blocks = 0;      // grid size of reductions
   int32_t *dec = nullptr;                  // scratch word
+  int64_t launches = 0;                    // kernels launched through this handle
   std::vector<cudaEvent_t> events;         // gain-kernel timing events (pairs)
 };
 
@@ -151,20 +170,32 @@ enum GainMode { kModeGain = 0, kModeFarness = 1 };
 // Evaluate cand[0..n_cand) in 64-lane batches.  Gain mode: out = Delta(v|S) with
 // dS; farness mode: out = f({v}) or -1 if cut by gctl->best_f.
 // n_cand_dev (optional) overrides n_cand with a count held in device memory.
+// lanes: candidates per batch (1..64); fewer lanes spread one step's work
+// over more CTAs.
 int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
-                 const int32_t *n_cand_dev, long long *out, int max_ctas);
+                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes = kLanes);
 size_t gain_ws_stride(int32_t n);
+// One batch of nl <= 64 candidates with every CTA (cooperative launch);
+// nl_dev (optional) gives min(64, *nl_dev) instead.
+int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,
+                      long long *out, int64_t timeout_ns);
+int grid_gain_occupancy(int *blocks_per_sm);
 int gain_kernel_occupancy(int *blocks_per_sm);
 
 // selection
 enum SelMode { kSelLazy = 0, kSelKey = 1 };
-int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, bool fixed_tau,
-                  long long tau);
+// tau_mode: kTauHistogram (find tau covering `want` keys), kTauHost (tau given),
+// kTauDevice (tau already in sctl->tau)
+enum TauMode { kTauHistogram = 0, kTauHost = 1, kTauDevice = 2 };
+int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, int tau_mode, long long tau);
 int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list);
 int launch_unevaluated_best(gc_graph *g, int32_t round);
 int launch_argmin_f0(gc_graph *g);
+int launch_argmin_lb(gc_graph *g);
+int launch_round0_seed(gc_graph *g);
 int launch_round_begin(gc_graph *g);
 int launch_round_end(gc_graph *g);
+int launch_clamp_nsel(gc_graph *g, int32_t cap);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 }  // namespace gc

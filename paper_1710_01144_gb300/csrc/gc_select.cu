@@ -73,15 +73,31 @@ __global__ void __launch_bounds__(kRedThreads) k_sel_range(int32_t n, const long
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
   mx = LLONG_MIN;
   mn = LLONG_MAX;
   c = 0;
-  for (int b = 0; b < gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     mx = max(mx, ((volatile long long *)partial)[3 * b]);
     mn = min(mn, ((volatile long long *)partial)[3 * b + 1]);
     c += ((volatile long long *)partial)[3 * b + 2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    smx[wid] = mx;
+    smn[wid] = mn;
+  }
+  c = block_sum(c, sh);
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < nw; ++w) {
+    mx = max(mx, smx[w]);
+    mn = min(mn, smn[w]);
   }
   ctl->hi = mx;
   ctl->lo = mn;
@@ -120,31 +136,59 @@ __global__ void __launch_bounds__(kRedThreads) k_sel_hist(int32_t n, const long 
 // the boundary bin keeps the selection within `cap` or is one key wide;
 // otherwise narrow [lo, hi] to the boundary bin (want reduced by what lies
 // above) for another pass.  Clears the histogram for the next pass.
-__global__ void k_sel_pick(unsigned int *hist, SelCtl *ctl, int32_t cap, int32_t *want_dev) {
-  if (threadIdx.x != 0) return;
-  if (ctl->done) return;
-  const unsigned long long lo = (unsigned long long)ctl->lo, hi = (unsigned long long)ctl->hi;
-  const unsigned long long span = hi - lo + 1ull;
-  const unsigned long long width = span / kHistBins + ((span % kHistBins) ? 1ull : 0ull);
-  const long long want = *want_dev;
-  long long above = 0;
-  int b = kHistBins - 1;
-  for (; b > 0; --b) {
-    if (above + (long long)hist[b] >= want) break;
-    above += hist[b];
+__global__ void __launch_bounds__(1024) k_sel_pick(unsigned int *hist, SelCtl *ctl, int32_t cap,
+                                                   int32_t *want_dev) {
+  static_assert(kHistBins == 2048, "two bins per thread of a 1024-thread CTA");
+  __shared__ int sh[33];
+  __shared__ int s_b;
+  __shared__ long long s_above, s_here;
+  const bool done = *(volatile int32_t *)&ctl->done;
+  if (!done) {
+    const long long want = *want_dev;
+    // thread t owns bins b0 = 2047 - 2t and b1 = b0 - 1 (walking down from the top)
+    const int b0 = kHistBins - 1 - 2 * (int)threadIdx.x, b1 = b0 - 1;
+    const int h0 = (int)hist[b0], h1 = (int)hist[b1];
+    if (threadIdx.x == 0) {
+      s_b = 0;
+      s_above = 0;
+      s_here = 0;
+    }
+    int total;
+    const long long above0 = block_excl_scan(h0 + h1, sh, &total);  // keys in bins > b0
+    if (above0 < want && above0 + h0 >= want) {
+      s_b = b0;
+      s_above = above0;
+      s_here = h0;
+    } else if (above0 + h0 < want && above0 + h0 + h1 >= want) {
+      s_b = b1;
+      s_above = above0 + h0;
+      s_here = h1;
+    }
+    if (threadIdx.x == 0 && (long long)total < want) {  // everything fits: select all
+      s_b = 0;
+      s_above = total - (long long)hist[0];
+      s_here = hist[0];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned long long lo = (unsigned long long)ctl->lo, hi = (unsigned long long)ctl->hi;
+      const unsigned long long span = hi - lo + 1ull;
+      const unsigned long long width = span / kHistBins + ((span % kHistBins) ? 1ull : 0ull);
+      const int b = s_b;
+      const long long above = s_above, here = s_here;
+      const unsigned long long bin_lo = lo + width * (unsigned long long)b;
+      ctl->tau = (long long)bin_lo;
+      if (above + here <= cap || width == 1ull || (b == 0 && above + here < want)) {
+        ctl->done = 1;
+      } else {
+        const unsigned long long room = hi - bin_lo;  // keys above bin_lo still in range
+        ctl->lo = (long long)bin_lo;
+        ctl->hi = (long long)(bin_lo + (width - 1ull < room ? width - 1ull : room));
+        *want_dev = (int32_t)(want - above);
+      }
+    }
   }
-  const long long here = hist[b];
-  const unsigned long long bin_lo = lo + width * (unsigned long long)b;
-  ctl->tau = (long long)bin_lo;
-  if (above + here <= cap || width == 1ull || (b == 0 && above + here < want)) {
-    ctl->done = 1;
-  } else {
-    const unsigned long long room = hi - bin_lo;  // keys above bin_lo still in range
-    ctl->lo = (long long)bin_lo;
-    ctl->hi = (long long)(bin_lo + (width - 1ull < room ? width - 1ull : room));
-    *want_dev = (int32_t)(want - above);
-  }
-  for (int i = 0; i < kHistBins; ++i) hist[i] = 0;
+  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0;
 }
 
 // Compaction, pass 1: per-block counts of selectable keys >= tau.
@@ -264,11 +308,11 @@ __global__ void __launch_bounds__(kRedThreads) k_after_eval_lazy(const int32_t *
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
   bv = ctl->best_gain;
   bid = ctl->best_id;
-  for (int b = 0; b < gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     const long long v = ((volatile long long *)partial)[2 * b];
     const int id = (int)((volatile long long *)partial)[2 * b + 1];
     if (id >= 0 && better_max(v, id, bv, bid)) {
@@ -276,6 +320,8 @@ __global__ void __launch_bounds__(kRedThreads) k_after_eval_lazy(const int32_t *
       bid = id;
     }
   }
+  block_arg<true>(bv, bid, sv, sid);
+  if (threadIdx.x != 0) return;
   ctl->best_gain = bv;
   ctl->best_id = bid;
   ctl->evals += n_list;  // evaluations of the call
@@ -310,11 +356,11 @@ __global__ void __launch_bounds__(kRedThreads) k_unevaluated_best(int32_t n, con
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
   bv = LLONG_MIN;
   bid = -1;
-  for (int b = 0; b < gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     const long long v = ((volatile long long *)partial)[2 * b];
     const int id = (int)((volatile long long *)partial)[2 * b + 1];
     if (id >= 0 && better_max(v, id, bv, bid)) {
@@ -322,6 +368,8 @@ __global__ void __launch_bounds__(kRedThreads) k_unevaluated_best(int32_t n, con
       bid = id;
     }
   }
+  block_arg<true>(bv, bid, sv, sid);
+  if (threadIdx.x != 0) return;
   ctl->unev_ub = bv;
   ctl->unev_id = bid;
   ctl->accepted = ctl->best_id >= 0 && (bid < 0 || better_max(ctl->best_gain, ctl->best_id, bv, bid));
@@ -339,17 +387,22 @@ __global__ void k_after_eval_round0(const int32_t *list, const long long *lgain,
   }
 }
 
-// s0 = argmin (f0, id) over exactly evaluated vertices -> ctl->arg_val / arg_id.
-__global__ void __launch_bounds__(kRedThreads) k_argmin_f0(int32_t n, const long long *f0,
-                                                           long long *partial, SelCtl *ctl) {
+// argmin (value, id): MODE 0 over exactly evaluated f0 (s0 of round 0);
+// MODE 1 over the round-0 lower bounds -key (the vertex whose BFS seeds the
+// cut threshold).  Result -> ctl->arg_val / arg_id.
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_argmin(int32_t n, const long long *arr,
+                                                        long long *partial, SelCtl *ctl) {
   __shared__ long long sv[32];
   __shared__ int sid[32];
   __shared__ bool last;
   long long bv = LLONG_MAX;
   int bid = -1;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const long long f = f0[v];
-    if (f >= 0 && better_min(f, v, bv, bid)) {
+    const long long a = arr[v];
+    const bool valid = MODE == 0 ? a >= 0 : a != LLONG_MIN;
+    const long long f = MODE == 0 ? a : -a;
+    if (valid && better_min(f, v, bv, bid)) {
       bv = f;
       bid = v;
     }
@@ -362,11 +415,11 @@ __global__ void __launch_bounds__(kRedThreads) k_argmin_f0(int32_t n, const long
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
   bv = LLONG_MAX;
   bid = -1;
-  for (int b = 0; b < gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     const long long v = ((volatile long long *)partial)[2 * b];
     const int id = (int)((volatile long long *)partial)[2 * b + 1];
     if (id >= 0 && better_min(v, id, bv, bid)) {
@@ -374,9 +427,25 @@ __global__ void __launch_bounds__(kRedThreads) k_argmin_f0(int32_t n, const long
       bid = id;
     }
   }
+  block_arg<false>(bv, bid, sv, sid);
+  if (threadIdx.x != 0) return;
   ctl->arg_val = bv;
   ctl->arg_id = bid;
   ctl->ticket = 0;
+}
+
+// Round 0 after the BFS from the lowest-bound vertex v_a: its exact farness
+// (ctl->sum) becomes f0[v_a], the cut threshold best_f, and the selection
+// threshold tau = -best_f (every vertex whose bound does not exceed it).
+__global__ void k_round0_seed(long long *f0, long long *key, SelCtl *ctl, GainCtl *gctl) {
+  const int v = ctl->arg_id;
+  const long long f = ctl->sum;
+  if (v >= 0) {
+    f0[v] = f;
+    key[v] = LLONG_MIN;
+  }
+  gctl->best_f = f;
+  ctl->tau = -f;
 }
 
 // Start of a lazy round: clear the round's best and the acceptance flag.
@@ -386,6 +455,12 @@ __global__ void k_round_begin(SelCtl *ctl) {
   ctl->accepted = 0;
 }
 
+// Keep at most `cap` entries of the compacted list (the list is in vertex
+// order; the dropped tail stays unevaluated and keeps its bound).
+__global__ void k_clamp_nsel(SelCtl *ctl, int32_t cap) {
+  if (ctl->n_sel > cap) ctl->n_sel = cap;
+}
+
 // End of a lazy round: remove the pick from the candidates.
 __global__ void k_round_end(long long *ub, const SelCtl *ctl) {
   const int v = ctl->best_id;
@@ -393,14 +468,15 @@ __global__ void k_round_end(long long *ub, const SelCtl *ctl) {
 }
 
 // ------------------------------------------------------------- launchers ----
-int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, bool fixed_tau,
+int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, int tau_mode,
                   long long tau) {
   const int rb = g->red_blocks;
-  if (fixed_tau) {
+  if (tau_mode == kTauHost) {
     // tau given: no range/histogram passes
     GC_CUDA(cudaMemcpyAsync(&g->sctl->tau, &tau, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
-  } else {
+  } else if (tau_mode == kTauHistogram) {
     GC_CUDA(cudaMemcpyAsync(g->blk + rb, &want, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+    ++g->launches;
     if (mode == kSelLazy)
       k_sel_range<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                g->partial, g->sctl);
@@ -409,26 +485,34 @@ int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, bool fixed
                                                               g->partial, g->sctl);
     GC_CUDA(cudaGetLastError());
     for (int pass = 0; pass < 3; ++pass) {
+      ++g->launches;
       if (mode == kSelLazy)
         k_sel_hist<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                 g->hist, g->sctl);
       else
         k_sel_hist<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                g->hist, g->sctl);
-      k_sel_pick<<<1, 32, 0, g->stream>>>(g->hist, g->sctl, 2 * want, g->blk + rb);
+      ++g->launches;
+      k_sel_pick<<<1, 1024, 0, g->stream>>>(g->hist, g->sctl, 2 * want, g->blk + rb);
       GC_CUDA(cudaGetLastError());
     }
   }
   if (mode == kSelLazy) {
+    ++g->launches;
     k_compact_count<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                  g->sctl, g->blk);
+    ++g->launches;
     k_compact_scan<<<1, 1024, 0, g->stream>>>(g->blk, rb, g->sctl);
+    ++g->launches;
     k_compact_write<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                  g->sctl, g->blk, g->list);
   } else {
+    ++g->launches;
     k_compact_count<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                 g->sctl, g->blk);
+    ++g->launches;
     k_compact_scan<<<1, 1024, 0, g->stream>>>(g->blk, rb, g->sctl);
+    ++g->launches;
     k_compact_write<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
                                                                 g->sctl, g->blk, g->list);
   }
@@ -438,6 +522,7 @@ int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, bool fixed
 
 int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list) {
   (void)n_list;
+  ++g->launches;
   if (round == 0)
     k_after_eval_round0<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->list, g->lgain, g->f0, g->key,
                                                                       g->sctl);
@@ -449,6 +534,7 @@ int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list) {
 }
 
 int launch_unevaluated_best(gc_graph *g, int32_t round) {
+  ++g->launches;
   k_unevaluated_best<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round,
                                                                    g->partial, g->sctl);
   GC_CUDA(cudaGetLastError());
@@ -456,18 +542,42 @@ int launch_unevaluated_best(gc_graph *g, int32_t round) {
 }
 
 int launch_argmin_f0(gc_graph *g) {
-  k_argmin_f0<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->n, g->f0, g->partial, g->sctl);
+  ++g->launches;
+  k_argmin<0><<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->n, g->f0, g->partial, g->sctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_argmin_lb(gc_graph *g) {
+  ++g->launches;
+  k_argmin<1><<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->n, g->key, g->partial, g->sctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_round0_seed(gc_graph *g) {
+  ++g->launches;
+  k_round0_seed<<<1, 1, 0, g->stream>>>(g->f0, g->key, g->sctl, g->gctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
 
 int launch_round_begin(gc_graph *g) {
+  ++g->launches;
   k_round_begin<<<1, 1, 0, g->stream>>>(g->sctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
 
+int launch_clamp_nsel(gc_graph *g, int32_t cap) {
+  ++g->launches;
+  k_clamp_nsel<<<1, 1, 0, g->stream>>>(g->sctl, cap);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
 int launch_round_end(gc_graph *g) {
+  ++g->launches;
   k_round_end<<<1, 1, 0, g->stream>>>(g->ub, g->sctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;

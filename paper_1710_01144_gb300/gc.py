@@ -43,14 +43,15 @@ class GcError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("eval_per_step", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("step_lanes", ctypes.c_int32), ("step_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "rounds", "steps", "evals", "batches", "edges_scalar", "edges_union", "levels", "frontier",
         "pushes", "lanes", "round0_evals")] + [
-        ("ms_round0", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
+        ("ms_round0", ctypes.c_double), ("ms_round1", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
         ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
@@ -172,10 +173,11 @@ class Graph:
                                                cand_dev.numel(), out_dev.data_ptr()))
 
     def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
-               use_proposal: bool = False):
+               use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
+        o.step_lanes, o.step_mode = step_lanes, step_mode
         if timeout_ms:
             o.timeout_ms = timeout_ms
         grp = np.zeros(max(int(k), 1), dtype=np.int32)

@@ -9,6 +9,10 @@ from tests import smallgraphs as sg
 
 pytestmark = pytest.mark.gpu
 
+# (eval_per_step, step_lanes, step_mode) of the lazy rounds: defaults,
+# CTA-per-batch steps, one grid-wide batch per step
+STEP_VARIANTS = [(0, 0, 0), (64, 8, 1), (0, 0, 2), (128, 1, 1)]
+
 
 @pytest.fixture(scope="module")
 def gcm():
@@ -80,8 +84,8 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
     k = min(12, n)
     grp, ft, _ = oracle.greedy_plain(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for eval_per_step in (0, 64):
-            got, f, st = G.greedy(k, eval_per_step=eval_per_step)
+        for eps, lanes, mode in STEP_VARIANTS:
+            got, f, st = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
             assert st["rounds"] == k
@@ -102,8 +106,8 @@ def test_greedy_rmat_vs_greedypp(gcm, scale, k):
     rp, ci = graphgen.rmat(scale, 16.0, seed=5)
     grp, ft, _, _ = oracle.greedypp(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for eps in (0, 64, 1024):
-            got, f, _ = G.greedy(k, eval_per_step=eps)
+        for eps, lanes, mode in STEP_VARIANTS + [(1024, 64, 1)]:
+            got, f, _ = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
 
@@ -118,6 +122,10 @@ def test_greedy_rmat20_k100_full_size(gcm):
         got, f, st = G.greedy(100)
         np.testing.assert_array_equal(got, grp)
         assert f == ft[-1]
+        for mode in (1, 2):
+            g2, f2, _ = G.greedy(100, step_mode=mode)
+            np.testing.assert_array_equal(g2, grp)
+            assert f2 == ft[-1]
         # farness of the prefixes by the library's own BFS, against the trace
         for kk in (10, 50):
             assert G.farness(got[:kk]) == ft[kk - 1]
