@@ -152,6 +152,37 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
 int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len,
                              const int32_t *cand_dev, int32_t n_cand, int64_t *out_gain_dev);
 
+/* gc_marginal_gains_static -- the gains of gc_marginal_gains for callers that
+ * cannot allocate device memory (for example code that runs while somebody
+ * else captures the stream into a CUDA graph, plugins confined to a host
+ * application's own allocator, or request paths where allocator calls and
+ * their implicit synchronisation are not allowed).  The paper has no
+ * counterpart; this is a deployment variant.
+ * It calls no cudaMalloc/cudaFree and creates no handle: all scratch lives in
+ * one 64 MiB array compiled into the library, which every GPU that loads the
+ * library keeps until the process exits.
+ * n, row_ptr, col_idx : the CSR as device pointers (same format as above); the
+ *            graph must be connected.
+ * S, cand, out_gain   : device int32[s_len], int32[n_cand], int64[n_cand];
+ *            s_len >= 1; out_gain[i] = Delta(cand[i] | S), -1 for an id
+ *            outside [0, n).  Ids in S must be in range.
+ * stream   : cudaStream_t (as void*); the call is asynchronous on it.
+ * Limits   : n is limited by the array (one 44-byte-per-vertex workspace plus
+ *            16 bytes per vertex must fit: n up to about 1.1 million); a larger
+ *            n returns GC_ERANGE before anything runs.  Smaller graphs get more
+ *            workspaces and therefore more parallel CTAs.
+ * Sharing  : all calls in the process share the one array.  Each call zeroes
+ *            the parts it uses, so calls ordered on one stream are safe, but
+ *            calls that overlap on the GPU (different streams or threads) race
+ *            and give wrong results.
+ * Set-up   : the first call on a device (with that device current) looks up the
+ *            array's device address once; make that first call before any
+ *            stream capture begins.
+ * Errors   : GC_EINVAL (NULL or bad sizes), GC_ERANGE (n too large), GC_ECUDA. */
+int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                             const int32_t *S, int32_t s_len, const int32_t *cand, int32_t n_cand,
+                             int64_t *out_gain, void *stream);
+
 /* gc_greedy -- Greedy++ (Algorithm 2 with pruned SSSPs, Sec. 4.1, and the lazy
  * supermodular bounds, Sec. 4.2): s0 = argmin_v f({v}) (top-1 closeness,
  * Sec. 3.1), then k-1 rounds adding argmax_v Delta(v | S).

@@ -31,7 +31,7 @@ GC_VALIDATE = 0x4
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
            "gc_group_farness", "gc_marginal_gains", "gc_marginal_gains_device", "gc_greedy",
-           "gc_last_error")
+           "gc_last_error", "gc_marginal_gains_static")
 
 
 class GcError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         lib.gc_marginal_gains.argtypes = [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Stats)]
         lib.gc_marginal_gains_device.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.gc_greedy.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_marginal_gains_static.argtypes = [i32, vp, vp, vp, i32, vp, i32, vp, vp]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error"):
@@ -186,3 +187,12 @@ class Graph:
         _check(load().gc_greedy(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
                                 ctypes.byref(st)))
         return grp[:k], f.value, st.as_dict()
+
+
+def gains_static(row_ptr_dev, col_idx_dev, S_dev, cand_dev, out_dev, stream=None):
+    """gc_marginal_gains_static on CUDA tensors: no device allocation by the
+    library (its scratch is a fixed array); asynchronous on ``stream``."""
+    st = _current_stream() if stream is None else int(stream)
+    _check(load().gc_marginal_gains_static(row_ptr_dev.numel() - 1, row_ptr_dev.data_ptr(), col_idx_dev.data_ptr(),
+                                           S_dev.data_ptr(), S_dev.numel(), cand_dev.data_ptr(), cand_dev.numel(),
+                                           out_dev.data_ptr(), st))
