@@ -62,6 +62,9 @@ extern "C" {
 
 typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays + scratch */
 
+/* gc_opts.flags */
+#define GC_OPT_NO_EXPAND_BOUND 0x1u
+
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
 typedef struct gc_opts {
@@ -74,10 +77,23 @@ typedef struct gc_opts {
   int32_t timeout_ms;      /* limit of every device-side wait; 0 = 10000 */
   int32_t step_lanes;      /* candidates per 64-lane batch in rounds >= 2 (1..64);
                               fewer lanes spread a step over more CTAs; 0 = 8 */
-  int32_t step_mode;       /* rounds >= 2: 0 = default, 1 = CTA-per-batch steps of
-                              eval_per_step candidates, 2 = one grid-wide batch of
-                              the 64 largest bounds per step */
-  int32_t reserved[2];
+  int32_t step_mode;       /* rounds >= 2: 0 = default (3), 1 = host-driven steps of
+                              eval_per_step candidates in CTA-per-batch form,
+                              2 = host-driven steps of one grid-wide batch of the
+                              64 largest bounds, 3 = one persistent device kernel
+                              for all remaining rounds (grid-wide batches of the
+                              64 largest bounds, certification and d_S update on
+                              the device) */
+  int32_t active_target;   /* step_mode 3: initial size of its candidate list
+                              (grown x4 when the list cannot certify a pick);
+                              0 = 4096 */
+  int32_t round1_heavy;    /* round 1: this many highest-degree candidates are
+                              evaluated by the grid-wide kernel before the
+                              CTA-per-batch sweep over the rest; 0 = 1024,
+                              negative = none */
+  uint32_t flags;          /* GC_OPT_NO_EXPAND_BOUND: do not skip expansions by the
+                              neighbour bound (work only; the group is the same) */
+  int32_t reserved[3];
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */
@@ -97,7 +113,11 @@ typedef struct gc_stats {
   double ms_round0;        /* time of round 0 (top-1 closeness + d_S) */
   double ms_round1;        /* time of round 1 (every vertex evaluated) */
   double ms_total;         /* time of the whole call */
-  double ms_gain_kernel;   /* summed duration of gain-kernel launches */
+  double ms_gain_kernel;   /* summed duration of gain-kernel launches (host-driven
+                              steps; the persistent kernel's phases are below) */
+  double ms_lazy_select;   /* persistent kernel: candidate selection and certification */
+  double ms_lazy_gain;     /* persistent kernel: grid-wide 64-lane gain batches */
+  double ms_lazy_update;   /* persistent kernel: d_S updates from the picks */
   int64_t gain_launches;   /* gain-kernel launches */
   int64_t kernel_launches; /* all kernel launches of the call */
 } gc_stats;
@@ -168,7 +188,7 @@ int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len,
  *            outside [0, n).  Ids in S must be in range.
  * stream   : cudaStream_t (as void*); the call is asynchronous on it.
  * Limits   : n is limited by the array (one 44-byte-per-vertex workspace plus
- *            16 bytes per vertex must fit: n up to about 1.1 million); a larger
+ *            20 bytes per vertex must fit: n up to about one million); a larger
  *            n returns GC_ERANGE before anything runs.  Smaller graphs get more
  *            workspaces and therefore more parallel CTAs.
  * Sharing  : all calls in the process share the one array.  Each call zeroes

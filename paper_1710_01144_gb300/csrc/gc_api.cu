@@ -59,12 +59,13 @@ static void release(gc_graph *g) {
   }
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
-                 g->ws, g->dec, g->ggctl, g->goff};
+                 g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
   if (g->h_gctl) cudaFreeHost(g->h_gctl);
   if (g->h_bctl) cudaFreeHost(g->h_bctl);
+  if (g->h_lctl) cudaFreeHost(g->h_lctl);
   for (cudaEvent_t e : g->events) cudaEventDestroy(e);
   delete g;
 }
@@ -217,6 +218,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   g->bfs_ctas = std::max(1, occ) * g->num_sms;
   if ((rc = grid_gain_occupancy(&occ))) return bail(rc);
   g->grid_ctas = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
+  if ((rc = lazy_occupancy(&occ))) return bail(rc);
+  g->lazy_ctas = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
   g->red_blocks = g->num_sms * 4;
   // per-vertex arrays
   const size_t N = (size_t)n;
@@ -228,11 +231,14 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->partial, 3 * (size_t)g->red_blocks + 8)) ||
       (rc = dalloc(&g->hist, (size_t)kHistBins)) || (rc = dalloc(&g->bctl, 1)) ||
       (rc = dalloc(&g->gctl, 1)) || (rc = dalloc(&g->sctl, 1)) || (rc = dalloc(&g->ggctl, 1)) ||
-      (rc = dalloc(&g->goff, N + 1)))
+      (rc = dalloc(&g->goff, N + 1)) || (rc = dalloc(&g->lctl, 1)) || (rc = dalloc(&g->picks, N)) ||
+      (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
+      (rc = dalloc(&g->mx_buf, N)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_gctl, sizeof(GainCtl)) != cudaSuccess ||
-      cudaMallocHost((void **)&g->h_bctl, sizeof(BfsCtl)) != cudaSuccess)
+      cudaMallocHost((void **)&g->h_bctl, sizeof(BfsCtl)) != cudaSuccess ||
+      cudaMallocHost((void **)&g->h_lctl, sizeof(LazyCtl)) != cudaSuccess)
     return bail(fail(GC_ENOMEM, "pinned host allocation failed"));
   // gain-kernel workspaces: one per resident CTA, within 40% of free memory
   g->ws_stride = gain_ws_stride(n);
@@ -276,6 +282,7 @@ int gc_group_farness(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_
 
 static int gains_core(gc_graph *g, const int32_t *S_dev, int32_t s_len, const int32_t *cand_dev,
                       int32_t n_cand, long long *out_dev, bool check) {
+  g->mx = nullptr;  // a fresh d_S: no neighbour bound
   GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
   if (check) {
     GC_TRY(distances_from(g, S_dev, s_len, timeout_ns(nullptr), nullptr));
@@ -292,6 +299,7 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
     return fail(GC_EINVAL, "bad argument to gc_marginal_gains");
   GC_TRY(check_ids(g, S, s_len, "S"));
   GC_TRY(check_ids(g, cand, n_cand, "cand"));
+  g->mx = nullptr;  // a fresh d_S: no neighbour bound
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   GC_CUDA(cudaMemcpyAsync(g->io_a, S, (size_t)s_len * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
@@ -379,6 +387,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_CUDA(cudaEventRecord(e1, g->stream));
     return GC_OK;
   };
+  g->mx = nullptr;
   GC_CUDA(cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), g->stream));
   GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
   GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
@@ -416,6 +425,11 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   int64_t f = 0;
   GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, &f));
   if (f != f_s0) return fail(GC_EINTERNAL, "farness of s0 disagrees between round 0 and the BFS");
+  // neighbour bound for the pruning of useless expansions in every later round
+  if (!(opts.flags & GC_OPT_NO_EXPAND_BOUND)) {
+    GC_TRY(launch_max_nbr(g));
+    g->mx = g->mx_buf;
+  }
   const double ms_round0 =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   double ms_round1 = 0;
@@ -431,11 +445,76 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const int32_t step_want = opts.eval_per_step > 0 ? opts.eval_per_step : 128;
   const int step_lanes = (opts.step_lanes > 0 && opts.step_lanes <= kLanes) ? opts.step_lanes : 8;
   const bool grid_steps = opts.step_mode == 2;
+  const bool persistent = opts.step_mode == 0 || opts.step_mode == 3;
+  const int32_t heavy = opts.round1_heavy < 0 ? 0 : (opts.round1_heavy == 0 ? 1024 : opts.round1_heavy);
+  int64_t lazy_steps = 0, lazy_evals = 0, lazy_launches = 0;
+  double lazy_ms[3] = {0, 0, 0};
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
   for (int32_t r = 1; r < k; ++r) {
+    if (r >= 2 && persistent) {
+      // rounds r..k-1 on the device: persistent kernel over an active list
+      LazyCtl init;
+      memset(&init, 0, sizeof(init));
+      init.round = r;
+      init.best_id = -1;
+      init.best_gain = -1;
+      *g->h_lctl = init;
+      GC_CUDA(cudaMemcpyAsync(g->lctl, g->h_lctl, sizeof(LazyCtl), cudaMemcpyHostToDevice, g->stream));
+      int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
+      for (;;) {
+        GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
+        GC_TRY(launch_lazy_rounds(g, k, tns));
+        ++lazy_launches;
+        GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
+        GC_TRY(read_ctl(g));
+        if (g->h_lctl->err) {
+          g->h_gctl->err = g->h_lctl->err;
+          return device_errors(g);
+        }
+        if (g->h_lctl->round >= k) break;
+        if (g->h_lctl->dec != 2) return fail(GC_EINTERNAL, "persistent lazy kernel stopped early");
+        target = target > (1 << 28) ? g->n : target * 4;
+      }
+      lazy_steps = g->h_lctl->steps;
+      lazy_evals = g->h_lctl->evals;
+      lazy_ms[0] = g->h_lctl->ns_select * 1e-6;
+      lazy_ms[1] = g->h_lctl->ns_gain * 1e-6;
+      lazy_ms[2] = g->h_lctl->ns_update * 1e-6;
+      std::vector<int32_t> pk(k);
+      std::vector<long long> pg(k), pd(k);
+      GC_CUDA(cudaMemcpyAsync(pk.data() + r, g->picks + r, (size_t)(k - r) * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, g->stream));
+      GC_CUDA(cudaMemcpyAsync(pg.data() + r, g->pgain + r, (size_t)(k - r) * sizeof(long long),
+                              cudaMemcpyDeviceToHost, g->stream));
+      GC_CUDA(cudaMemcpyAsync(pd.data() + r, g->pdec + r, (size_t)(k - r) * sizeof(long long),
+                              cudaMemcpyDeviceToHost, g->stream));
+      GC_TRY(sync(g));
+      for (int32_t q = r; q < k; ++q) {
+        if (pg[q] != pd[q])
+          return fail(GC_EINTERNAL, "gain of the pick disagrees with the d_S update (round " +
+                                        std::to_string(q) + ")");
+        f -= pg[q];
+        out_group[q] = pk[q];
+      }
+      break;
+    }
     GC_TRY(launch_round_begin(g));
     for (int step = 0;; ++step) {
-      if (r == 1) {  // no bounds yet: all of V \ S, 64-lane batches over all CTAs
+      if (r == 1) {  // no bounds yet: all of V \ S
+        if (heavy > 0) {
+          // the highest-degree candidates have the largest searches: one
+          // grid-wide batch per 64 of them, so no CTA is left with a hub batch
+          GC_TRY(launch_degree_keys(g));
+          GC_TRY(launch_select(g, kSelKey, 0, heavy, kTauHistogram, 0));
+          GC_TRY(read_ctl(g));
+          const int32_t nh = std::min<int32_t>(g->h_sctl->n_sel, 4 * heavy);
+          for (int32_t off = 0; off < nh; off += kLanes)
+            GC_TRY(grid_timed(kModeGain, g->list + off, std::min<int32_t>(kLanes, nh - off), nullptr,
+                              g->lgain + off));
+          GC_TRY(launch_clamp_nsel(g, nh));
+          GC_TRY(launch_after_eval(g, r, 0));
+        }
+        // the rest in 64-lane batches, one CTA each
         GC_TRY(launch_select(g, kSelLazy, r, 0, kTauHost, 0));
         GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel, kLanes));
       } else if (grid_steps) {  // the top-64 bounds as one grid-wide batch
@@ -471,14 +550,15 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       ms_round1 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() -
                   ms_round0;
   }
+  g->mx = nullptr;
   GC_TRY(read_ctl(g));
   GC_TRY(device_errors(g));
   *out_farness = f;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->rounds = k;
-    stats->steps = g->h_sctl->steps;
-    stats->evals = g->h_sctl->evals;
+    stats->steps = g->h_sctl->steps + lazy_steps;
+    stats->evals = g->h_sctl->evals + lazy_evals;
     stats->batches = (int64_t)g->h_gctl->batches;
     stats->edges_scalar = (int64_t)g->h_gctl->edges_scalar;
     stats->edges_union = (int64_t)g->h_gctl->edges_union;
@@ -496,6 +576,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       ms_k += ms;
     }
     stats->ms_gain_kernel = ms_k;
+    stats->ms_lazy_select = lazy_ms[0];
+    stats->ms_lazy_gain = lazy_ms[1];
+    stats->ms_lazy_update = lazy_ms[2];
     stats->gain_launches = (int64_t)(ev_used / 2);
     stats->kernel_launches = g->launches - launches0;
     stats->ms_total =

@@ -4,7 +4,10 @@
 // lower bound, and CSR validation.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "gc_device.cuh"
+#include "gc_grid.cuh"
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -30,73 +33,10 @@ __global__ void k_fill_i64(long long *p, long long v, int64_t count) {
 // farness decrease Delta(s | S).
 __global__ void __launch_bounds__(kBfsThreads) k_bfs_relabel(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
-    const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, BfsCtl *ctl,
-    unsigned long long timeout_ns) {
-  __shared__ unsigned long long sh[32];
-  const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned long long dec = 0, rel = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x) {
-    const int s = seeds[i];
-    if (s < 0 || s >= n) {
-      atomicExch(&ctl->err, GC_EINVAL);
-      continue;
-    }
-    const int old = atomicMin(&dist[s], 0);
-    if (old > 0) {
-      const int p = atomicAdd(&ctl->qsize[0], 1);
-      q0[p] = s;
-      if (old < kInf) dec += (unsigned long long)old;
-      ++rel;
-    }
-  }
-  bool ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-  for (int L = 0; ok; ++L) {
-    const int F = *(volatile int32_t *)&ctl->qsize[L % 3];
-    if (F == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->qsize[(L + 2) % 3] = 0;
-    const int32_t *qc = (L & 1) ? q1 : q0;
-    int32_t *qn = (L & 1) ? q0 : q1;
-    int32_t *qn_size = &ctl->qsize[(L + 1) % 3];
-    const int nl = L + 1;
-    for (int i = gwarp; i < F; i += nwarps) {
-      const int u = qc[i];
-      const int beg = rp[u], end = rp[u + 1];
-      for (int base = beg; base < end; base += 32) {
-        const int e = base + lane;
-        bool push = false;
-        int w = 0;
-        if (e < end) {
-          w = ci[e];
-          if (nl < dist[w]) {
-            const int old = atomicMin(&dist[w], nl);
-            if (old > nl) {
-              push = true;
-              if (old < kInf) dec += (unsigned long long)(old - nl);
-              ++rel;
-            }
-          }
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, push);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          int pos = 0;
-          if (lane == leader) pos = atomicAdd(qn_size, __popc(m));
-          pos = __shfl_sync(0xffffffffu, pos, leader);
-          if (push) qn[pos + __popc(m & ((1u << lane) - 1u))] = w;
-        }
-      }
-    }
-    ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-    if (ok && blockIdx.x == 0 && threadIdx.x == 0) ctl->levels = L + 1;
-  }
-  dec = block_sum(dec, sh);
-  rel = block_sum(rel, sh);
-  if (threadIdx.x == 0) {
-    if (dec) atomicAdd(&ctl->decrease, dec);
-    if (rel) atomicAdd(&ctl->relabelled, rel);
-  }
+    const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *goff,
+    BfsCtl *ctl, unsigned long long timeout_ns) {
+  grid_relabel_bfs(rp, ci, n, dist, seeds, n_seeds, q0, q1, ctl->qsize, &ctl->levels, &ctl->decrease,
+                   &ctl->relabelled, goff, ctl->blk_tot, &ctl->bar, &ctl->err, timeout_ns);
 }
 
 // sum(dist) and the count of unreached vertices; the last CTA to finish folds
@@ -166,6 +106,26 @@ __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__re
   }
 }
 
+// mx[u] = max over neighbours w of d_S[w].  d_S only decreases as the group
+// grows, so the value stays an upper bound; a frontier vertex u at level L can
+// claim a neighbour only if that neighbour's d_S exceeds L+1, so mx[u] <= L+1
+// means expanding u is useless (the pruning test of Sec. 4.1 applied one level
+// ahead).
+__global__ void __launch_bounds__(kRedThreads) k_max_nbr(const int32_t *__restrict__ rp,
+                                                         const int32_t *__restrict__ ci, int32_t n,
+                                                         const int32_t *__restrict__ dS, int32_t *mx) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = gwarp; v < n; v += nwarps) {
+    int m = 0;
+    for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) m = max(m, dS[ci[e]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) mx[v] = m;
+  }
+}
+
 // CSR validation, part 1: row_ptr monotone within [0, nnz].
 __global__ void k_validate_rowptr(const int32_t *__restrict__ rp, int32_t n, int64_t nnz,
                                   SelCtl *ctl) {
@@ -230,13 +190,14 @@ int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t
   GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
-  int32_t *q0 = g->bq0, *q1 = g->bq1;
+  int32_t *q0 = g->bq0, *q1 = g->bq1, *goff = g->goff;
   BfsCtl *ctl = g->bctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
-  void *args[] = {(void *)&rp, (void *)&ci, (void *)&n, (void *)&dist, (void *)&seeds,
-                  (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&ctl, (void *)&tns};
+  void *args[] = {(void *)&rp,      (void *)&ci, (void *)&n,  (void *)&dist, (void *)&seeds,
+                  (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&goff, (void *)&ctl,
+                  (void *)&tns};
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(g->bfs_ctas),
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(std::min(g->bfs_ctas, kMaxGridCtas)),
                                       dim3(kBfsThreads), args, 0, g->stream));
   return GC_OK;
 }
@@ -257,6 +218,14 @@ int launch_round0_keys(gc_graph *g) {
   ++g->launches;
   k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
                   g->stream>>>(g->rp, g->ci, g->n, g->key);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_max_nbr(gc_graph *g) {
+  ++g->launches;
+  k_max_nbr<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0, g->stream>>>(
+      g->rp, g->ci, g->n, g->dS, g->mx_buf);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     k_gains64(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
               const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t n_cand_arg,
               const int32_t *__restrict__ n_cand_dev, long long *__restrict__ out,
-              unsigned char *ws_base, size_t ws_stride, GainCtl *ctl, int lanes) {
+              unsigned char *ws_base, size_t ws_stride, GainCtl *ctl, int lanes,
+              const int32_t *__restrict__ mx) {
   constexpr int T = kGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ int s_cnt[kLanes];
@@ -156,6 +157,8 @@ __global__ void __launch_bounds__(kGainThreads, 2)
           const int u = qcur_v[i];
           m = qcur_m[i];
           if (MODE == kModeFarness) m &= s_alive;
+          // no neighbour of u can still be claimed: skip the scan
+          if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
           if (m) {
             rs = rp[u];
             deg = rp[u + 1] - rs;
@@ -295,10 +298,10 @@ int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
   ++g->launches;
   if (mode == kModeGain)
     k_gains64<kModeGain><<<ctas, kGainThreads, 0, g->stream>>>(
-        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes);
+        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes, g->mx);
   else
     k_gains64<kModeFarness><<<ctas, kGainThreads, 0, g->stream>>>(
-        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes);
+        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes, nullptr);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -16,317 +16,19 @@
 //      applies the same BFScut test to its copy of the live-lane mask.
 // Per-lane gains accumulate in shared memory and reach global memory once per
 // CTA (gain mode) or once per level (farness mode, where the cut needs them).
-#include <limits.h>
-
-#include "gc_device.cuh"
-#include "gc_internal.cuh"
+#include "gc_grid.cuh"
 
 namespace gc {
-
-typedef unsigned long long u64;
-
-size_t gain_ws_stride(int32_t n);
-
-struct GainWsG {
-  u64 *vis, *nxt, *qm0, *qm1;
-  int32_t *qv0, *qv1, *touched;
-};
-
-static __device__ __forceinline__ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-__device__ __forceinline__ GainWsG grid_ws(unsigned char *p, int32_t n) {
-  const size_t a8 = al256((size_t)n * sizeof(u64)), a4 = al256((size_t)n * sizeof(int32_t));
-  GainWsG w;
-  w.vis = (u64 *)p;
-  w.nxt = (u64 *)(p + a8);
-  w.qm0 = (u64 *)(p + 2 * a8);
-  w.qm1 = (u64 *)(p + 3 * a8);
-  w.qv0 = (int32_t *)(p + 4 * a8);
-  w.qv1 = (int32_t *)(p + 4 * a8 + a4);
-  w.touched = (int32_t *)(p + 4 * a8 + 2 * a4);
-  return w;
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(kGridGainThreads, 2)
     k_gains_grid(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
                  const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t nl_arg,
-                 const int32_t *__restrict__ nl_dev, long long *__restrict__ out, unsigned char *ws_base, int32_t *__restrict__ goff,
-                 GridGainCtl *ctl, GainCtl *gctl, unsigned long long timeout_ns) {
-  constexpr int T = kGridGainThreads;
-  __shared__ u64 s_gain[kLanes];
-  __shared__ unsigned int s_cnt[kLanes];
-  __shared__ int s_scan[33];
-  __shared__ long long s_blkoff[kMaxGridCtas + 1];
-  __shared__ u64 s_red[32];
-  __shared__ int s_qn, s_touched;
-
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int G = gridDim.x, b = blockIdx.x;
-  const int nl = nl_dev ? min(kLanes, *nl_dev) : nl_arg;
-  const GainWsG ws = grid_ws(ws_base, n);
-  u64 c_scalar = 0, c_union = 0, c_front = 0, c_push = 0;
-  if (tid < kLanes) {
-    s_gain[tid] = 0;
-    s_cnt[tid] = 0;
-  }
-  u64 alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
-
-  // ---- level 0 (CTA 0): lanes start at their candidates ----
-  if (b == 0) {
-    if (tid == 0) {
-      s_qn = 0;
-      s_touched = 0;
-    }
-    __syncthreads();
-    if (tid < nl) {
-      const int c = cand[tid];
-      const u64 bit = 1ull << tid;
-      bool push = false;
-      if (c < 0 || c >= n) {
-        atomicExch(&ctl->err, GC_EINVAL);
-      } else if (MODE == kModeGain) {
-        const int dc = dS[c];
-        if (dc > 0) {
-          ctl->gain[tid] = (u64)dc;
-          push = true;
-        }
-      } else {
-        ctl->cnt[tid] = 1;
-        push = true;
-      }
-      if (push) {
-        const u64 old = atomicOr(&ws.nxt[c], bit);
-        if (old == 0) ws.qv0[atomicAdd(&s_qn, 1)] = c;
-      }
-    }
-    __syncthreads();
-    const int F0 = s_qn;
-    for (int i = tid; i < F0; i += T) {
-      const int w = ws.qv0[i];
-      const u64 m = ws.nxt[w];
-      ws.nxt[w] = 0;
-      ws.vis[w] = m;
-      ws.touched[atomicAdd(&s_touched, 1)] = w;
-      ws.qm0[i] = m;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      ctl->F = F0;
-      ctl->touched = s_touched;
-    }
-  }
-  bool ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-  // invalid candidate ids leave their lanes empty
-  if (ok && MODE == kModeFarness) {
-    for (int j = 0; j < nl; ++j)
-      if (((volatile unsigned long long *)ctl->cnt)[j] == 0) alive &= ~(1ull << j);
-  }
-
-  int L = 0;
-  for (; ok; ++L) {
-    const int F = *(volatile int32_t *)&ctl->F;
-    if (F == 0) break;
-    const int32_t *qcur_v = (L & 1) ? ws.qv1 : ws.qv0;
-    const u64 *qcur_m = (L & 1) ? ws.qm1 : ws.qm0;
-    int32_t *qnxt_v = (L & 1) ? ws.qv0 : ws.qv1;
-    u64 *qnxt_m = (L & 1) ? ws.qm0 : ws.qm1;
-    int32_t *qn_ctr = &ctl->qn[L & 1];
-    const int nlev = L + 1;
-    // ---- phase 1: degree offsets of this CTA's contiguous frontier slice ----
-    const int P = (F + G - 1) / G;
-    const int lo = min(F, b * P), hi = min(F, lo + P);
-    int carry = 0;
-    for (int base = lo; base < hi; base += T) {
-      const int i = base + tid;
-      int deg = 0;
-      if (i < hi) {
-        const int u = qcur_v[i];
-        u64 m = qcur_m[i];
-        if (MODE == kModeFarness) m &= alive;
-        if (m) deg = rp[u + 1] - rp[u];
-        c_union += (u64)deg;
-        c_scalar += (u64)__popcll(m) * (u64)deg;
-        c_front += (m != 0);
-      }
-      int total;
-      const int off = block_excl_scan(deg, s_scan, &total);
-      if (i < hi) goff[i] = carry + off;
-      carry += total;
-    }
-    if (tid == 0) {
-      ctl->blk_tot[b] = carry;
-      if (b == 0) *qn_ctr = 0;
-    }
-    ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-    if (!ok) break;
-    // ---- phase 2: expand an equal slice of the level's adjacency entries ----
-    {
-      long long run = 0;
-      for (int base = 0; base < G; base += T) {
-        const int j = base + tid;
-        const int v = j < G ? ((volatile int32_t *)ctl->blk_tot)[j] : 0;
-        int total;
-        const int off = block_excl_scan(v, s_scan, &total);
-        if (j < G) s_blkoff[j] = run + off;
-        run += total;
-      }
-      if (tid == 0) s_blkoff[G] = run;
-      __syncthreads();
-    }
-    const long long E = s_blkoff[G];
-    const long long es = E * b / G, ee = E * (b + 1) / G;
-    for (long long e0 = es + (tid & ~31); e0 < ee; e0 += T) {
-      const long long e = e0 + lane;
-      bool push = false;
-      int w = 0;
-      if (e < ee) {
-        // owning CTA slice: largest c with s_blkoff[c] <= e (its slice is non-empty)
-        int a = 0, z = G - 1;
-        while (a < z) {
-          const int mid = (a + z + 1) >> 1;
-          if (s_blkoff[mid] <= e) a = mid;
-          else z = mid - 1;
-        }
-        const int local = (int)(e - s_blkoff[a]);
-        int x = min(F, a * P), y = min(F, a * P + P) - 1;  // entry with largest goff <= local
-        while (x < y) {
-          const int mid = (x + y + 1) >> 1;
-          if (goff[mid] <= local) x = mid;
-          else y = mid - 1;
-        }
-        const int u = qcur_v[x];
-        u64 m = qcur_m[x];
-        if (MODE == kModeFarness) m &= alive;
-        w = ci[rp[u] + (local - goff[x])];
-        int dw = 0;
-        bool pass = true;
-        if (MODE == kModeGain) {
-          dw = dS[w];
-          pass = dw > nlev;
-        }
-        if (pass) {
-          const u64 nb = m & ~ws.vis[w];
-          if (nb) {
-            const u64 old = atomicOr(&ws.nxt[w], nb);
-            u64 won = nb & ~old;
-            if (won) {
-              const u64 wt = MODE == kModeGain ? (u64)(dw - nlev) : (u64)nlev;
-              do {
-                const int j = __ffsll((long long)won) - 1;
-                won &= won - 1;
-                atomicAdd(&s_gain[j], wt);
-                if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1u);
-              } while (won);
-            }
-            push = old == 0;
-          }
-        }
-      }
-      const unsigned pm = __ballot_sync(0xffffffffu, push);
-      if (pm) {
-        const int leader = __ffs(pm) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(qn_ctr, __popc(pm));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (push) qnxt_v[pos + __popc(pm & ((1u << lane) - 1u))] = w;
-        c_push += (lane == leader) ? (u64)__popc(pm) : 0ull;
-      }
-    }
-    ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-    if (!ok) break;
-    // ---- phase 3: commit level L+1 ----
-    const int Fn = *(volatile int32_t *)qn_ctr;
-    for (int base = b * T; base < Fn; base += G * T) {
-      const int i = base + tid;
-      bool fresh = false;
-      int w = 0;
-      if (i < Fn) {
-        w = qnxt_v[i];
-        const u64 m = ws.nxt[w];
-        ws.nxt[w] = 0;
-        const u64 ov = ws.vis[w];
-        ws.vis[w] = ov | m;
-        fresh = ov == 0;
-        qnxt_m[i] = m;
-      }
-      const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-      if (fm) {
-        const int leader = __ffs(fm) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(&ctl->touched, __popc(fm));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (fresh) ws.touched[pos + __popc(fm & ((1u << lane) - 1u))] = w;
-      }
-    }
-    if (MODE == kModeFarness) {
-      __syncthreads();
-      if (tid < kLanes) {
-        if (s_gain[tid]) atomicAdd(&ctl->gain[tid], s_gain[tid]);
-        if (s_cnt[tid]) atomicAdd(&ctl->cnt[tid], (u64)s_cnt[tid]);
-        s_gain[tid] = 0;
-        s_cnt[tid] = 0;
-      }
-    }
-    if (b == 0 && tid == 0) ctl->F = Fn;
-    ok = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-    if (!ok) break;
-    if (MODE == kModeFarness) {
-      // the same BFScut test in every CTA: all vertices within L+1 are
-      // counted, the rest are at least L+2 away
-      const long long best = *(volatile long long *)&gctl->best_f;
-      for (int j = 0; j < nl; ++j) {
-        if (!((alive >> j) & 1ull)) continue;
-        const long long s = (long long)((volatile u64 *)ctl->gain)[j];
-        const long long c = (long long)((volatile u64 *)ctl->cnt)[j];
-        if (Fn > 0 && s + (long long)(L + 2) * ((long long)n - c) > best) alive &= ~(1ull << j);
-      }
-      if (alive == 0) break;
-    }
-  }
-  // ---- results ----
-  if (MODE == kModeGain) {
-    __syncthreads();
-    if (tid < kLanes && s_gain[tid]) atomicAdd(&ctl->gain[tid], s_gain[tid]);
-  }
-  c_scalar = block_sum(c_scalar, s_red);
-  c_union = block_sum(c_union, s_red);
-  c_front = block_sum(c_front, s_red);
-  c_push = block_sum(c_push, s_red);
-  if (tid == 0) {
-    atomicAdd(&gctl->edges_scalar, c_scalar);
-    atomicAdd(&gctl->edges_union, c_union);
-    atomicAdd(&gctl->frontier, c_front);
-    atomicAdd(&gctl->pushes, c_push);
-    if (b == 0) {
-      atomicAdd(&gctl->levels, (u64)L);
-      atomicAdd(&gctl->batches, 1ull);
-      atomicAdd(&gctl->lanes, (u64)nl);
-    }
-  }
-  const bool ok2 = grid_sync(&ctl->bar, &ctl->err, timeout_ns);
-  if (b == 0 && tid < nl) {
-    const int c = cand[tid];
-    long long r;
-    if (!ok2 || c < 0 || c >= n) {
-      r = -1;
-    } else if (MODE == kModeGain) {
-      r = (long long)((volatile u64 *)ctl->gain)[tid];
-    } else if (!((alive >> tid) & 1ull)) {
-      r = -1;
-    } else if ((long long)((volatile u64 *)ctl->cnt)[tid] != n) {
-      r = -1;
-      atomicExch(&gctl->err, GC_EDISCONNECTED);
-    } else {
-      r = (long long)((volatile u64 *)ctl->gain)[tid];
-      atomicMin(&gctl->best_f, r);
-    }
-    out[tid] = r;
-  }
-  // leave the workspace zero for the next launch
-  const int nt = *(volatile int32_t *)&ctl->touched;
-  for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i]] = 0;
-  if (!ok2 && b == 0 && tid == 0) atomicExch(&gctl->err, GC_ETIMEOUT);
+                 const int32_t *__restrict__ nl_dev, long long *__restrict__ out, unsigned char *ws_base,
+                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, unsigned long long timeout_ns,
+                 const int32_t *__restrict__ mx) {
+  grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, goff, ctl, gctl, &ctl->bar,
+                        &ctl->err, timeout_ns, mx);
 }
 
 int grid_gain_occupancy(int *blocks_per_sm) {
@@ -349,9 +51,10 @@ int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, co
   GridGainCtl *ctl = g->ggctl;
   GainCtl *gctl = g->gctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
+  const int32_t *mx = mode == kModeGain ? g->mx : nullptr;
   void *args[] = {(void *)&rp,  (void *)&ci,   (void *)&n,   (void *)&dS,  (void *)&cand,
                   (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&goff,
-                  (void *)&ctl, (void *)&gctl, (void *)&tns};
+                  (void *)&ctl, (void *)&gctl, (void *)&tns, (void *)&mx};
   ++g->launches;
   if (mode == kModeGain)
     GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gains_grid<kModeGain>, dim3(g->grid_ctas),

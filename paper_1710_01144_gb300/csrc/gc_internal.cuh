@@ -38,6 +38,7 @@ struct BfsCtl {
   int32_t pad;
   unsigned long long decrease;  // sum over relabelled vertices of (old - new), old finite
   unsigned long long relabelled;
+  int32_t blk_tot[kMaxGridCtas];  // per-CTA adjacency totals of the level
 };
 
 // Gain-kernel control block.  batch_next is zeroed before every launch; err,
@@ -66,6 +67,26 @@ struct GridGainCtl {
   unsigned long long gain[kLanes];  // per-lane gain (gain mode) / distance sum (farness)
   unsigned long long cnt[kLanes];   // farness mode: per-lane visited count
   int32_t blk_tot[kMaxGridCtas];    // per-CTA adjacency totals of the level
+};
+
+// Persistent lazy-rounds kernel control block (gc_lazy.cu).
+struct LazyCtl {
+  GridBar bar;
+  int32_t err;
+  int32_t dec;          // step decision: 0 evaluate, 1 accept, 2 rebuild the active list
+  int32_t round;        // current round (in/out across launches)
+  int32_t n_sel;        // candidates of the current batch
+  int32_t best_id;      // round's best exact gain so far (-1 none)
+  int32_t rounds_done;
+  long long best_gain;
+  long long theta;      // every candidate outside the active list has ub < theta
+  int32_t qsize[3];     // relabel BFS frontier sizes
+  int32_t pad;
+  unsigned long long decrease;
+  long long steps, evals;
+  unsigned long long ns_select, ns_gain, ns_update;  // time in each phase (CTA 0's clock)
+  int32_t sel[kLanes];
+  long long gsel[kLanes];
 };
 
 // Selection / reduction control block (lives across a whole greedy call).
@@ -106,6 +127,8 @@ struct gc_graph {
   int32_t *rp = nullptr;  // row_ptr[n+1]
   int32_t *ci = nullptr;  // col_idx[nnz]
   int32_t *dS = nullptr;  // distance to the current group
+  int32_t *mx = nullptr;  // mx[u] >= max over neighbours w of d_S[w] (or nullptr: no pruning)
+  int32_t *mx_buf = nullptr;
   long long *ub = nullptr;     // lazy bound / exact gain of the round in stamp
   int32_t *stamp = nullptr;    // round of the last exact evaluation (0 = never)
   long long *key = nullptr;    // round-0 selection key (-lower bound), INT64_MIN = done
@@ -120,6 +143,10 @@ struct gc_graph {
   int32_t *io_b = nullptr;
   gc::BfsCtl *bctl = nullptr;
   gc::GridGainCtl *ggctl = nullptr;
+  gc::LazyCtl *lctl = nullptr;
+  gc::LazyCtl *h_lctl = nullptr;           // pinned host mirror
+  int32_t *picks = nullptr;                // per-round picks / gains / d_S decreases [n]
+  long long *pgain = nullptr, *pdec = nullptr;
   int32_t *goff = nullptr;                 // grid gain kernel: frontier offsets [n+1]
   gc::GainCtl *gctl = nullptr;
   gc::SelCtl *sctl = nullptr;
@@ -133,6 +160,7 @@ struct gc_graph {
   int gain_ctas = 0;       // resident CTAs of the gain kernel
   int bfs_ctas = 0;        // resident CTAs of the cooperative BFS
   int grid_ctas = 0;       // resident CTAs of the grid-wide gain kernel
+  int lazy_ctas = 0;       // resident CTAs of the persistent lazy kernel
   int red_blocks = 0;      // grid size of reductions
   int32_t *dec = nullptr;                  // scratch word
   int64_t launches = 0;                    // kernels launched through this handle
@@ -183,10 +211,12 @@ int grid_gain_occupancy(int *blocks_per_sm);
 int gain_kernel_occupancy(int *blocks_per_sm);
 
 // selection
-enum SelMode { kSelLazy = 0, kSelKey = 1 };
+// kSelLazy: bound of a candidate not evaluated in `round`; kSelKey: round-0
+// key; kSelActive: bound of any non-member (active-list build)
+enum SelMode { kSelLazy = 0, kSelKey = 1, kSelActive = 2 };
 // tau_mode: kTauHistogram (find tau covering `want` keys), kTauHost (tau given),
 // kTauDevice (tau already in sctl->tau)
-enum TauMode { kTauHistogram = 0, kTauHost = 1, kTauDevice = 2 };
+enum TauMode { kTauHistogram = 0, kTauHost = 1, kTauDevice = 2, kTauHistogramTheta = 3 };
 int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, int tau_mode, long long tau);
 int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list);
 int launch_unevaluated_best(gc_graph *g, int32_t round);
@@ -196,6 +226,12 @@ int launch_round0_seed(gc_graph *g);
 int launch_round_begin(gc_graph *g);
 int launch_round_end(gc_graph *g);
 int launch_clamp_nsel(gc_graph *g, int32_t cap);
+int launch_degree_keys(gc_graph *g);
+// mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
+int launch_max_nbr(gc_graph *g);
+int launch_active_theta(gc_graph *g);
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns);
+int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 }  // namespace gc

@@ -1,0 +1,355 @@
+// Persistent lazy greedy (Sec. 4.2) for rounds >= 2: one cooperative launch
+// runs round after round on the device -- select, evaluate, certify, update
+// d_S -- with no host round trip.
+//
+// Candidates live in an "active list" (vertex ids in increasing order) that
+// holds every non-member whose bound ub is at least theta; every candidate
+// outside it has ub < theta.  Each step, CTA 0
+//   * folds the gains of the batch just evaluated (ub <- exact gain, stamp <-
+//     round) into the round's best (gain desc, id asc);
+//   * finds the best bound (ub desc, id asc) among active candidates not yet
+//     evaluated in this round.  If the round's best beats it and is >= theta,
+//     the best is the plain greedy's choice (nothing outside the list can
+//     reach theta): accept.  If it beats the list but is below theta, the list
+//     is too short: the kernel stops and the host rebuilds it with a lower
+//     theta.  Otherwise
+//   * selects exactly the 64 largest (ub, smaller id first) unevaluated active
+//     candidates: histogram passes over the bounds fix the threshold value,
+//     ties at the threshold go to the smallest ids (list order).
+// Then every CTA runs the 64-lane pruned BFS on that batch (grid_gain_batch).
+// On acceptance every CTA runs the relabel BFS from the pick (the pruned SSSP
+// that turns d_S into min(d_S, d(pick, .)), Sec. 4.1) and the round advances.
+#include <limits.h>
+
+#include "gc_grid.cuh"
+
+namespace gc {
+
+constexpr int kLazyBins = 1024;  // two bins per thread of a 512-thread CTA
+
+__device__ __forceinline__ long long block_min_ll(long long v, long long *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) v = min(v, sh[w]);
+    sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+// (value, id) block arg-max; every thread gets the result.
+__device__ __forceinline__ void block_argmax_all(long long &v, int &id, long long *sv, int *sid) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oid = __shfl_xor_sync(0xffffffffu, id, o);
+    if (better_max(ov, oid, v, id)) {
+      v = ov;
+      id = oid;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sv[wid] = v;
+    sid[wid] = id;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w)
+      if (better_max(sv[w], sid[w], v, id)) {
+        v = sv[w];
+        id = sid[w];
+      }
+    sv[0] = v;
+    sid[0] = id;
+  }
+  __syncthreads();
+  v = sv[0];
+  id = sid[0];
+  __syncthreads();
+}
+
+// CTA 0's part of a step (see the file comment).  Writes lc->dec (0 evaluate
+// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).
+__device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+                               LazyCtl *lc, GridGainCtl *gg, bool fold) {
+  __shared__ unsigned int s_hist[kLazyBins];
+  __shared__ int s_scan[33];
+  __shared__ long long s_v[32];
+  __shared__ int s_id[32];
+  __shared__ long long s_ll[32];
+  __shared__ int s_b;
+  __shared__ long long s_ab;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int r = lc->round;
+
+  if (fold) {  // the batch just evaluated: exact gains become the bounds
+    const int ns = lc->n_sel;
+    long long bv = -1;
+    int bid = -1;
+    if (tid < ns) {
+      const int v = lc->sel[tid];
+      const long long gv = lc->gsel[tid];
+      ub[v] = gv;
+      stamp[v] = r;
+      bv = gv;
+      bid = v;
+    }
+    block_argmax_all(bv, bid, s_v, s_id);
+    if (tid == 0) {
+      if (bid >= 0 && better_max(bv, bid, lc->best_gain, lc->best_id)) {
+        lc->best_gain = bv;
+        lc->best_id = bid;
+      }
+      lc->steps += 1;
+      lc->evals += ns;
+    }
+    __syncthreads();
+  }
+  const long long gb = *(volatile long long *)&lc->best_gain;
+  const int vb = *(volatile int32_t *)&lc->best_id;
+  const long long theta = lc->theta;
+
+  // best unevaluated bound, smallest bound, count
+  long long umax = LLONG_MIN, umin = LLONG_MAX, cnt = 0;
+  int vmax = -1;
+  for (int i = tid; i < m; i += T) {
+    const int v = act[i];
+    const long long u = ub[v];
+    if (u < 0 || stamp[v] == r) continue;
+    if (better_max(u, v, umax, vmax)) {
+      umax = u;
+      vmax = v;
+    }
+    umin = min(umin, u);
+    ++cnt;
+  }
+  block_argmax_all(umax, vmax, s_v, s_id);
+  umin = block_min_ll(umin, s_ll);
+  cnt = block_sum(cnt, s_ll);
+  int dec;
+  if (vb >= 0 && (cnt == 0 || better_max(gb, vb, umax, vmax))) dec = gb >= theta ? 1 : 2;
+  else if (cnt == 0) dec = 2;
+  else dec = 0;
+  if (dec != 0) {
+    if (tid == 0) lc->dec = dec;
+    return;
+  }
+
+  // exact threshold value tau: fewer than `need` keys above it, at least `need` at or above
+  const long long need = cnt < kLanes ? cnt : kLanes;
+  long long tau = umin, above = 0;  // above = unevaluated keys > tau
+  if (cnt > kLanes) {
+    unsigned long long lo = (unsigned long long)umin, hi = (unsigned long long)umax;
+    long long want = kLanes, acc = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+      const unsigned long long span = hi - lo + 1ull;
+      const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
+      for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < m; i += T) {
+        const int v = act[i];
+        const long long u = ub[v];
+        if (u < 0 || stamp[v] == r) continue;
+        const unsigned long long uu = (unsigned long long)u;
+        if (uu < lo || uu > hi) continue;
+        atomicAdd(&s_hist[(uu - lo) / width], 1u);
+      }
+      __syncthreads();
+      // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
+      const int b0 = kLazyBins - 1 - 2 * tid, b1 = b0 - 1;
+      const int h0 = tid < kLazyBins / 2 ? (int)s_hist[b0] : 0;
+      const int h1 = tid < kLazyBins / 2 ? (int)s_hist[b1] : 0;
+      if (tid == 0) {
+        s_b = 0;
+        s_ab = 0;
+      }
+      int total;
+      const long long a0 = block_excl_scan(h0 + h1, s_scan, &total);
+      if (tid < kLazyBins / 2) {
+        if (a0 < want && a0 + h0 >= want) {
+          s_b = b0;
+          s_ab = a0;
+        } else if (a0 + h0 < want && a0 + h0 + h1 >= want) {
+          s_b = b1;
+          s_ab = a0 + h0;
+        }
+      }
+      __syncthreads();
+      const int b = s_b;
+      const long long ab = s_ab;
+      const unsigned long long bin_lo = lo + width * (unsigned long long)b;
+      if (width == 1ull) {
+        tau = (long long)bin_lo;
+        above = acc + ab;
+        break;
+      }
+      acc += ab;
+      want -= ab;
+      const unsigned long long room = hi - bin_lo;
+      lo = bin_lo;
+      hi = bin_lo + (width - 1ull < room ? width - 1ull : room);
+      __syncthreads();
+    }
+  }
+  // select in list (id) order: every key > tau, then keys == tau by smallest id
+  int taken = 0, eq_seen = 0;
+  for (int base = 0; base < m && taken < need; base += T) {
+    const int i = base + tid;
+    int gt = 0, eq = 0, v = -1;
+    if (i < m) {
+      v = act[i];
+      const long long u = ub[v];
+      if (u >= 0 && stamp[v] != r) {
+        gt = u > tau;
+        eq = u == tau;
+      }
+    }
+    int tot_eq, tot_take;
+    const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
+    const int take = gt || (eq && eq_rank < need - above);
+    const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
+    if (take && pos < kLanes) lc->sel[pos] = v;
+    eq_seen += tot_eq;
+    taken += tot_take;
+  }
+  // a fresh grid-batch control block for the evaluation
+  if (tid < kLanes) {
+    gg->gain[tid] = 0;
+    gg->cnt[tid] = 0;
+  }
+  if (tid == 0) {
+    lc->n_sel = taken < kLanes ? taken : kLanes;
+    lc->dec = 0;
+    gg->F = 0;
+    gg->qn[0] = 0;
+    gg->qn[1] = 0;
+    gg->touched = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kGridGainThreads, 2)
+    k_lazy_rounds(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dS,
+                  long long *ub, int32_t *stamp, const int32_t *__restrict__ act, const int32_t *m_dev,
+                  int32_t k, int32_t *picks, long long *pgain, long long *pdec, unsigned char *ws,
+                  int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
+                  unsigned long long tns, const int32_t *__restrict__ mx) {
+  const int m = *m_dev;
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t0 = timer ? global_ns() : 0, t1;
+  bool fold = false;
+  for (;;) {
+    const int r = *(volatile int32_t *)&lc->round;
+    if (r >= k) break;
+    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold);
+    if (!grid_sync(&lc->bar, &lc->err, tns)) break;
+    if (timer) {
+      t1 = global_ns();
+      lc->ns_select += t1 - t0;
+      t0 = t1;
+    }
+    const int dec = *(volatile int32_t *)&lc->dec;
+    if (dec == 2) break;  // the host lowers theta and relaunches
+    if (dec == 0) {
+      bool ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, goff, gg,
+                                           gctl, &lc->bar, &lc->err, tns, mx);
+      ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
+      if (!ok) break;
+      if (timer) {
+        t1 = global_ns();
+        lc->ns_gain += t1 - t0;
+        t0 = t1;
+      }
+      fold = true;
+      continue;
+    }
+    // accept the round's best: record it and update d_S from it
+    fold = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      picks[r] = lc->best_id;
+      pgain[r] = lc->best_gain;
+      lc->qsize[0] = lc->qsize[1] = lc->qsize[2] = 0;
+      lc->decrease = 0;
+    }
+    if (!grid_sync(&lc->bar, &lc->err, tns)) break;
+    bool ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease,
+                               nullptr, goff, gg->blk_tot, &lc->bar, &lc->err, tns);
+    ok = ok && grid_sync(&lc->bar, &lc->err, tns);
+    if (!ok) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      pdec[r] = (long long)lc->decrease;
+      ub[lc->best_id] = -1;  // a member: never a candidate again
+      lc->best_id = -1;
+      lc->best_gain = -1;
+      lc->rounds_done += 1;
+      lc->round = r + 1;
+    }
+    if (!grid_sync(&lc->bar, &lc->err, tns)) break;
+    if (timer) {
+      t1 = global_ns();
+      lc->ns_update += t1 - t0;
+      t0 = t1;
+    }
+  }
+}
+
+// After a threshold pass over the bounds: never let theta exceed the round's
+// best exact gain (so that the rebuilt list can certify it), then record theta.
+__global__ void k_active_theta(SelCtl *sc, LazyCtl *lc) {
+  long long tau = sc->tau;
+  if (lc->best_id >= 0 && lc->best_gain < tau) tau = lc->best_gain;
+  if (sc->sel_count == 0) tau = LLONG_MAX;
+  sc->tau = tau;
+  lc->theta = tau;
+}
+
+int lazy_occupancy(int *blocks_per_sm) {
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lazy_rounds, kGridGainThreads, 0));
+  return GC_OK;
+}
+
+int launch_active_theta(gc_graph *g) {
+  ++g->launches;
+  k_active_theta<<<1, 1, 0, g->stream>>>(g->sctl, g->lctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns) {
+  const int32_t *rp = g->rp, *ci = g->ci;
+  int32_t n = g->n;
+  int32_t *dS = g->dS;
+  long long *ub = g->ub;
+  int32_t *stamp = g->stamp;
+  const int32_t *act = g->list;
+  const int32_t *m_dev = &g->sctl->n_sel;
+  int32_t *picks = g->picks;
+  long long *pgain = g->pgain, *pdec = g->pdec;
+  unsigned char *ws = g->ws;
+  int32_t *goff = g->goff;
+  GridGainCtl *gg = g->ggctl;
+  LazyCtl *lc = g->lctl;
+  GainCtl *gctl = g->gctl;
+  int32_t *q0 = g->bq0, *q1 = g->bq1;
+  unsigned long long tns = (unsigned long long)timeout_ns;
+  const int32_t *mx = g->mx;
+  void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
+                  (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
+                  (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
+                  (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
+                  (void *)&mx};
+  ++g->launches;
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(g->lazy_ctas), dim3(kGridGainThreads),
+                                      args, 0, g->stream));
+  return GC_OK;
+}
+
+}  // namespace gc

@@ -29,6 +29,10 @@ __device__ __forceinline__ long long sel_key(int v, const long long *__restrict_
     const long long u = ub[v];
     return (u >= 0 && stamp[v] != round) ? u : LLONG_MIN;
   }
+  if (MODE == kSelActive) {
+    const long long u = ub[v];
+    return u >= 0 ? u : LLONG_MIN;
+  }
   return key[v];
 }
 
@@ -455,6 +459,13 @@ __global__ void k_round_begin(SelCtl *ctl) {
   ctl->accepted = 0;
 }
 
+// Round 1 work estimate: key[v] = deg(v) for non-members, LLONG_MIN for members.
+__global__ void k_degree_keys(const int32_t *__restrict__ rp, int32_t n, const long long *__restrict__ ub,
+                              long long *key) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    key[v] = ub[v] >= 0 ? (long long)(rp[v + 1] - rp[v]) : LLONG_MIN;
+}
+
 // Keep at most `cap` entries of the compacted list (the list is in vertex
 // order; the dropped tail stays unevaluated and keeps its bound).
 __global__ void k_clamp_nsel(SelCtl *ctl, int32_t cap) {
@@ -468,56 +479,47 @@ __global__ void k_round_end(long long *ub, const SelCtl *ctl) {
 }
 
 // ------------------------------------------------------------- launchers ----
-int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, int tau_mode,
-                  long long tau) {
+template <int MODE>
+static int select_impl(gc_graph *g, int32_t round, int32_t want, int tau_mode, long long tau) {
   const int rb = g->red_blocks;
   if (tau_mode == kTauHost) {
     // tau given: no range/histogram passes
     GC_CUDA(cudaMemcpyAsync(&g->sctl->tau, &tau, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
-  } else if (tau_mode == kTauHistogram) {
+  } else if (tau_mode == kTauHistogram || tau_mode == kTauHistogramTheta) {
     GC_CUDA(cudaMemcpyAsync(g->blk + rb, &want, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
     ++g->launches;
-    if (mode == kSelLazy)
-      k_sel_range<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                               g->partial, g->sctl);
-    else
-      k_sel_range<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                              g->partial, g->sctl);
+    k_sel_range<MODE><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key, g->partial,
+                                                         g->sctl);
     GC_CUDA(cudaGetLastError());
     for (int pass = 0; pass < 3; ++pass) {
       ++g->launches;
-      if (mode == kSelLazy)
-        k_sel_hist<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                                g->hist, g->sctl);
-      else
-        k_sel_hist<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                               g->hist, g->sctl);
+      k_sel_hist<MODE><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key, g->hist,
+                                                          g->sctl);
       ++g->launches;
       k_sel_pick<<<1, 1024, 0, g->stream>>>(g->hist, g->sctl, 2 * want, g->blk + rb);
       GC_CUDA(cudaGetLastError());
     }
+    if (tau_mode == kTauHistogramTheta) {
+      const int rc = launch_active_theta(g);
+      if (rc != GC_OK) return rc;
+    }
   }
-  if (mode == kSelLazy) {
-    ++g->launches;
-    k_compact_count<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                                 g->sctl, g->blk);
-    ++g->launches;
-    k_compact_scan<<<1, 1024, 0, g->stream>>>(g->blk, rb, g->sctl);
-    ++g->launches;
-    k_compact_write<kSelLazy><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                                 g->sctl, g->blk, g->list);
-  } else {
-    ++g->launches;
-    k_compact_count<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                                g->sctl, g->blk);
-    ++g->launches;
-    k_compact_scan<<<1, 1024, 0, g->stream>>>(g->blk, rb, g->sctl);
-    ++g->launches;
-    k_compact_write<kSelKey><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key,
-                                                                g->sctl, g->blk, g->list);
-  }
+  ++g->launches;
+  k_compact_count<MODE><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key, g->sctl,
+                                                           g->blk);
+  ++g->launches;
+  k_compact_scan<<<1, 1024, 0, g->stream>>>(g->blk, rb, g->sctl);
+  ++g->launches;
+  k_compact_write<MODE><<<rb, kRedThreads, 0, g->stream>>>(g->n, g->ub, g->stamp, round, g->key, g->sctl,
+                                                           g->blk, g->list);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
+}
+
+int launch_select(gc_graph *g, int mode, int32_t round, int32_t want, int tau_mode, long long tau) {
+  if (mode == kSelLazy) return select_impl<kSelLazy>(g, round, want, tau_mode, tau);
+  if (mode == kSelActive) return select_impl<kSelActive>(g, round, want, tau_mode, tau);
+  return select_impl<kSelKey>(g, round, want, tau_mode, tau);
 }
 
 int launch_after_eval(gc_graph *g, int32_t round, int32_t n_list) {
@@ -565,6 +567,13 @@ int launch_round0_seed(gc_graph *g) {
 int launch_round_begin(gc_graph *g) {
   ++g->launches;
   k_round_begin<<<1, 1, 0, g->stream>>>(g->sctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_degree_keys(gc_graph *g) {
+  ++g->launches;
+  k_degree_keys<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->rp, g->n, g->ub, g->key);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -11,9 +11,10 @@
 //
 // The scratch is a file-scope __device__ array of kStaticScratchBytes (64 MiB).
 // Every GPU that loads the library reserves it until the process exits.  It
-// holds d(., S), two BFS queues, the kernels' control words and as many
-// per-CTA gain workspaces (44 bytes per vertex each) as fit; a graph needs
-// at least one workspace, which caps n at about 1.1 million vertices.
+// holds d(., S), two BFS queues and a frontier-offset array, the kernels'
+// control words and as many per-CTA gain workspaces (44 bytes per vertex
+// each) as fit; a graph needs at least one workspace, which caps n at about
+// one million vertices (64 bytes per vertex in all).
 //
 // Host code cannot use the array's name as a device address; on the first
 // call on each device (with that device current) the library looks the
@@ -94,7 +95,8 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   // carve the array: control words, d(., S), BFS queues, then workspaces
   const size_t stride = gain_ws_stride(n);
   const size_t a4 = round_up((size_t)n * sizeof(int32_t));
-  const size_t head = round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)) + 3 * a4;
+  const size_t head = round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)) + 3 * a4 +
+                      round_up(((size_t)n + 1) * sizeof(int32_t));
   if (head + stride > kStaticScratchBytes) {
     set_error("gc_marginal_gains_static: n = " + std::to_string(n) + " needs " +
               std::to_string(head + stride) + " bytes of scratch, the static array holds " +
@@ -121,6 +123,8 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   p += a4;
   g.bq1 = (int32_t *)p;
   p += a4;
+  g.goff = (int32_t *)p;
+  p += round_up(((size_t)n + 1) * sizeof(int32_t));
   g.ws = p;
   g.ws_stride = stride;
   const int fit = (int)((kStaticScratchBytes - head) / stride);
@@ -131,7 +135,7 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
 
   // The array keeps whatever the previous call left (possibly for another n):
   // zero the control words and every workspace this call will use.
-  if (cudaMemsetAsync(base, 0, head - 3 * a4, g.stream) != cudaSuccess ||
+  if (cudaMemsetAsync(base, 0, round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)), g.stream) != cudaSuccess ||
       cudaMemsetAsync(g.ws, 0, (size_t)g.gain_ctas * stride, g.stream) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMemsetAsync on the static scratch failed");

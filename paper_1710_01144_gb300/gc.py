@@ -27,6 +27,7 @@ GC_EINTERNAL = -7
 GC_DEVICE_PTRS = 0x1
 GC_ADOPT = 0x2
 GC_VALIDATE = 0x4
+GC_OPT_NO_EXPAND_BOUND = 0x1
 
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
@@ -44,7 +45,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("eval_per_step", ctypes.c_int32), ("use_proposal", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
                 ("step_lanes", ctypes.c_int32), ("step_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -52,6 +54,7 @@ class Stats(ctypes.Structure):
         "rounds", "steps", "evals", "batches", "edges_scalar", "edges_union", "levels", "frontier",
         "pushes", "lanes", "round0_evals")] + [
         ("ms_round0", ctypes.c_double), ("ms_round1", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
+        ("ms_lazy_select", ctypes.c_double), ("ms_lazy_gain", ctypes.c_double), ("ms_lazy_update", ctypes.c_double),
         ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
@@ -174,11 +177,14 @@ class Graph:
                                                cand_dev.numel(), out_dev.data_ptr()))
 
     def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
-               use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0):
+               use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
+               active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
-        o.step_lanes, o.step_mode = step_lanes, step_mode
+        o.step_lanes, o.step_mode, o.active_target = step_lanes, step_mode, active_target
+        o.round1_heavy = round1_heavy
+        o.flags = 0 if expand_bound else GC_OPT_NO_EXPAND_BOUND
         if timeout_ms:
             o.timeout_ms = timeout_ms
         grp = np.zeros(max(int(k), 1), dtype=np.int32)

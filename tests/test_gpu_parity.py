@@ -9,9 +9,12 @@ from tests import smallgraphs as sg
 
 pytestmark = pytest.mark.gpu
 
-# (eval_per_step, step_lanes, step_mode) of the lazy rounds: defaults,
-# CTA-per-batch steps, one grid-wide batch per step
-STEP_VARIANTS = [(0, 0, 0), (64, 8, 1), (0, 0, 2), (128, 1, 1)]
+# (eval_per_step, step_lanes, step_mode, active_target) of the lazy rounds:
+# defaults (persistent device kernel), host-driven CTA-per-batch steps,
+# host-driven grid-wide steps, and the persistent kernel with a tiny active
+# list so that it must stop and have the list rebuilt many times
+STEP_VARIANTS = [(0, 0, 0, 0), (64, 8, 1, 0), (0, 0, 2, 0), (128, 1, 1, 0), (0, 0, 3, 64), (0, 0, 3, 1)]
+# (the neighbour bound is on in all of them; test_greedy_bound_off turns it off)
 
 
 @pytest.fixture(scope="module")
@@ -84,11 +87,23 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
     k = min(12, n)
     grp, ft, _ = oracle.greedy_plain(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for eps, lanes, mode in STEP_VARIANTS:
-            got, f, st = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode)
+        for eps, lanes, mode, act in STEP_VARIANTS:
+            got, f, st = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode, active_target=act)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
             assert st["rounds"] == k
+
+
+@pytest.mark.parametrize("name,g", small_cases())
+def test_greedy_bound_off(gcm, name, g):
+    rp, ci = g
+    n = rp.size - 1
+    k = min(12, n)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, k)
+    with gcm.Graph(rp, ci) as G:
+        got, f, st = G.greedy(k, expand_bound=False, round1_heavy=-1)
+        np.testing.assert_array_equal(got, grp)
+        assert f == ft[-1]
 
 
 def test_greedy_ba2000_k10(gcm):
@@ -106,8 +121,9 @@ def test_greedy_rmat_vs_greedypp(gcm, scale, k):
     rp, ci = graphgen.rmat(scale, 16.0, seed=5)
     grp, ft, _, _ = oracle.greedypp(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for eps, lanes, mode in STEP_VARIANTS + [(1024, 64, 1)]:
-            got, f, _ = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode)
+        for eps, lanes, mode, act in STEP_VARIANTS + [(1024, 64, 1, 0)]:
+            got, f, _ = G.greedy(k, eval_per_step=eps, step_lanes=lanes, step_mode=mode, active_target=act,
+                                 round1_heavy=-1 if mode == 1 else 0)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
 
@@ -122,8 +138,8 @@ def test_greedy_rmat20_k100_full_size(gcm):
         got, f, st = G.greedy(100)
         np.testing.assert_array_equal(got, grp)
         assert f == ft[-1]
-        for mode in (1, 2):
-            g2, f2, _ = G.greedy(100, step_mode=mode)
+        for mode, heavy, bound in ((1, -1, False), (2, 64, True), (3, 4096, True), (3, 0, False)):
+            g2, f2, _ = G.greedy(100, step_mode=mode, round1_heavy=heavy, expand_bound=bound)
             np.testing.assert_array_equal(g2, grp)
             assert f2 == ft[-1]
         # farness of the prefixes by the library's own BFS, against the trace
