@@ -70,9 +70,9 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
 typedef struct gc_opts {
   int32_t eval_per_step;   /* candidates evaluated exactly per lazy step
                               (rounded up to a multiple of 64); 0 = autotuned */
-  int32_t use_proposal;    /* 1: order exact evaluations by the learned proposal
-                              network (see gc_set_proposal); the accepted vertex
-                              and therefore the group are unchanged */
+  int32_t use_proposal;    /* 1: let the learned proposal network set by
+                              gc_set_proposal choose part of every batch; the
+                              accepted vertex and the group are unchanged */
   int32_t max_ctas;        /* cap on resident CTAs of the gain kernel; 0 = all */
   int32_t timeout_ms;      /* limit of every device-side wait; 0 = 10000 */
   int32_t step_lanes;      /* candidates per 64-lane batch in rounds >= 2 (1..64);
@@ -215,6 +215,69 @@ int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const int32_t *c
  * Errors   : GC_EINVAL, GC_EDISCONNECTED, GC_ETIMEOUT, GC_ENOMEM, GC_ECUDA. */
 int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group,
               int64_t *out_farness, gc_stats *stats);
+
+/* ------------------------------------------------- learned proposal ---- */
+/* A small network that only ORDERS exact evaluations (not part of the paper;
+ * the acceptance rule of Sec. 4.2 is unchanged, so the group is identical with
+ * or without it).  Network: 8 float features -> 64 -> 64 (ReLU) -> 1, float32,
+ * GC_MLP_PARAMS parameters in the order W1[8][64], b1[64], W2[64][64], b2[64],
+ * W3[64], b3.  Features of candidate v in round r: log1p(deg v), d_S[v],
+ * log1p(stale bound), r - (round of its last evaluation), log1p(sum over
+ * neighbours of (deg - 1)), max d_S over neighbours - d_S[v], log1p(gain of
+ * the previous pick), and feature 2 - feature 6.  Trained (mean squared error
+ * on log1p of exact gains, Adam) by the library's own kernels. */
+#define GC_MLP_IN 8
+#define GC_MLP_HIDDEN 64
+#define GC_MLP_PARAMS 4801
+
+typedef struct gc_mlp gc_mlp; /* opaque: parameters, Adam state, activation scratch */
+
+/* gc_mlp_create -- a network with zero parameters; max_batch bounds the
+ * minibatch of gc_mlp_grad / gc_mlp_adam_step / gc_mlp_train.  stream as in
+ * gc_load_csr.  Errors: GC_EINVAL, GC_ENOMEM. */
+int gc_mlp_create(int32_t max_batch, void *stream, gc_mlp **out);
+/* gc_mlp_free -- release (NULL accepted). */
+int gc_mlp_free(gc_mlp *mlp);
+/* gc_mlp_set_params / gc_mlp_get_params -- host float[GC_MLP_PARAMS]; setting
+ * resets the Adam state.  Synchronous. */
+int gc_mlp_set_params(gc_mlp *mlp, const float *params);
+int gc_mlp_get_params(gc_mlp *mlp, float *params);
+/* gc_mlp_forward -- out[i] = network(X[i]) for device float X[m][8], out[m];
+ * asynchronous on the network's stream. */
+int gc_mlp_forward(gc_mlp *mlp, const float *X, int32_t m, float *out);
+/* gc_mlp_grad -- gradient of L = (1/m) sum (out_i - y_i)^2 with respect to the
+ * parameters, for device X[m][8], y[m], 1 <= m <= max_batch; grad is a host
+ * float[GC_MLP_PARAMS] (may be NULL), loss a host double (may be NULL).
+ * Synchronous. */
+int gc_mlp_grad(gc_mlp *mlp, const float *X, const float *y, int32_t m, float *grad, double *loss);
+/* gc_mlp_adam_step -- one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * minibatch X[m][8], y[m] (device); asynchronous. */
+int gc_mlp_adam_step(gc_mlp *mlp, const float *X, const float *y, int32_t m, float lr);
+/* gc_mlp_train -- `epochs` passes over device X[m][8], y[m] in minibatches of
+ * `batch` (<= max_batch) taken in a seeded random order; final_loss (host, may be
+ * NULL) gets the mean squared error over the whole set afterwards. */
+int gc_mlp_train(gc_mlp *mlp, const float *X, const float *y, int32_t m, int32_t epochs, int32_t batch,
+                 float lr, uint64_t seed, double *final_loss);
+/* gc_candidate_features -- the network's input rows X[m][8] (device float) for
+ * candidates cand[m] given the per-vertex device arrays row_ptr[n+1], d_S[n],
+ * bound ub[n], evaluation round stamp[n], two_hop[n] (sum over neighbours of
+ * deg - 1) and mx[n] (max d_S over neighbours; NULL = d_S itself), the round
+ * and the previous pick's gain.  Asynchronous on `stream`. */
+int gc_candidate_features(const int32_t *row_ptr, const int32_t *dS, const int64_t *ub, const int32_t *stamp,
+                          const int64_t *two_hop, const int32_t *mx, const int32_t *cand, int32_t m, int32_t round,
+                          int64_t prev_gain, float *X, void *stream);
+/* gc_set_proposal -- let gc_greedy (opts.use_proposal = 1, persistent rounds)
+ * give `fill` of every 64-candidate batch (0 = 16) to the unevaluated
+ * candidates whose stale bound most exceeds the network's predicted gain, the
+ * rest to the largest bounds.  The network must outlive its use; NULL
+ * disables.  Errors: GC_EINVAL (fill outside [0, 63]). */
+int gc_set_proposal(gc_graph *g, const gc_mlp *mlp, int32_t fill);
+/* gc_set_recorder -- while set (cap > 0), gc_greedy's host-driven lazy steps
+ * (opts.step_mode 1 or 2) append, for every candidate evaluated in rounds >= 2,
+ * its features at selection time to X[cap][8] and log1p(exact gain) to y[cap]
+ * (device arrays owned by the caller); gc_recorded returns the row count. */
+int gc_set_recorder(gc_graph *g, float *X, float *y, int32_t cap);
+int64_t gc_recorded(gc_graph *g);
 
 /* gc_last_error -- thread-local description of the last failure ("" if none). */
 const char *gc_last_error(void);

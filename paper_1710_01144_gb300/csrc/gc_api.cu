@@ -59,7 +59,8 @@ static void release(gc_graph *g) {
   }
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
-                 g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf};
+                 g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
+                 g->two_hop, g->score, g->rec_count};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -233,7 +234,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->gctl, 1)) || (rc = dalloc(&g->sctl, 1)) || (rc = dalloc(&g->ggctl, 1)) ||
       (rc = dalloc(&g->goff, N + 1)) || (rc = dalloc(&g->lctl, 1)) || (rc = dalloc(&g->picks, N)) ||
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
-      (rc = dalloc(&g->mx_buf, N)))
+      (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
+      (rc = dalloc(&g->rec_count, 1)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_gctl, sizeof(GainCtl)) != cudaSuccess ||
@@ -360,7 +362,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   gc_opts opts;
   if (opts_in) opts = *opts_in;
   else gc_opts_default(&opts);
-  if (opts.use_proposal) return fail(GC_EINVAL, "no proposal network is loaded");
+  if (opts.use_proposal && !g->prop_params) return fail(GC_EINVAL, "no proposal network is set (gc_set_proposal)");
   const int64_t tns = timeout_ns(&opts);
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
@@ -450,6 +452,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   int64_t lazy_steps = 0, lazy_evals = 0, lazy_launches = 0;
   double lazy_ms[3] = {0, 0, 0};
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
+  gains_picked[0] = f;
   for (int32_t r = 1; r < k; ++r) {
     if (r >= 2 && persistent) {
       // rounds r..k-1 on the device: persistent kernel over an active list
@@ -458,12 +461,14 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       init.round = r;
       init.best_id = -1;
       init.best_gain = -1;
+      init.last_gain = gains_picked[r - 1];
+      init.scored_round = -1;
       *g->h_lctl = init;
       GC_CUDA(cudaMemcpyAsync(g->lctl, g->h_lctl, sizeof(LazyCtl), cudaMemcpyHostToDevice, g->stream));
       int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
-        GC_TRY(launch_lazy_rounds(g, k, tns));
+        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
         GC_TRY(read_ctl(g));
@@ -521,9 +526,11 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         GC_TRY(launch_select(g, kSelLazy, r, kLanes, kTauHistogram, 0));
         GC_TRY(launch_clamp_nsel(g, kLanes));
         GC_TRY(grid_timed(kModeGain, g->list, 0, &g->sctl->n_sel, g->lgain));
+        GC_TRY(launch_record(g, r, gains_picked[r - 1]));
       } else {
         GC_TRY(launch_select(g, kSelLazy, r, step_want, kTauHistogram, 0));
         GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel, step_lanes));
+        GC_TRY(launch_record(g, r, gains_picked[r - 1]));
       }
       GC_TRY(launch_after_eval(g, r, 0));
       GC_TRY(launch_unevaluated_best(g, r));

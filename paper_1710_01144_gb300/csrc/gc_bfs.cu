@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_dist(const int32_t *__restr
 // is at least 3 away.  key[v] = -(deg + 2 c2 + 3 (n - 1 - deg - c2)).
 __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__restrict__ rp,
                                                              const int32_t *__restrict__ ci,
-                                                             int32_t n, long long *key) {
+                                                             int32_t n, long long *key, long long *two_hop) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__re
       if (rest < 0) rest = 0;
       const long long c2 = x < rest ? x : rest;
       key[v] = -(deg + 2 * c2 + 3 * (rest - c2));
+      if (two_hop) two_hop[v] = x;
     }
   }
 }
@@ -217,7 +218,7 @@ int launch_sum_dist(gc_graph *g, const int32_t *dist) {
 int launch_round0_keys(gc_graph *g) {
   ++g->launches;
   k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
-                  g->stream>>>(g->rp, g->ci, g->n, g->key);
+                  g->stream>>>(g->rp, g->ci, g->n, g->key, g->two_hop);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

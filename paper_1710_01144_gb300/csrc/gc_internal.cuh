@@ -85,6 +85,9 @@ struct LazyCtl {
   unsigned long long decrease;
   long long steps, evals;
   unsigned long long ns_select, ns_gain, ns_update;  // time in each phase (CTA 0's clock)
+  long long last_gain;  // gain of the previous pick (proposal feature)
+  int32_t scored_round;  // round whose proposal scores are in g->score
+  int32_t pad2;
   int32_t sel[kLanes];
   long long gsel[kLanes];
 };
@@ -129,6 +132,14 @@ struct gc_graph {
   int32_t *dS = nullptr;  // distance to the current group
   int32_t *mx = nullptr;  // mx[u] >= max over neighbours w of d_S[w] (or nullptr: no pruning)
   int32_t *mx_buf = nullptr;
+  long long *two_hop = nullptr;            // sum over neighbours of (deg - 1), feature input
+  float *score = nullptr;                  // proposal scores of the active list [n]
+  // learned proposal (caller-owned weights) and training-data recorder
+  const float *prop_params = nullptr;
+  int32_t prop_fill = 0;
+  float *rec_X = nullptr, *rec_y = nullptr;
+  int32_t rec_cap = 0;
+  int32_t *rec_count = nullptr;            // device counter
   long long *ub = nullptr;     // lazy bound / exact gain of the round in stamp
   int32_t *stamp = nullptr;    // round of the last exact evaluation (0 = never)
   long long *key = nullptr;    // round-0 selection key (-lower bound), INT64_MIN = done
@@ -227,10 +238,13 @@ int launch_round_begin(gc_graph *g);
 int launch_round_end(gc_graph *g);
 int launch_clamp_nsel(gc_graph *g, int32_t cap);
 int launch_degree_keys(gc_graph *g);
+// features of list entries + log1p(gain) targets appended to the recorder
+int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 // mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
 int launch_max_nbr(gc_graph *g);
 int launch_active_theta(gc_graph *g);
-int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns);
+// prop: proposal weights (nullptr = plain bound order); fill: lanes it chooses
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill);
 int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 

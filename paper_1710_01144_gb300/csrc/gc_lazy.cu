@@ -22,6 +22,7 @@
 #include <limits.h>
 
 #include "gc_grid.cuh"
+#include "gc_mlp.cuh"
 
 namespace gc {
 
@@ -77,18 +78,110 @@ __device__ __forceinline__ void block_argmax_all(long long &v, int &id, long lon
   __syncthreads();
 }
 
-// CTA 0's part of a step (see the file comment).  Writes lc->dec (0 evaluate
-// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).
-__device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
-                               LazyCtl *lc, GridGainCtl *gg, bool fold) {
-  __shared__ unsigned int s_hist[kLazyBins];
+// Exact top-`need` of the list entries by key (larger first; ties by list
+// order, i.e. smaller id), written to sel[base..).  key(i, v) returns LLONG_MIN
+// for entries that are not eligible; kmin/kmax/cnt describe the eligible keys.
+// Histogram passes over [kmin, kmax] fix the threshold value; every key above it
+// is taken, then keys equal to it in list order.  Returns the number taken.
+template <class KeyFn>
+__device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
+                        long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist) {
   __shared__ int s_scan[33];
-  __shared__ long long s_v[32];
-  __shared__ int s_id[32];
-  __shared__ long long s_ll[32];
   __shared__ int s_b;
   __shared__ long long s_ab;
   const int tid = threadIdx.x, T = blockDim.x;
+  if (need <= 0 || cnt <= 0) return 0;
+  if (need > cnt) need = (int)cnt;
+  long long tau = kmin, above = 0;  // above = eligible keys > tau
+  if (cnt > need) {
+    unsigned long long lo = (unsigned long long)kmin, hi = (unsigned long long)kmax;
+    long long want = need, acc = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+      const unsigned long long span = hi - lo + 1ull;
+      const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
+      for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < m; i += T) {
+        const long long k = key(i, act[i]);
+        if (k == LLONG_MIN) continue;
+        const unsigned long long uu = (unsigned long long)k;
+        if (uu - lo > hi - lo) continue;  // outside [lo, hi] (unsigned wrap)
+        atomicAdd(&s_hist[(uu - lo) / width], 1u);
+      }
+      __syncthreads();
+      // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
+      const int b0 = kLazyBins - 1 - 2 * tid, b1 = b0 - 1;
+      const int h0 = tid < kLazyBins / 2 ? (int)s_hist[b0] : 0;
+      const int h1 = tid < kLazyBins / 2 ? (int)s_hist[b1] : 0;
+      if (tid == 0) {
+        s_b = 0;
+        s_ab = 0;
+      }
+      int total;
+      const long long a0 = block_excl_scan(h0 + h1, s_scan, &total);
+      if (tid < kLazyBins / 2) {
+        if (a0 < want && a0 + h0 >= want) {
+          s_b = b0;
+          s_ab = a0;
+        } else if (a0 + h0 < want && a0 + h0 + h1 >= want) {
+          s_b = b1;
+          s_ab = a0 + h0;
+        }
+      }
+      __syncthreads();
+      const int bb = s_b;
+      const long long ab = s_ab;
+      const unsigned long long bin_lo = lo + width * (unsigned long long)bb;
+      if (width == 1ull) {
+        tau = (long long)bin_lo;
+        above = acc + ab;
+        break;
+      }
+      acc += ab;
+      want -= ab;
+      const unsigned long long room = hi - bin_lo;
+      lo = bin_lo;
+      hi = bin_lo + (width - 1ull < room ? width - 1ull : room);
+      __syncthreads();
+    }
+  }
+  int taken = 0, eq_seen = 0;
+  for (int b = 0; b < m && taken < need; b += T) {
+    const int i = b + tid;
+    int gt = 0, eq = 0, v = -1;
+    if (i < m) {
+      v = act[i];
+      const long long k = key(i, v);
+      if (k != LLONG_MIN) {
+        gt = k > tau;
+        eq = k == tau;
+      }
+    }
+    int tot_eq, tot_take;
+    const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
+    const int take = gt || (eq && eq_rank < need - above);
+    const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
+    if (take && base + pos < kLanes) sel[base + pos] = v;
+    eq_seen += tot_eq;
+    taken += tot_take;
+  }
+  __syncthreads();
+  return taken < need ? taken : need;
+}
+
+// CTA 0's part of a step (see the file comment).  Writes lc->dec (0 evaluate
+// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).  With a
+// proposal network (score != nullptr), `fill` of the 64 lanes go to the
+// unevaluated candidates whose bound most exceeds the network's predicted
+// gain: evaluating them tightens the bounds later rounds must beat.
+__device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+                               LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill) {
+  __shared__ long long s_v[32];
+  __shared__ int s_id[32];
+  __shared__ long long s_ll[32];
+  __shared__ unsigned int s_hist[kLazyBins];
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
   const int r = lc->round;
 
   if (fold) {  // the batch just evaluated: exact gains become the bounds
@@ -143,83 +236,36 @@ __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long 
     if (tid == 0) lc->dec = dec;
     return;
   }
-
-  // exact threshold value tau: fewer than `need` keys above it, at least `need` at or above
-  const long long need = cnt < kLanes ? cnt : kLanes;
-  long long tau = umin, above = 0;  // above = unevaluated keys > tau
-  if (cnt > kLanes) {
-    unsigned long long lo = (unsigned long long)umin, hi = (unsigned long long)umax;
-    long long want = kLanes, acc = 0;
-    for (int pass = 0; pass < 8; ++pass) {
-      const unsigned long long span = hi - lo + 1ull;
-      const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
-      for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
-      __syncthreads();
-      for (int i = tid; i < m; i += T) {
-        const int v = act[i];
-        const long long u = ub[v];
-        if (u < 0 || stamp[v] == r) continue;
-        const unsigned long long uu = (unsigned long long)u;
-        if (uu < lo || uu > hi) continue;
-        atomicAdd(&s_hist[(uu - lo) / width], 1u);
-      }
-      __syncthreads();
-      // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
-      const int b0 = kLazyBins - 1 - 2 * tid, b1 = b0 - 1;
-      const int h0 = tid < kLazyBins / 2 ? (int)s_hist[b0] : 0;
-      const int h1 = tid < kLazyBins / 2 ? (int)s_hist[b1] : 0;
-      if (tid == 0) {
-        s_b = 0;
-        s_ab = 0;
-      }
-      int total;
-      const long long a0 = block_excl_scan(h0 + h1, s_scan, &total);
-      if (tid < kLazyBins / 2) {
-        if (a0 < want && a0 + h0 >= want) {
-          s_b = b0;
-          s_ab = a0;
-        } else if (a0 + h0 < want && a0 + h0 + h1 >= want) {
-          s_b = b1;
-          s_ab = a0 + h0;
-        }
-      }
-      __syncthreads();
-      const int b = s_b;
-      const long long ab = s_ab;
-      const unsigned long long bin_lo = lo + width * (unsigned long long)b;
-      if (width == 1ull) {
-        tau = (long long)bin_lo;
-        above = acc + ab;
-        break;
-      }
-      acc += ab;
-      want -= ab;
-      const unsigned long long room = hi - bin_lo;
-      lo = bin_lo;
-      hi = bin_lo + (width - 1ull < room ? width - 1ull : room);
-      __syncthreads();
-    }
-  }
-  // select in list (id) order: every key > tau, then keys == tau by smallest id
-  int taken = 0, eq_seen = 0;
-  for (int base = 0; base < m && taken < need; base += T) {
-    const int i = base + tid;
-    int gt = 0, eq = 0, v = -1;
-    if (i < m) {
-      v = act[i];
+  // the largest bounds (all 64 lanes without a proposal)
+  const int need1 = score ? kLanes - fill : kLanes;
+  auto by_bound = [=] __device__(int, int v) -> long long {
+    const long long u = ub[v];
+    return (u >= 0 && stamp[v] != r) ? u : LLONG_MIN;
+  };
+  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist);
+  if (score && taken < kLanes && cnt > taken) {
+    // mark the bound picks as evaluated in this round (their fold does it again)
+    if (tid < taken) stamp[lc->sel[tid]] = r;
+    __syncthreads();
+    auto by_slack = [=] __device__(int i, int v) -> long long {
       const long long u = ub[v];
-      if (u >= 0 && stamp[v] != r) {
-        gt = u > tau;
-        eq = u == tau;
-      }
+      if (u < 0 || stamp[v] == r) return LLONG_MIN;
+      float p = expm1f(score[i]);
+      p = p < 0.f ? 0.f : (p > (float)u ? (float)u : p);
+      return u - (long long)p;
+    };
+    long long smin = LLONG_MAX, smax = LLONG_MIN, scnt = 0;
+    for (int i = tid; i < m; i += T) {
+      const long long k = by_slack(i, act[i]);
+      if (k == LLONG_MIN) continue;
+      smin = min(smin, k);
+      smax = max(smax, k);
+      ++scnt;
     }
-    int tot_eq, tot_take;
-    const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
-    const int take = gt || (eq && eq_rank < need - above);
-    const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
-    if (take && pos < kLanes) lc->sel[pos] = v;
-    eq_seen += tot_eq;
-    taken += tot_take;
+    smin = block_min_ll(smin, s_ll);
+    smax = -block_min_ll(-smax, s_ll);
+    scnt = block_sum(scnt, s_ll);
+    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist);
   }
   // a fresh grid-batch control block for the evaluation
   if (tid < kLanes) {
@@ -236,12 +282,35 @@ __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long 
   }
 }
 
+// Proposal scores of the active list for this round (every CTA, one warp per
+// candidate): score[i] = network output on the candidate's features.
+__device__ void lazy_score(const int32_t *__restrict__ act, int32_t m, const float *__restrict__ prop,
+                           const int32_t *__restrict__ rp, const int32_t *__restrict__ dS,
+                           const long long *__restrict__ ub, const int32_t *__restrict__ stamp,
+                           const long long *__restrict__ two_hop, const int32_t *__restrict__ mx, int32_t round,
+                           long long prev_gain, float *score) {
+  __shared__ float sw[kMlpParams];
+  __shared__ float sh[kGridGainThreads / 32][kMlpHidden];
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = prop[i];
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid, nw = gridDim.x * (blockDim.x >> 5);
+  for (int i = gw; i < m; i += nw) {
+    float f[kMlpIn];
+    cand_features(act[i], rp, dS, ub, stamp, two_hop, mx, round, prev_gain, f);
+    const float o = mlp_forward_warp(sw, f, sh[wid]);
+    if (lane == 0) score[i] = o;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kGridGainThreads, 2)
     k_lazy_rounds(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dS,
                   long long *ub, int32_t *stamp, const int32_t *__restrict__ act, const int32_t *m_dev,
                   int32_t k, int32_t *picks, long long *pgain, long long *pdec, unsigned char *ws,
                   int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
-                  unsigned long long tns, const int32_t *__restrict__ mx) {
+                  unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
+                  int32_t fill, const long long *__restrict__ two_hop, float *score) {
   const int m = *m_dev;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t0 = timer ? global_ns() : 0, t1;
@@ -249,7 +318,12 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
   for (;;) {
     const int r = *(volatile int32_t *)&lc->round;
     if (r >= k) break;
-    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold);
+    if (prop && *(volatile int32_t *)&lc->scored_round != r) {
+      lazy_score(act, m, prop, rp, dS, ub, stamp, two_hop, mx, r, lc->last_gain, score);
+      if (!grid_sync(&lc->bar, &lc->err, tns)) break;
+      if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
+    }
+    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold, prop ? score : nullptr, fill);
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();
@@ -286,6 +360,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
     if (!ok) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       pdec[r] = (long long)lc->decrease;
+      lc->last_gain = lc->best_gain;
       ub[lc->best_id] = -1;  // a member: never a candidate again
       lc->best_id = -1;
       lc->best_gain = -1;
@@ -323,7 +398,7 @@ int launch_active_theta(gc_graph *g) {
   return GC_OK;
 }
 
-int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns) {
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill) {
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
   int32_t *dS = g->dS;
@@ -341,11 +416,13 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns) {
   int32_t *q0 = g->bq0, *q1 = g->bq1;
   unsigned long long tns = (unsigned long long)timeout_ns;
   const int32_t *mx = g->mx;
+  const long long *two_hop = g->two_hop;
+  float *score = g->score;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
-                  (void *)&mx};
+                  (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(g->lazy_ctas), dim3(kGridGainThreads),
                                       args, 0, g->stream));

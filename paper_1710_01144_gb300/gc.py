@@ -32,7 +32,10 @@ GC_OPT_NO_EXPAND_BOUND = 0x1
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
            "gc_group_farness", "gc_marginal_gains", "gc_marginal_gains_device", "gc_greedy",
-           "gc_last_error", "gc_marginal_gains_static")
+           "gc_last_error", "gc_marginal_gains_static", "gc_mlp_create", "gc_mlp_free", "gc_mlp_set_params",
+           "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
+           "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded")
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
 class GcError(RuntimeError):
@@ -87,9 +90,23 @@ def load(path: str = LIB_PATH):
         lib.gc_marginal_gains_device.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.gc_greedy.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_marginal_gains_static.argtypes = [i32, vp, vp, vp, i32, vp, i32, vp, vp]
+        lib.gc_mlp_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+        lib.gc_mlp_free.argtypes = [vp]
+        lib.gc_mlp_set_params.argtypes = [vp, vp]
+        lib.gc_mlp_get_params.argtypes = [vp, vp]
+        lib.gc_mlp_forward.argtypes = [vp, vp, i32, vp]
+        lib.gc_mlp_grad.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.gc_mlp_adam_step.argtypes = [vp, vp, vp, i32, ctypes.c_float]
+        lib.gc_mlp_train.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_double)]
+        lib.gc_candidate_features.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, i64, vp, vp]
+        lib.gc_set_proposal.argtypes = [vp, vp, i32]
+        lib.gc_set_recorder.argtypes = [vp, vp, vp, i32]
+        lib.gc_recorded.argtypes = [vp]
+        lib.gc_recorded.restype = i64
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error"):
+            if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -176,6 +193,24 @@ class Graph:
         _check(load().gc_marginal_gains_device(self._h, S_dev.data_ptr(), S_dev.numel(), cand_dev.data_ptr(),
                                                cand_dev.numel(), out_dev.data_ptr()))
 
+    def set_proposal(self, mlp, fill: int = 0):
+        """Use `mlp` (an Mlp, or None to disable) for part of every batch."""
+        self._prop = mlp
+        _check(load().gc_set_proposal(self._h, mlp._h if mlp is not None else None, fill))
+
+    def set_recorder(self, X_dev, y_dev):
+        """Record (features, log1p gain) of host-driven lazy steps into CUDA tensors
+        X_dev [cap, 8] and y_dev [cap] (float32); None disables."""
+        if X_dev is None:
+            _check(load().gc_set_recorder(self._h, None, None, 0))
+            self._rec = None
+            return
+        self._rec = (X_dev, y_dev)
+        _check(load().gc_set_recorder(self._h, X_dev.data_ptr(), y_dev.data_ptr(), int(y_dev.numel())))
+
+    def recorded(self) -> int:
+        return int(load().gc_recorded(self._h))
+
     def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True):
@@ -202,3 +237,63 @@ def gains_static(row_ptr_dev, col_idx_dev, S_dev, cand_dev, out_dev, stream=None
     _check(load().gc_marginal_gains_static(row_ptr_dev.numel() - 1, row_ptr_dev.data_ptr(), col_idx_dev.data_ptr(),
                                            S_dev.data_ptr(), S_dev.numel(), cand_dev.data_ptr(), cand_dev.numel(),
                                            out_dev.data_ptr(), st))
+
+
+class Mlp:
+    """The proposal network (8 -> 64 -> 64 -> 1, float32) on the current device."""
+
+    def __init__(self, max_batch: int = 4096, stream=None):
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(load().gc_mlp_create(max_batch, self.stream, ctypes.byref(h)))
+        self._h = h
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gc_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == MLP_PARAMS
+        _check(load().gc_mlp_set_params(self._h, p.ctypes.data))
+
+    def get_params(self):
+        p = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(load().gc_mlp_get_params(self._h, p.ctypes.data))
+        return p
+
+    def forward(self, X_dev, out_dev):
+        _check(load().gc_mlp_forward(self._h, X_dev.data_ptr(), int(X_dev.shape[0]), out_dev.data_ptr()))
+
+    def grad(self, X_dev, y_dev):
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load().gc_mlp_grad(self._h, X_dev.data_ptr(), y_dev.data_ptr(), int(X_dev.shape[0]), g.ctypes.data,
+                                  ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, X_dev, y_dev, lr: float):
+        _check(load().gc_mlp_adam_step(self._h, X_dev.data_ptr(), y_dev.data_ptr(), int(X_dev.shape[0]), lr))
+
+    def train(self, X_dev, y_dev, epochs: int = 20, batch: int = 1024, lr: float = 1e-3, seed: int = 1) -> float:
+        loss = ctypes.c_double()
+        _check(load().gc_mlp_train(self._h, X_dev.data_ptr(), y_dev.data_ptr(), int(X_dev.shape[0]), epochs, batch,
+                                   lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+
+def candidate_features(row_ptr, dS, ub, stamp, two_hop, mx, cand, rnd, prev_gain, X_out, stream=None):
+    """gc_candidate_features on CUDA tensors (asynchronous)."""
+    st = _current_stream() if stream is None else int(stream)
+    _check(load().gc_candidate_features(row_ptr.data_ptr(), dS.data_ptr(), ub.data_ptr(), stamp.data_ptr(),
+                                        two_hop.data_ptr(), mx.data_ptr() if mx is not None else None,
+                                        cand.data_ptr(), int(cand.numel()), int(rnd), int(prev_gain),
+                                        X_out.data_ptr(), st))

@@ -1,0 +1,126 @@
+"""GPU kernels of the proposal network against the float64 reference, and the
+proposal's effect on Greedy++ (the group must not change)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as mref
+from paper_1710_01144_gb300 import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1710_01144_gb300 import build, gc
+
+    build.build()
+    return torch, gc
+
+
+def test_forward_grad_adam_match_reference(env):
+    torch, gc = env
+    rng = np.random.default_rng(11)
+    p = mref.init_params(2)
+    net = gc.Mlp(max_batch=512)
+    net.set_params(p.astype(np.float32))
+    p32 = net.get_params().astype(np.float64)  # the float32-rounded parameters
+    for m in (1, 37, 512):
+        X = rng.normal(size=(m, 8)).astype(np.float32)
+        y = rng.normal(size=m).astype(np.float32)
+        Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+        out = torch.empty(m, dtype=torch.float32, device="cuda")
+        net.forward(Xd, out)
+        torch.cuda.synchronize()
+        ref = mref.forward(p32, X.astype(np.float64))
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+        g, loss = net.grad(Xd, yd)
+        gref = mref.grad(p32, X.astype(np.float64), y.astype(np.float64))
+        assert abs(loss - mref.loss(p32, X, y)) <= 1e-4 * max(1.0, abs(loss))
+        # float32 accumulation: relative error of the whole gradient vector
+        assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    # one Adam step against the reference
+    X = rng.normal(size=(256, 8)).astype(np.float32)
+    y = rng.normal(size=256).astype(np.float32)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    net.set_params(p32.astype(np.float32))
+    gref = mref.grad(p32, X.astype(np.float64), y.astype(np.float64))
+    pref, _, _ = mref.adam_step(p32, gref, np.zeros_like(p32), np.zeros_like(p32), 1, lr=1e-3)
+    net.adam_step(Xd, yd, 1e-3)
+    got = net.get_params().astype(np.float64)
+    # where |g| is not tiny the step is -lr*sign(g); compare the step itself
+    big = np.abs(gref) > 1e-5
+    np.testing.assert_allclose((got - p32)[big], (pref - p32)[big], rtol=1e-3, atol=1e-7)
+    net.close()
+
+
+def test_features_match_reference(env):
+    torch, gc = env
+    rng = np.random.default_rng(5)
+    rp, ci = graphgen.rmat(10, 8.0, seed=2)
+    n = rp.size - 1
+    deg = np.diff(rp)
+    dS = rng.integers(0, 6, size=n).astype(np.int32)
+    ub = rng.integers(-1, 10**6, size=n).astype(np.int64)
+    stamp = rng.integers(0, 9, size=n).astype(np.int32)
+    two_hop = rng.integers(0, 10**5, size=n).astype(np.int64)
+    mx = (dS + rng.integers(0, 3, size=n)).astype(np.int32)
+    cand = rng.integers(0, n, size=300).astype(np.int32)
+    d = lambda a: torch.from_numpy(a).cuda()
+    X = torch.empty((cand.size, 8), dtype=torch.float32, device="cuda")
+    gc.candidate_features(d(rp), d(dS), d(ub), d(stamp), d(two_hop), d(mx), d(cand), 9, 1234, X)
+    torch.cuda.synchronize()
+    ref = mref.features(deg[cand], dS[cand], ub[cand], stamp[cand], two_hop[cand], mx[cand], 9, 1234)
+    np.testing.assert_allclose(X.cpu().numpy(), ref, rtol=1e-6, atol=1e-5)
+
+
+def _record_and_train(torch, gc, graphs, k, epochs=30):
+    Xs, ys = [], []
+    for rp, ci in graphs:
+        cap = 200_000
+        X = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+        y = torch.zeros(cap, dtype=torch.float32, device="cuda")
+        with gc.Graph(rp, ci) as G:
+            G.set_recorder(X, y)
+            G.greedy(k, step_mode=1, eval_per_step=64, step_lanes=8)
+            m = G.recorded()
+            G.set_recorder(None, None)
+        Xs.append(X[:m].clone())
+        ys.append(y[:m].clone())
+    X = torch.cat(Xs)
+    y = torch.cat(ys)
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    X, y = X[perm].contiguous(), y[perm].contiguous()
+    net = gc.Mlp(max_batch=1024)
+    net.set_params(mref.init_params(0).astype(np.float32))
+    _, loss0 = net.grad(X[:1024], y[:1024])
+    loss = net.train(X, y, epochs=epochs, batch=1024, lr=2e-3, seed=3)
+    return net, X.shape[0], loss0, loss
+
+
+def test_trained_proposal_keeps_group_and_reports_gain(env, capsys):
+    """Trained on exact gains of R-MAT graphs (other seeds), the proposal
+    chooses part of every batch; the group must equal the oracle's, and the
+    evaluation counts with and without it are reported."""
+    torch, gc = env
+    train = [graphgen.rmat(13, 16.0, seed=s) for s in (2, 3)]
+    net, m, loss0, loss = _record_and_train(torch, gc, train, 60)
+    assert m > 500
+    assert loss < 0.5 * loss0  # the network learned something about the gains
+    rp, ci = graphgen.rmat(14, 16.0, seed=1)
+    grp, ft, _, _ = oracle.greedypp(rp, ci, 60)
+    with gc.Graph(rp, ci) as G:
+        g0, f0, s0 = G.greedy(60)
+        G.set_proposal(net, 16)
+        g1, f1, s1 = G.greedy(60, use_proposal=True)
+    np.testing.assert_array_equal(g0, grp)
+    np.testing.assert_array_equal(g1, grp)
+    assert f0 == f1 == ft[-1]
+    with capsys.disabled():
+        print("\nproposal: samples %d, loss %.4f -> %.4f; rounds>=2 steps %d -> %d, evals %d -> %d"
+              % (m, loss0, loss, s0["steps"], s1["steps"], s0["evals"], s1["evals"]))
+    net.close()
