@@ -64,6 +64,9 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
 
 /* gc_opts.flags */
 #define GC_OPT_NO_EXPAND_BOUND 0x1u
+#define GC_OPT_CAPTURE 0x2u /* gc_batch_greedy: record the launch sequence in a
+                               CUDA graph once and replay it while ks and the
+                               options stay the same */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
@@ -120,6 +123,7 @@ typedef struct gc_stats {
   double ms_lazy_update;   /* persistent kernel: d_S updates from the picks */
   int64_t gain_launches;   /* gain-kernel launches */
   int64_t kernel_launches; /* all kernel launches of the call */
+  int64_t graph_replay;    /* gc_batch_greedy: 1 if the solve ran from a captured CUDA graph */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */
@@ -278,6 +282,32 @@ int gc_set_proposal(gc_graph *g, const gc_mlp *mlp, int32_t fill);
  * (device arrays owned by the caller); gc_recorded returns the row count. */
 int gc_set_recorder(gc_graph *g, float *X, float *y, int32_t cap);
 int64_t gc_recorded(gc_graph *g);
+
+/* ------------------------------------------------- batched solving ----- */
+/* Many graphs solved together: the batch is held as one block-diagonal union
+ * graph on the device and solved by ONE persistent cooperative kernel (round 0,
+ * round 1 and every lazy round of every graph, no host round trip), optionally
+ * replayed from a captured CUDA graph (opts.flags & GC_OPT_CAPTURE).  Each
+ * graph's group equals gc_greedy's on that graph alone. */
+typedef struct gc_batch gc_batch; /* opaque: union CSR + per-graph state */
+
+/* gc_batch_load -- count graphs given by host CSR arrays row_ptrs[g],
+ * col_idxs[g] with ns[g] vertices (each connected, format as for gc_load_csr).
+ * flags: reserved (0).  Errors: GC_EINVAL, GC_ERANGE (union beyond int32 CSR),
+ * GC_ENOMEM, GC_ECUDA. */
+int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *const *col_idxs, const int32_t *ns,
+                  uint32_t flags, void *stream, gc_batch **out);
+int gc_batch_free(gc_batch *b);
+int64_t gc_batch_vertices(const gc_batch *b);
+/* gc_batch_greedy -- ks[count] group sizes (1 <= ks[g] <= ns[g]).  groups
+ * (host int32[sum ks]) receives each graph's group in pick order, graph after
+ * graph, in the graph's own vertex ids; farness (host int64[count]) each
+ * group's farness.  opts: active_target = per-graph candidate-list capacity
+ * (0 = 1024), step_lanes = candidates per round-1 batch (0 = 64), timeout_ms,
+ * flags (GC_OPT_CAPTURE).  Errors: GC_EINVAL, GC_EDISCONNECTED, GC_ETIMEOUT,
+ * GC_ERANGE (a gain >= 2^31), GC_ENOMEM, GC_ECUDA. */
+int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts, int32_t *groups, int64_t *farness,
+                    gc_stats *stats);
 
 /* gc_last_error -- thread-local description of the last failure ("" if none). */
 const char *gc_last_error(void);

@@ -1,0 +1,944 @@
+// Batched Greedy++ over many graphs in ONE persistent cooperative launch.
+//
+// The batch is stored as one block-diagonal union CSR (global vertex ids;
+// graph g owns ids [off[g], off[g+1])).  Distances never cross components, so
+// the multi-source relabel BFS computes every graph's BFS at once (one seed
+// per graph), and 64-lane gain batches stay inside one graph.  What is per
+// graph -- round-0 cut thresholds, argmin/argmax, the lazy round state and its
+// acceptance test (Sec. 4.2), the group -- lives in per-graph arrays.
+//
+// Phases (bounded grid barriers between them):
+//   P0  lower bounds LB(v) and, per graph, the vertex v_a of smallest bound
+//   P1  BFS from all v_a; per-graph farness f_a
+//   P2  per graph (one CTA): every v with LB(v) <= f_a evaluated by the
+//       64-lane BFS in farness mode with per-graph cuts; s0 = argmin (f, id)
+//   P3  BFS from all s0 (d_S), per-graph farness, neighbour bound mx
+//   P4  round 1: every candidate of every graph, graph-aligned 64-lane batches
+//       from a dynamic task counter; per-graph argmax; picks; BFS from picks
+//   P5  per graph (one CTA): active list of the largest bounds
+//   P6  iterations until every graph has its k picks: per graph one lazy step
+//       (fold, decide, select 64); one grid BFS from all picks accepted in the
+//       iteration; per graph one 64-lane evaluation.
+//   P7  check: one BFS from every graph's whole group; each graph's farness
+//       must equal f(s0) minus the sum of its accepted gains.
+#include <limits.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "gc_cta.cuh"
+#include "gc_lazy.cuh"
+
+namespace gc {
+
+struct BatchCtl {
+  GridBar bar;
+  int32_t err;
+  int32_t remaining;  // graphs that still need lazy rounds
+  int32_t nseeds;     // seeds of the next relabel BFS
+  int32_t task;       // dynamic task counter of P4
+  int32_t qsize[3];
+  int32_t pad;
+  unsigned long long decrease;
+  long long iterations;
+  long long dbg[4];  // first failed check: phase, graph, expected, found
+  int32_t blk_tot[kMaxGridCtas];
+};
+
+static __device__ void check_fail(BatchCtl *c, int phase, int g, long long want, long long got) {
+  if (atomicCAS((unsigned long long *)&c->dbg[0], 0ull, (unsigned long long)phase) == 0ull) {
+    c->dbg[1] = g;
+    c->dbg[2] = want;
+    c->dbg[3] = got;
+  }
+  atomicExch(&c->err, GC_EINTERNAL);
+}
+
+struct BatchArgs {
+  const int32_t *rp, *ci;
+  int32_t N;
+  int32_t count;
+  const int32_t *gid, *off, *ng, *kk, *iota;
+  const int32_t *bstart;  // round-1 task prefix per graph ([count+1])
+  int32_t lanes1;         // candidates per round-1 batch
+  int32_t max_n;          // vertices of the largest graph (workspace layout)
+  int32_t *dS, *mx, *stamp, *q0, *q1, *goff;
+  long long *ub, *key, *f0;
+  unsigned char *ws;
+  size_t ws_stride;
+  unsigned long long *packed;
+  long long *fa, *farness, *bestf;
+  LazyCtl *lc;
+  int32_t *act, *act_n, *full;
+  int32_t A;
+  int32_t kmax;
+  int32_t *picks;
+  long long *pgain;
+  int32_t *seeds;  // [max(count, sum k)]
+  BatchCtl *ctl;
+  GainCtl *gctl;
+  unsigned long long tns;
+};
+
+constexpr int kBatchThreads = kGainThreads;
+
+static __device__ __forceinline__ bool bsync(const BatchArgs &a) { return grid_sync(&a.ctl->bar, &a.ctl->err, a.tns); }
+
+// per-graph sum of d over all vertices (warp-aggregated when a warp's vertices
+// share a graph); unreached vertices raise GC_EDISCONNECTED
+static __device__ void seg_sum_dist(const BatchArgs &a, long long *out) {
+  const int lane = threadIdx.x & 31;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < a.N; base += gridDim.x * blockDim.x) {
+    const int v = base + lane;
+    long long d = 0;
+    int g = -1;
+    if (v < a.N) {
+      const int x = a.dS[v];
+      if (x >= kInf) atomicExch(&a.ctl->err, GC_EDISCONNECTED);
+      else d = x;
+      g = a.gid[v];
+    }
+    const int g0 = __shfl_sync(0xffffffffu, g, 0);
+    const bool uniform = __all_sync(0xffffffffu, g == g0 || g < 0);
+    if (uniform) {
+      const long long s = warp_sum(d);
+      if (lane == 0 && g0 >= 0 && s) atomicAdd((unsigned long long *)&out[g0], (unsigned long long)s);
+    } else if (g >= 0 && d) {
+      atomicAdd((unsigned long long *)&out[g], (unsigned long long)d);
+    }
+  }
+}
+
+// one CTA: argmin (f0, local id) over graph g's vertices with f0 >= 0
+static __device__ int cta_argmin_f0(const BatchArgs &a, int g) {
+  __shared__ long long s_v[32];
+  __shared__ int s_id[32];
+  const int o = a.off[g], n = a.ng[g];
+  long long bv = LLONG_MAX;
+  int bid = -1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long f = a.f0[o + i];
+    if (f >= 0 && better_min(f, i, bv, bid)) {
+      bv = f;
+      bid = i;
+    }
+  }
+  // block arg-min through the arg-max helper on negated values
+  long long nv = bv == LLONG_MAX ? LLONG_MIN : -bv;
+  block_argmax_all(nv, bid, s_v, s_id);
+  return bid;
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArgs a) {
+  __shared__ int32_t s_c[kLanes + kBatchThreads];
+  __shared__ long long s_out[kLanes];
+  __shared__ int s_cn, s_task;
+  __shared__ int s_scan[33];
+  __shared__ unsigned long long s_red[32];
+  __shared__ long long s_ll[32];
+  const int tid = threadIdx.x, lane = tid & 31, b = blockIdx.x, G = gridDim.x, T = blockDim.x;
+  GainCounters cnt;
+  const unsigned long long t_start = global_ns();
+  const GainWs myws = gain_ws(a.ws, a.ws_stride, a.max_n, b);  // this CTA's workspace, sized for the largest graph
+  // ---- P0: lower bounds, per-graph argmin ----
+  {
+    const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+    for (int v = gw; v < a.N; v += nw) {
+      const int beg = a.rp[v], end = a.rp[v + 1];
+      long long x = 0;
+      for (int e = beg + lane; e < end; e += 32) {
+        const int w = a.ci[e];
+        x += (long long)(a.rp[w + 1] - a.rp[w] - 1);
+      }
+      x = warp_sum(x);
+      if (lane == 0) {
+        const int g = a.gid[v];
+        const long long deg = end - beg;
+        long long rest = (long long)a.ng[g] - 1 - deg;
+        if (rest < 0) rest = 0;
+        const long long c2 = x < rest ? x : rest;
+        const long long lb = deg + 2 * c2 + 3 * (rest - c2);
+        a.key[v] = -lb;
+        a.f0[v] = -1;
+        a.dS[v] = kInf;
+        a.stamp[v] = 0;
+        a.ub[v] = LLONG_MAX;
+        atomicMin(&a.packed[g], ((unsigned long long)lb << 32) | (unsigned long long)(v - a.off[g]));
+      }
+    }
+  }
+  if (!bsync(a)) return;
+  // ---- P1: BFS from all v_a ----
+  for (int g = b * T + tid; g < a.count; g += G * T) a.seeds[g] = a.off[g] + (int)(a.packed[g] & 0xffffffffull);
+  if (!bsync(a)) return;
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->qsize, nullptr,
+                        &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar, &a.ctl->err, a.tns))
+    return;
+  if (!bsync(a)) return;
+  seg_sum_dist(a, a.fa);
+  if (b == 0 && tid == 0) a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+  if (!bsync(a)) return;
+  // ---- P2: round-0 survivors per graph (one CTA per graph) ----
+  for (int g = b; g < a.count; g += G) {
+    const int o = a.off[g], n = a.ng[g];
+    const long long fa = a.fa[g];
+    const int va = a.seeds[g];
+    if (tid == 0) {
+      a.bestf[g] = fa;
+      a.f0[va] = fa;
+      a.key[va] = LLONG_MIN;
+      s_cn = 0;
+    }
+    __syncthreads();
+    const LaneGraphs lg{a.gid, a.ng, a.bestf};
+    for (int base = 0; base < n; base += T) {
+      const int i = base + tid;
+      int flag = 0;
+      if (i < n) {
+        const long long k = a.key[o + i];
+        flag = k != LLONG_MIN && -k <= fa;
+      }
+      int total;
+      const int pos = block_excl_scan(flag, s_scan, &total);
+      if (flag) s_c[s_cn + pos] = o + i;
+      __syncthreads();
+      if (tid == 0) s_cn += total;
+      __syncthreads();
+      while (s_cn >= kLanes) {
+        cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, s_c, kLanes, s_out, myws, a.gctl, nullptr, lg, cnt, o);
+        if (tid < kLanes) a.f0[s_c[tid]] = s_out[tid];
+        __syncthreads();
+        const int rest = s_cn - kLanes;  // < T: at most one entry per thread
+        const int t = tid < rest ? s_c[kLanes + tid] : 0;
+        __syncthreads();
+        if (tid < rest) s_c[tid] = t;
+        if (tid == 0) s_cn = rest;
+        __syncthreads();
+      }
+    }
+    if (s_cn > 0) {
+      const int nl = s_cn;
+      cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, s_c, nl, s_out, myws, a.gctl, nullptr, lg, cnt, o);
+      if (tid < nl) a.f0[s_c[tid]] = s_out[tid];
+      __syncthreads();
+    }
+    const int s0 = cta_argmin_f0(a, g);
+    if (tid == 0) a.seeds[g] = o + (s0 >= 0 ? s0 : 0);
+    __syncthreads();
+  }
+  if (!bsync(a)) return;
+  // ---- P3: d_S = BFS from all s0; farness; neighbour bound ----
+  for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
+  if (!bsync(a)) return;
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->qsize, nullptr,
+                        &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar, &a.ctl->err, a.tns))
+    return;
+  if (!bsync(a)) return;
+  seg_sum_dist(a, a.farness);
+  {
+    const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+    for (int v = gw; v < a.N; v += nw) {
+      int m = 0;
+      for (int e = a.rp[v] + lane; e < a.rp[v + 1]; e += 32) m = max(m, a.dS[a.ci[e]]);
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 4));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      if (lane == 0) a.mx[v] = m;
+    }
+  }
+  if (b == 0 && tid == 0) {
+    a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+    a.ctl->task = 0;
+  }
+  if (!bsync(a)) return;
+  for (int g = b * T + tid; g < a.count; g += G * T) {
+    const int s0 = a.seeds[g];
+    if (a.f0[s0] != a.farness[g]) check_fail(a.ctl, 3, g, a.f0[s0], a.farness[g]);
+    a.picks[(size_t)g * a.kmax] = s0;
+    a.pgain[(size_t)g * a.kmax] = a.farness[g];
+    a.packed[g] = 0;  // reused as the round-1 arg-max key
+  }
+  // ---- P4: round 1 (graph-aligned batches from a dynamic counter) ----
+  const int n_tasks = a.bstart[a.count];
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= n_tasks) break;
+    int lo = 0, hi = a.count - 1;  // graph with bstart[g] <= t < bstart[g+1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.bstart[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const int g = lo;
+    if (a.kk[g] < 2) continue;
+    const int o = a.off[g], first = (t - a.bstart[g]) * a.lanes1;
+    const int nl = min(a.lanes1, a.ng[g] - first);
+    cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, a.iota + o + first, nl, a.ub + o + first, myws, a.gctl,
+                              a.mx, LaneGraphs(), cnt, o);
+  }
+  if (!bsync(a)) return;
+  for (int v = b * T + tid; v < a.N; v += G * T) a.stamp[v] = 1;
+  for (int g = b * T + tid; g < a.count; g += G * T) a.ub[a.seeds[g]] = -1;  // s0 is a member
+  if (!bsync(a)) return;
+  // per-graph argmax (gain desc, id asc) of round 1
+  for (int base = (b * T + tid) & ~31; base < a.N; base += G * T) {
+    const int v = base + lane;
+    unsigned long long key = 0;
+    int g = -1;
+    if (v < a.N) {
+      g = a.gid[v];
+      const long long u = a.ub[v];
+      if (u >= 0 && a.kk[g] >= 2) {
+        if (u >= (1ll << 31)) atomicExch(&a.ctl->err, GC_ERANGE);
+        key = ((unsigned long long)u << 32) | (0xffffffffull - (unsigned long long)(v - a.off[g]));
+      }
+    }
+    const int g0 = __shfl_sync(0xffffffffu, g, 0);
+    if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
+      unsigned long long m = key;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+      if (lane == 0 && g0 >= 0 && m) atomicMax(&a.packed[g0], m);
+    } else if (g >= 0 && key) {
+      atomicMax(&a.packed[g], key);
+    }
+  }
+  if (!bsync(a)) return;
+  if (b == 0) {
+    if (tid == 0) {
+      a.ctl->nseeds = 0;
+      a.ctl->remaining = 0;
+    }
+    __syncthreads();
+    for (int g = tid; g < a.count; g += T) {
+      if (a.kk[g] < 2) {
+        a.lc[g].round = a.kk[g];  // nothing after round 0
+        continue;
+      }
+      const unsigned long long key = a.packed[g];
+      const int v = a.off[g] + (int)(0xffffffffull - (key & 0xffffffffull));
+      const long long gain = (long long)(key >> 32);
+      a.picks[(size_t)g * a.kmax + 1] = v;
+      a.pgain[(size_t)g * a.kmax + 1] = gain;
+      a.ub[v] = -1;
+      a.seeds[atomicAdd(&a.ctl->nseeds, 1)] = v;
+      LazyCtl *lc = &a.lc[g];
+      lc->round = 2;
+      lc->best_id = -1;
+      lc->best_gain = -1;
+      lc->last_gain = gain;
+      lc->pad = 0;  // fold flag
+      if (a.kk[g] > 2) atomicAdd(&a.ctl->remaining, 1);
+    }
+  }
+  if (!bsync(a)) return;
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
+                        a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
+                        &a.ctl->err, a.tns))
+    return;
+  if (!bsync(a)) return;
+  if (b == 0 && tid == 0) {
+    a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+    a.ctl->nseeds = 0;
+  }
+  // ---- P5: active lists (one CTA per graph) ----
+  for (int g = b; g < a.count; g += G) {
+    if (a.kk[g] <= 2) continue;
+    const int o = a.off[g], n = a.ng[g];
+    long long umin = LLONG_MAX, umax = LLONG_MIN, c = 0;
+    for (int i = tid; i < n; i += T) {
+      const long long u = a.ub[o + i];
+      if (u < 0) continue;
+      umin = min(umin, u);
+      umax = max(umax, u);
+      ++c;
+    }
+    umin = block_min_ll(umin, s_ll);
+    umax = block_max_ll(umax, s_ll);
+    c = block_sum(c, s_ll);
+    int32_t *act = a.act + (size_t)g * a.A;
+    // list = {ub >= thr} with thr the smallest value whose list fits in A
+    // (thr = umin when everything fits); every dropped candidate has ub < thr
+    long long thr = umin;
+    if (c > a.A) {
+      long long lo2 = umin, hi2 = umax + 1;  // count(>= lo2) > A, count(>= hi2) <= A
+      while (hi2 - lo2 > 1) {
+        const long long mid = lo2 + (hi2 - lo2) / 2;
+        long long cc = 0;
+        for (int i = tid; i < n; i += T) cc += a.ub[o + i] >= mid;
+        cc = block_sum(cc, s_ll);
+        if (cc <= a.A) hi2 = mid;
+        else lo2 = mid;
+      }
+      thr = hi2;
+    }
+    int carry = 0;
+    for (int base = 0; base < n; base += T) {
+      const int i = base + tid;
+      const int f = i < n && a.ub[o + i] >= 0 && a.ub[o + i] >= thr;
+      int total;
+      const int pos = block_excl_scan(f, s_scan, &total);
+      if (f && carry + pos < a.A) act[carry + pos] = o + i;
+      carry += total;
+    }
+    if (carry > a.A) {  // cannot happen (count(ub >= thr) <= A); never write past the list
+      if (tid == 0) check_fail(a.ctl, 5, g, a.A, carry);
+      carry = a.A;
+    }
+    if (tid == 0) {
+      a.act_n[g] = carry;
+      a.lc[g].theta = c > a.A ? thr : LLONG_MIN;
+    }
+    if (tid == 0) a.full[g] = 0;
+    __syncthreads();
+  }
+  if (!bsync(a)) return;
+  // ---- P6: lazy iterations for every graph ----
+  for (long long it = 0; it < (1ll << 24); ++it) {
+    for (int g = b; g < a.count; g += G) {
+      LazyCtl *lc = &a.lc[g];
+      if (lc->round >= a.kk[g]) continue;
+      const bool full = a.full[g] != 0;
+      const int32_t *act = full ? a.iota + a.off[g] : a.act + (size_t)g * a.A;
+      const int m = full ? a.ng[g] : a.act_n[g];
+      if (full && tid == 0) lc->theta = LLONG_MIN;
+      __syncthreads();
+      lazy_cta0_step(act, m, a.ub, a.stamp, lc, nullptr, lc->pad != 0, nullptr, 0);
+      __syncthreads();
+      const int dec = *(volatile int32_t *)&lc->dec;
+      if (tid == 0) {
+        lc->pad = dec == 0;  // fold the batch next time
+        if (dec == 1) {
+          const int r = lc->round;
+          a.picks[(size_t)g * a.kmax + r] = lc->best_id;
+          a.pgain[(size_t)g * a.kmax + r] = lc->best_gain;
+          a.ub[lc->best_id] = -1;
+          a.seeds[atomicAdd(&a.ctl->nseeds, 1)] = lc->best_id;
+          lc->last_gain = lc->best_gain;
+          lc->best_id = -1;
+          lc->best_gain = -1;
+          lc->round = r + 1;
+          if (r + 1 >= a.kk[g]) atomicSub(&a.ctl->remaining, 1);
+        } else if (dec == 2) {
+          a.full[g] = 1;  // the list cannot certify: use every candidate of the graph
+        }
+      }
+      __syncthreads();
+    }
+    if (!bsync(a)) return;
+    if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
+                          a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
+                          &a.ctl->err, a.tns))
+      return;
+    for (int g = b; g < a.count; g += G) {
+      LazyCtl *lc = &a.lc[g];
+      if (lc->round >= a.kk[g] || *(volatile int32_t *)&lc->dec != 0) continue;
+      cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
+                                LaneGraphs(), cnt, a.off[g]);
+    }
+    if (!bsync(a)) return;
+    const int remaining = *(volatile int32_t *)&a.ctl->remaining;
+    // the whole lazy phase is bounded too: 6 x the per-wait limit of wall time
+    if (b == 0 && tid == 0 && global_ns() - t_start > 6ull * a.tns) atomicExch(&a.ctl->err, GC_ETIMEOUT);
+    if (b == 0 && tid == 0) {
+      a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+      a.ctl->nseeds = 0;
+      a.ctl->iterations = it + 1;
+    }
+    if (!bsync(a)) return;
+    if (remaining == 0) break;
+  }
+  // ---- P7: check every group's farness with one BFS ----
+  for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
+  if (b == 0) {
+    if (tid == 0) a.ctl->nseeds = 0;
+    __syncthreads();
+    for (int g = tid; g < a.count; g += T) {
+      long long f = a.pgain[(size_t)g * a.kmax];
+      for (int r = 1; r < a.kk[g]; ++r) f -= a.pgain[(size_t)g * a.kmax + r];
+      a.fa[g] = f;  // farness implied by the accepted gains
+      a.farness[g] = 0;
+    }
+  }
+  if (!bsync(a)) return;
+  if (b == 0) {
+    for (int g = 0; g < a.count; ++g) {
+      for (int r = tid; r < a.kk[g]; r += T) a.seeds[atomicAdd(&a.ctl->nseeds, 1)] = a.picks[(size_t)g * a.kmax + r];
+    }
+  }
+  if (!bsync(a)) return;
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
+                        a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
+                        &a.ctl->err, a.tns))
+    return;
+  if (!bsync(a)) return;
+  seg_sum_dist(a, a.farness);
+  if (!bsync(a)) return;
+  for (int g = b * T + tid; g < a.count; g += G * T)
+    if (a.farness[g] != a.fa[g]) check_fail(a.ctl, 7, g, a.fa[g], a.farness[g]);
+  // work counters
+  u64 c_scalar = block_sum(cnt.scalar, s_red);
+  u64 c_union = block_sum(cnt.uni, s_red);
+  u64 c_front = block_sum(cnt.front, s_red);
+  u64 c_push = block_sum(cnt.push, s_red);
+  if (tid == 0) {
+    atomicAdd(&a.gctl->edges_scalar, c_scalar);
+    atomicAdd(&a.gctl->edges_union, c_union);
+    atomicAdd(&a.gctl->frontier, c_front);
+    atomicAdd(&a.gctl->pushes, c_push);
+    atomicAdd(&a.gctl->levels, cnt.levels);
+    atomicAdd(&a.gctl->batches, cnt.batches);
+    atomicAdd(&a.gctl->lanes, cnt.lanes);
+  }
+}
+
+__global__ void k_iota(int32_t *p, int32_t n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+// union CSR: shift graph g's row pointers by its first edge and its neighbour
+// ids by its first vertex; gid[v] = graph of v
+__global__ void k_union_fix(int32_t *rp, int32_t *ci, int32_t *gid, const int32_t *off, const int64_t *eoff,
+                            int32_t count, int32_t N, int64_t nnz) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += stride) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= v) lo = mid;
+      else hi = mid - 1;
+    }
+    gid[v] = lo;
+    rp[v] += (int32_t)eoff[lo];
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (eoff[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    ci[e] += off[lo];
+  }
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+struct gc_batch {
+  int32_t count = 0;
+  int32_t N = 0;
+  int64_t nnz = 0;
+  int32_t max_n = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0, ctas = 0;
+  std::vector<int32_t> h_off, h_n;
+  int32_t *rp = nullptr, *ci = nullptr, *gid = nullptr, *off = nullptr, *ng = nullptr, *iota = nullptr;
+  int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr;
+  long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
+  unsigned char *ws = nullptr;
+  size_t ws_stride = 0;
+  unsigned long long *packed = nullptr;
+  long long *fa = nullptr, *farness = nullptr, *bestf = nullptr;
+  LazyCtl *lc = nullptr;
+  int32_t *act = nullptr, *act_n = nullptr, *full = nullptr, *kk = nullptr, *bstart = nullptr;
+  int32_t A = 0, act_cap = 0;
+  int32_t kcap = 0;
+  int32_t *picks = nullptr;
+  long long *pgain = nullptr;
+  int32_t *seeds = nullptr;
+  int32_t seeds_cap = 0;
+  BatchCtl *ctl = nullptr, *h_ctl = nullptr;
+  GainCtl *gctl = nullptr, *h_gctl = nullptr;
+  // captured launch sequence
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the sequence is captured on
+  std::vector<int32_t> cap_k;
+  int32_t cap_A = 0, cap_lanes = 0;
+  std::vector<int32_t> h_picks;
+  std::vector<long long> h_pgain, h_far;
+  int32_t *h_picks_pinned = nullptr;
+  long long *h_far_pinned = nullptr;
+  int32_t *h_k_pinned = nullptr, *h_bstart_pinned = nullptr;  // sources of the captured copies
+};
+
+static void batch_release(gc_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff,
+                 b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
+                 b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->h_gctl) cudaFreeHost(b->h_gctl);
+  if (b->h_picks_pinned) cudaFreeHost(b->h_picks_pinned);
+  if (b->h_far_pinned) cudaFreeHost(b->h_far_pinned);
+  if (b->h_k_pinned) cudaFreeHost(b->h_k_pinned);
+  if (b->h_bstart_pinned) cudaFreeHost(b->h_bstart_pinned);
+  delete b;
+}
+
+template <typename T>
+static bool balloc(T **p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+extern "C" {
+
+int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *const *col_idxs, const int32_t *ns,
+                  uint32_t flags, void *stream, gc_batch **out) {
+  (void)flags;
+  if (!out || count < 1 || !row_ptrs || !col_idxs || !ns) {
+    set_error("bad argument to gc_batch_load");
+    return GC_EINVAL;
+  }
+  *out = nullptr;
+  gc_batch *b = new gc_batch();
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  b->h_off.resize(count + 1);
+  b->h_n.assign(ns, ns + count);
+  std::vector<int64_t> eoff(count + 1);
+  int64_t N = 0, E = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    if (ns[g] < 1 || !row_ptrs[g] || row_ptrs[g][0] != 0 || (row_ptrs[g][ns[g]] > 0 && !col_idxs[g])) {
+      batch_release(b);
+      set_error("gc_batch_load: graph " + std::to_string(g) + " is malformed");
+      return GC_EINVAL;
+    }
+    b->h_off[g] = (int32_t)N;
+    eoff[g] = E;
+    N += ns[g];
+    E += row_ptrs[g][ns[g]];
+    b->max_n = std::max(b->max_n, ns[g]);
+    if (N >= INT32_MAX || E >= INT32_MAX) {
+      batch_release(b);
+      set_error("gc_batch_load: the union exceeds int32 CSR limits");
+      return GC_ERANGE;
+    }
+  }
+  b->h_off[count] = (int32_t)N;
+  eoff[count] = E;
+  b->N = (int32_t)N;
+  b->nnz = E;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_solve, kBatchThreads, 0) != cudaSuccess || occ < 1) {
+    batch_release(b);
+    set_error("gc_batch_load: the batch kernel cannot be resident");
+    return GC_ECUDA;
+  }
+  b->ctas = std::min(kMaxGridCtas, occ * b->num_sms);
+  const size_t Nn = (size_t)N;
+  bool ok = balloc(&b->rp, Nn + 1) && balloc(&b->ci, (size_t)E) && balloc(&b->gid, Nn) &&
+            balloc(&b->off, (size_t)count + 1) && balloc(&b->ng, (size_t)count) && balloc(&b->iota, Nn) &&
+            balloc(&b->dS, Nn) && balloc(&b->mx, Nn) && balloc(&b->stamp, Nn) && balloc(&b->q0, Nn) &&
+            balloc(&b->q1, Nn) && balloc(&b->goff, Nn + 1) && balloc(&b->ub, Nn) && balloc(&b->key, Nn) &&
+            balloc(&b->f0, Nn) && balloc(&b->packed, (size_t)count) && balloc(&b->fa, (size_t)count) &&
+            balloc(&b->farness, (size_t)count) && balloc(&b->bestf, (size_t)count) &&
+            balloc(&b->lc, (size_t)count) && balloc(&b->act_n, (size_t)count) && balloc(&b->full, (size_t)count) &&
+            balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
+            balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
+            cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
+  int64_t *d_eoff = nullptr;
+  ok = ok && balloc(&d_eoff, (size_t)count + 1);
+  // one workspace per CTA, sized for the largest graph
+  b->ws_stride = gain_ws_stride(b->max_n);
+  ok = ok && balloc(&b->ws, b->ws_stride * (size_t)b->ctas);
+  if (!ok) {
+    cudaFree(d_eoff);
+    batch_release(b);
+    set_error("gc_batch_load: device allocation failed");
+    return GC_ENOMEM;
+  }
+  cudaStream_t st = b->stream;
+  bool cp = true;
+  for (int32_t g = 0; g < count; ++g) {
+    cp = cp && cudaMemcpyAsync(b->rp + b->h_off[g], row_ptrs[g], (size_t)ns[g] * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st) == cudaSuccess;
+    const int64_t e = eoff[g + 1] - eoff[g];
+    if (e) cp = cp && cudaMemcpyAsync(b->ci + eoff[g], col_idxs[g], (size_t)e * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, st) == cudaSuccess;
+  }
+  const int32_t last = (int32_t)E;
+  cp = cp && cudaMemcpyAsync(b->rp + N, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(b->off, b->h_off.data(), ((size_t)count + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       st) == cudaSuccess &&
+       cudaMemcpyAsync(b->ng, ns, (size_t)count * sizeof(int32_t), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(d_eoff, eoff.data(), ((size_t)count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) ==
+           cudaSuccess &&
+       cudaMemsetAsync(b->ws, 0, b->ws_stride * (size_t)b->ctas, st) == cudaSuccess;
+  if (cp) {
+    k_union_fix<<<b->num_sms * 8, 256, 0, st>>>(b->rp, b->ci, b->gid, b->off, d_eoff, count, (int32_t)N, E);
+    k_iota<<<b->num_sms * 8, 256, 0, st>>>(b->iota, (int32_t)N);
+    cp = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  cudaFree(d_eoff);
+  if (!cp) {
+    batch_release(b);
+    set_error("gc_batch_load: copy to the device failed");
+    return GC_ECUDA;
+  }
+  *out = b;
+  return GC_OK;
+}
+
+int gc_batch_free(gc_batch *b) {
+  if (b) {
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+  }
+  return GC_OK;
+}
+
+int64_t gc_batch_vertices(const gc_batch *b) { return b ? b->N : -1; }
+
+int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int32_t *groups, int64_t *farness,
+                    gc_stats *stats) {
+  if (!b || !ks || !groups || !farness) {
+    set_error("bad argument to gc_batch_greedy");
+    return GC_EINVAL;
+  }
+  gc_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gc_opts_default(&opts);
+  int32_t kmax = 1;
+  int64_t ksum = 0;
+  for (int32_t g = 0; g < b->count; ++g) {
+    if (ks[g] < 1 || ks[g] > b->h_n[g]) {
+      set_error("gc_batch_greedy: k of graph " + std::to_string(g) + " outside [1, n]");
+      return GC_EINVAL;
+    }
+    kmax = std::max(kmax, ks[g]);
+    ksum += ks[g];
+  }
+  const int32_t A = opts.active_target > 0 ? opts.active_target : 1024;
+  const int32_t lanes1 = (opts.step_lanes > 0 && opts.step_lanes <= kLanes) ? opts.step_lanes : kLanes;
+  const bool capture = (opts.flags & GC_OPT_CAPTURE) != 0;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = b->stream;
+  // (re)size per-call buffers; a resize invalidates a captured sequence
+  bool resized = false;
+  if (kmax > b->kcap) {
+    cudaFree(b->picks);
+    cudaFree(b->pgain);
+    b->picks = nullptr;
+    b->pgain = nullptr;
+    if (!balloc(&b->picks, (size_t)b->count * kmax) || !balloc(&b->pgain, (size_t)b->count * kmax)) {
+      set_error("gc_batch_greedy: allocation failed");
+      return GC_ENOMEM;
+    }
+    b->kcap = kmax;
+    resized = true;
+    if (b->h_picks_pinned) cudaFreeHost(b->h_picks_pinned);
+    if (cudaMallocHost((void **)&b->h_picks_pinned, (size_t)b->count * kmax * sizeof(int32_t)) != cudaSuccess) {
+      set_error("gc_batch_greedy: pinned allocation failed");
+      return GC_ENOMEM;
+    }
+  }
+  if (!b->h_far_pinned && cudaMallocHost((void **)&b->h_far_pinned, (size_t)b->count * sizeof(long long)) != cudaSuccess) {
+    set_error("gc_batch_greedy: pinned allocation failed");
+    return GC_ENOMEM;
+  }
+  const int64_t need_seeds = std::max<int64_t>(b->count, ksum);
+  if (need_seeds > b->seeds_cap) {
+    cudaFree(b->seeds);
+    if (!balloc(&b->seeds, (size_t)need_seeds)) {
+      set_error("gc_batch_greedy: allocation failed");
+      return GC_ENOMEM;
+    }
+    b->seeds_cap = (int32_t)need_seeds;
+    resized = true;
+  }
+  if (A > b->act_cap) {
+    cudaFree(b->act);
+    if (!balloc(&b->act, (size_t)b->count * A)) {
+      set_error("gc_batch_greedy: allocation failed");
+      return GC_ENOMEM;
+    }
+    b->act_cap = A;
+    resized = true;
+  }
+  if (!b->h_k_pinned && (cudaMallocHost((void **)&b->h_k_pinned, (size_t)b->count * sizeof(int32_t)) != cudaSuccess ||
+                         cudaMallocHost((void **)&b->h_bstart_pinned, ((size_t)b->count + 1) * sizeof(int32_t)) !=
+                             cudaSuccess)) {
+    set_error("gc_batch_greedy: pinned allocation failed");
+    return GC_ENOMEM;
+  }
+  std::vector<int32_t> bstart(b->count + 1, 0);
+  for (int32_t g = 0; g < b->count; ++g) bstart[g + 1] = bstart[g] + (b->h_n[g] + lanes1 - 1) / lanes1;
+  const bool same = b->exec && !resized && b->cap_k == std::vector<int32_t>(ks, ks + b->count) && b->cap_A == A &&
+                    b->cap_lanes == lanes1;
+  BatchArgs a;
+  a.rp = b->rp;
+  a.ci = b->ci;
+  a.N = b->N;
+  a.count = b->count;
+  a.gid = b->gid;
+  a.off = b->off;
+  a.ng = b->ng;
+  a.kk = b->kk;
+  a.iota = b->iota;
+  a.bstart = b->bstart;
+  a.lanes1 = lanes1;
+  a.max_n = b->max_n;
+  a.dS = b->dS;
+  a.mx = b->mx;
+  a.stamp = b->stamp;
+  a.q0 = b->q0;
+  a.q1 = b->q1;
+  a.goff = b->goff;
+  a.ub = b->ub;
+  a.key = b->key;
+  a.f0 = b->f0;
+  a.ws = b->ws;
+  a.ws_stride = b->ws_stride;
+  a.packed = b->packed;
+  a.fa = b->fa;
+  a.farness = b->farness;
+  a.bestf = b->bestf;
+  a.lc = b->lc;
+  a.act = b->act;
+  a.act_n = b->act_n;
+  a.full = b->full;
+  a.A = A;
+  a.kmax = kmax;
+  a.picks = b->picks;
+  a.pgain = b->pgain;
+  a.seeds = b->seeds;
+  a.ctl = b->ctl;
+  a.gctl = b->gctl;
+  a.tns = (unsigned long long)((opts.timeout_ms > 0 ? opts.timeout_ms : 10000) * 1000000LL);
+  auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->kk, b->h_k_pinned, (size_t)b->count * sizeof(int32_t), cudaMemcpyHostToDevice, st)))
+      return e;
+    if ((e = cudaMemcpyAsync(b->bstart, b->h_bstart_pinned, bstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st)))
+      return e;
+    if ((e = cudaMemsetAsync(b->packed, 0xff, (size_t)b->count * sizeof(unsigned long long), st))) return e;
+    if ((e = cudaMemsetAsync(b->fa, 0, (size_t)b->count * sizeof(long long), st))) return e;
+    if ((e = cudaMemsetAsync(b->farness, 0, (size_t)b->count * sizeof(long long), st))) return e;
+    if ((e = cudaMemsetAsync(b->lc, 0, (size_t)b->count * sizeof(LazyCtl), st))) return e;
+    if ((e = cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), st))) return e;
+    if ((e = cudaMemsetAsync(b->gctl, 0, sizeof(GainCtl), st))) return e;
+    void *args[] = {(void *)&a};
+    if ((e = cudaLaunchCooperativeKernel((const void *)k_batch_solve, dim3(b->ctas), dim3(kBatchThreads), args, 0,
+                                         st)))
+      return e;
+    if ((e = cudaMemcpyAsync(b->h_picks_pinned, b->picks, (size_t)b->count * kmax * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, st)))
+      return e;
+    if ((e = cudaMemcpyAsync(b->h_far_pinned, b->farness, (size_t)b->count * sizeof(long long),
+                             cudaMemcpyDeviceToHost, st)))
+      return e;
+    if ((e = cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st))) return e;
+    return cudaMemcpyAsync(b->h_gctl, b->gctl, sizeof(GainCtl), cudaMemcpyDeviceToHost, st);
+  };
+  bool used_graph = false;
+  if (!(capture && same)) {  // a replay reads the pinned buffers it was captured from (same contents)
+    cudaStreamSynchronize(st);  // no earlier copy may still read them
+    memcpy(b->h_k_pinned, ks, (size_t)b->count * sizeof(int32_t));
+    memcpy(b->h_bstart_pinned, bstart.data(), bstart.size() * sizeof(int32_t));
+  }
+  if (capture && same) {
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
+    used_graph = true;
+  } else if (capture) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+    }
+    b->cap_k.assign(ks, ks + b->count);
+    b->cap_A = A;
+    b->cap_lanes = lanes1;
+    // capture on a private non-blocking stream (the legacy default stream
+    // cannot be captured); the graph is then launched on the caller's stream
+    cudaError_t e = cudaSuccess;
+    if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = enqueue(b->cap_stream);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+      b->graph = graph;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      return cuda_fail(e, "capture of the batched solve");
+    }
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
+    used_graph = true;
+  } else {
+    const cudaError_t e = enqueue(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batched solve launch");
+  }
+  GC_CUDA(cudaStreamSynchronize(st));
+  if (b->h_ctl->err) {
+    cudaMemsetAsync(b->ws, 0, b->ws_stride * (size_t)b->ctas, st);
+    cudaStreamSynchronize(st);
+    const int e = b->h_ctl->err;
+    set_error(e == GC_ETIMEOUT ? "device-side wait timed out" : e == GC_EDISCONNECTED ? "a graph is disconnected"
+              : e == GC_ERANGE ? "a gain exceeds the batched solver's 31-bit key"
+                               : "device-side check failed (phase " + std::to_string(b->h_ctl->dbg[0]) + ", graph " +
+                                     std::to_string(b->h_ctl->dbg[1]) + ": expected " +
+                                     std::to_string(b->h_ctl->dbg[2]) + ", found " +
+                                     std::to_string(b->h_ctl->dbg[3]) + ")");
+    return e;
+  }
+  int64_t pos = 0;
+  for (int32_t g = 0; g < b->count; ++g) {
+    for (int32_t r = 0; r < ks[g]; ++r) groups[pos + r] = b->h_picks_pinned[(size_t)g * kmax + r];
+    for (int32_t r = 0; r < ks[g]; ++r) groups[pos + r] -= b->h_off[g];  // local ids
+    pos += ks[g];
+    farness[g] = b->h_far_pinned[g];
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->rounds = ksum;
+    stats->steps = b->h_ctl->iterations;
+    stats->batches = (int64_t)b->h_gctl->batches;
+    stats->edges_scalar = (int64_t)b->h_gctl->edges_scalar;
+    stats->edges_union = (int64_t)b->h_gctl->edges_union;
+    stats->levels = (int64_t)b->h_gctl->levels;
+    stats->frontier = (int64_t)b->h_gctl->frontier;
+    stats->pushes = (int64_t)b->h_gctl->pushes;
+    stats->lanes = (int64_t)b->h_gctl->lanes;
+    stats->kernel_launches = 1;
+    stats->graph_replay = used_graph ? 1 : 0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return GC_OK;
+}
+
+}  // extern "C"

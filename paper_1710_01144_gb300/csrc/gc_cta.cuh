@@ -1,0 +1,237 @@
+// The CTA-per-batch form of the 64-lane pruned multi-source BFS (see
+// gc_gain.cu for the method and layout), as a device function so that the
+// batched multi-graph solver can run it inside a persistent kernel.
+#pragma once
+
+#include "gc_device.cuh"
+#include "gc_internal.cuh"
+
+namespace gc {
+
+typedef unsigned long long u64;
+
+struct GainWs {
+  u64 *vis, *nxt, *qm0, *qm1;
+  int32_t *qv0, *qv1, *touched;
+};
+
+__host__ __device__ inline size_t align256_(size_t x) { return (x + 255) & ~(size_t)255; }
+
+
+__device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, int32_t n, int idx) {
+  unsigned char *p = base + stride * (size_t)idx;
+  const size_t a8 = align256_((size_t)n * sizeof(u64)), a4 = align256_((size_t)n * sizeof(int32_t));
+  GainWs w;
+  w.vis = (u64 *)p;
+  w.nxt = (u64 *)(p + a8);
+  w.qm0 = (u64 *)(p + 2 * a8);
+  w.qm1 = (u64 *)(p + 3 * a8);
+  w.qv0 = (int32_t *)(p + 4 * a8);
+  w.qv1 = (int32_t *)(p + 4 * a8 + a4);
+  w.touched = (int32_t *)(p + 4 * a8 + 2 * a4);
+  return w;
+}
+
+struct GainCounters {
+  u64 scalar = 0, uni = 0, levels = 0, batches = 0, front = 0, push = 0, lanes = 0;
+};
+
+// One batch of nl <= 64 candidates (cand[0..nl)) by the whole CTA, results to
+// out[0..nl).  The workspace's vis/nxt words are zero on entry and on exit.
+template <int MODE>
+__device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                               int32_t n, const int32_t *__restrict__ dS,
+                                               const int32_t *__restrict__ cand, int nl,
+                                               long long *__restrict__ out, const GainWs &ws, GainCtl *ctl,
+                                               const int32_t *__restrict__ mx, const LaneGraphs lg,
+                                               GainCounters &cnt, int voff = 0) {
+  constexpr int T = kGainThreads;
+  __shared__ u64 s_gain[kLanes];
+  __shared__ int s_cnt[kLanes];
+  __shared__ int s_cand[kLanes];
+  __shared__ int s_nlane[kLanes];
+  __shared__ long long s_best[kLanes];
+  __shared__ int s_off[T + 1];
+  __shared__ int s_rs[T];
+  __shared__ u64 s_m[T];
+  __shared__ int s_scan[33];
+  __shared__ int s_qn, s_touched;
+  __shared__ u64 s_alive;
+
+  const int tid = threadIdx.x;
+  if (tid < kLanes) {
+    s_gain[tid] = 0;
+    s_cnt[tid] = 0;
+    const int c = tid < nl ? cand[tid] : -1;
+    s_cand[tid] = c;
+    if (MODE == kModeFarness) {
+      const int g = (lg.gid && c >= 0 && c < n) ? lg.gid[c] : -1;
+      s_nlane[tid] = g >= 0 ? lg.ng[g] : n;
+      s_best[tid] = g >= 0 ? *(volatile long long *)&lg.best_f[g] : 0;
+    }
+  }
+  if (tid == 0) {
+    s_qn = 0;
+    s_touched = 0;
+    s_alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
+  }
+  __syncthreads();
+  int32_t *qcur_v = ws.qv0, *qnxt_v = ws.qv1;
+  u64 *qcur_m = ws.qm0, *qnxt_m = ws.qm1;
+
+  // level 0: lane j starts at its candidate
+  if (tid < nl) {
+    const int c = s_cand[tid];
+    const u64 bit = 1ull << tid;
+    bool push = false;
+    if (c < 0 || c >= n) {
+      s_cand[tid] = -2;  // invalid id
+      atomicAnd(&s_alive, ~bit);
+    } else if (MODE == kModeGain) {
+      const int dc = dS[c];
+      if (dc > 0) {  // v not in S: it contributes d_S[v] - 0 and expands
+        s_gain[tid] = (u64)dc;
+        push = true;
+      }
+    } else {
+      s_cnt[tid] = 1;
+      push = true;
+    }
+    if (push) {
+      const u64 old = atomicOr(&ws.nxt[c - voff], bit);
+      if (old == 0) qnxt_v[atomicAdd(&s_qn, 1)] = c;
+    }
+  }
+  __syncthreads();
+  int F = s_qn;
+  for (int i = tid; i < F; i += T) {  // commit level 0
+    const int w = qnxt_v[i];
+    const u64 m = ws.nxt[w - voff];
+    ws.nxt[w - voff] = 0;
+    ws.vis[w - voff] = m;
+    ws.touched[atomicAdd(&s_touched, 1)] = w;
+    qnxt_m[i] = m;
+  }
+  __syncthreads();
+  if (tid == 0) s_qn = 0;
+  { int32_t *t = qcur_v; qcur_v = qnxt_v; qnxt_v = t; }
+  { u64 *t = qcur_m; qcur_m = qnxt_m; qnxt_m = t; }
+  __syncthreads();
+
+  int L = 0;
+  for (; F > 0; ++L) {
+    const int nlev = L + 1;
+    // ---- expand level L into level L+1 ----
+    for (int chunk = 0; chunk < F; chunk += T) {
+      const int i = chunk + tid;
+      int deg = 0, rs = 0;
+      u64 m = 0;
+      if (i < F) {
+        const int u = qcur_v[i];
+        m = qcur_m[i];
+        if (MODE == kModeFarness) m &= s_alive;
+        // no neighbour of u can still be claimed: skip the scan
+        if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
+        if (m) {
+          rs = rp[u];
+          deg = rp[u + 1] - rs;
+        }
+        cnt.uni += (u64)deg;
+        cnt.scalar += (u64)__popcll(m) * (u64)deg;
+        cnt.front += (m != 0);
+      }
+      int total;
+      const int off = block_excl_scan(deg, s_scan, &total);
+      s_off[tid] = off;
+      s_rs[tid] = rs;
+      s_m[tid] = m;
+      if (tid == T - 1) s_off[T] = total;
+      __syncthreads();
+      for (int e = tid; e < total; e += T) {
+        int lo = 0, hi = T - 1;  // largest j with s_off[j] <= e (its row is non-empty)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        const int w = ci[s_rs[lo] + (e - s_off[lo])];
+        int dw = 0;
+        if (MODE == kModeGain) {
+          dw = dS[w];
+          if (dw <= nlev) continue;  // pruned: w cannot be strictly closer to v than to S
+        }
+        const u64 nb = s_m[lo] & ~ws.vis[w - voff];
+        if (!nb) continue;
+        const u64 old = atomicOr(&ws.nxt[w - voff], nb);
+        u64 won = nb & ~old;
+        if (won) {
+          const u64 wt = MODE == kModeGain ? (u64)(dw - nlev) : (u64)nlev;
+          do {
+            const int j = __ffsll((long long)won) - 1;
+            won &= won - 1;
+            atomicAdd(&s_gain[j], wt);
+            if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
+          } while (won);
+        }
+        if (old == 0) {
+          qnxt_v[atomicAdd(&s_qn, 1)] = w;
+          ++cnt.push;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- commit level L+1: fold the claimed words into vis ----
+    const int Fn = s_qn;
+    for (int i = tid; i < Fn; i += T) {
+      const int w = qnxt_v[i];
+      const u64 m = ws.nxt[w - voff];
+      ws.nxt[w - voff] = 0;
+      const u64 ov = ws.vis[w - voff];
+      ws.vis[w - voff] = ov | m;
+      if (ov == 0) ws.touched[atomicAdd(&s_touched, 1)] = w;
+      qnxt_m[i] = m;
+    }
+    __syncthreads();
+    if (MODE == kModeFarness && tid < kLanes && ((s_alive >> tid) & 1ull)) {
+      // every vertex within distance L+1 is counted; the rest are >= L+2 away
+      const long long lb = (long long)s_gain[tid] + (long long)(L + 2) * (long long)(s_nlane[tid] - s_cnt[tid]);
+      const long long best = lg.gid ? s_best[tid] : *(volatile long long *)&ctl->best_f;
+      if (Fn > 0 && lb > best) atomicAnd(&s_alive, ~(1ull << tid));
+    }
+    if (tid == 0) s_qn = 0;
+    { int32_t *t = qcur_v; qcur_v = qnxt_v; qnxt_v = t; }
+    { u64 *t = qcur_m; qcur_m = qnxt_m; qnxt_m = t; }
+    F = Fn;
+    __syncthreads();
+    if (MODE == kModeFarness && s_alive == 0) break;
+  }
+  cnt.levels += (u64)L;
+  ++cnt.batches;
+  cnt.lanes += (u64)nl;
+
+  if (tid < nl) {
+    const int c = s_cand[tid];
+    long long r;
+    if (c == -2) {
+      r = -1;
+      atomicExch(&ctl->err, GC_EINVAL);
+    } else if (MODE == kModeGain) {
+      r = (long long)s_gain[tid];
+    } else if (!((s_alive >> tid) & 1ull)) {
+      r = -1;  // cut: cannot beat the best farness
+    } else if (s_cnt[tid] != s_nlane[tid]) {
+      r = -1;
+      atomicExch(&ctl->err, GC_EDISCONNECTED);
+    } else {
+      r = (long long)s_gain[tid];
+      if (lg.gid) atomicMin(&lg.best_f[lg.gid[c]], r);
+      else atomicMin(&ctl->best_f, r);
+    }
+    out[tid] = r;
+  }
+  const int nt = s_touched;
+  for (int i = tid; i < nt; i += T) ws.vis[ws.touched[i] - voff] = 0;
+  __syncthreads();
+}
+
+}  // namespace gc

@@ -117,6 +117,15 @@ struct SelCtl {
   long long evals, steps;  // lazy-step counters of the call
 };
 
+// Per-lane graph data for gain batches that mix graphs of a block-diagonal
+// union (farness mode): lane j's vertex count and cut threshold come from its
+// graph.  Empty (gid == nullptr) for a single graph.
+struct LaneGraphs {
+  const int32_t *gid = nullptr;  // graph of each vertex
+  const int32_t *ng = nullptr;   // vertex count of each graph
+  long long *best_f = nullptr;   // per-graph best exact farness (atomicMin)
+};
+
 // --------------------------------------------------------------- handle ----
 }  // namespace gc
 
@@ -175,6 +184,7 @@ struct gc_graph {
   int red_blocks = 0;      // grid size of reductions
   int32_t *dec = nullptr;                  // scratch word
   int64_t launches = 0;                    // kernels launched through this handle
+  gc::LaneGraphs lane_graphs;              // set for block-diagonal graph batches
   std::vector<cudaEvent_t> events;         // gain-kernel timing events (pairs)
 };
 

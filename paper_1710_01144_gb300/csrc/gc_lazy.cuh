@@ -1,0 +1,311 @@
+// Device-side pieces of the lazy greedy (Sec. 4.2) shared by the persistent
+// single-graph kernel (gc_lazy.cu) and the batched multi-graph solver
+// (gc_batch.cu): exact top-K selection by one CTA, the per-step decision of a
+// graph's lazy round, and proposal scoring.
+#pragma once
+
+#include <limits.h>
+
+#include "gc_grid.cuh"
+#include "gc_mlp.cuh"
+
+namespace gc {
+
+constexpr int kLazyBins = 1024;  // two bins per thread of a 512-thread CTA
+
+static __device__ __forceinline__ long long block_min_ll(long long v, long long *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) v = min(v, sh[w]);
+    sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+static __device__ __forceinline__ long long block_max_ll(long long v, long long *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) v = max(v, sh[w]);
+    sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+// (value, id) block arg-max; every thread gets the result.
+static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, long long *sv, int *sid) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oid = __shfl_xor_sync(0xffffffffu, id, o);
+    if (better_max(ov, oid, v, id)) {
+      v = ov;
+      id = oid;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sv[wid] = v;
+    sid[wid] = id;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w)
+      if (better_max(sv[w], sid[w], v, id)) {
+        v = sv[w];
+        id = sid[w];
+      }
+    sv[0] = v;
+    sid[0] = id;
+  }
+  __syncthreads();
+  v = sv[0];
+  id = sid[0];
+  __syncthreads();
+}
+
+// Exact top-`need` of the list entries by key (larger first; ties by list
+// order, i.e. smaller id), written to sel[base..).  key(i, v) returns LLONG_MIN
+// for entries that are not eligible; kmin/kmax/cnt describe the eligible keys.
+// Histogram passes over [kmin, kmax] fix the threshold value; every key above it
+// is taken, then keys equal to it in list order.  Returns the number taken.
+template <class KeyFn>
+static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
+                        long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist) {
+  __shared__ int s_scan[33];
+  __shared__ int s_b;
+  __shared__ long long s_ab;
+  const int tid = threadIdx.x, T = blockDim.x;
+  if (need <= 0 || cnt <= 0) return 0;
+  if (need > cnt) need = (int)cnt;
+  long long tau = kmin, above = 0;  // above = eligible keys > tau
+  if (cnt > need) {
+    unsigned long long lo = (unsigned long long)kmin, hi = (unsigned long long)kmax;
+    long long want = need, acc = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+      const unsigned long long span = hi - lo + 1ull;
+      const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
+      for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < m; i += T) {
+        const long long k = key(i, act[i]);
+        if (k == LLONG_MIN) continue;
+        const unsigned long long uu = (unsigned long long)k;
+        if (uu - lo > hi - lo) continue;  // outside [lo, hi] (unsigned wrap)
+        atomicAdd(&s_hist[(uu - lo) / width], 1u);
+      }
+      __syncthreads();
+      // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
+      const int b0 = kLazyBins - 1 - 2 * tid, b1 = b0 - 1;
+      const int h0 = tid < kLazyBins / 2 ? (int)s_hist[b0] : 0;
+      const int h1 = tid < kLazyBins / 2 ? (int)s_hist[b1] : 0;
+      if (tid == 0) {
+        s_b = 0;
+        s_ab = 0;
+      }
+      int total;
+      const long long a0 = block_excl_scan(h0 + h1, s_scan, &total);
+      if (tid < kLazyBins / 2) {
+        if (a0 < want && a0 + h0 >= want) {
+          s_b = b0;
+          s_ab = a0;
+        } else if (a0 + h0 < want && a0 + h0 + h1 >= want) {
+          s_b = b1;
+          s_ab = a0 + h0;
+        }
+      }
+      __syncthreads();
+      const int bb = s_b;
+      const long long ab = s_ab;
+      const unsigned long long bin_lo = lo + width * (unsigned long long)bb;
+      if (width == 1ull) {
+        tau = (long long)bin_lo;
+        above = acc + ab;
+        break;
+      }
+      acc += ab;
+      want -= ab;
+      const unsigned long long room = hi - bin_lo;
+      lo = bin_lo;
+      hi = bin_lo + (width - 1ull < room ? width - 1ull : room);
+      __syncthreads();
+    }
+  }
+  int taken = 0, eq_seen = 0;
+  for (int b = 0; b < m && taken < need; b += T) {
+    const int i = b + tid;
+    int gt = 0, eq = 0, v = -1;
+    if (i < m) {
+      v = act[i];
+      const long long k = key(i, v);
+      if (k != LLONG_MIN) {
+        gt = k > tau;
+        eq = k == tau;
+      }
+    }
+    int tot_eq, tot_take;
+    const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
+    const int take = gt || (eq && eq_rank < need - above);
+    const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
+    if (take && base + pos < kLanes) sel[base + pos] = v;
+    eq_seen += tot_eq;
+    taken += tot_take;
+  }
+  __syncthreads();
+  return taken < need ? taken : need;
+}
+
+// CTA 0's part of a step (see the file comment).  Writes lc->dec (0 evaluate
+// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).  With a
+// proposal network (score != nullptr), `fill` of the 64 lanes go to the
+// unevaluated candidates whose bound most exceeds the network's predicted
+// gain: evaluating them tightens the bounds later rounds must beat.
+static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+                               LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill) {
+  __shared__ long long s_v[32];
+  __shared__ int s_id[32];
+  __shared__ long long s_ll[32];
+  __shared__ unsigned int s_hist[kLazyBins];
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  const int r = lc->round;
+
+  if (fold) {  // the batch just evaluated: exact gains become the bounds
+    const int ns = lc->n_sel;
+    long long bv = -1;
+    int bid = -1;
+    if (tid < ns) {
+      const int v = lc->sel[tid];
+      const long long gv = lc->gsel[tid];
+      ub[v] = gv;
+      stamp[v] = r;
+      bv = gv;
+      bid = v;
+    }
+    block_argmax_all(bv, bid, s_v, s_id);
+    if (tid == 0) {
+      if (bid >= 0 && better_max(bv, bid, lc->best_gain, lc->best_id)) {
+        lc->best_gain = bv;
+        lc->best_id = bid;
+      }
+      lc->steps += 1;
+      lc->evals += ns;
+    }
+    __syncthreads();
+  }
+  const long long gb = *(volatile long long *)&lc->best_gain;
+  const int vb = *(volatile int32_t *)&lc->best_id;
+  const long long theta = lc->theta;
+
+  // best unevaluated bound, smallest bound, count
+  long long umax = LLONG_MIN, umin = LLONG_MAX, cnt = 0;
+  int vmax = -1;
+  for (int i = tid; i < m; i += T) {
+    const int v = act[i];
+    const long long u = ub[v];
+    if (u < 0 || stamp[v] == r) continue;
+    if (better_max(u, v, umax, vmax)) {
+      umax = u;
+      vmax = v;
+    }
+    umin = min(umin, u);
+    ++cnt;
+  }
+  block_argmax_all(umax, vmax, s_v, s_id);
+  umin = block_min_ll(umin, s_ll);
+  cnt = block_sum(cnt, s_ll);
+  int dec;
+  if (vb >= 0 && (cnt == 0 || better_max(gb, vb, umax, vmax))) dec = gb >= theta ? 1 : 2;
+  else if (cnt == 0) dec = 2;
+  else dec = 0;
+  if (dec != 0) {
+    if (tid == 0) lc->dec = dec;
+    return;
+  }
+  // the largest bounds (all 64 lanes without a proposal)
+  const int need1 = score ? kLanes - fill : kLanes;
+  auto by_bound = [=] __device__(int, int v) -> long long {
+    const long long u = ub[v];
+    return (u >= 0 && stamp[v] != r) ? u : LLONG_MIN;
+  };
+  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist);
+  if (score && taken < kLanes && cnt > taken) {
+    // mark the bound picks as evaluated in this round (their fold does it again)
+    if (tid < taken) stamp[lc->sel[tid]] = r;
+    __syncthreads();
+    auto by_slack = [=] __device__(int i, int v) -> long long {
+      const long long u = ub[v];
+      if (u < 0 || stamp[v] == r) return LLONG_MIN;
+      float p = expm1f(score[i]);
+      p = p < 0.f ? 0.f : (p > (float)u ? (float)u : p);
+      return u - (long long)p;
+    };
+    long long smin = LLONG_MAX, smax = LLONG_MIN, scnt = 0;
+    for (int i = tid; i < m; i += T) {
+      const long long k = by_slack(i, act[i]);
+      if (k == LLONG_MIN) continue;
+      smin = min(smin, k);
+      smax = max(smax, k);
+      ++scnt;
+    }
+    smin = block_min_ll(smin, s_ll);
+    smax = block_max_ll(smax, s_ll);
+    scnt = block_sum(scnt, s_ll);
+    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist);
+  }
+  // a fresh grid-batch control block for the evaluation (grid form only)
+  if (gg && tid < kLanes) {
+    gg->gain[tid] = 0;
+    gg->cnt[tid] = 0;
+  }
+  if (tid == 0) {
+    lc->n_sel = taken < kLanes ? taken : kLanes;
+    lc->dec = 0;
+    if (gg) {
+      gg->F = 0;
+      gg->qn[0] = 0;
+      gg->qn[1] = 0;
+      gg->touched = 0;
+    }
+  }
+}
+
+// Proposal scores of the active list for this round (every CTA, one warp per
+// candidate): score[i] = network output on the candidate's features.
+static __device__ void lazy_score(const int32_t *__restrict__ act, int32_t m, const float *__restrict__ prop,
+                           const int32_t *__restrict__ rp, const int32_t *__restrict__ dS,
+                           const long long *__restrict__ ub, const int32_t *__restrict__ stamp,
+                           const long long *__restrict__ two_hop, const int32_t *__restrict__ mx, int32_t round,
+                           long long prev_gain, float *score) {
+  __shared__ float sw[kMlpParams];
+  __shared__ float sh[kGridGainThreads / 32][kMlpHidden];
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = prop[i];
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid, nw = gridDim.x * (blockDim.x >> 5);
+  for (int i = gw; i < m; i += nw) {
+    float f[kMlpIn];
+    cand_features(act[i], rp, dS, ub, stamp, two_hop, mx, round, prev_gain, f);
+    const float o = mlp_forward_warp(sw, f, sh[wid]);
+    if (lane == 0) score[i] = o;
+  }
+  __syncthreads();
+}
+
+}  // namespace gc

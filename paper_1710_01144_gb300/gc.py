@@ -28,13 +28,15 @@ GC_DEVICE_PTRS = 0x1
 GC_ADOPT = 0x2
 GC_VALIDATE = 0x4
 GC_OPT_NO_EXPAND_BOUND = 0x1
+GC_OPT_CAPTURE = 0x2
 
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
            "gc_group_farness", "gc_marginal_gains", "gc_marginal_gains_device", "gc_greedy",
            "gc_last_error", "gc_marginal_gains_static", "gc_mlp_create", "gc_mlp_free", "gc_mlp_set_params",
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
-           "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded")
+           "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
+           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -58,7 +60,7 @@ class Stats(ctypes.Structure):
         "pushes", "lanes", "round0_evals")] + [
         ("ms_round0", ctypes.c_double), ("ms_round1", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
         ("ms_lazy_select", ctypes.c_double), ("ms_lazy_gain", ctypes.c_double), ("ms_lazy_update", ctypes.c_double),
-        ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+        ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("graph_replay", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -104,9 +106,15 @@ def load(path: str = LIB_PATH):
         lib.gc_set_recorder.argtypes = [vp, vp, vp, i32]
         lib.gc_recorded.argtypes = [vp]
         lib.gc_recorded.restype = i64
+        lib.gc_batch_load.argtypes = [i32, vp, vp, vp, ctypes.c_uint32, vp, ctypes.POINTER(vp)]
+        lib.gc_batch_free.argtypes = [vp]
+        lib.gc_batch_vertices.argtypes = [vp]
+        lib.gc_batch_vertices.restype = i64
+        lib.gc_batch_greedy.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded"):
+            if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded",
+                            "gc_batch_vertices"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -297,3 +305,56 @@ def candidate_features(row_ptr, dS, ub, stamp, two_hop, mx, cand, rnd, prev_gain
                                         two_hop.data_ptr(), mx.data_ptr() if mx is not None else None,
                                         cand.data_ptr(), int(cand.numel()), int(rnd), int(prev_gain),
                                         X_out.data_ptr(), st))
+
+
+class Batch:
+    """Many graphs solved together by one persistent kernel (gc_batch_*)."""
+
+    def __init__(self, graphs, stream=None):
+        lib = load()
+        self._keep = [(np.ascontiguousarray(rp, dtype=np.int32), _i32(ci)) for rp, ci in graphs]
+        cnt = len(self._keep)
+        rps = (ctypes.c_void_p * cnt)(*[rp.ctypes.data for rp, _ in self._keep])
+        cis = (ctypes.c_void_p * cnt)(*[ci.ctypes.data for _, ci in self._keep])
+        self.ns = np.array([rp.size - 1 for rp, _ in self._keep], dtype=np.int32)
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(lib.gc_batch_load(cnt, rps, cis, self.ns.ctypes.data, 0, self.stream, ctypes.byref(h)))
+        self._h = h
+        self.count = cnt
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def greedy(self, ks, active_target: int = 0, lanes: int = 0, capture: bool = False, timeout_ms: int = 0):
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        o = Opts()
+        load().gc_opts_default(ctypes.byref(o))
+        o.active_target, o.step_lanes = active_target, lanes
+        o.flags = GC_OPT_CAPTURE if capture else 0
+        if timeout_ms:
+            o.timeout_ms = timeout_ms
+        groups = np.zeros(max(int(ks.sum()), 1), dtype=np.int32)
+        far = np.zeros(self.count, dtype=np.int64)
+        st = Stats()
+        _check(load().gc_batch_greedy(self._h, ks.ctypes.data, ctypes.byref(o), groups.ctypes.data, far.ctypes.data,
+                                      ctypes.byref(st)))
+        out, pos = [], 0
+        for k in ks:
+            out.append(groups[pos:pos + k].copy())
+            pos += k
+        return out, far, st.as_dict()

@@ -1,0 +1,84 @@
+"""Batched solving: many graphs of uneven size and k in one persistent launch
+(optionally replayed from a captured CUDA graph).  Every graph's group must
+equal the CPU oracle's on that graph alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_01144_gb300 import graphgen
+from tests import smallgraphs as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gcm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1710_01144_gb300 import build, gc
+
+    build.build()
+    return gc
+
+
+def mixed_batch():
+    graphs = [graphgen.barabasi_albert(800 + 97 * i, 1 + i % 4, 10 + i) for i in range(6)]
+    graphs += [graphgen.rmat(9 + i % 4, 4.0 + 3 * i, seed=20 + i) for i in range(6)]
+    graphs += [sg.path(30), sg.star(25), sg.cycle(17), sg.grid(6, 9), sg.caterpillar(7, 2), sg.complete(5),
+               graphgen.grid_road(25, 31, 0.2, 0.01, 4)]
+    ks = [1 + (7 * i) % 23 for i in range(len(graphs))]
+    ks = [min(k, rp.size - 1) for k, (rp, _) in zip(ks, graphs)]
+    ks[0], ks[1] = 1, 2  # the round-0-only and round-1-only cases
+    return graphs, ks
+
+
+def oracle_groups(graphs, ks):
+    out = []
+    for (rp, ci), k in zip(graphs, ks):
+        g, ft, _, _ = oracle.greedypp(rp, ci, k)
+        out.append((g, int(ft[-1])))
+    return out
+
+
+def test_batch_matches_oracle(gcm):
+    graphs, ks = mixed_batch()
+    ref = oracle_groups(graphs, ks)
+    with gcm.Batch(graphs) as B:
+        for act, lanes in ((0, 0), (2, 16), (64, 64)):
+            groups, far, st = B.greedy(ks, active_target=act, lanes=lanes)
+            for i, ((g, f), got) in enumerate(zip(ref, groups)):
+                np.testing.assert_array_equal(got, g, err_msg="graph %d (act %d)" % (i, act))
+                assert far[i] == f
+
+
+def test_batch_capture_replay(gcm):
+    graphs, ks = mixed_batch()
+    ref = oracle_groups(graphs, ks)
+    with gcm.Batch(graphs) as B:
+        for call in range(3):
+            groups, far, st = B.greedy(ks, capture=True)
+            assert st["graph_replay"] == 1
+            for (g, f), got, ff in zip(ref, groups, far):
+                np.testing.assert_array_equal(got, g)
+                assert ff == f
+        # changing ks re-captures
+        ks2 = [max(1, k - 1) for k in ks]
+        ref2 = oracle_groups(graphs, ks2)
+        groups, far, st = B.greedy(ks2, capture=True)
+        for (g, f), got in zip(ref2, groups):
+            np.testing.assert_array_equal(got, g)
+
+
+def test_batch_errors(gcm):
+    graphs, ks = mixed_batch()
+    with gcm.Batch(graphs[:3]) as B:
+        with pytest.raises(gcm.GcError) as e:
+            B.greedy([0, 1, 1])
+        assert e.value.code == gcm.GC_EINVAL
+    rp, ci = sg.disjoint_union(sg.path(3), sg.path(3))
+    with gcm.Batch([rp, ci] and [(rp, ci), sg.path(4)]) as B:
+        with pytest.raises(gcm.GcError) as e:
+            B.greedy([1, 1])
+        assert e.value.code == gcm.GC_EDISCONNECTED
