@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--scale", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the plain-vs-learned+batched comparison legs")
+    p.add_argument("--batch-graphs", type=int, default=256,
+                   help="graphs of the mixed batched workload (0 = skip)")
     return p.parse_args()
 
 
@@ -307,10 +311,96 @@ def run_gc(args):
         }
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(rp, ci, args.k, grp0, f0)
+        if not args.no_extras:
+            line["comparison"] = comparison_legs(gc, rp, ci, args, grp0, f0)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def _best_ms(fn, reps):
+    import torch
+
+    best, out = float("inf"), None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        best = min(best, (time.perf_counter() - t0) * 1e3)
+    return best, out
+
+
+def comparison_legs(gc, rp, ci, args, grp0, f0):
+    """Plain GPU lazy greedy vs the learned + batched forms, same GPU, same
+    groups.  Plain: host-driven lazy steps of 64 candidates in bound order (one
+    CTA per batch), no grid-wide steps, no heavy split, no expansion bound."""
+    from paper_1710_01144_gb300 import autotune, graphgen, proposal
+
+    out = {}
+    with gc.Graph(rp, ci) as G:
+        ms, (g, f, _) = _best_ms(lambda: G.greedy(args.k, step_mode=1, eval_per_step=64, step_lanes=64,
+                                                  round1_heavy=-1, expand_bound=False), 3)
+        assert np.array_equal(g, grp0) and f == f0
+        out["plain_gpu_lazy_ms"] = ms
+        ms, (g, f, _) = _best_ms(lambda: G.greedy(args.k), 3)
+        out["batched_persistent_ms"] = ms
+        # learned proposal trained on this family's exact gains (other seeds, scale 18)
+        t0 = time.perf_counter()
+        train = [graphgen.rmat(18, 16.0, seed=s) for s in (2, 3)]
+        net, (m, l0, l1) = proposal.train(train, k=args.k)
+        out["proposal"] = {"train_graphs": "R-MAT scale 18, ef 16, seeds 2 and 3", "samples": m,
+                           "loss_initial": l0, "loss_final": l1, "train_s": time.perf_counter() - t0}
+        G.set_proposal(net, 16)
+        ms, (g, f, st) = _best_ms(lambda: G.greedy(args.k, use_proposal=True), 3)
+        assert np.array_equal(g, grp0) and f == f0
+        out["learned_batched_ms"] = ms
+        out["learned_steps"] = st["steps"]
+        G.set_proposal(None)
+        net.close()
+    out["speedup_learned_batched_vs_plain"] = out["plain_gpu_lazy_ms"] / out["learned_batched_ms"]
+    if args.batch_graphs > 0:
+        out["mixed_batch"] = mixed_batch_leg(gc, args.batch_graphs)
+    return out
+
+
+def mixed_batch_leg(gc, count):
+    """The serving-style workload: `count` BA/R-MAT graphs, n log-uniform in
+    [1e4, 5e5], degree 4-32, k in 5-50, solved (a) in one persistent launch
+    replayed from a captured CUDA graph with autotuned lanes/list size and (b)
+    one graph at a time through gc_greedy; groups must be identical."""
+    from paper_1710_01144_gb300 import autotune, graphgen
+
+    items = graphgen.batch_params(count, seed=1)
+    graphs = [graphgen.batch_graph(it) for it in items]
+    ks = np.array([min(it.k, rp.size - 1) for it, (rp, _) in zip(items, graphs)], dtype=np.int32)
+    sizes = [rp.size - 1 for rp, _ in graphs]
+    res = {"graphs": count, "vertices": int(sum(sizes)), "entries": int(sum(ci.size for _, ci in graphs)),
+           "sum_k": int(ks.sum())}
+    with gc.Batch(graphs) as B:
+        space = [{"lanes": 64, "A": 4096}, {"lanes": 32, "A": 1024}]
+        best, entry = autotune.tune_batch(B, ks, sizes, reps=1, space=space)
+        res["autotuned"] = best
+        res["autotune_trials"] = entry.get("trials")
+        # first call records the CUDA graph, the timed call replays it
+        B.greedy(ks, active_target=best["A"], lanes=best["lanes"], capture=True)
+        ms, (groups, far, st) = _best_ms(
+            lambda: B.greedy(ks, active_target=best["A"], lanes=best["lanes"], capture=True), 1)
+        res["batched_ms"] = ms
+        res["graph_replay"] = bool(st["graph_replay"])
+        res["iterations"] = int(st["steps"])
+    seq = 0.0
+    same = True
+    for i, ((rp, ci), k) in enumerate(zip(graphs, ks)):
+        with gc.Graph(rp, ci) as G:
+            ms, (g, f, _) = _best_ms(lambda: G.greedy(int(k)), 1)
+        seq += ms
+        same = same and np.array_equal(g, groups[i]) and f == far[i]
+    res["sequential_gc_greedy_ms"] = seq
+    res["groups_identical"] = bool(same)
+    res["speedup_batched_vs_sequential"] = seq / res["batched_ms"]
+    return res
 
 
 def cpu_baseline(rp, ci, k, grp_gpu, f_gpu):

@@ -10,15 +10,16 @@
 // Phases (bounded grid barriers between them):
 //   P0  lower bounds LB(v) and, per graph, the vertex v_a of smallest bound
 //   P1  BFS from all v_a; per-graph farness f_a
-//   P2  per graph (one CTA): every v with LB(v) <= f_a evaluated by the
-//       64-lane BFS in farness mode with per-graph cuts; s0 = argmin (f, id)
+//   P2  every v with LB(v) <= f_a evaluated by the 64-lane BFS in farness
+//       mode with per-graph cuts (graph-aligned batches from a dynamic task
+//       counter over all CTAs); per graph s0 = argmin (f, id)
 //   P3  BFS from all s0 (d_S), per-graph farness, neighbour bound mx
 //   P4  round 1: every candidate of every graph, graph-aligned 64-lane batches
 //       from a dynamic task counter; per-graph argmax; picks; BFS from picks
 //   P5  per graph (one CTA): active list of the largest bounds
-//   P6  iterations until every graph has its k picks: per graph one lazy step
-//       (fold, decide, select 64); one grid BFS from all picks accepted in the
-//       iteration; per graph one 64-lane evaluation.
+//   P6  lazy rounds: each CTA runs its graphs' rounds to completion -- fold,
+//       decide, select 64, evaluate them (64-lane BFS), and on acceptance a
+//       CTA-local pruned BFS from the pick -- so no graph waits for another.
 //   P7  check: one BFS from every graph's whole group; each graph's farness
 //       must equal f(s0) minus the sum of its accepted gains.
 #include <limits.h>
@@ -79,6 +80,8 @@ struct BatchArgs {
   int32_t *picks;
   long long *pgain;
   int32_t *seeds;  // [max(count, sum k)]
+  int32_t *slist;  // round-0 survivors, graph-aligned [N]
+  int32_t *scount, *tstart;  // per-graph survivor counts, task prefix [count+1]
   BatchCtl *ctl;
   GainCtl *gctl;
   unsigned long long tns;
@@ -134,9 +137,8 @@ static __device__ int cta_argmin_f0(const BatchArgs &a, int g) {
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArgs a) {
-  __shared__ int32_t s_c[kLanes + kBatchThreads];
   __shared__ long long s_out[kLanes];
-  __shared__ int s_cn, s_task;
+  __shared__ int s_task;
   __shared__ int s_scan[33];
   __shared__ unsigned long long s_red[32];
   __shared__ long long s_ll[32];
@@ -182,7 +184,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   seg_sum_dist(a, a.fa);
   if (b == 0 && tid == 0) a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
   if (!bsync(a)) return;
-  // ---- P2: round-0 survivors per graph (one CTA per graph) ----
+  // ---- P2: round-0 survivors (every v with LB(v) <= f_a) ----
+  // P2a, one CTA per graph: compact the graph's survivors into its own region
+  // of slist (graph-aligned, so batches never mix graphs)
   for (int g = b; g < a.count; g += G) {
     const int o = a.off[g], n = a.ng[g];
     const long long fa = a.fa[g];
@@ -191,10 +195,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
       a.bestf[g] = fa;
       a.f0[va] = fa;
       a.key[va] = LLONG_MIN;
-      s_cn = 0;
     }
     __syncthreads();
-    const LaneGraphs lg{a.gid, a.ng, a.bestf};
+    int carry = 0;
     for (int base = 0; base < n; base += T) {
       const int i = base + tid;
       int flag = 0;
@@ -204,30 +207,53 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
       }
       int total;
       const int pos = block_excl_scan(flag, s_scan, &total);
-      if (flag) s_c[s_cn + pos] = o + i;
+      if (flag) a.slist[o + carry + pos] = o + i;
+      carry += total;
+    }
+    if (tid == 0) a.scount[g] = carry;
+    __syncthreads();
+  }
+  if (!bsync(a)) return;
+  // P2b: task prefix over graphs (64 survivors per task)
+  if (b == 0 && tid == 0) {
+    int acc = 0;
+    for (int g = 0; g < a.count; ++g) {
+      a.tstart[g] = acc;
+      acc += (a.scount[g] + kLanes - 1) / kLanes;
+    }
+    a.tstart[a.count] = acc;
+    a.ctl->task = 0;
+  }
+  if (!bsync(a)) return;
+  // P2c: every CTA takes survivor batches from a dynamic counter
+  {
+    const int n_tasks = a.tstart[a.count];
+    const LaneGraphs lg{a.gid, a.ng, a.bestf};
+    for (;;) {
+      if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
       __syncthreads();
-      if (tid == 0) s_cn += total;
+      const int t = s_task;
       __syncthreads();
-      while (s_cn >= kLanes) {
-        cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, s_c, kLanes, s_out, myws, a.gctl, nullptr, lg, cnt, o);
-        if (tid < kLanes) a.f0[s_c[tid]] = s_out[tid];
-        __syncthreads();
-        const int rest = s_cn - kLanes;  // < T: at most one entry per thread
-        const int t = tid < rest ? s_c[kLanes + tid] : 0;
-        __syncthreads();
-        if (tid < rest) s_c[tid] = t;
-        if (tid == 0) s_cn = rest;
-        __syncthreads();
+      if (t >= n_tasks) break;
+      int lo = 0, hi = a.count - 1;  // graph with tstart[g] <= t < tstart[g+1] (non-empty)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.tstart[mid] <= t) lo = mid;
+        else hi = mid - 1;
       }
-    }
-    if (s_cn > 0) {
-      const int nl = s_cn;
-      cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, s_c, nl, s_out, myws, a.gctl, nullptr, lg, cnt, o);
-      if (tid < nl) a.f0[s_c[tid]] = s_out[tid];
+      const int g = lo, o = a.off[g], first = (t - a.tstart[g]) * kLanes;
+      const int nl = min(kLanes, a.scount[g] - first);
+      cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, a.slist + o + first, nl, s_out, myws, a.gctl, nullptr,
+                                   lg, cnt, o);
+      if (tid < nl) a.f0[a.slist[o + first + tid]] = s_out[tid];
       __syncthreads();
     }
+  }
+  if (!bsync(a)) return;
+  // P2d, one CTA per graph: s0 = argmin (f, id) over the exact farness values
+  for (int g = b; g < a.count; g += G) {
     const int s0 = cta_argmin_f0(a, g);
-    if (tid == 0) a.seeds[g] = o + (s0 >= 0 ? s0 : 0);
+    if (tid == 0) a.seeds[g] = a.off[g] + (s0 >= 0 ? s0 : 0);
     __syncthreads();
   }
   if (!bsync(a)) return;
@@ -402,61 +428,60 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     __syncthreads();
   }
   if (!bsync(a)) return;
-  // ---- P6: lazy iterations for every graph ----
-  for (long long it = 0; it < (1ll << 24); ++it) {
+  // ---- P6: lazy rounds; each CTA runs its graphs to completion (no grid
+  // barrier: a graph never waits for another graph's step) ----
+  {
+    __shared__ int s_stop;
     for (int g = b; g < a.count; g += G) {
       LazyCtl *lc = &a.lc[g];
-      if (lc->round >= a.kk[g]) continue;
-      const bool full = a.full[g] != 0;
-      const int32_t *act = full ? a.iota + a.off[g] : a.act + (size_t)g * a.A;
-      const int m = full ? a.ng[g] : a.act_n[g];
-      if (full && tid == 0) lc->theta = LLONG_MIN;
-      __syncthreads();
-      lazy_cta0_step(act, m, a.ub, a.stamp, lc, nullptr, lc->pad != 0, nullptr, 0);
-      __syncthreads();
-      const int dec = *(volatile int32_t *)&lc->dec;
-      if (tid == 0) {
-        lc->pad = dec == 0;  // fold the batch next time
-        if (dec == 1) {
+      const int o = a.off[g];
+      for (;;) {
+        if (tid == 0) s_stop = (lc->round >= a.kk[g]) || (*(volatile int32_t *)&a.ctl->err != 0);
+        __syncthreads();
+        if (s_stop) break;
+        const bool full = a.full[g] != 0;
+        const int32_t *act = full ? a.iota + o : a.act + (size_t)g * a.A;
+        const int m = full ? a.ng[g] : a.act_n[g];
+        if (full && tid == 0) lc->theta = LLONG_MIN;
+        __syncthreads();
+        lazy_cta0_step(act, m, a.ub, a.stamp, lc, nullptr, lc->pad != 0, nullptr, 0);
+        __syncthreads();
+        const int dec = *(volatile int32_t *)&lc->dec;
+        if (dec == 0) {  // evaluate the selected batch
+          cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
+                                    LaneGraphs(), cnt, o);
+          if (tid == 0) lc->pad = 1;  // fold it next step
+        } else if (dec == 1) {  // accept: record, then update d_S from the pick
+          const int pick = lc->best_id;
+          const long long gain = lc->best_gain;
           const int r = lc->round;
-          a.picks[(size_t)g * a.kmax + r] = lc->best_id;
-          a.pgain[(size_t)g * a.kmax + r] = lc->best_gain;
-          a.ub[lc->best_id] = -1;
-          a.seeds[atomicAdd(&a.ctl->nseeds, 1)] = lc->best_id;
-          lc->last_gain = lc->best_gain;
-          lc->best_id = -1;
-          lc->best_gain = -1;
-          lc->round = r + 1;
-          if (r + 1 >= a.kk[g]) atomicSub(&a.ctl->remaining, 1);
-        } else if (dec == 2) {
-          a.full[g] = 1;  // the list cannot certify: use every candidate of the graph
+          __syncthreads();
+          const long long decr = cta_relabel_bfs(a.rp, a.ci, a.dS, pick, myws.qv0, myws.qv1);
+          if (tid == 0) {
+            if (decr != gain) check_fail(a.ctl, 6, g, gain, decr);
+            a.picks[(size_t)g * a.kmax + r] = pick;
+            a.pgain[(size_t)g * a.kmax + r] = gain;
+            a.ub[pick] = -1;
+            lc->last_gain = gain;
+            lc->best_id = -1;
+            lc->best_gain = -1;
+            lc->pad = 0;
+            lc->round = r + 1;
+            lc->steps += 0;
+          }
+        } else {  // the list cannot certify: use every candidate of the graph
+          if (tid == 0) {
+            a.full[g] = 1;
+            lc->pad = 0;
+          }
         }
+        if (tid == 0 && global_ns() - t_start > 6ull * a.tns) atomicExch(&a.ctl->err, GC_ETIMEOUT);
+        __syncthreads();
       }
-      __syncthreads();
+      if (tid == 0) atomicAdd((unsigned long long *)&a.ctl->iterations, (unsigned long long)lc->steps);
     }
-    if (!bsync(a)) return;
-    if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
-                          a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
-                          &a.ctl->err, a.tns))
-      return;
-    for (int g = b; g < a.count; g += G) {
-      LazyCtl *lc = &a.lc[g];
-      if (lc->round >= a.kk[g] || *(volatile int32_t *)&lc->dec != 0) continue;
-      cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
-                                LaneGraphs(), cnt, a.off[g]);
-    }
-    if (!bsync(a)) return;
-    const int remaining = *(volatile int32_t *)&a.ctl->remaining;
-    // the whole lazy phase is bounded too: 6 x the per-wait limit of wall time
-    if (b == 0 && tid == 0 && global_ns() - t_start > 6ull * a.tns) atomicExch(&a.ctl->err, GC_ETIMEOUT);
-    if (b == 0 && tid == 0) {
-      a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
-      a.ctl->nseeds = 0;
-      a.ctl->iterations = it + 1;
-    }
-    if (!bsync(a)) return;
-    if (remaining == 0) break;
   }
+  if (!bsync(a)) return;
   // ---- P7: check every group's farness with one BFS ----
   for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
   if (b == 0) {
@@ -558,6 +583,7 @@ struct gc_batch {
   long long *pgain = nullptr;
   int32_t *seeds = nullptr;
   int32_t seeds_cap = 0;
+  int32_t *slist = nullptr, *scount = nullptr, *tstart = nullptr;
   BatchCtl *ctl = nullptr, *h_ctl = nullptr;
   GainCtl *gctl = nullptr, *h_gctl = nullptr;
   // captured launch sequence
@@ -580,7 +606,8 @@ static void batch_release(gc_batch *b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
-                 b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl};
+                 b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
+                 b->scount, b->tstart};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -660,6 +687,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
             balloc(&b->farness, (size_t)count) && balloc(&b->bestf, (size_t)count) &&
             balloc(&b->lc, (size_t)count) && balloc(&b->act_n, (size_t)count) && balloc(&b->full, (size_t)count) &&
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
+            balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
   int64_t *d_eoff = nullptr;
@@ -828,6 +856,9 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.picks = b->picks;
   a.pgain = b->pgain;
   a.seeds = b->seeds;
+  a.slist = b->slist;
+  a.scount = b->scount;
+  a.tstart = b->tstart;
   a.ctl = b->ctl;
   a.gctl = b->gctl;
   a.tns = (unsigned long long)((opts.timeout_ms > 0 ? opts.timeout_ms : 10000) * 1000000LL);

@@ -234,4 +234,79 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
   __syncthreads();
 }
 
+// CTA-local pruned relabel BFS from seed s (the pruned SSSP of Sec. 4.1 that
+// turns d_S into min(d_S, d(s, .))): only vertices whose label improves are
+// relabelled and expanded.  q0/q1 are queues of at least the component's size.
+// Returns the farness decrease sum(old - new) (every thread gets it).
+static __device__ __noinline__ long long cta_relabel_bfs(const int32_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci, int32_t *dist, int s,
+                                                        int32_t *q0, int32_t *q1) {
+  constexpr int T = kGainThreads;
+  __shared__ int s_off[T + 1];
+  __shared__ int s_rs[T];
+  __shared__ int s_scan[33];
+  __shared__ int s_qn, s_F;
+  __shared__ long long s_red[32];
+  const int tid = threadIdx.x;
+  long long dec = 0;
+  if (tid == 0) {
+    s_qn = 0;
+    s_F = 0;
+    const int old = dist[s];
+    if (old > 0) {
+      dec = old;
+      dist[s] = 0;
+      q0[0] = s;
+      s_F = 1;
+    }
+  }
+  __syncthreads();
+  int32_t *qc = q0, *qn = q1;
+  for (int L = 0; s_F > 0; ++L) {
+    const int F = s_F;
+    const int nl = L + 1;
+    for (int chunk = 0; chunk < F; chunk += T) {
+      const int i = chunk + tid;
+      int deg = 0, rs = 0;
+      if (i < F) {
+        const int u = qc[i];
+        rs = rp[u];
+        deg = rp[u + 1] - rs;
+      }
+      int total;
+      const int off = block_excl_scan(deg, s_scan, &total);
+      s_off[tid] = off;
+      s_rs[tid] = rs;
+      if (tid == T - 1) s_off[T] = total;
+      __syncthreads();
+      for (int e = tid; e < total; e += T) {
+        int lo = 0, hi = T - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        const int w = ci[s_rs[lo] + (e - s_off[lo])];
+        if (nl < dist[w]) {
+          const int old = atomicMin(&dist[w], nl);
+          if (old > nl) {
+            dec += (long long)(old - nl);
+            qn[atomicAdd(&s_qn, 1)] = w;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      s_F = s_qn;
+      s_qn = 0;
+    }
+    __syncthreads();
+    int32_t *t = qc;
+    qc = qn;
+    qn = t;
+  }
+  return block_sum(dec, s_red);
+}
+
 }  // namespace gc

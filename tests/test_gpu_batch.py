@@ -82,3 +82,18 @@ def test_batch_errors(gcm):
         with pytest.raises(gcm.GcError) as e:
             B.greedy([1, 1])
         assert e.value.code == gcm.GC_EDISCONNECTED
+
+
+def test_autotune_batch(gcm, tmp_path):
+    from paper_1710_01144_gb300 import autotune
+
+    graphs, ks = mixed_batch()
+    sizes = [rp.size - 1 for rp, _ in graphs]
+    cache = str(tmp_path / "tune.json")
+    space = [{"lanes": 64, "A": 1024}, {"lanes": 16, "A": 4}]
+    with gcm.Batch(graphs) as B:
+        best, entry = autotune.tune_batch(B, ks, sizes, reps=1, cache=cache, space=space)
+        assert best in [{"lanes": s["lanes"], "A": s["A"]} for s in space]
+        assert len(entry["trials"]) == 2
+        again, _ = autotune.tune_batch(B, ks, sizes, cache=cache, space=space)  # from the cache
+        assert again == best
