@@ -1,0 +1,76 @@
+"""Parity at the full sizes of the evaluation workloads where the plain oracle
+cannot run the whole greedy: sampled outputs the oracle computes one by one
+(exact gains by full BFS, group farness), plus the full greedy where CPU
+Greedy++ finishes in reasonable time."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_01144_gb300 import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gcm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1710_01144_gb300 import build, gc
+
+    build.build()
+    return gc
+
+
+def _sampled(gcm, rp, ci, seed, n_group, n_cand):
+    n = rp.size - 1
+    rng = np.random.default_rng(seed)
+    deg = np.diff(rp)
+    # groups mixing high-degree and random vertices, candidates spread over the graph
+    S = np.unique(np.concatenate([np.argsort(-deg)[:2], rng.choice(n, size=n_group, replace=False)])).astype(np.int32)
+    cand = np.concatenate([rng.choice(n, size=n_cand, replace=False), S[:2], np.argsort(-deg)[2:6]]).astype(np.int32)
+    with gcm.Graph(rp, ci) as G:
+        assert G.farness(S) == oracle.farness(rp, ci, S)
+        got = G.gains(S, cand)
+    np.testing.assert_array_equal(got, oracle.gains(rp, ci, S, cand))
+
+
+def test_road_grid_2048_sampled_gains(gcm):
+    """Road-like 2048 x 2048 grid (20% of edges deleted, 1% diagonals, LCC):
+    deep BFS (thousands of levels) through the 64-lane kernel."""
+    rp, ci = graphgen.road_grid_2048()
+    assert rp.size - 1 > 4_000_000
+    _sampled(gcm, rp, ci, seed=3, n_group=6, n_cand=58)
+
+
+def test_road_grid_192_greedy(gcm):
+    """A 192 x 192 road-like grid (deep BFS, large pruned regions), whole
+    greedy (k=12) against CPU Greedy++."""
+    rp, ci = graphgen.grid_road(192, 192, 0.2, 0.01, 1)
+    grp, ft, _, _ = oracle.greedypp(rp, ci, 12)
+    with gcm.Graph(rp, ci) as G:
+        got, f, _ = G.greedy(12)
+    np.testing.assert_array_equal(got, grp)
+    assert f == ft[-1]
+
+
+def test_rmat24_sampled_gains(gcm):
+    """R-MAT scale 24, edge factor 16 (about 10M vertices, 0.5G entries)."""
+    rp, ci = graphgen.rmat_s24_ef16()
+    assert rp.size - 1 > 5_000_000
+    _sampled(gcm, rp, ci, seed=5, n_group=4, n_cand=60)
+
+
+def test_mixed_batch_subset_vs_oracle(gcm):
+    """The 48 smallest graphs of the mixed 256-graph workload, solved in one
+    batched launch, against CPU Greedy++ graph by graph."""
+    items = sorted(graphgen.batch_params(256, seed=1), key=lambda it: it.n_target)[:48]
+    graphs = [graphgen.batch_graph(it) for it in items]
+    ks = [min(it.k, rp.size - 1) for it, (rp, _) in zip(items, graphs)]
+    with gcm.Batch(graphs) as B:
+        groups, far, _ = B.greedy(ks, capture=True)
+    for (rp, ci), k, got, f in zip(graphs, ks, groups, far):
+        g, ft, _, _ = oracle.greedypp(rp, ci, k)
+        np.testing.assert_array_equal(got, g)
+        assert f == ft[-1]
