@@ -96,7 +96,12 @@ typedef struct gc_opts {
                               negative = none */
   uint32_t flags;          /* GC_OPT_NO_EXPAND_BOUND: do not skip expansions by the
                               neighbour bound (work only; the group is the same) */
-  int32_t reserved[3];
+  int32_t spread_max_gain; /* step_mode 3: a step whose largest bound is at most this
+                              evaluates one candidate per CTA (no grid barrier
+                              inside); 0 or negative = always grid-wide */
+  int32_t local_update_max_gain; /* step_mode 3: a pick whose gain is at most this
+                              updates d_S on one CTA; 0 or negative = never */
+  int32_t reserved[1];
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */

@@ -449,6 +449,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const bool grid_steps = opts.step_mode == 2;
   const bool persistent = opts.step_mode == 0 || opts.step_mode == 3;
   const int32_t heavy = opts.round1_heavy < 0 ? 0 : (opts.round1_heavy == 0 ? 1024 : opts.round1_heavy);
+  // measured on R-MAT graphs: the grid-wide forms win, so both default off
+  const long long spread_max = opts.spread_max_gain <= 0 ? -1 : opts.spread_max_gain;
+  const long long local_max = opts.local_update_max_gain <= 0 ? -1 : opts.local_update_max_gain;
   int64_t lazy_steps = 0, lazy_evals = 0, lazy_launches = 0;
   double lazy_ms[3] = {0, 0, 0};
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
@@ -468,7 +471,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
-        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill));
+        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill, spread_max,
+                                  local_max));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
         GC_TRY(read_ctl(g));

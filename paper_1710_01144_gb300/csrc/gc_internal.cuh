@@ -254,7 +254,11 @@ int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 int launch_max_nbr(gc_graph *g);
 int launch_active_theta(gc_graph *g);
 // prop: proposal weights (nullptr = plain bound order); fill: lanes it chooses
-int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill);
+// spread_max: largest bound of a step evaluated one candidate per CTA (above
+// it, one grid-wide 64-lane batch); local_max: largest pick gain whose d_S
+// update runs on one CTA (above it, grid-wide)
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
+                       long long spread_max, long long local_max);
 int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 

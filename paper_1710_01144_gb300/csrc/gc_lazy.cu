@@ -19,6 +19,9 @@
 // Then every CTA runs the 64-lane pruned BFS on that batch (grid_gain_batch).
 // On acceptance every CTA runs the relabel BFS from the pick (the pruned SSSP
 // that turns d_S into min(d_S, d(pick, .)), Sec. 4.1) and the round advances.
+#include <algorithm>
+
+#include "gc_cta.cuh"
 #include "gc_lazy.cuh"
 
 namespace gc {
@@ -29,9 +32,13 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                   int32_t k, int32_t *picks, long long *pgain, long long *pdec, unsigned char *ws,
                   int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
-                  int32_t fill, const long long *__restrict__ two_hop, float *score) {
+                  int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
+                  long long spread_max, long long local_max) {
+  __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const GainWs myws = gain_ws(ws, ws_stride, n, blockIdx.x);  // this CTA's own workspace
+  GainCounters cnt;
   unsigned long long t0 = timer ? global_ns() : 0, t1;
   bool fold = false;
   for (;;) {
@@ -52,8 +59,21 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
     const int dec = *(volatile int32_t *)&lc->dec;
     if (dec == 2) break;  // the host lowers theta and relaunches
     if (dec == 0) {
-      bool ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, goff, gg,
-                                           gctl, &lc->bar, &lc->err, tns, mx);
+      // small searches: one candidate per CTA, no barrier inside; large ones:
+      // the whole grid on one 64-lane batch.  Every CTA sees the same bounds.
+      const int ns = *(volatile int32_t *)&lc->n_sel;
+      long long umax = 0;
+      for (int j = 0; j < ns; ++j) umax = max(umax, ub[lc->sel[j]]);
+      bool ok;
+      if (umax <= spread_max) {
+        if (blockIdx.x < ns)
+          cta_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel + blockIdx.x, 1, lc->gsel + blockIdx.x, myws, gctl, mx,
+                                    LaneGraphs(), cnt);
+        ok = true;
+      } else {
+        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, goff, gg, gctl,
+                                        &lc->bar, &lc->err, tns, mx);
+      }
       ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
       if (!ok) break;
       if (timer) {
@@ -73,8 +93,16 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
       lc->decrease = 0;
     }
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
-    bool ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease,
-                               nullptr, goff, gg->blk_tot, &lc->bar, &lc->err, tns);
+    bool ok = true;
+    if (*(volatile long long *)&lc->best_gain <= local_max) {  // small region: CTA 0 alone
+      if (blockIdx.x == 0) {
+        const long long d = cta_relabel_bfs(rp, ci, dS, *(volatile int32_t *)&lc->best_id, myws.qv0, myws.qv1);
+        if (threadIdx.x == 0) lc->decrease = (unsigned long long)d;
+      }
+    } else {
+      ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease, nullptr,
+                            goff, gg->blk_tot, &lc->bar, &lc->err, tns);
+    }
     ok = ok && grid_sync(&lc->bar, &lc->err, tns);
     if (!ok) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -92,6 +120,18 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
       lc->ns_update += t1 - t0;
       t0 = t1;
     }
+  }
+  // work counters of the spread evaluations
+  const u64 c_scalar = block_sum(cnt.scalar, s_red), c_union = block_sum(cnt.uni, s_red);
+  const u64 c_front = block_sum(cnt.front, s_red), c_push = block_sum(cnt.push, s_red);
+  if (threadIdx.x == 0 && cnt.batches) {
+    atomicAdd(&gctl->edges_scalar, c_scalar);
+    atomicAdd(&gctl->edges_union, c_union);
+    atomicAdd(&gctl->frontier, c_front);
+    atomicAdd(&gctl->pushes, c_push);
+    atomicAdd(&gctl->levels, cnt.levels);
+    atomicAdd(&gctl->batches, cnt.batches);
+    atomicAdd(&gctl->lanes, cnt.lanes);
   }
 }
 
@@ -117,7 +157,8 @@ int launch_active_theta(gc_graph *g) {
   return GC_OK;
 }
 
-int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill) {
+int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
+                       long long spread_max, long long local_max) {
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
   int32_t *dS = g->dS;
@@ -137,13 +178,16 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   const int32_t *mx = g->mx;
   const long long *two_hop = g->two_hop;
   float *score = g->score;
+  size_t ws_stride = g->ws_stride;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
-                  (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score};
+                  (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
+                  (void *)&ws_stride, (void *)&spread_max, (void *)&local_max};
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(g->lazy_ctas), dim3(kGridGainThreads),
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(std::min(g->lazy_ctas, g->ws_count)),
+                                      dim3(kGridGainThreads),
                                       args, 0, g->stream));
   return GC_OK;
 }
