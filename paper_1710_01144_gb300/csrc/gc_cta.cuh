@@ -130,11 +130,13 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
         const int u = qcur_v[i];
         m = qcur_m[i];
         if (MODE == kModeFarness) m &= s_alive;
+        // the row bounds and the neighbour bound are loaded together
+        const int r0 = rp[u], r1 = rp[u + 1];
         // no neighbour of u can still be claimed: skip the scan
         if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
         if (m) {
-          rs = rp[u];
-          deg = rp[u + 1] - rs;
+          rs = r0;
+          deg = r1 - r0;
         }
         cnt.uni += (u64)deg;
         cnt.scalar += (u64)__popcll(m) * (u64)deg;
@@ -147,35 +149,56 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       s_m[tid] = m;
       if (tid == T - 1) s_off[T] = total;
       __syncthreads();
-      for (int e = tid; e < total; e += T) {
-        int lo = 0, hi = T - 1;  // largest j with s_off[j] <= e (its row is non-empty)
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= e) lo = mid;
-          else hi = mid - 1;
+      // kEdgeIlp adjacency entries per thread are in flight at once: the
+      // column, d_S, visited-word loads and the claiming atomics of
+      // independent entries are issued before any result is used.
+      for (int e0 = tid; e0 < total; e0 += kEdgeIlp * T) {
+        int w[kEdgeIlp], sl[kEdgeIlp];
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) {
+          const int e = e0 + k * T;
+          w[k] = -1;
+          sl[k] = 0;
+          if (e < total) {
+            int lo = 0, hi = T - 1;  // largest j with s_off[j] <= e (its row is non-empty)
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (s_off[mid] <= e) lo = mid;
+              else hi = mid - 1;
+            }
+            sl[k] = lo;
+            w[k] = ci[s_rs[lo] + (e - s_off[lo])];
+          }
         }
-        const int w = ci[s_rs[lo] + (e - s_off[lo])];
-        int dw = 0;
-        if (MODE == kModeGain) {
-          dw = dS[w];
-          if (dw <= nlev) continue;  // pruned: w cannot be strictly closer to v than to S
+        int dw[kEdgeIlp];
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) dw[k] = (MODE == kModeGain && w[k] >= 0) ? dS[w[k]] : 0;
+        u64 nb[kEdgeIlp];
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) {
+          // pruned unless w is strictly closer to the lane's candidate than to S
+          const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
+          nb[k] = live ? (s_m[sl[k]] & ~ws.vis[w[k] - voff]) : 0ull;
         }
-        const u64 nb = s_m[lo] & ~ws.vis[w - voff];
-        if (!nb) continue;
-        const u64 old = atomicOr(&ws.nxt[w - voff], nb);
-        u64 won = nb & ~old;
-        if (won) {
-          const u64 wt = MODE == kModeGain ? (u64)(dw - nlev) : (u64)nlev;
-          do {
-            const int j = __ffsll((long long)won) - 1;
-            won &= won - 1;
-            atomicAdd(&s_gain[j], wt);
-            if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
-          } while (won);
-        }
-        if (old == 0) {
-          qnxt_v[atomicAdd(&s_qn, 1)] = w;
-          ++cnt.push;
+        u64 old[kEdgeIlp];
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) old[k] = nb[k] ? atomicOr(&ws.nxt[w[k] - voff], nb[k]) : ~0ull;
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) {
+          u64 won = nb[k] & ~old[k];
+          if (won) {
+            const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
+            do {
+              const int j = __ffsll((long long)won) - 1;
+              won &= won - 1;
+              atomicAdd(&s_gain[j], wt);
+              if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
+            } while (won);
+          }
+          if (old[k] == 0) {
+            qnxt_v[atomicAdd(&s_qn, 1)] = w[k];
+            ++cnt.push;
+          }
         }
       }
       __syncthreads();

@@ -15,6 +15,7 @@ namespace gc {
 constexpr int32_t kInf = 0x3fffffff;  // "unreached" distance (d + 1 cannot overflow)
 constexpr int kLanes = 64;            // candidates per bit-parallel batch (one uint64 word)
 constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
+constexpr int kEdgeIlp = 4;           // adjacency entries in flight per thread (CTA gain batch)
 constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS
 constexpr int kRedThreads = 256;      // threads per CTA of reductions / scans
 constexpr int kHistBins = 2048;       // bins of the selection histogram
