@@ -101,7 +101,9 @@ typedef struct gc_opts {
                               inside); 0 or negative = always grid-wide */
   int32_t local_update_max_gain; /* step_mode 3: a pick whose gain is at most this
                               updates d_S on one CTA; 0 or negative = never */
-  int32_t reserved[1];
+  int32_t lazy_ctas;       /* step_mode 3: CTAs of the persistent kernel (fewer
+                              CTAs make its grid barriers cheaper); 0 = one per
+                              resident slot; clamped to that */
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */
@@ -129,6 +131,19 @@ typedef struct gc_stats {
   int64_t gain_launches;   /* gain-kernel launches */
   int64_t kernel_launches; /* all kernel launches of the call */
   int64_t graph_replay;    /* gc_batch_greedy: 1 if the solve ran from a captured CUDA graph */
+  /* gc_greedy: the CTA-batched 64-lane gain kernel alone (its launches are a
+     subset of gain_launches; the grid-wide batches are the rest) */
+  int64_t gain64_launches; /* its launches */
+  double ms_gain64;        /* their summed duration (CUDA events on the launch stream) */
+  int64_t gain64_frontier; /* frontier entries they expanded */
+  int64_t gain64_edges;    /* adjacency entries they scanned */
+  int64_t gain64_pushes;   /* vertices they pushed into a next-level frontier */
+  int64_t gain64_lanes;    /* candidate lanes they processed */
+  /* gc_greedy: gain phases of the persistent lazy kernel (time: ms_lazy_gain) */
+  int64_t lazy_frontier;
+  int64_t lazy_edges;
+  int64_t lazy_pushes;
+  int64_t lazy_lanes;
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -367,12 +367,14 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   size_t ev_used = 0;
+  std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched kernel, 0 = grid-wide
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
                          int lanes) -> int {
     cudaEvent_t e0, e1;
     GC_TRY(gain_event(g, ev_used, &e0));
     GC_TRY(gain_event(g, ev_used + 1, &e1));
     ev_used += 2;
+    ev_k64.push_back(1);
     GC_CUDA(cudaEventRecord(e0, g->stream));
     GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas, lanes));
     GC_CUDA(cudaEventRecord(e1, g->stream));
@@ -384,6 +386,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(gain_event(g, ev_used, &e0));
     GC_TRY(gain_event(g, ev_used + 1, &e1));
     ev_used += 2;
+    ev_k64.push_back(0);
     GC_CUDA(cudaEventRecord(e0, g->stream));
     GC_TRY(launch_gains_grid(g, mode, cand, nl, nl_dev, out, tns));
     GC_CUDA(cudaEventRecord(e1, g->stream));
@@ -453,6 +456,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const long long spread_max = opts.spread_max_gain <= 0 ? -1 : opts.spread_max_gain;
   const long long local_max = opts.local_update_max_gain <= 0 ? -1 : opts.local_update_max_gain;
   int64_t lazy_steps = 0, lazy_evals = 0, lazy_launches = 0;
+  GainCtl lazy0, lazy1;  // gain counters around the persistent kernel
+  memset(&lazy0, 0, sizeof(lazy0));
+  memset(&lazy1, 0, sizeof(lazy1));
   double lazy_ms[3] = {0, 0, 0};
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
   gains_picked[0] = f;
@@ -469,10 +475,12 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       *g->h_lctl = init;
       GC_CUDA(cudaMemcpyAsync(g->lctl, g->h_lctl, sizeof(LazyCtl), cudaMemcpyHostToDevice, g->stream));
       int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
+      GC_TRY(read_ctl(g));
+      lazy0 = *g->h_gctl;
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
         GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill, spread_max,
-                                  local_max));
+                                  local_max, opts.lazy_ctas));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
         GC_TRY(read_ctl(g));
@@ -484,6 +492,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         if (g->h_lctl->dec != 2) return fail(GC_EINTERNAL, "persistent lazy kernel stopped early");
         target = target > (1 << 28) ? g->n : target * 4;
       }
+      lazy1 = *g->h_gctl;
       lazy_steps = g->h_lctl->steps;
       lazy_evals = g->h_lctl->evals;
       lazy_ms[0] = g->h_lctl->ns_select * 1e-6;
@@ -587,6 +596,21 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       ms_k += ms;
     }
     stats->ms_gain_kernel = ms_k;
+    for (size_t i = 0; i + 1 < ev_used; i += 2) {
+      if (!ev_k64[i / 2]) continue;
+      float ms = 0.f;
+      GC_CUDA(cudaEventElapsedTime(&ms, g->events[i], g->events[i + 1]));
+      stats->ms_gain64 += ms;
+      ++stats->gain64_launches;
+    }
+    stats->gain64_frontier = (int64_t)g->h_gctl->k_front;
+    stats->gain64_edges = (int64_t)g->h_gctl->k_union;
+    stats->gain64_pushes = (int64_t)g->h_gctl->k_push;
+    stats->gain64_lanes = (int64_t)g->h_gctl->k_lanes;
+    stats->lazy_frontier = (int64_t)(lazy1.frontier - lazy0.frontier);
+    stats->lazy_edges = (int64_t)(lazy1.edges_union - lazy0.edges_union);
+    stats->lazy_pushes = (int64_t)(lazy1.pushes - lazy0.pushes);
+    stats->lazy_lanes = (int64_t)(lazy1.lanes - lazy0.lanes);
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

@@ -15,40 +15,39 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier for cooperative launches (all CTAs co-resident).  Thread 0 of
-// each CTA arrives on bar->count; the last arrival resets the counter and bumps
-// bar->gen; the others poll bar->gen.  The poll is bounded twice: by
+// Grid barrier for cooperative launches (all CTAs co-resident).  One 32-bit
+// word per barrier: in every episode CTA 0 adds 2^31 - (G - 1) and each other
+// CTA adds 1 (G = gridDim.x), so the episode adds exactly 2^31: bit 31 of the
+// word flips at the last arrival and the low 31 bits come back to zero, ready
+// for the next episode (of any grid size).  Arrival is a release atomic by
+// thread 0, the wait an acquire poll of bit 31; the CTA barriers on both sides
+// extend the ordering to every thread.  The poll is bounded twice: by
 // `timeout_ns` of global time and by an iteration cap.  On expiry the CTA
 // records GC_ETIMEOUT in *err and the barrier returns false; every caller then
-// leaves its kernel.  Returns false as well when *err is already set.
+// leaves its kernel.  Returns false as well when *err is already set.  A word
+// left mid-episode by such an exit must be zeroed before its next launch.
 __device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
                                           unsigned long long timeout_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int *vgen = &bar->gen;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      unsigned int it = 0;
-      while (*vgen == g0) {
-        __nanosleep(40);
-        ++it;
-        if ((it & 127u) == 0 && (global_ns() - t0 > timeout_ns || it > (1u << 30))) {
-          atomicExch(err, GC_ETIMEOUT);
-          ok = 0;
-          break;
-        }
+    const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(&bar->count), "r"(add) : "memory");
+    const unsigned long long t0 = global_ns();
+    unsigned int it = 0;
+    for (;;) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
+      if ((cur ^ old) & 0x80000000u) break;
+      ++it;
+      if ((it & 127u) == 0 && (global_ns() - t0 > timeout_ns || it > (1u << 30))) {
+        atomicExch(err, GC_ETIMEOUT);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     s_ok = ok && (*(volatile int32_t *)err == 0);
   }
   __syncthreads();

@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     atomicAdd(&ctl->frontier, c_front);
     atomicAdd(&ctl->pushes, c_push);
     atomicAdd(&ctl->lanes, cnt.lanes);
+    atomicAdd(&ctl->k_front, c_front);
+    atomicAdd(&ctl->k_union, c_union);
+    atomicAdd(&ctl->k_push, c_push);
+    atomicAdd(&ctl->k_lanes, cnt.lanes);
   }
 }
 

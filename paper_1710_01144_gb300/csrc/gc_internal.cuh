@@ -23,8 +23,9 @@ constexpr int kGridGainThreads = 512; // threads per CTA of the grid-wide gain k
 constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
 
 // ----------------------------------------------------------- control words --
-// Bounded grid barrier used by cooperative kernels: arrival counter and
-// generation.  Every wait gives up after a time limit and reports GC_ETIMEOUT.
+// Bounded grid barrier used by cooperative kernels: one arrival word whose
+// bit 31 flips once per episode (`gen` is padding).  Every wait gives up
+// after a time limit and reports GC_ETIMEOUT.
 struct GridBar {
   unsigned int count;
   unsigned int gen;
@@ -55,6 +56,8 @@ struct GainCtl {
   unsigned long long frontier;      // frontier entries expanded
   unsigned long long pushes;        // vertices that entered a next frontier
   unsigned long long lanes;         // candidate lanes processed
+  // the same counters, added by the CTA-batched kernel (k_gains64) alone
+  unsigned long long k_front, k_union, k_push, k_lanes;
 };
 
 // Grid-wide gain kernel control block (zeroed before each launch).
@@ -259,7 +262,7 @@ int launch_active_theta(gc_graph *g);
 // it, one grid-wide 64-lane batch); local_max: largest pick gain whose d_S
 // update runs on one CTA (above it, grid-wide)
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       long long spread_max, long long local_max);
+                       long long spread_max, long long local_max, int ctas);
 int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 

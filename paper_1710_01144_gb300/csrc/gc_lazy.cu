@@ -158,7 +158,7 @@ int launch_active_theta(gc_graph *g) {
 }
 
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       long long spread_max, long long local_max) {
+                       long long spread_max, long long local_max, int ctas) {
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
   int32_t *dS = g->dS;
@@ -186,7 +186,9 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&spread_max, (void *)&local_max};
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(std::min(g->lazy_ctas, g->ws_count)),
+  int grid = std::min(g->lazy_ctas, g->ws_count);
+  if (ctas > 0 && ctas < grid) grid = ctas;
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
                                       dim3(kGridGainThreads),
                                       args, 0, g->stream));
   return GC_OK;

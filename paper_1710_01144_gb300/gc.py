@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("step_lanes", ctypes.c_int32), ("step_mode", ctypes.c_int32),
                 ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("spread_max_gain", ctypes.c_int32),
-                ("local_update_max_gain", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +61,10 @@ class Stats(ctypes.Structure):
         "pushes", "lanes", "round0_evals")] + [
         ("ms_round0", ctypes.c_double), ("ms_round1", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_gain_kernel", ctypes.c_double),
         ("ms_lazy_select", ctypes.c_double), ("ms_lazy_gain", ctypes.c_double), ("ms_lazy_update", ctypes.c_double),
-        ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("graph_replay", ctypes.c_int64)]
+        ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("graph_replay", ctypes.c_int64),
+        ("gain64_launches", ctypes.c_int64), ("ms_gain64", ctypes.c_double)] + [(n, ctypes.c_int64) for n in (
+        "gain64_frontier", "gain64_edges", "gain64_pushes", "gain64_lanes",
+        "lazy_frontier", "lazy_edges", "lazy_pushes", "lazy_lanes")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -223,7 +226,7 @@ class Graph:
     def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
-               spread_max_gain: int = 0, local_update_max_gain: int = 0):
+               spread_max_gain: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
@@ -231,6 +234,7 @@ class Graph:
         o.round1_heavy = round1_heavy
         o.flags = 0 if expand_bound else GC_OPT_NO_EXPAND_BOUND
         o.spread_max_gain, o.local_update_max_gain = spread_max_gain, local_update_max_gain
+        o.lazy_ctas = lazy_ctas
         if timeout_ms:
             o.timeout_ms = timeout_ms
         grp = np.zeros(max(int(k), 1), dtype=np.int32)
