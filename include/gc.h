@@ -103,7 +103,7 @@ typedef struct gc_opts {
                               updates d_S on one CTA; 0 or negative = never */
   int32_t lazy_ctas;       /* step_mode 3: CTAs of the persistent kernel (fewer
                               CTAs make its grid barriers cheaper); 0 = one per
-                              resident slot; clamped to that */
+                              SM; clamped to that */
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */

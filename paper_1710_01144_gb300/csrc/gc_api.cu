@@ -60,7 +60,7 @@ static void release(gc_graph *g) {
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
-                 g->two_hop, g->score, g->rec_count};
+                 g->two_hop, g->score, g->rec_count, g->akey, g->ast};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -219,8 +219,10 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   g->bfs_ctas = std::max(1, occ) * g->num_sms;
   if ((rc = grid_gain_occupancy(&occ))) return bail(rc);
   g->grid_ctas = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
+  // persistent lazy kernel: one CTA per SM (its steps are short and barrier
+  // bound; a second CTA per SM measured slower on R-MAT and grid graphs)
   if ((rc = lazy_occupancy(&occ))) return bail(rc);
-  g->lazy_ctas = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
+  g->lazy_ctas = std::min(kMaxGridCtas, std::min(std::max(1, occ), 1) * g->num_sms);
   g->red_blocks = g->num_sms * 4;
   // per-vertex arrays
   const size_t N = (size_t)n;
@@ -235,6 +237,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->goff, N + 1)) || (rc = dalloc(&g->lctl, 1)) || (rc = dalloc(&g->picks, N)) ||
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
+      (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) ||
       (rc = dalloc(&g->rec_count, 1)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
@@ -469,6 +472,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       memset(&init, 0, sizeof(init));
       init.round = r;
       init.best_id = -1;
+      init.best_pos = -1;
       init.best_gain = -1;
       init.last_gain = gains_picked[r - 1];
       init.scored_round = -1;

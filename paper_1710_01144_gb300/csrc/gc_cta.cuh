@@ -11,7 +11,8 @@ namespace gc {
 typedef unsigned long long u64;
 
 struct GainWs {
-  u64 *vis, *nxt, *qm0, *qm1;
+  LaneWords vis, nxt;  // interleaved (2n words from the workspace base)
+  u64 *qm0, *qm1;
   int32_t *qv0, *qv1, *touched;
 };
 
@@ -22,8 +23,8 @@ __device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, in
   unsigned char *p = base + stride * (size_t)idx;
   const size_t a8 = align256_((size_t)n * sizeof(u64)), a4 = align256_((size_t)n * sizeof(int32_t));
   GainWs w;
-  w.vis = (u64 *)p;
-  w.nxt = (u64 *)(p + a8);
+  w.vis.p = (u64 *)p;
+  w.nxt.p = (u64 *)p + 1;
   w.qm0 = (u64 *)(p + 2 * a8);
   w.qm1 = (u64 *)(p + 3 * a8);
   w.qv0 = (int32_t *)(p + 4 * a8);

@@ -13,7 +13,8 @@ namespace gc {
 typedef unsigned long long u64;
 
 struct GainWsG {
-  u64 *vis, *nxt, *qm0, *qm1;
+  LaneWords vis, nxt;  // interleaved (2n words from the workspace base)
+  u64 *qm0, *qm1;
   int32_t *qv0, *qv1, *touched;
 };
 
@@ -22,8 +23,8 @@ static __device__ __forceinline__ size_t al256(size_t x) { return (x + 255) & ~(
 __device__ __forceinline__ GainWsG grid_ws(unsigned char *p, int32_t n) {
   const size_t a8 = al256((size_t)n * sizeof(u64)), a4 = al256((size_t)n * sizeof(int32_t));
   GainWsG w;
-  w.vis = (u64 *)p;
-  w.nxt = (u64 *)(p + a8);
+  w.vis.p = (u64 *)p;
+  w.nxt.p = (u64 *)p + 1;
   w.qm0 = (u64 *)(p + 2 * a8);
   w.qm1 = (u64 *)(p + 3 * a8);
   w.qv0 = (int32_t *)(p + 4 * a8);

@@ -23,6 +23,14 @@ constexpr int kGridGainThreads = 512; // threads per CTA of the grid-wide gain k
 constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
 
 // ----------------------------------------------------------- control words --
+// The visited and next-level lane words of a gain workspace, interleaved: the
+// words of vertex w sit at 2w (visited) and 2w + 1 (next level), so the read of
+// one and the claiming atomic on the other touch the same 32-byte sector.
+struct LaneWords {
+  unsigned long long *p;
+  __device__ __forceinline__ unsigned long long &operator[](long long i) const { return p[2 * i]; }
+};
+
 // Bounded grid barrier used by cooperative kernels: one arrival word whose
 // bit 31 flips once per episode (`gen` is padding).  Every wait gives up
 // after a time limit and reports GC_ETIMEOUT.
@@ -91,9 +99,10 @@ struct LazyCtl {
   unsigned long long ns_select, ns_gain, ns_update;  // time in each phase (CTA 0's clock)
   long long last_gain;  // gain of the previous pick (proposal feature)
   int32_t scored_round;  // round whose proposal scores are in g->score
-  int32_t pad2;
+  int32_t best_pos;     // list position of best_id (compact keys only)
   int32_t sel[kLanes];
   long long gsel[kLanes];
+  int32_t selpos[kLanes];  // list positions of sel[] (compact keys only)
 };
 
 // Selection / reduction control block (lives across a whole greedy call).
@@ -159,6 +168,8 @@ struct gc_graph {
   long long *f0 = nullptr;     // round 0: exact f({v}) or -1
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
+  long long *akey = nullptr;   // persistent lazy kernel: ub of list entry i [n]
+  int32_t *ast = nullptr;      // persistent lazy kernel: stamp of list entry i [n]
   int32_t *bq0 = nullptr, *bq1 = nullptr;  // grid BFS queues [n]
   int32_t *blk = nullptr;                  // per-block counts / offsets
   long long *partial = nullptr;            // per-block partial reductions (x4)

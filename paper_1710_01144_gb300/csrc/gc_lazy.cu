@@ -33,9 +33,19 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                   int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
-                  long long spread_max, long long local_max) {
+                  long long spread_max, long long local_max, long long *akey, int32_t *ast) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
+  {  // compact copies of the bounds of the (new) active list, and best_id's position
+    const int b0 = *(volatile int32_t *)&lc->best_id;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+      const int v = act[i];
+      akey[i] = ub[v];
+      ast[i] = stamp[v];
+      if (v == b0) lc->best_pos = i;
+    }
+  }
+  if (!grid_sync(&lc->bar, &lc->err, tns)) return;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const GainWs myws = gain_ws(ws, ws_stride, n, blockIdx.x);  // this CTA's own workspace
   GainCounters cnt;
@@ -49,7 +59,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
       if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
     }
-    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold, prop ? score : nullptr, fill);
+    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold, prop ? score : nullptr, fill, akey, ast);
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();
@@ -109,6 +119,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
       pdec[r] = (long long)lc->decrease;
       lc->last_gain = lc->best_gain;
       ub[lc->best_id] = -1;  // a member: never a candidate again
+      const int bp = lc->best_pos;
+      if (bp >= 0 && bp < m && act[bp] == lc->best_id) akey[bp] = -1;
       lc->best_id = -1;
       lc->best_gain = -1;
       lc->rounds_done += 1;
@@ -179,12 +191,15 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   const long long *two_hop = g->two_hop;
   float *score = g->score;
   size_t ws_stride = g->ws_stride;
+  long long *akey = g->akey;
+  int32_t *ast = g->ast;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
-                  (void *)&ws_stride, (void *)&spread_max, (void *)&local_max};
+                  (void *)&ws_stride, (void *)&spread_max, (void *)&local_max, (void *)&akey,
+                  (void *)&ast};
   ++g->launches;
   int grid = std::min(g->lazy_ctas, g->ws_count);
   if (ctas > 0 && ctas < grid) grid = ctas;

@@ -81,13 +81,15 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
 }
 
 // Exact top-`need` of the list entries by key (larger first; ties by list
-// order, i.e. smaller id), written to sel[base..).  key(i, v) returns LLONG_MIN
+// order, i.e. smaller id), written to sel[base..) and, when selpos is given,
+// their list positions to selpos[base..).  key(i, v) returns LLONG_MIN
 // for entries that are not eligible; kmin/kmax/cnt describe the eligible keys.
 // Histogram passes over [kmin, kmax] fix the threshold value; every key above it
 // is taken, then keys equal to it in list order.  Returns the number taken.
 template <class KeyFn>
 static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
-                        long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist) {
+                        long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist,
+                        int32_t *selpos = nullptr) {
   __shared__ int s_scan[33];
   __shared__ int s_b;
   __shared__ long long s_ab;
@@ -163,7 +165,10 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
     const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
     const int take = gt || (eq && eq_rank < need - above);
     const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
-    if (take && base + pos < kLanes) sel[base + pos] = v;
+    if (take && base + pos < kLanes) {
+      sel[base + pos] = v;
+      if (selpos) selpos[base + pos] = i;
+    }
     eq_seen += tot_eq;
     taken += tot_take;
   }
@@ -172,16 +177,21 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
 }
 
 // CTA 0's part of a step (see the file comment).  Writes lc->dec (0 evaluate
-// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).  With a
+// lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).  With compact
+// keys (akey/ast non-null: ub and stamp of list entry i at position i, kept in
+// step with ub/stamp), every scan of the list reads contiguous words instead of
+// gathering ub[v] and stamp[v]; lc->selpos/best_pos then hold list positions.  With a
 // proposal network (score != nullptr), `fill` of the 64 lanes go to the
 // unevaluated candidates whose bound most exceeds the network's predicted
 // gain: evaluating them tightens the bounds later rounds must beat.
 static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
-                               LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill) {
+                               LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill,
+                               long long *akey = nullptr, int32_t *ast = nullptr) {
   __shared__ long long s_v[32];
   __shared__ int s_id[32];
   __shared__ long long s_ll[32];
   __shared__ unsigned int s_hist[kLazyBins];
+  __shared__ int s_bpos;
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int r = lc->round;
@@ -189,20 +199,29 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
   if (fold) {  // the batch just evaluated: exact gains become the bounds
     const int ns = lc->n_sel;
     long long bv = -1;
-    int bid = -1;
+    int bid = -1, mine = -1, mypos = -1;
     if (tid < ns) {
       const int v = lc->sel[tid];
       const long long gv = lc->gsel[tid];
       ub[v] = gv;
       stamp[v] = r;
+      if (akey) {
+        mypos = lc->selpos[tid];
+        akey[mypos] = gv;
+        ast[mypos] = r;
+      }
       bv = gv;
       bid = v;
+      mine = v;
     }
     block_argmax_all(bv, bid, s_v, s_id);
+    if (mine >= 0 && mine == bid) s_bpos = mypos;
+    __syncthreads();
     if (tid == 0) {
       if (bid >= 0 && better_max(bv, bid, lc->best_gain, lc->best_id)) {
         lc->best_gain = bv;
         lc->best_id = bid;
+        lc->best_pos = s_bpos;
       }
       lc->steps += 1;
       lc->evals += ns;
@@ -218,8 +237,8 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
   int vmax = -1;
   for (int i = tid; i < m; i += T) {
     const int v = act[i];
-    const long long u = ub[v];
-    if (u < 0 || stamp[v] == r) continue;
+    const long long u = akey ? akey[i] : ub[v];
+    if (u < 0 || (akey ? ast[i] : stamp[v]) == r) continue;
     if (better_max(u, v, umax, vmax)) {
       umax = u;
       vmax = v;
@@ -240,18 +259,22 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
   }
   // the largest bounds (all 64 lanes without a proposal)
   const int need1 = score ? kLanes - fill : kLanes;
-  auto by_bound = [=] __device__(int, int v) -> long long {
-    const long long u = ub[v];
-    return (u >= 0 && stamp[v] != r) ? u : LLONG_MIN;
+  auto by_bound = [=] __device__(int i, int v) -> long long {
+    const long long u = akey ? akey[i] : ub[v];
+    return (u >= 0 && (akey ? ast[i] : stamp[v]) != r) ? u : LLONG_MIN;
   };
-  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist);
+  int32_t *selpos = akey ? lc->selpos : nullptr;
+  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist, selpos);
   if (score && taken < kLanes && cnt > taken) {
     // mark the bound picks as evaluated in this round (their fold does it again)
-    if (tid < taken) stamp[lc->sel[tid]] = r;
+    if (tid < taken) {
+      stamp[lc->sel[tid]] = r;
+      if (akey) ast[lc->selpos[tid]] = r;
+    }
     __syncthreads();
     auto by_slack = [=] __device__(int i, int v) -> long long {
-      const long long u = ub[v];
-      if (u < 0 || stamp[v] == r) return LLONG_MIN;
+      const long long u = akey ? akey[i] : ub[v];
+      if (u < 0 || (akey ? ast[i] : stamp[v]) == r) return LLONG_MIN;
       float p = expm1f(score[i]);
       p = p < 0.f ? 0.f : (p > (float)u ? (float)u : p);
       return u - (long long)p;
@@ -267,7 +290,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     smin = block_min_ll(smin, s_ll);
     smax = block_max_ll(smax, s_ll);
     scnt = block_sum(scnt, s_ll);
-    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist);
+    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist, selpos);
   }
   // a fresh grid-batch control block for the evaluation (grid form only)
   if (gg && tid < kLanes) {
