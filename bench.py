@@ -147,36 +147,50 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-GAIN_KERNEL_SOURCES = ("gc_gain.cu", "gc_cta.cuh", "gc_device.cuh", "gc_internal.cuh")
+# sources of each profiled kernel: a committed DRAM figure is used only while
+# they are unchanged
+KERNEL_SOURCES = {
+    "k_gains64": ("gc_gain.cu", "gc_cta.cuh", "gc_device.cuh", "gc_internal.cuh"),
+    "k_lazy_rounds": ("gc_lazy.cu", "gc_lazy.cuh", "gc_grid.cuh", "gc_cta.cuh", "gc_mlp.cuh", "gc_device.cuh",
+                      "gc_internal.cuh"),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_rmat_s20_k100.txt")
 
 
-def gain_kernel_hash() -> str:
-    """Hash of the sources that make up k_gains64 (the traffic figure in the
-    committed ncu summary is only used while they are unchanged)."""
+def kernel_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for name in GAIN_KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1710_01144_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per gain-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "gain_kernel_rmat_s20_dram.txt")
-    if not os.path.exists(p):
+def profiled_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload from
+    the committed ncu summary, if it was taken on the current sources."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
     kv = {}
-    for line in open(p):
-        if "=" in line and not line.startswith("#"):
+    for line in open(TRAFFIC_FILE):
+        if "=" in line and not line.lstrip().startswith("#"):
             a, b = line.split("=", 1)
             kv[a.strip()] = b.strip()
-    if kv.get("kernel_source_sha256_16") != gain_kernel_hash():
+    if kv.get(kernel + ".source_sha256_16") != kernel_hash(kernel):
         return None
     try:
-        return float(kv["dram_bytes_per_launch_full_workload"])
+        return float(kv[kernel + ".dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def lazy_kernel_bytes(t) -> float:
+    """Algorithmic bytes of the persistent lazy kernel: its gain phases (the
+    model above), its d_S updates (row pointers 8 B per frontier entry, 4 B
+    per adjacency entry, 4 B per lowered label) and its selection passes
+    (list id, bound and stamp: 16 B per active-list entry read)."""
+    return (algorithmic_bytes(t["lazy_frontier"], t["lazy_edges"], t["lazy_pushes"], t["lazy_lanes"]) +
+            8.0 * t["lazy_upd_frontier"] + 4.0 * t["lazy_upd_edges"] + 4.0 * t["lazy_upd_relabels"] +
+            16.0 * t["lazy_sel_scanned"])
 
 
 def algorithmic_bytes(frontier, edges, pushes, lanes) -> float:
@@ -266,16 +280,22 @@ def run_gc(args):
 
     if rank == 0:
         tot = {k: sum(s[k] for s in stats) for k in stats[0]}
-        kern_ms = tot["ms_gain64"]
-        launches = tot["gain64_launches"]
-        bytes_alg = algorithmic_bytes(tot["gain64_frontier"], tot["gain64_edges"], tot["gain64_pushes"],
-                                      tot["gain64_lanes"])
-        achieved = bytes_alg / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0
-        lazy_bytes = algorithmic_bytes(tot["lazy_frontier"], tot["lazy_edges"], tot["lazy_pushes"],
-                                       tot["lazy_lanes"])
-        lazy_ms = tot["ms_lazy_gain"]
         peak, peak_kind = measured_peaks()
-        traffic = profiled_traffic()
+
+        def roof(name, bytes_alg, ms, launches):
+            achieved = bytes_alg / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+            return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(name),
+                    "algorithmic_bytes_per_launch": bytes_alg / max(launches, 1),
+                    "avg_launch_ms": ms / max(launches, 1), "launches": launches,
+                    "share_of_step": ms / sum(times)}
+
+        # the largest kernel by device time (the persistent lazy kernel), then
+        # the round-1 gain kernel
+        roof_lazy = roof("k_lazy_rounds", lazy_kernel_bytes(tot), tot["ms_lazy_kernel"], tot["lazy_launches"])
+        roof_g64 = roof("k_gains64", algorithmic_bytes(tot["gain64_frontier"], tot["gain64_edges"],
+                                                       tot["gain64_pushes"], tot["gain64_lanes"]),
+                        tot["ms_gain64"], tot["gain64_launches"])
         line = {
             "metric": METRIC,
             "value": ws * 1000.0 / t_step,
@@ -300,31 +320,8 @@ def run_gc(args):
             "ms_round1": tot["ms_round1"] / args.steps,
             "group_farness": int(f0),
             "group_prefix": [int(x) for x in grp0[:10]],
-            "roofline": {
-                "kernel": "k_gains64 (64-lane pruned multi-source BFS)",
-                "bound": "hbm",
-                "achieved": achieved,
-                "peak": peak,
-                "peak_kind": peak_kind,
-                "unit": "GB/s",
-                "frac": achieved / peak,
-                "traffic": traffic,
-                "algorithmic_bytes_per_launch": bytes_alg / max(launches, 1),
-                "avg_launch_ms": kern_ms / max(launches, 1),
-                "launches": launches,
-                "share_of_step": kern_ms / sum(times),
-            },
-            # the gain phases of the persistent lazy kernel (same byte model)
-            "roofline_lazy_gain": {
-                "kernel": "k_lazy_rounds, grid-wide 64-lane gain phases",
-                "bound": "hbm",
-                "achieved": lazy_bytes / (lazy_ms * 1e-3) / 1e9 if lazy_ms > 0 else 0.0,
-                "peak": peak,
-                "unit": "GB/s",
-                "frac": (lazy_bytes / (lazy_ms * 1e-3) / 1e9 / peak) if lazy_ms > 0 else 0.0,
-                "algorithmic_bytes_per_step": lazy_bytes / args.steps,
-                "ms_per_step": lazy_ms / args.steps,
-            },
+            "roofline": roof_lazy,
+            "roofline_gain64": roof_g64,
             "e2e": {"value": ws * 1000.0 / t_e2e, "unit": "size-%d groups/s" % args.k,
                     "ms_per_step": t_e2e,
                     "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),

@@ -144,6 +144,13 @@ typedef struct gc_stats {
   int64_t lazy_edges;
   int64_t lazy_pushes;
   int64_t lazy_lanes;
+  /* gc_greedy: the persistent lazy kernel as a whole */
+  int64_t lazy_launches;     /* its launches (1 + list rebuilds) */
+  double ms_lazy_kernel;     /* their summed duration (CUDA events on the launch stream) */
+  int64_t lazy_upd_frontier; /* d_S updates: frontier entries expanded */
+  int64_t lazy_upd_edges;    /* d_S updates: adjacency entries scanned */
+  int64_t lazy_upd_relabels; /* d_S updates: labels lowered */
+  int64_t lazy_sel_scanned;  /* selection: active-list entries read */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -370,7 +370,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   size_t ev_used = 0;
-  std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched kernel, 0 = grid-wide
+  std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
                          int lanes) -> int {
     cudaEvent_t e0, e1;
@@ -483,8 +483,15 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       lazy0 = *g->h_gctl;
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
+        cudaEvent_t le0, le1;
+        GC_TRY(gain_event(g, ev_used, &le0));
+        GC_TRY(gain_event(g, ev_used + 1, &le1));
+        ev_used += 2;
+        ev_k64.push_back(2);
+        GC_CUDA(cudaEventRecord(le0, g->stream));
         GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill, spread_max,
                                   local_max, opts.lazy_ctas));
+        GC_CUDA(cudaEventRecord(le1, g->stream));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
         GC_TRY(read_ctl(g));
@@ -593,19 +600,21 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->round0_evals = round0_evals;
     stats->ms_round0 = ms_round0;
     stats->ms_round1 = ms_round1;
-    double ms_k = 0;
     for (size_t i = 0; i + 1 < ev_used; i += 2) {
       float ms = 0.f;
       GC_CUDA(cudaEventElapsedTime(&ms, g->events[i], g->events[i + 1]));
-      ms_k += ms;
-    }
-    stats->ms_gain_kernel = ms_k;
-    for (size_t i = 0; i + 1 < ev_used; i += 2) {
-      if (!ev_k64[i / 2]) continue;
-      float ms = 0.f;
-      GC_CUDA(cudaEventElapsedTime(&ms, g->events[i], g->events[i + 1]));
-      stats->ms_gain64 += ms;
-      ++stats->gain64_launches;
+      const int kind = ev_k64[i / 2];
+      if (kind == 2) {
+        stats->ms_lazy_kernel += ms;
+        ++stats->lazy_launches;
+        continue;
+      }
+      stats->ms_gain_kernel += ms;
+      ++stats->gain_launches;
+      if (kind == 1) {
+        stats->ms_gain64 += ms;
+        ++stats->gain64_launches;
+      }
     }
     stats->gain64_frontier = (int64_t)g->h_gctl->k_front;
     stats->gain64_edges = (int64_t)g->h_gctl->k_union;
@@ -615,10 +624,13 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lazy_edges = (int64_t)(lazy1.edges_union - lazy0.edges_union);
     stats->lazy_pushes = (int64_t)(lazy1.pushes - lazy0.pushes);
     stats->lazy_lanes = (int64_t)(lazy1.lanes - lazy0.lanes);
+    stats->lazy_upd_frontier = (int64_t)g->h_lctl->upd_work[0];
+    stats->lazy_upd_edges = (int64_t)g->h_lctl->upd_work[1];
+    stats->lazy_upd_relabels = (int64_t)g->h_lctl->upd_relabels;
+    stats->lazy_sel_scanned = (int64_t)g->h_lctl->sel_scanned;
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];
-    stats->gain_launches = (int64_t)(ev_used / 2);
     stats->kernel_launches = g->launches - launches0;
     stats->ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

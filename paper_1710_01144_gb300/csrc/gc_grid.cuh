@@ -329,12 +329,14 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
 // Each level is edge-balanced like grid_gain_batch: CTA slices of the frontier
 // scan their degrees into goff (phase 1), then every CTA takes an equal slice
 // of the level's adjacency entries (phase 2), so a hub row is shared by all
-// CTAs instead of serialising one warp.
+// CTAs instead of serialising one warp.  With `work` given, CTA 0 adds the
+// frontier entries and adjacency entries of every level to work[0], work[1].
 static __device__ __forceinline__ bool grid_relabel_bfs(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
     const int32_t *seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *qsize, int32_t *levels_out,
     unsigned long long *decrease, unsigned long long *relabelled, int32_t *__restrict__ goff,
-    int32_t *blk_tot, GridBar *bar, int32_t *err, unsigned long long timeout_ns) {
+    int32_t *blk_tot, GridBar *bar, int32_t *err, unsigned long long timeout_ns,
+    unsigned long long *work = nullptr) {
   __shared__ unsigned long long sh_bfs[32];
   __shared__ int s_scan_b[33];
   __shared__ long long s_boff[kMaxGridCtas + 1];
@@ -396,6 +398,10 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
       __syncthreads();
     }
     const long long E = s_boff[G];
+    if (work && b == 0 && tid == 0) {
+      work[0] += (unsigned long long)F;
+      work[1] += (unsigned long long)E;
+    }
     const long long es = E * b / G, ee = E * (b + 1) / G;
     for (long long e0 = es + (tid & ~31); e0 < ee; e0 += T) {
       const long long e = e0 + lane;

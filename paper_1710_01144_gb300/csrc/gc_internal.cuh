@@ -103,6 +103,10 @@ struct LazyCtl {
   int32_t sel[kLanes];
   long long gsel[kLanes];
   int32_t selpos[kLanes];  // list positions of sel[] (compact keys only)
+  // work of the persistent kernel's update and selection phases
+  unsigned long long upd_work[2];  // relabel BFS: frontier entries, adjacency entries
+  unsigned long long upd_relabels; // relabel BFS: vertices whose d_S decreased
+  unsigned long long sel_scanned;  // selection: active-list entries read
 };
 
 // Selection / reduction control block (lives across a whole greedy call).

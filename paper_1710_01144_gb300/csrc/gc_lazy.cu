@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
         if (threadIdx.x == 0) lc->decrease = (unsigned long long)d;
       }
     } else {
-      ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease, nullptr,
-                            goff, gg->blk_tot, &lc->bar, &lc->err, tns);
+      ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease,
+                            &lc->upd_relabels, goff, gg->blk_tot, &lc->bar, &lc->err, tns, lc->upd_work);
     }
     ok = ok && grid_sync(&lc->bar, &lc->err, tns);
     if (!ok) break;

@@ -89,7 +89,7 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
 template <class KeyFn>
 static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
                         long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist,
-                        int32_t *selpos = nullptr) {
+                        int32_t *selpos = nullptr, unsigned long long *scanned = nullptr) {
   __shared__ int s_scan[33];
   __shared__ int s_b;
   __shared__ long long s_ab;
@@ -104,6 +104,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
       const unsigned long long span = hi - lo + 1ull;
       const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
       for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
+      if (scanned && tid == 0) *scanned += (unsigned long long)m;
       __syncthreads();
       for (int i = tid; i < m; i += T) {
         const long long k = key(i, act[i]);
@@ -151,6 +152,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
   }
   int taken = 0, eq_seen = 0;
   for (int b = 0; b < m && taken < need; b += T) {
+    if (scanned && tid == 0) *scanned += (unsigned long long)min(T, m - b);
     const int i = b + tid;
     int gt = 0, eq = 0, v = -1;
     if (i < m) {
@@ -246,6 +248,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     umin = min(umin, u);
     ++cnt;
   }
+  if (akey && tid == 0) lc->sel_scanned += (unsigned long long)m;
   block_argmax_all(umax, vmax, s_v, s_id);
   umin = block_min_ll(umin, s_ll);
   cnt = block_sum(cnt, s_ll);
@@ -264,7 +267,8 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     return (u >= 0 && (akey ? ast[i] : stamp[v]) != r) ? u : LLONG_MIN;
   };
   int32_t *selpos = akey ? lc->selpos : nullptr;
-  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist, selpos);
+  unsigned long long *scanned = akey ? &lc->sel_scanned : nullptr;
+  int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist, selpos, scanned);
   if (score && taken < kLanes && cnt > taken) {
     // mark the bound picks as evaluated in this round (their fold does it again)
     if (tid < taken) {
@@ -290,7 +294,8 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     smin = block_min_ll(smin, s_ll);
     smax = block_max_ll(smax, s_ll);
     scnt = block_sum(scnt, s_ll);
-    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist, selpos);
+    taken += cta_topk(act, m, by_slack, smin, smax, scnt, kLanes - taken, lc->sel, taken, s_hist, selpos,
+                      scanned);
   }
   // a fresh grid-batch control block for the evaluation (grid form only)
   if (gg && tid < kLanes) {

@@ -64,7 +64,9 @@ class Stats(ctypes.Structure):
         ("gain_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("graph_replay", ctypes.c_int64),
         ("gain64_launches", ctypes.c_int64), ("ms_gain64", ctypes.c_double)] + [(n, ctypes.c_int64) for n in (
         "gain64_frontier", "gain64_edges", "gain64_pushes", "gain64_lanes",
-        "lazy_frontier", "lazy_edges", "lazy_pushes", "lazy_lanes")]
+        "lazy_frontier", "lazy_edges", "lazy_pushes", "lazy_lanes", "lazy_launches")] + [
+        ("ms_lazy_kernel", ctypes.c_double)] + [(n, ctypes.c_int64) for n in (
+        "lazy_upd_frontier", "lazy_upd_edges", "lazy_upd_relabels", "lazy_sel_scanned")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
