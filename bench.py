@@ -59,6 +59,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest value of x over the ranks of the default process group
+    (x itself without one); every rank gets it."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: each of `world` replicas solves one group per
+    step, and a step takes ms_per_step (the slowest rank's time)."""
+    return world * 1000.0 / ms_per_step
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -247,11 +266,7 @@ def run_gc(args):
         assert np.array_equal(grp, grp0) and f == f0, "non-deterministic group"
     barrier()
     clocks = clk.stop()
-    t_step = sum(times) / len(times)
-    if ws > 1:
-        t = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(sum(times) / len(times), "cuda")
 
     # e2e: public API from pinned host buffers, copies inside the timed region
     trp = torch.from_numpy(rp).pin_memory()
@@ -272,11 +287,7 @@ def run_gc(args):
         e2e_t.append((time.perf_counter() - t0) * 1e3)
         assert np.array_equal(g_e, grp0) and f_e == f0
     barrier()
-    t_e2e = sum(e2e_t) / len(e2e_t)
-    if ws > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(sum(e2e_t) / len(e2e_t), "cuda")
 
     if rank == 0:
         tot = {k: sum(s[k] for s in stats) for k in stats[0]}
@@ -298,7 +309,7 @@ def run_gc(args):
                         tot["ms_gain64"], tot["gain64_launches"])
         line = {
             "metric": METRIC,
-            "value": ws * 1000.0 / t_step,
+            "value": job_value(ws, t_step),
             "unit": "size-%d groups/s" % args.k,
             "n_gpus": ws,
             "steps": args.steps,
@@ -322,7 +333,7 @@ def run_gc(args):
             "group_prefix": [int(x) for x in grp0[:10]],
             "roofline": roof_lazy,
             "roofline_gain64": roof_g64,
-            "e2e": {"value": ws * 1000.0 / t_e2e, "unit": "size-%d groups/s" % args.k,
+            "e2e": {"value": job_value(ws, t_e2e), "unit": "size-%d groups/s" % args.k,
                     "ms_per_step": t_e2e,
                     "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
                     "d2h_bytes_per_step": int(4 * args.k + 8)},
