@@ -10,35 +10,20 @@ namespace gc {
 
 typedef unsigned long long u64;
 
-struct GainWs {
-  LaneWords vis, nxt;  // interleaved (2n words from the workspace base)
-  u64 *qm0, *qm1;
-  int32_t *qv0, *qv1, *touched;
-};
-
-__host__ __device__ inline size_t align256_(size_t x) { return (x + 255) & ~(size_t)255; }
-
-
-__device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, int32_t n, int idx) {
-  unsigned char *p = base + stride * (size_t)idx;
-  const size_t a8 = align256_((size_t)n * sizeof(u64)), a4 = align256_((size_t)n * sizeof(int32_t));
-  GainWs w;
-  w.vis.p = (u64 *)p;
-  w.nxt.p = (u64 *)p + 1;
-  w.qm0 = (u64 *)(p + 2 * a8);
-  w.qm1 = (u64 *)(p + 3 * a8);
-  w.qv0 = (int32_t *)(p + 4 * a8);
-  w.qv1 = (int32_t *)(p + 4 * a8 + a4);
-  w.touched = (int32_t *)(p + 4 * a8 + 2 * a4);
-  return w;
-}
-
 struct GainCounters {
   u64 scalar = 0, uni = 0, levels = 0, batches = 0, front = 0, push = 0, lanes = 0;
 };
 
 // One batch of nl <= 64 candidates (cand[0..nl)) by the whole CTA, results to
-// out[0..nl).  The workspace's vis/nxt words are zero on entry and on exit.
+// out[0..nl).  The workspace's lane words are zero on entry and on exit.
+//
+// Lane words of vertex w: vis (every lane that has reached w) and the claims
+// of the current and the next level, nx[L & 1] and nx[(L + 1) & 1].  A lane
+// claims w at level L + 1 by setting its bit in vis with atomicOr: the bit
+// was clear exactly for the lanes that reach w first here, and those lanes
+// are then recorded in nx[(L + 1) & 1][w].  Level L + 1 expands w with the
+// lanes of that word, which the expanding thread reads and clears; so no
+// separate commit pass is needed between levels.
 template <int MODE>
 __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                int32_t n, const int32_t *__restrict__ dS,
@@ -78,13 +63,12 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
   }
   __syncthreads();
   int32_t *qcur_v = ws.qv0, *qnxt_v = ws.qv1;
-  u64 *qcur_m = ws.qm0, *qnxt_m = ws.qm1;
 
-  // level 0: lane j starts at its candidate
+  // level 0: lane j reaches its candidate
   if (tid < nl) {
     const int c = s_cand[tid];
     const u64 bit = 1ull << tid;
-    bool push = false;
+    bool reach = false;
     if (c < 0 || c >= n) {
       s_cand[tid] = -2;  // invalid id
       atomicAnd(&s_alive, ~bit);
@@ -92,36 +76,30 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       const int dc = dS[c];
       if (dc > 0) {  // v not in S: it contributes d_S[v] - 0 and expands
         s_gain[tid] = (u64)dc;
-        push = true;
+        reach = true;
       }
     } else {
       s_cnt[tid] = 1;
-      push = true;
+      reach = true;
     }
-    if (push) {
-      const u64 old = atomicOr(&ws.nxt[c - voff], bit);
-      if (old == 0) qnxt_v[atomicAdd(&s_qn, 1)] = c;
+    if (reach) {
+      const u64 ov = atomicOr(&ws.vis[c - voff], bit);
+      if (ov == 0) ws.touched[atomicAdd(&s_touched, 1)] = c;
+      const u64 on = atomicOr(&ws.nx[0][c - voff], bit);
+      if (on == 0) qcur_v[atomicAdd(&s_qn, 1)] = c;
     }
   }
   __syncthreads();
   int F = s_qn;
-  for (int i = tid; i < F; i += T) {  // commit level 0
-    const int w = qnxt_v[i];
-    const u64 m = ws.nxt[w - voff];
-    ws.nxt[w - voff] = 0;
-    ws.vis[w - voff] = m;
-    ws.touched[atomicAdd(&s_touched, 1)] = w;
-    qnxt_m[i] = m;
-  }
   __syncthreads();
   if (tid == 0) s_qn = 0;
-  { int32_t *t = qcur_v; qcur_v = qnxt_v; qnxt_v = t; }
-  { u64 *t = qcur_m; qcur_m = qnxt_m; qnxt_m = t; }
   __syncthreads();
 
   int L = 0;
   for (; F > 0; ++L) {
     const int nlev = L + 1;
+    // (selected, not indexed: a dynamic index would put ws in local memory)
+    const LaneWords cur = (L & 1) ? ws.nx[1] : ws.nx[0], nxt = (L & 1) ? ws.nx[0] : ws.nx[1];
     // ---- expand level L into level L+1 ----
     for (int chunk = 0; chunk < F; chunk += T) {
       const int i = chunk + tid;
@@ -129,9 +107,10 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       u64 m = 0;
       if (i < F) {
         const int u = qcur_v[i];
-        m = qcur_m[i];
+        // the lanes that reached u at level L; the word is free for level L+2
+        m = cur[u - voff];
+        cur[u - voff] = 0;
         if (MODE == kModeFarness) m &= s_alive;
-        // the row bounds and the neighbour bound are loaded together
         const int r0 = rp[u], r1 = rp[u + 1];
         // no neighbour of u can still be claimed: skip the scan
         if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
@@ -181,53 +160,46 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
           const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
           nb[k] = live ? (s_m[sl[k]] & ~ws.vis[w[k] - voff]) : 0ull;
         }
-        u64 old[kEdgeIlp];
+        u64 ov[kEdgeIlp];
 #pragma unroll
-        for (int k = 0; k < kEdgeIlp; ++k) old[k] = nb[k] ? atomicOr(&ws.nxt[w[k] - voff], nb[k]) : ~0ull;
+        for (int k = 0; k < kEdgeIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
 #pragma unroll
         for (int k = 0; k < kEdgeIlp; ++k) {
-          u64 won = nb[k] & ~old[k];
-          if (won) {
-            const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
-            do {
-              const int j = __ffsll((long long)won) - 1;
-              won &= won - 1;
-              atomicAdd(&s_gain[j], wt);
-              if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
-            } while (won);
-          }
-          if (old[k] == 0) {
+          u64 won = nb[k] & ~ov[k];
+          if (!won) continue;
+          if (ov[k] == 0) ws.touched[atomicAdd(&s_touched, 1)] = w[k];
+          if (atomicOr(&nxt[w[k] - voff], won) == 0) {
             qnxt_v[atomicAdd(&s_qn, 1)] = w[k];
             ++cnt.push;
           }
+          const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
+          do {
+            const int j = __ffsll((long long)won) - 1;
+            won &= won - 1;
+            atomicAdd(&s_gain[j], wt);
+            if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
+          } while (won);
         }
       }
       __syncthreads();
     }
-    // ---- commit level L+1: fold the claimed words into vis ----
     const int Fn = s_qn;
-    for (int i = tid; i < Fn; i += T) {
-      const int w = qnxt_v[i];
-      const u64 m = ws.nxt[w - voff];
-      ws.nxt[w - voff] = 0;
-      const u64 ov = ws.vis[w - voff];
-      ws.vis[w - voff] = ov | m;
-      if (ov == 0) ws.touched[atomicAdd(&s_touched, 1)] = w;
-      qnxt_m[i] = m;
-    }
-    __syncthreads();
     if (MODE == kModeFarness && tid < kLanes && ((s_alive >> tid) & 1ull)) {
       // every vertex within distance L+1 is counted; the rest are >= L+2 away
       const long long lb = (long long)s_gain[tid] + (long long)(L + 2) * (long long)(s_nlane[tid] - s_cnt[tid]);
       const long long best = lg.gid ? s_best[tid] : *(volatile long long *)&ctl->best_f;
       if (Fn > 0 && lb > best) atomicAnd(&s_alive, ~(1ull << tid));
     }
+    __syncthreads();
     if (tid == 0) s_qn = 0;
     { int32_t *t = qcur_v; qcur_v = qnxt_v; qnxt_v = t; }
-    { u64 *t = qcur_m; qcur_m = qnxt_m; qnxt_m = t; }
     F = Fn;
     __syncthreads();
-    if (MODE == kModeFarness && s_alive == 0) break;
+    if (MODE == kModeFarness && s_alive == 0) {
+      // every lane is cut: clear the claims of the frontier that is not expanded
+      for (int i = tid; i < F; i += T) nxt[qcur_v[i] - voff] = 0;
+      break;
+    }
   }
   cnt.levels += (u64)L;
   ++cnt.batches;

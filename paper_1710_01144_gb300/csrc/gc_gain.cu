@@ -13,8 +13,9 @@
 // depends only on d_S[w] > L+1, so a neighbour failing it is skipped before
 // any bitmask traffic; the frontier of level L only holds vertices with
 // d_S > L, all of which expand.  Each (vertex, lane) pair is claimed by exactly
-// one thread through atomicOr on the next-level word; that thread adds the
-// contribution d_S[w] - (L+1) to the lane's int64 gain.
+// one thread through atomicOr on the vertex's visited word; that thread adds
+// the contribution d_S[w] - (L+1) to the lane's int64 gain and records the
+// lane in w's claim word of level L+1.
 //
 // Farness mode (round 0, top-1 closeness, Sec. 3.1 / Algorithm 3): no pruning,
 // each claimed (w, lane) adds L+1 and counts one visited vertex; after every
@@ -22,9 +23,10 @@
 // farness found so far (any CTA) is cut, as BFScut does.
 //
 // Layout.  One persistent CTA per workspace; a CTA takes 64-candidate batches
-// from a global counter.  Per-CTA workspace in HBM: vis[n], nxt[n] (uint64
-// lane words, zero between batches), two frontier queues of (vertex, word) and
-// a touched list used to zero vis after the batch.  Frontier expansion is
+// from a global counter.  Per-CTA workspace in HBM: one 32-byte record of lane
+// words per vertex (visited, claims of even and of odd levels; zero between
+// batches), two frontier queues of vertex ids and a touched list used to zero
+// the visited words after the batch.  Frontier expansion is
 // edge-balanced across the CTA: a block scan of the frontier's degrees, then
 // every thread takes adjacency entries at stride blockDim and finds its
 // frontier slot by binary search, so hub rows and tiny rows share the work.
@@ -32,9 +34,7 @@
 
 namespace gc {
 
-size_t gain_ws_stride(int32_t n) {
-  return 4 * align256_((size_t)n * sizeof(u64)) + 3 * align256_((size_t)n * sizeof(int32_t));
-}
+size_t gain_ws_stride(int32_t n) { return gain_ws_bytes(n); }
 
 template <int MODE>
 __global__ void __launch_bounds__(kGainThreads, 2)

@@ -3,17 +3,19 @@
 // cooperative launch, for candidates whose searches are large -- the hubs that
 // survive the round-0 bound, and the top-bound candidates of a lazy step.
 //
-// Per level, three phases separated by bounded grid barriers:
-//   1. each CTA scans the degrees of a contiguous slice of the frontier
-//      (degree 0 for entries whose lanes are all cut), giving local offsets;
-//   2. every CTA prefix-sums the per-CTA totals, takes an equal slice of the
-//      level's adjacency entries, finds each entry's frontier slot by binary
-//      search (CTA slice, then the slice's local offsets) and claims
-//      (neighbour, lane) pairs with atomicOr on the next-level word, exactly as
-//      the CTA-per-batch kernel does; pushes are aggregated per warp;
-//   3. the next frontier is committed (visited |= claimed) grid-wide; in
-//      farness mode per-lane sums and counts are folded globally and every CTA
-//      applies the same BFScut test to its copy of the live-lane mask.
+// Per level, two phases separated by bounded grid barriers:
+//   1. each CTA takes a contiguous slice of the frontier, moves each entry's
+//      claim word (the lanes that reached it at this level) into the mask list
+//      and clears it, and scans the entries' degrees (degree 0 where no lane
+//      can claim anything), giving slice-local offsets;
+//   2. every CTA prefix-sums the per-CTA totals and takes an equal slice of
+//      the level's adjacency entries.  It locates the first frontier entry of
+//      its slice with one warp-wide search, stages the entries that cover the
+//      slice in shared memory (start, row, mask) and expands them edge by edge,
+//      claiming (neighbour, lane) pairs with atomicOr on the visited word as the
+//      CTA-per-batch kernel does; pushes are aggregated per warp.  In farness
+//      mode per-lane sums and counts are folded globally, and after the barrier
+//      every CTA applies the same BFScut test to its copy of the live-lane mask.
 // Per-lane gains accumulate in shared memory and reach global memory once per
 // CTA (gain mode) or once per level (farness mode, where the cut needs them).
 #include "gc_grid.cuh"
@@ -25,9 +27,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
     k_gains_grid(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
                  const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t nl_arg,
                  const int32_t *__restrict__ nl_dev, long long *__restrict__ out, unsigned char *ws_base,
-                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, unsigned long long timeout_ns,
-                 const int32_t *__restrict__ mx) {
-  grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, goff, ctl, gctl, &ctl->bar,
+                 unsigned long long *qm, int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl,
+                 unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
+  grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, qm, goff, ctl, gctl, &ctl->bar,
                         &ctl->err, timeout_ns, mx);
 }
 
@@ -47,13 +49,14 @@ int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, co
   const int32_t *rp = g->rp, *ci = g->ci, *dS = g->dS;
   int32_t n = g->n;
   unsigned char *ws = g->ws;
+  unsigned long long *qm = g->qm;
   int32_t *goff = g->goff;
   GridGainCtl *ctl = g->ggctl;
   GainCtl *gctl = g->gctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
   const int32_t *mx = mode == kModeGain ? g->mx : nullptr;
   void *args[] = {(void *)&rp,  (void *)&ci,   (void *)&n,   (void *)&dS,  (void *)&cand,
-                  (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&goff,
+                  (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&qm, (void *)&goff,
                   (void *)&ctl, (void *)&gctl, (void *)&tns, (void *)&mx};
   ++g->launches;
   if (mode == kModeGain)

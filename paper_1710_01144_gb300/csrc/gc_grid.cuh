@@ -12,36 +12,57 @@ namespace gc {
 
 typedef unsigned long long u64;
 
-struct GainWsG {
-  LaneWords vis, nxt;  // interleaved (2n words from the workspace base)
-  u64 *qm0, *qm1;
-  int32_t *qv0, *qv1, *touched;
-};
+constexpr int kGridIlp = 2;  // adjacency entries in flight per thread (grid forms)
 
-static __device__ __forceinline__ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-__device__ __forceinline__ GainWsG grid_ws(unsigned char *p, int32_t n) {
-  const size_t a8 = al256((size_t)n * sizeof(u64)), a4 = al256((size_t)n * sizeof(int32_t));
-  GainWsG w;
-  w.vis.p = (u64 *)p;
-  w.nxt.p = (u64 *)p + 1;
-  w.qm0 = (u64 *)(p + 2 * a8);
-  w.qm1 = (u64 *)(p + 3 * a8);
-  w.qv0 = (int32_t *)(p + 4 * a8);
-  w.qv1 = (int32_t *)(p + 4 * a8 + a4);
-  w.touched = (int32_t *)(p + 4 * a8 + 2 * a4);
-  return w;
+// Per-level frontier layout of the grid forms: CTA b owns the contiguous
+// slice [b*P, min(F, b*P + P)) of the frontier list (P = ceil(F / G)) and
+// writes the slice-local exclusive prefix of its entries' degrees to goff;
+// blkoff (shared, per CTA) is the exclusive prefix of the slices' totals.
+// Entry x then owns the global adjacency indices starting at
+// blkoff[x / P] + goff[x].  grid_find_entry returns, for one warp, the
+// largest x whose start is <= e (an entry with a non-empty range).
+static __device__ __forceinline__ int grid_find_entry(long long e, const long long *blkoff, int G,
+                                                      const int32_t *__restrict__ goff, int F, int P) {
+  int a = 0, z = G - 1;  // largest slice with blkoff <= e (non-empty)
+  while (a < z) {
+    const int mid = (a + z + 1) >> 1;
+    if (blkoff[mid] <= e) a = mid;
+    else z = mid - 1;
+  }
+  const int local = (int)(e - blkoff[a]);
+  const int lane = threadIdx.x & 31;
+  int lo = min(F, a * P), hi = min(F, a * P + P) - 1;
+  // 32-ary search: goff is non-decreasing in the slice
+  while (hi - lo >= 32) {
+    const int step = (hi - lo + 32) / 32;  // 32 probes cover [lo, hi]
+    const int idx = min(hi, lo + lane * step);
+    const unsigned ok = __ballot_sync(0xffffffffu, goff[idx] <= local);
+    const int j = 31 - __clz(ok);  // ok holds lane 0 (goff[lo] <= local)
+    const int next = lo + (j + 1) * step;  // first probe past the answer, if any
+    const int nlo = min(hi, lo + j * step);
+    if (j < 31 && next <= hi) hi = next - 1;
+    lo = nlo;
+  }
+  const int idx = lo + lane;
+  const unsigned ok = __ballot_sync(0xffffffffu, idx <= hi && goff[min(idx, hi)] <= local);
+  return lo + 31 - __clz(ok);
 }
 
 // One batch of nl <= 64 candidates advanced by every CTA of the grid.  ctl
 // must hold zeros in F, qn, touched, gain and cnt on entry (blk_tot is
-// overwritten); the workspace's vis/nxt words must be zero and are zero again
-// when the last CTA passes the caller's next barrier.  Returns false if a
-// barrier gave up (the error code is in *err / gctl->err).
+// overwritten); the workspace's lane words must be zero and are zero again
+// when the last CTA passes the caller's next barrier.  qm holds 2n words (the
+// lane masks of the frontier lists).  Returns false if a barrier gave up (the
+// error code is in *err / gctl->err).
+//
+// Claims work as in the CTA form (gc_cta.cuh): atomicOr on the visited word
+// decides, and the claim words of levels L and L+1 alternate, so a level needs
+// two grid barriers: after the degree scan of the frontier (which also moves
+// each entry's claim word into qm and clears it) and after the expansion.
 template <int MODE>
-static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
-                                const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
-                                const int32_t *nl_dev, long long *out, unsigned char *ws_base,
+static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
+                                const int32_t *nl_dev, long long *out, unsigned char *ws_base, u64 *qm,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
   constexpr int T = kGridGainThreads;
@@ -49,13 +70,17 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   __shared__ unsigned int s_cnt[kLanes];
   __shared__ int s_scan[33];
   __shared__ long long s_blkoff[kMaxGridCtas + 1];
+  __shared__ int s_go[T + 1];  // staged entries: start of each entry's range, relative to the level
+  __shared__ int s_rs[T];
+  __shared__ u64 s_sm[T];
+  __shared__ int s_x0;
   __shared__ u64 s_red[32];
   __shared__ int s_qn, s_touched;
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int G = gridDim.x, b = blockIdx.x;
   const int nl = nl_dev ? min(kLanes, *(volatile const int32_t *)nl_dev) : nl_arg;
-  const GainWsG ws = grid_ws(ws_base, n);
+  const GainWs ws = gain_ws(ws_base, 0, n, 0);
   u64 c_scalar = 0, c_union = 0, c_front = 0, c_push = 0;
   if (tid < kLanes) {
     s_gain[tid] = 0;
@@ -63,7 +88,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   }
   u64 alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
 
-  // ---- level 0 (CTA 0): lanes start at their candidates ----
+  // ---- level 0 (CTA 0): lanes reach their candidates ----
   if (b == 0) {
     if (tid == 0) {
       s_qn = 0;
@@ -73,37 +98,27 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     if (tid < nl) {
       const int c = cand[tid];
       const u64 bit = 1ull << tid;
-      bool push = false;
+      bool reach = false;
       if (c < 0 || c >= n) {
         atomicExch(&ctl->err, GC_EINVAL);
       } else if (MODE == kModeGain) {
         const int dc = dS[c];
         if (dc > 0) {
           ctl->gain[tid] = (u64)dc;
-          push = true;
+          reach = true;
         }
       } else {
         ctl->cnt[tid] = 1;
-        push = true;
+        reach = true;
       }
-      if (push) {
-        const u64 old = atomicOr(&ws.nxt[c], bit);
-        if (old == 0) ws.qv0[atomicAdd(&s_qn, 1)] = c;
+      if (reach) {
+        if (atomicOr(&ws.vis[c], bit) == 0) ws.touched[atomicAdd(&s_touched, 1)] = c;
+        if (atomicOr(&ws.nx[0][c], bit) == 0) ws.qv0[atomicAdd(&s_qn, 1)] = c;
       }
-    }
-    __syncthreads();
-    const int F0 = s_qn;
-    for (int i = tid; i < F0; i += T) {
-      const int w = ws.qv0[i];
-      const u64 m = ws.nxt[w];
-      ws.nxt[w] = 0;
-      ws.vis[w] = m;
-      ws.touched[atomicAdd(&s_touched, 1)] = w;
-      ws.qm0[i] = m;
     }
     __syncthreads();
     if (tid == 0) {
-      ctl->F = F0;
+      ctl->qn[0] = s_qn;
       ctl->touched = s_touched;
     }
   }
@@ -116,15 +131,15 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
 
   int L = 0;
   for (; ok; ++L) {
-    const int F = *(volatile int32_t *)&ctl->F;
+    const int F = *(volatile int32_t *)&ctl->qn[L & 1];
     if (F == 0) break;
     const int32_t *qcur_v = (L & 1) ? ws.qv1 : ws.qv0;
-    const u64 *qcur_m = (L & 1) ? ws.qm1 : ws.qm0;
     int32_t *qnxt_v = (L & 1) ? ws.qv0 : ws.qv1;
-    u64 *qnxt_m = (L & 1) ? ws.qm0 : ws.qm1;
-    int32_t *qn_ctr = &ctl->qn[L & 1];
+    u64 *qcur_m = qm + (size_t)(L & 1) * (size_t)n;
+    int32_t *qn_ctr = &ctl->qn[(L + 1) & 1];
+    const LaneWords cur = (L & 1) ? ws.nx[1] : ws.nx[0], nxt = (L & 1) ? ws.nx[0] : ws.nx[1];
     const int nlev = L + 1;
-    // ---- phase 1: degree offsets of this CTA's contiguous frontier slice ----
+    // ---- phase 1: masks and degree offsets of this CTA's frontier slice ----
     const int P = (F + G - 1) / G;
     const int lo = min(F, b * P), hi = min(F, lo + P);
     int carry = 0;
@@ -133,10 +148,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       int deg = 0;
       if (i < hi) {
         const int u = qcur_v[i];
-        u64 m = qcur_m[i];
+        u64 m = cur[u];
+        cur[u] = 0;  // free for level L+2
+        const int r0 = rp[u], r1 = rp[u + 1];
         if (MODE == kModeFarness) m &= alive;
         if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;  // nothing left to claim
-        if (m) deg = rp[u + 1] - rp[u];
+        if (m) deg = r1 - r0;
+        qcur_m[i] = m;
         c_union += (u64)deg;
         c_scalar += (u64)__popcll(m) * (u64)deg;
         c_front += (m != 0);
@@ -168,42 +186,70 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     }
     const long long E = s_blkoff[G];
     const long long es = E * b / G, ee = E * (b + 1) / G;
-    for (long long e0 = es + (tid & ~31); e0 < ee; e0 += T) {
-      const long long e = e0 + lane;
-      bool push = false;
-      int w = 0;
-      if (e < ee) {
-        // owning CTA slice: largest c with s_blkoff[c] <= e (its slice is non-empty)
-        int a = 0, z = G - 1;
-        while (a < z) {
-          const int mid = (a + z + 1) >> 1;
-          if (s_blkoff[mid] <= e) a = mid;
-          else z = mid - 1;
+    if (es < ee) {
+      if (tid < 32) {
+        const int x = grid_find_entry(es, s_blkoff, G, goff, F, P);
+        if (tid == 0) s_x0 = x;
+      }
+      __syncthreads();
+      int x = s_x0;
+      if (x < 0 || x >= F) {  // cannot happen for a consistent frontier; never index with it
+        if (tid == 0) atomicExch(err, GC_EINTERNAL);
+        x = F;
+      }
+      while (x < F) {
+        // stage up to T entries from x: range starts, row starts, lane masks
+        const int xi = x + tid;
+        if (xi < F) {
+          const u64 m = qcur_m[xi];
+          s_go[tid] = (int)(s_blkoff[xi / P] + goff[xi]);
+          s_sm[tid] = m;
+          s_rs[tid] = m ? rp[qcur_v[xi]] : 0;
         }
-        const int local = (int)(e - s_blkoff[a]);
-        int x = min(F, a * P), y = min(F, a * P + P) - 1;  // entry with largest goff <= local
-        while (x < y) {
-          const int mid = (x + y + 1) >> 1;
-          if (goff[mid] <= local) x = mid;
-          else y = mid - 1;
-        }
-        const int u = qcur_v[x];
-        u64 m = qcur_m[x];
-        if (MODE == kModeFarness) m &= alive;
-        w = ci[rp[u] + (local - goff[x])];
-        int dw = 0;
-        bool pass = true;
-        if (MODE == kModeGain) {
-          dw = dS[w];
-          pass = dw > nlev;
-        }
-        if (pass) {
-          const u64 nb = m & ~ws.vis[w];
-          if (nb) {
-            const u64 old = atomicOr(&ws.nxt[w], nb);
-            u64 won = nb & ~old;
+        const int cntx = min(T, F - x);
+        if (tid == 0) s_go[cntx] = (x + cntx < F) ? (int)(s_blkoff[(x + cntx) / P] + goff[x + cntx]) : (int)E;
+        __syncthreads();
+        const long long a0 = max((long long)s_go[0], es), a1 = min((long long)s_go[cntx], ee);
+        for (long long e0 = a0 + (long long)(tid & ~31) * kGridIlp; e0 < a1; e0 += (long long)T * kGridIlp) {
+          // kGridIlp entries per thread: loads of all are issued before any claim
+          int w[kGridIlp], sl[kGridIlp];
+#pragma unroll
+          for (int k = 0; k < kGridIlp; ++k) {
+            const long long e = e0 + k * 32 + lane;
+            w[k] = -1;
+            sl[k] = 0;
+            if (e < a1) {
+              int l = 0, h = cntx - 1;  // staged entry holding e (non-empty range)
+              while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (s_go[mid] <= e) l = mid;
+                else h = mid - 1;
+              }
+              sl[k] = l;
+              w[k] = ci[s_rs[l] + (int)(e - s_go[l])];
+            }
+          }
+          int dw[kGridIlp];
+#pragma unroll
+          for (int k = 0; k < kGridIlp; ++k) dw[k] = (MODE == kModeGain && w[k] >= 0) ? dS[w[k]] : 0;
+          u64 nb[kGridIlp];
+#pragma unroll
+          for (int k = 0; k < kGridIlp; ++k) {
+            // pruned unless w is strictly closer to the lane's candidate than to S
+            const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
+            nb[k] = live ? (s_sm[sl[k]] & ~ws.vis[w[k]]) : 0ull;
+          }
+          u64 ov[kGridIlp];
+#pragma unroll
+          for (int k = 0; k < kGridIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k]], nb[k]) : ~0ull;
+#pragma unroll
+          for (int k = 0; k < kGridIlp; ++k) {
+            u64 won = nb[k] & ~ov[k];
+            const bool fresh = won && ov[k] == 0;
+            bool push = false;
             if (won) {
-              const u64 wt = MODE == kModeGain ? (u64)(dw - nlev) : (u64)nlev;
+              push = atomicOr(&nxt[w[k]], won) == 0;
+              const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
                 const int j = __ffsll((long long)won) - 1;
                 won &= won - 1;
@@ -211,44 +257,29 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1u);
               } while (won);
             }
-            push = old == 0;
+            const unsigned pm = __ballot_sync(0xffffffffu, push);
+            if (pm) {
+              const int leader = __ffs(pm) - 1;
+              int pos = 0;
+              if (lane == leader) pos = atomicAdd(qn_ctr, __popc(pm));
+              pos = __shfl_sync(0xffffffffu, pos, leader);
+              if (push) qnxt_v[pos + __popc(pm & ((1u << lane) - 1u))] = w[k];
+              c_push += (lane == leader) ? (u64)__popc(pm) : 0ull;
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            if (fm) {
+              const int leader = __ffs(fm) - 1;
+              int pos = 0;
+              if (lane == leader) pos = atomicAdd(&ctl->touched, __popc(fm));
+              pos = __shfl_sync(0xffffffffu, pos, leader);
+              if (fresh) ws.touched[pos + __popc(fm & ((1u << lane) - 1u))] = w[k];
+            }
           }
         }
-      }
-      const unsigned pm = __ballot_sync(0xffffffffu, push);
-      if (pm) {
-        const int leader = __ffs(pm) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(qn_ctr, __popc(pm));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (push) qnxt_v[pos + __popc(pm & ((1u << lane) - 1u))] = w;
-        c_push += (lane == leader) ? (u64)__popc(pm) : 0ull;
-      }
-    }
-    ok = grid_sync(bar, err, timeout_ns);
-    if (!ok) break;
-    // ---- phase 3: commit level L+1 ----
-    const int Fn = *(volatile int32_t *)qn_ctr;
-    for (int base = b * T; base < Fn; base += G * T) {
-      const int i = base + tid;
-      bool fresh = false;
-      int w = 0;
-      if (i < Fn) {
-        w = qnxt_v[i];
-        const u64 m = ws.nxt[w];
-        ws.nxt[w] = 0;
-        const u64 ov = ws.vis[w];
-        ws.vis[w] = ov | m;
-        fresh = ov == 0;
-        qnxt_m[i] = m;
-      }
-      const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-      if (fm) {
-        const int leader = __ffs(fm) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(&ctl->touched, __popc(fm));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (fresh) ws.touched[pos + __popc(fm & ((1u << lane) - 1u))] = w;
+        const int done_end = s_go[cntx];
+        __syncthreads();  // the staged arrays are reused
+        if ((long long)done_end >= ee) break;
+        x += cntx;
       }
     }
     if (MODE == kModeFarness) {
@@ -260,12 +291,12 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         s_cnt[tid] = 0;
       }
     }
-    if (b == 0 && tid == 0) ctl->F = Fn;
     ok = grid_sync(bar, err, timeout_ns);
     if (!ok) break;
     if (MODE == kModeFarness) {
       // the same BFScut test in every CTA: all vertices within L+1 are
       // counted, the rest are at least L+2 away
+      const int Fn = *(volatile int32_t *)qn_ctr;
       const long long best = *(volatile long long *)&gctl->best_f;
       for (int j = 0; j < nl; ++j) {
         if (!((alive >> j) & 1ull)) continue;
@@ -273,7 +304,11 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         const long long c = (long long)((volatile u64 *)ctl->cnt)[j];
         if (Fn > 0 && s + (long long)(L + 2) * ((long long)n - c) > best) alive &= ~(1ull << j);
       }
-      if (alive == 0) break;
+      if (alive == 0) {
+        // every lane is cut: clear the claims of the frontier that is not expanded
+        for (int i = b * T + tid; i < Fn; i += G * T) nxt[qnxt_v[i]] = 0;
+        break;
+      }
     }
   }
   // ---- results ----

@@ -23,13 +23,42 @@ constexpr int kGridGainThreads = 512; // threads per CTA of the grid-wide gain k
 constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
 
 // ----------------------------------------------------------- control words --
-// The visited and next-level lane words of a gain workspace, interleaved: the
-// words of vertex w sit at 2w (visited) and 2w + 1 (next level), so the read of
-// one and the claiming atomic on the other touch the same 32-byte sector.
+// Lane words of a gain workspace: one 32-byte record per vertex w holding its
+// visited word (4w), the claims of even levels (4w + 1) and of odd levels
+// (4w + 2); the fourth word is unused.  A claim reads the visited word and
+// sets two words of the same record, so it touches one 32-byte sector.
 struct LaneWords {
   unsigned long long *p;
-  __device__ __forceinline__ unsigned long long &operator[](long long i) const { return p[2 * i]; }
+  __device__ __forceinline__ unsigned long long &operator[](long long i) const { return p[4 * i]; }
 };
+
+// A gain workspace: the lane-word records, two frontier queues (vertex ids)
+// and a touched list.  One per CTA of the CTA-batched kernel; workspace 0 also
+// serves the grid-wide batch.  All lane words are zero between batches.
+struct GainWs {
+  LaneWords vis, nx[2];
+  int32_t *qv0, *qv1, *touched;
+};
+
+__host__ __device__ inline size_t ws_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bytes of one workspace for n vertices (44 per vertex, each part 256-aligned)
+__host__ __device__ inline size_t gain_ws_bytes(int32_t n) {
+  return ws_align((size_t)n * 32) + 3 * ws_align((size_t)n * sizeof(int32_t));
+}
+
+__device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, int32_t n, int idx) {
+  unsigned char *p = base + stride * (size_t)idx;
+  const size_t a32 = ws_align((size_t)n * 32), a4 = ws_align((size_t)n * sizeof(int32_t));
+  GainWs w;
+  w.vis.p = (unsigned long long *)p;
+  w.nx[0].p = (unsigned long long *)p + 1;
+  w.nx[1].p = (unsigned long long *)p + 2;
+  w.qv0 = (int32_t *)(p + a32);
+  w.qv1 = (int32_t *)(p + a32 + a4);
+  w.touched = (int32_t *)(p + a32 + 2 * a4);
+  return w;
+}
 
 // Bounded grid barrier used by cooperative kernels: one arrival word whose
 // bit 31 flips once per episode (`gen` is padding).  Every wait gives up
@@ -172,6 +201,7 @@ struct gc_graph {
   long long *f0 = nullptr;     // round 0: exact f({v}) or -1
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
+  unsigned long long *qm = nullptr;  // grid-wide gain batch: frontier lane masks [2n]
   long long *akey = nullptr;   // persistent lazy kernel: ub of list entry i [n]
   int32_t *ast = nullptr;      // persistent lazy kernel: stamp of list entry i [n]
   int32_t *bq0 = nullptr, *bq1 = nullptr;  // grid BFS queues [n]

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                   int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
-                  long long spread_max, long long local_max, long long *akey, int32_t *ast) {
+                  long long spread_max, long long local_max, long long *akey, int32_t *ast,
+                  unsigned long long *qm) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   {  // compact copies of the bounds of the (new) active list, and best_id's position
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                                     LaneGraphs(), cnt);
         ok = true;
       } else {
-        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, goff, gg, gctl,
+        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, qm, goff, gg, gctl,
                                         &lc->bar, &lc->err, tns, mx);
       }
       ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
@@ -193,13 +194,14 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   size_t ws_stride = g->ws_stride;
   long long *akey = g->akey;
   int32_t *ast = g->ast;
+  unsigned long long *qm = g->qm;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&spread_max, (void *)&local_max, (void *)&akey,
-                  (void *)&ast};
+                  (void *)&ast, (void *)&qm};
   ++g->launches;
   int grid = std::min(g->lazy_ctas, g->ws_count);
   if (ctas > 0 && ctas < grid) grid = ctas;
