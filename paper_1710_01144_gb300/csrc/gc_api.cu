@@ -60,7 +60,7 @@ static void release(gc_graph *g) {
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
-                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->qm};
+                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -237,7 +237,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->goff, N + 1)) || (rc = dalloc(&g->lctl, 1)) || (rc = dalloc(&g->picks, N)) ||
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
-      (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->qm, 2 * N)) ||
+      (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
       (rc = dalloc(&g->rec_count, 1)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||

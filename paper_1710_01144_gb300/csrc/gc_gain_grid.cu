@@ -27,9 +27,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
     k_gains_grid(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
                  const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t nl_arg,
                  const int32_t *__restrict__ nl_dev, long long *__restrict__ out, unsigned char *ws_base,
-                 unsigned long long *qm, int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl,
+                 int32_t *gx, int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl,
                  unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
-  grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, qm, goff, ctl, gctl, &ctl->bar,
+  grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, gx, goff, ctl, gctl, &ctl->bar,
                         &ctl->err, timeout_ns, mx);
 }
 
@@ -49,14 +49,14 @@ int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, co
   const int32_t *rp = g->rp, *ci = g->ci, *dS = g->dS;
   int32_t n = g->n;
   unsigned char *ws = g->ws;
-  unsigned long long *qm = g->qm;
+  int32_t *gx = g->gx;
   int32_t *goff = g->goff;
   GridGainCtl *ctl = g->ggctl;
   GainCtl *gctl = g->gctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
   const int32_t *mx = mode == kModeGain ? g->mx : nullptr;
   void *args[] = {(void *)&rp,  (void *)&ci,   (void *)&n,   (void *)&dS,  (void *)&cand,
-                  (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&qm, (void *)&goff,
+                  (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&gx, (void *)&goff,
                   (void *)&ctl, (void *)&gctl, (void *)&tns, (void *)&mx};
   ++g->launches;
   if (mode == kModeGain)

@@ -14,73 +14,71 @@ typedef unsigned long long u64;
 
 constexpr int kGridIlp = 2;  // adjacency entries in flight per thread (grid forms)
 
-// Per-level frontier layout of the grid forms: CTA b owns the contiguous
-// slice [b*P, min(F, b*P + P)) of the frontier list (P = ceil(F / G)) and
-// writes the slice-local exclusive prefix of its entries' degrees to goff;
-// blkoff (shared, per CTA) is the exclusive prefix of the slices' totals.
-// Entry x then owns the global adjacency indices starting at
-// blkoff[x / P] + goff[x].  grid_find_entry returns, for one warp, the
-// largest x whose start is <= e (an entry with a non-empty range).
-static __device__ __forceinline__ int grid_find_entry(long long e, const long long *blkoff, int G,
-                                                      const int32_t *__restrict__ goff, int F, int P) {
-  int a = 0, z = G - 1;  // largest slice with blkoff <= e (non-empty)
-  while (a < z) {
-    const int mid = (a + z + 1) >> 1;
-    if (blkoff[mid] <= e) a = mid;
-    else z = mid - 1;
-  }
-  const int local = (int)(e - blkoff[a]);
+// Largest x in [0, F) with start[x] <= e, for one warp; start is
+// non-decreasing and start[0] <= e.  A 32-ary search: about log32(F) rounds
+// of one coalesced probe each.
+static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict__ start, int F, long long e) {
   const int lane = threadIdx.x & 31;
-  int lo = min(F, a * P), hi = min(F, a * P + P) - 1;
-  // 32-ary search: goff is non-decreasing in the slice
+  int lo = 0, hi = F - 1;
   while (hi - lo >= 32) {
     const int step = (hi - lo + 32) / 32;  // 32 probes cover [lo, hi]
     const int idx = min(hi, lo + lane * step);
-    const unsigned ok = __ballot_sync(0xffffffffu, goff[idx] <= local);
-    const int j = 31 - __clz(ok);  // ok holds lane 0 (goff[lo] <= local)
+    const unsigned ok = __ballot_sync(0xffffffffu, (long long)start[idx] <= e);
+    const int j = 31 - __clz(ok);  // ok holds lane 0 (start[lo] <= e)
     const int next = lo + (j + 1) * step;  // first probe past the answer, if any
     const int nlo = min(hi, lo + j * step);
     if (j < 31 && next <= hi) hi = next - 1;
     lo = nlo;
   }
   const int idx = lo + lane;
-  const unsigned ok = __ballot_sync(0xffffffffu, idx <= hi && goff[min(idx, hi)] <= local);
+  const unsigned ok = __ballot_sync(0xffffffffu, idx <= hi && (long long)start[min(idx, hi)] <= e);
   return lo + 31 - __clz(ok);
 }
 
-// One batch of nl <= 64 candidates advanced by every CTA of the grid.  ctl
-// must hold zeros in F, qn, touched, gain and cnt on entry (blk_tot is
-// overwritten); the workspace's lane words must be zero and are zero again
-// when the last CTA passes the caller's next barrier.  qm holds 2n words (the
-// lane masks of the frontier lists).  Returns false if a barrier gave up (the
-// error code is in *err / gctl->err).
+// One batch of nl <= 64 candidates advanced by every CTA of the grid, with one
+// grid barrier per BFS level.  ctl must hold zeros in pk, touched, gain and
+// cnt on entry; the workspace's lane words must be zero and are zero again
+// when the last CTA passes the caller's next barrier.  gx holds 3n int32
+// (entry offsets by level parity, a third frontier list).  Returns false if a
+// barrier gave up (the error code is in *err / gctl->err).
 //
 // Claims work as in the CTA form (gc_cta.cuh): atomicOr on the visited word
-// decides, and the claim words of levels L and L+1 alternate, so a level needs
-// two grid barriers: after the degree scan of the frontier (which also moves
-// each entry's claim word into qm and clears it) and after the expansion.
+// decides.  Claim words cycle through three per vertex (level L mod 3): level
+// L reads word L, claims into word L+1, and clears word L-1 of the previous
+// frontier, which nobody reads any more.  A vertex entering the next frontier
+// takes its list slot and the start of its adjacency range in the level's
+// edge space with one packed atomicAdd (count << 32 | degree), so the list is
+// born sorted by range start: every CTA takes an equal slice of the level's
+// adjacency entries right after the barrier, finds its first entry by one
+// warp-wide search, stages the entries covering its slice in shared memory
+// and expands them edge by edge.  A vertex with nothing left to claim (gain
+// mode: every neighbour's d_S <= its level + 1) is counted but never queued.
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
-                                const int32_t *nl_dev, long long *out, unsigned char *ws_base, u64 *qm,
+                                const int32_t *nl_dev, long long *out, unsigned char *ws_base, int32_t *gx,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
-  __shared__ int s_scan[33];
-  __shared__ long long s_blkoff[kMaxGridCtas + 1];
-  __shared__ int s_go[T + 1];  // staged entries: start of each entry's range, relative to the level
+  __shared__ int s_go[T + 1];  // staged entries: start of each entry's range in the level's edge space
   __shared__ int s_rs[T];
   __shared__ u64 s_sm[T];
   __shared__ int s_x0;
   __shared__ u64 s_red[32];
-  __shared__ int s_qn, s_touched;
+  (void)goff;
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int G = gridDim.x, b = blockIdx.x;
   const int nl = nl_dev ? min(kLanes, *(volatile const int32_t *)nl_dev) : nl_arg;
   const GainWs ws = gain_ws(ws_base, 0, n, 0);
+  // frontier lists by level mod 3 and range starts by level parity (selected,
+  // not indexed, so that nothing lands in local memory)
+  int32_t *const list2 = gx + 2 * (size_t)n;
+  auto list_of = [&](int r) -> int32_t * { return r == 0 ? ws.qv0 : (r == 1 ? ws.qv1 : list2); };
+  auto starts_of = [&](int p) -> int32_t * { return p ? gx + (size_t)n : gx; };
+  auto words_of = [&](int r) -> LaneWords { return r == 0 ? ws.nx[0] : (r == 1 ? ws.nx[1] : ws.nx[2]); };
   u64 c_scalar = 0, c_union = 0, c_front = 0, c_push = 0;
   if (tid < kLanes) {
     s_gain[tid] = 0;
@@ -88,38 +86,61 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   }
   u64 alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
 
-  // ---- level 0 (CTA 0): lanes reach their candidates ----
-  if (b == 0) {
-    if (tid == 0) {
-      s_qn = 0;
-      s_touched = 0;
+  // Queue w for level lev (its lanes are already in claim word lev mod 3):
+  // warp-aggregated slot and range start.  Every lane of the warp calls it.
+  auto enqueue = [&](bool q, int w, int lev) {
+    const unsigned qm = __ballot_sync(0xffffffffu, q);
+    if (!qm) return;
+    int deg = q ? rp[w + 1] - rp[w] : 0;
+    int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    __syncthreads();
-    if (tid < nl) {
-      const int c = cand[tid];
-      const u64 bit = 1ull << tid;
-      bool reach = false;
-      if (c < 0 || c >= n) {
-        atomicExch(&ctl->err, GC_EINVAL);
-      } else if (MODE == kModeGain) {
-        const int dc = dS[c];
-        if (dc > 0) {
-          ctl->gain[tid] = (u64)dc;
+    const int sum = __shfl_sync(0xffffffffu, incl, 31);
+    const int leader = __ffs(qm) - 1;
+    unsigned long long base = 0;
+    if (lane == leader)
+      base = atomicAdd(&ctl->pk[lev % 3], ((unsigned long long)__popc(qm) << 32) | (unsigned long long)sum);
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (q) {
+      const int slot = (int)(base >> 32) + __popc(qm & ((1u << lane) - 1u));
+      list_of(lev % 3)[slot] = w;
+      starts_of(lev & 1)[slot] = (int)(base & 0xffffffffull) + incl - deg;
+    }
+    c_push += (lane == leader) ? (u64)__popc(qm) : 0ull;
+  };
+
+  // ---- level 0 (warp 0 of CTA 0): lanes reach their candidates ----
+  if (b == 0 && tid < 32) {
+    // lane t handles lanes t and t + 32 of the batch, one after the other
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const int c = j < nl ? cand[j] : -1;
+      bool q = false;
+      if (j < nl) {
+        const u64 bit = 1ull << j;
+        bool reach = false;
+        if (c < 0 || c >= n) {
+          atomicExch(&ctl->err, GC_EINVAL);
+        } else if (MODE == kModeGain) {
+          const int dc = dS[c];
+          if (dc > 0) {
+            ctl->gain[j] = (u64)dc;
+            reach = true;
+          }
+        } else {
+          ctl->cnt[j] = 1;
           reach = true;
         }
-      } else {
-        ctl->cnt[tid] = 1;
-        reach = true;
+        if (reach) {
+          if (atomicOr(&ws.vis[c], bit) == 0) ws.touched[atomicAdd(&ctl->touched, 1)] = c;
+          const bool expand = MODE != kModeGain || !mx || mx[c] > 1;
+          if (expand) q = atomicOr(&ws.nx[0][c], bit) == 0;
+        }
       }
-      if (reach) {
-        if (atomicOr(&ws.vis[c], bit) == 0) ws.touched[atomicAdd(&s_touched, 1)] = c;
-        if (atomicOr(&ws.nx[0][c], bit) == 0) ws.qv0[atomicAdd(&s_qn, 1)] = c;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      ctl->qn[0] = s_qn;
-      ctl->touched = s_touched;
+      enqueue(q, c, 0);
     }
   }
   bool ok = grid_sync(bar, err, timeout_ns);
@@ -129,85 +150,50 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       if (((volatile unsigned long long *)ctl->cnt)[j] == 0) alive &= ~(1ull << j);
   }
 
-  int L = 0;
+  int L = 0, F_prev = 0;
   for (; ok; ++L) {
-    const int F = *(volatile int32_t *)&ctl->qn[L & 1];
+    const unsigned long long pk = *(volatile unsigned long long *)&ctl->pk[L % 3];
+    const int F = (int)(pk >> 32);
+    const long long E = (long long)(pk & 0xffffffffull);
+    // clear the claim words of the previous frontier (read by nobody now)
+    if (L > 0) {
+      const LaneWords prev = words_of((L + 2) % 3);
+      const int32_t *pl = list_of((L + 2) % 3);
+      for (int i = b * T + tid; i < F_prev; i += G * T) prev[pl[i]] = 0;
+    }
     if (F == 0) break;
-    const int32_t *qcur_v = (L & 1) ? ws.qv1 : ws.qv0;
-    int32_t *qnxt_v = (L & 1) ? ws.qv0 : ws.qv1;
-    u64 *qcur_m = qm + (size_t)(L & 1) * (size_t)n;
-    int32_t *qn_ctr = &ctl->qn[(L + 1) & 1];
-    const LaneWords cur = (L & 1) ? ws.nx[1] : ws.nx[0], nxt = (L & 1) ? ws.nx[0] : ws.nx[1];
+    if (b == 0 && tid == 0) ctl->pk[(L + 2) % 3] = 0;  // the frontier after next (read two levels ago)
+    const int32_t *qcur_v = list_of(L % 3);
+    const int32_t *qstart = starts_of(L & 1);
+    const LaneWords cur = words_of(L % 3), nxt = words_of((L + 1) % 3);
     const int nlev = L + 1;
-    // ---- phase 1: masks and degree offsets of this CTA's frontier slice ----
-    const int P = (F + G - 1) / G;
-    const int lo = min(F, b * P), hi = min(F, lo + P);
-    int carry = 0;
-    for (int base = lo; base < hi; base += T) {
-      const int i = base + tid;
-      int deg = 0;
-      if (i < hi) {
-        const int u = qcur_v[i];
-        u64 m = cur[u];
-        cur[u] = 0;  // free for level L+2
-        const int r0 = rp[u], r1 = rp[u + 1];
-        if (MODE == kModeFarness) m &= alive;
-        if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;  // nothing left to claim
-        if (m) deg = r1 - r0;
-        qcur_m[i] = m;
-        c_union += (u64)deg;
-        c_scalar += (u64)__popcll(m) * (u64)deg;
-        c_front += (m != 0);
-      }
-      int total;
-      const int off = block_excl_scan(deg, s_scan, &total);
-      if (i < hi) goff[i] = carry + off;
-      carry += total;
-    }
-    if (tid == 0) {
-      ctl->blk_tot[b] = carry;
-      if (b == 0) *qn_ctr = 0;
-    }
-    ok = grid_sync(bar, err, timeout_ns);
-    if (!ok) break;
-    // ---- phase 2: expand an equal slice of the level's adjacency entries ----
-    {
-      long long run = 0;
-      for (int base = 0; base < G; base += T) {
-        const int j = base + tid;
-        const int v = j < G ? ((volatile int32_t *)ctl->blk_tot)[j] : 0;
-        int total;
-        const int off = block_excl_scan(v, s_scan, &total);
-        if (j < G) s_blkoff[j] = run + off;
-        run += total;
-      }
-      if (tid == 0) s_blkoff[G] = run;
-      __syncthreads();
-    }
-    const long long E = s_blkoff[G];
     const long long es = E * b / G, ee = E * (b + 1) / G;
     if (es < ee) {
       if (tid < 32) {
-        const int x = grid_find_entry(es, s_blkoff, G, goff, F, P);
+        const int x = warp_find_start(qstart, F, es);
         if (tid == 0) s_x0 = x;
       }
       __syncthreads();
       int x = s_x0;
-      if (x < 0 || x >= F) {  // cannot happen for a consistent frontier; never index with it
-        if (tid == 0) atomicExch(err, GC_EINTERNAL);
-        x = F;
-      }
       while (x < F) {
         // stage up to T entries from x: range starts, row starts, lane masks
         const int xi = x + tid;
-        if (xi < F) {
-          const u64 m = qcur_m[xi];
-          s_go[tid] = (int)(s_blkoff[xi / P] + goff[xi]);
-          s_sm[tid] = m;
-          s_rs[tid] = m ? rp[qcur_v[xi]] : 0;
-        }
         const int cntx = min(T, F - x);
-        if (tid == 0) s_go[cntx] = (x + cntx < F) ? (int)(s_blkoff[(x + cntx) / P] + goff[x + cntx]) : (int)E;
+        if (xi < F) {
+          const int u = qcur_v[xi];
+          u64 m = cur[u];
+          if (MODE == kModeFarness) m &= alive;
+          s_go[tid] = qstart[xi];
+          s_sm[tid] = m;
+          s_rs[tid] = rp[u];
+          if (s_go[tid] >= es && s_go[tid] < ee) {  // counted once: by the CTA holding the entry's first edge
+            const int deg = rp[u + 1] - s_rs[tid];
+            c_union += (u64)deg;
+            c_scalar += (u64)__popcll(m) * (u64)deg;
+            c_front += 1;
+          }
+        }
+        if (tid == 0) s_go[cntx] = (x + cntx < F) ? qstart[x + cntx] : (int)E;
         __syncthreads();
         const long long a0 = max((long long)s_go[0], es), a1 = min((long long)s_go[cntx], ee);
         for (long long e0 = a0 + (long long)(tid & ~31) * kGridIlp; e0 < a1; e0 += (long long)T * kGridIlp) {
@@ -219,7 +205,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             w[k] = -1;
             sl[k] = 0;
             if (e < a1) {
-              int l = 0, h = cntx - 1;  // staged entry holding e (non-empty range)
+              int l = 0, h = cntx - 1;  // staged entry holding e (every entry's range is non-empty)
               while (l < h) {
                 const int mid = (l + h + 1) >> 1;
                 if (s_go[mid] <= e) l = mid;
@@ -246,9 +232,11 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           for (int k = 0; k < kGridIlp; ++k) {
             u64 won = nb[k] & ~ov[k];
             const bool fresh = won && ov[k] == 0;
-            bool push = false;
+            bool q = false;
             if (won) {
-              push = atomicOr(&nxt[w[k]], won) == 0;
+              // expanded at level nlev only if some neighbour may still be claimed
+              const bool expand = MODE != kModeGain || !mx || mx[w[k]] > nlev + 1;
+              if (expand) q = atomicOr(&nxt[w[k]], won) == 0;
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
                 const int j = __ffsll((long long)won) - 1;
@@ -257,15 +245,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1u);
               } while (won);
             }
-            const unsigned pm = __ballot_sync(0xffffffffu, push);
-            if (pm) {
-              const int leader = __ffs(pm) - 1;
-              int pos = 0;
-              if (lane == leader) pos = atomicAdd(qn_ctr, __popc(pm));
-              pos = __shfl_sync(0xffffffffu, pos, leader);
-              if (push) qnxt_v[pos + __popc(pm & ((1u << lane) - 1u))] = w[k];
-              c_push += (lane == leader) ? (u64)__popc(pm) : 0ull;
-            }
+            enqueue(q, w[k], nlev);
             const unsigned fm = __ballot_sync(0xffffffffu, fresh);
             if (fm) {
               const int leader = __ffs(fm) - 1;
@@ -291,12 +271,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         s_cnt[tid] = 0;
       }
     }
+    F_prev = F;
     ok = grid_sync(bar, err, timeout_ns);
     if (!ok) break;
     if (MODE == kModeFarness) {
       // the same BFScut test in every CTA: all vertices within L+1 are
       // counted, the rest are at least L+2 away
-      const int Fn = *(volatile int32_t *)qn_ctr;
+      const int Fn = (int)(*(volatile unsigned long long *)&ctl->pk[(L + 1) % 3] >> 32);
       const long long best = *(volatile long long *)&gctl->best_f;
       for (int j = 0; j < nl; ++j) {
         if (!((alive >> j) & 1ull)) continue;
@@ -305,12 +286,19 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         if (Fn > 0 && s + (long long)(L + 2) * ((long long)n - c) > best) alive &= ~(1ull << j);
       }
       if (alive == 0) {
-        // every lane is cut: clear the claims of the frontier that is not expanded
-        for (int i = b * T + tid; i < Fn; i += G * T) nxt[qnxt_v[i]] = 0;
+        // every lane is cut: clear the claim words of this frontier and of the
+        // next one, which is not expanded
+        const LaneWords lw0 = cur, lw1 = nxt;
+        const int32_t *l0 = list_of(L % 3), *l1 = list_of((L + 1) % 3);
+        for (int i = b * T + tid; i < F; i += G * T) lw0[l0[i]] = 0;
+        for (int i = b * T + tid; i < Fn; i += G * T) lw1[l1[i]] = 0;
+        F_prev = 0;
+        ++L;
         break;
       }
     }
   }
+  // L = levels expanded
   // ---- results ----
   if (MODE == kModeGain) {
     __syncthreads();

@@ -24,9 +24,10 @@ constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
 
 // ----------------------------------------------------------- control words --
 // Lane words of a gain workspace: one 32-byte record per vertex w holding its
-// visited word (4w), the claims of even levels (4w + 1) and of odd levels
-// (4w + 2); the fourth word is unused.  A claim reads the visited word and
-// sets two words of the same record, so it touches one 32-byte sector.
+// visited word (4w) and three claim words (4w + 1 .. 4w + 3).  The CTA form
+// alternates the first two between even and odd levels; the grid form cycles
+// through all three.  A claim reads the visited word and sets two words of the
+// same record, so it touches one 32-byte sector.
 struct LaneWords {
   unsigned long long *p;
   __device__ __forceinline__ unsigned long long &operator[](long long i) const { return p[4 * i]; }
@@ -36,7 +37,7 @@ struct LaneWords {
 // and a touched list.  One per CTA of the CTA-batched kernel; workspace 0 also
 // serves the grid-wide batch.  All lane words are zero between batches.
 struct GainWs {
-  LaneWords vis, nx[2];
+  LaneWords vis, nx[3];
   int32_t *qv0, *qv1, *touched;
 };
 
@@ -54,6 +55,7 @@ __device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, in
   w.vis.p = (unsigned long long *)p;
   w.nx[0].p = (unsigned long long *)p + 1;
   w.nx[1].p = (unsigned long long *)p + 2;
+  w.nx[2].p = (unsigned long long *)p + 3;
   w.qv0 = (int32_t *)(p + a32);
   w.qv1 = (int32_t *)(p + a32 + a4);
   w.touched = (int32_t *)(p + a32 + 2 * a4);
@@ -101,10 +103,13 @@ struct GainCtl {
 struct GridGainCtl {
   GridBar bar;
   int32_t err;
-  int32_t F;          // current frontier size
-  int32_t qn[2];      // next-frontier counters by level parity
+  int32_t F;          // (unused)
+  int32_t qn[2];      // (unused)
   int32_t touched;    // vertices with a non-zero visited word
   int32_t pad;
+  // frontier of level L, by L mod 3: entries (high 32 bits) and adjacency
+  // entries (low 32 bits), both taken by one atomicAdd per push
+  unsigned long long pk[3];
   unsigned long long gain[kLanes];  // per-lane gain (gain mode) / distance sum (farness)
   unsigned long long cnt[kLanes];   // farness mode: per-lane visited count
   int32_t blk_tot[kMaxGridCtas];    // per-CTA adjacency totals of the level
@@ -201,7 +206,7 @@ struct gc_graph {
   long long *f0 = nullptr;     // round 0: exact f({v}) or -1
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
-  unsigned long long *qm = nullptr;  // grid-wide gain batch: frontier lane masks [2n]
+  int32_t *gx = nullptr;       // grid-wide gain batch: entry offsets by level parity, third list [3n]
   long long *akey = nullptr;   // persistent lazy kernel: ub of list entry i [n]
   int32_t *ast = nullptr;      // persistent lazy kernel: stamp of list entry i [n]
   int32_t *bq0 = nullptr, *bq1 = nullptr;  // grid BFS queues [n]

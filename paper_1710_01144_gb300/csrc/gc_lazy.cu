@@ -26,7 +26,8 @@
 
 namespace gc {
 
-__global__ void __launch_bounds__(kGridGainThreads, 2)
+// One CTA per SM (the launch uses one), so the register budget is 128.
+__global__ void __launch_bounds__(kGridGainThreads, 1)
     k_lazy_rounds(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dS,
                   long long *ub, int32_t *stamp, const int32_t *__restrict__ act, const int32_t *m_dev,
                   int32_t k, int32_t *picks, long long *pgain, long long *pdec, unsigned char *ws,
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
                   long long spread_max, long long local_max, long long *akey, int32_t *ast,
-                  unsigned long long *qm) {
+                  int32_t *gx) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   {  // compact copies of the bounds of the (new) active list, and best_id's position
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                                     LaneGraphs(), cnt);
         ok = true;
       } else {
-        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, qm, goff, gg, gctl,
+        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
                                         &lc->bar, &lc->err, tns, mx);
       }
       ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
@@ -194,14 +195,14 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   size_t ws_stride = g->ws_stride;
   long long *akey = g->akey;
   int32_t *ast = g->ast;
-  unsigned long long *qm = g->qm;
+  int32_t *gx = g->gx;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&spread_max, (void *)&local_max, (void *)&akey,
-                  (void *)&ast, (void *)&qm};
+                  (void *)&ast, (void *)&gx};
   ++g->launches;
   int grid = std::min(g->lazy_ctas, g->ws_count);
   if (ctas > 0 && ctas < grid) grid = ctas;

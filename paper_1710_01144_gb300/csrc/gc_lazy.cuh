@@ -306,9 +306,9 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     lc->n_sel = taken < kLanes ? taken : kLanes;
     lc->dec = 0;
     if (gg) {
-      gg->F = 0;
-      gg->qn[0] = 0;
-      gg->qn[1] = 0;
+      gg->pk[0] = 0;
+      gg->pk[1] = 0;
+      gg->pk[2] = 0;
       gg->touched = 0;
     }
   }
