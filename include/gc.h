@@ -219,7 +219,7 @@ int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len,
  *            outside [0, n).  Ids in S must be in range.
  * stream   : cudaStream_t (as void*); the call is asynchronous on it.
  * Limits   : n is limited by the array (one 44-byte-per-vertex workspace plus
- *            20 bytes per vertex must fit: n up to about one million); a larger
+ *            24 bytes per vertex must fit: n up to about 980,000); a larger
  *            n returns GC_ERANGE before anything runs.  Smaller graphs get more
  *            workspaces and therefore more parallel CTAs.
  * Sharing  : all calls in the process share the one array.  Each call zeroes

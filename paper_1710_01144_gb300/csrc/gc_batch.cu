@@ -42,7 +42,8 @@ struct BatchCtl {
   int32_t remaining;  // graphs that still need lazy rounds
   int32_t nseeds;     // seeds of the next relabel BFS
   int32_t task;       // dynamic task counter of P4
-  int32_t qsize[3];
+  int32_t pad0;
+  unsigned long long pk[3];  // relabel BFS frontiers (see BfsCtl)
   int32_t pad;
   unsigned long long decrease;
   long long iterations;
@@ -67,7 +68,7 @@ struct BatchArgs {
   const int32_t *bstart;  // round-1 task prefix per graph ([count+1])
   int32_t lanes1;         // candidates per round-1 batch
   int32_t max_n;          // vertices of the largest graph (workspace layout)
-  int32_t *dS, *mx, *stamp, *q0, *q1, *goff;
+  int32_t *dS, *mx, *stamp, *q0, *q1, *goff, *st1;
   long long *ub, *key, *f0;
   unsigned char *ws;
   size_t ws_stride;
@@ -177,12 +178,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   // ---- P1: BFS from all v_a ----
   for (int g = b * T + tid; g < a.count; g += G * T) a.seeds[g] = a.off[g] + (int)(a.packed[g] & 0xffffffffull);
   if (!bsync(a)) return;
-  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->qsize, nullptr,
-                        &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar, &a.ctl->err, a.tns))
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->pk, nullptr,
+                        &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar, &a.ctl->err, a.tns))
     return;
   if (!bsync(a)) return;
   seg_sum_dist(a, a.fa);
-  if (b == 0 && tid == 0) a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+  if (b == 0 && tid == 0) a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
   if (!bsync(a)) return;
   // ---- P2: round-0 survivors (every v with LB(v) <= f_a) ----
   // P2a, one CTA per graph: compact the graph's survivors into its own region
@@ -260,8 +261,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   // ---- P3: d_S = BFS from all s0; farness; neighbour bound ----
   for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
   if (!bsync(a)) return;
-  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->qsize, nullptr,
-                        &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar, &a.ctl->err, a.tns))
+  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, a.count, a.q0, a.q1, a.ctl->pk, nullptr,
+                        &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar, &a.ctl->err, a.tns))
     return;
   if (!bsync(a)) return;
   seg_sum_dist(a, a.farness);
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     }
   }
   if (b == 0 && tid == 0) {
-    a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+    a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
     a.ctl->task = 0;
   }
   if (!bsync(a)) return;
@@ -368,12 +369,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   }
   if (!bsync(a)) return;
   if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
-                        a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
+                        a.ctl->pk, nullptr, &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar,
                         &a.ctl->err, a.tns))
     return;
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) {
-    a.ctl->qsize[0] = a.ctl->qsize[1] = a.ctl->qsize[2] = 0;
+    a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
     a.ctl->nseeds = 0;
   }
   // ---- P5: active lists (one CTA per graph) ----
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   }
   if (!bsync(a)) return;
   if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
-                        a.ctl->qsize, nullptr, &a.ctl->decrease, nullptr, a.goff, a.ctl->blk_tot, &a.ctl->bar,
+                        a.ctl->pk, nullptr, &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar,
                         &a.ctl->err, a.tns))
     return;
   if (!bsync(a)) return;
@@ -569,7 +570,8 @@ struct gc_batch {
   int num_sms = 0, ctas = 0;
   std::vector<int32_t> h_off, h_n;
   int32_t *rp = nullptr, *ci = nullptr, *gid = nullptr, *off = nullptr, *ng = nullptr, *iota = nullptr;
-  int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr;
+  int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr,
+          *st1 = nullptr;
   long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
   unsigned char *ws = nullptr;
   size_t ws_stride = 0;
@@ -604,7 +606,7 @@ static void batch_release(gc_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff,
+  void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
                  b->scount, b->tstart};
@@ -682,7 +684,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
   bool ok = balloc(&b->rp, Nn + 1) && balloc(&b->ci, (size_t)E) && balloc(&b->gid, Nn) &&
             balloc(&b->off, (size_t)count + 1) && balloc(&b->ng, (size_t)count) && balloc(&b->iota, Nn) &&
             balloc(&b->dS, Nn) && balloc(&b->mx, Nn) && balloc(&b->stamp, Nn) && balloc(&b->q0, Nn) &&
-            balloc(&b->q1, Nn) && balloc(&b->goff, Nn + 1) && balloc(&b->ub, Nn) && balloc(&b->key, Nn) &&
+            balloc(&b->q1, Nn) && balloc(&b->goff, Nn + 1) && balloc(&b->st1, Nn) && balloc(&b->ub, Nn) && balloc(&b->key, Nn) &&
             balloc(&b->f0, Nn) && balloc(&b->packed, (size_t)count) && balloc(&b->fa, (size_t)count) &&
             balloc(&b->farness, (size_t)count) && balloc(&b->bestf, (size_t)count) &&
             balloc(&b->lc, (size_t)count) && balloc(&b->act_n, (size_t)count) && balloc(&b->full, (size_t)count) &&
@@ -838,6 +840,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.q0 = b->q0;
   a.q1 = b->q1;
   a.goff = b->goff;
+  a.st1 = b->st1;
   a.ub = b->ub;
   a.key = b->key;
   a.f0 = b->f0;

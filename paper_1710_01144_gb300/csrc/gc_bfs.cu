@@ -33,10 +33,10 @@ __global__ void k_fill_i64(long long *p, long long v, int64_t count) {
 // farness decrease Delta(s | S).
 __global__ void __launch_bounds__(kBfsThreads) k_bfs_relabel(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
-    const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *goff,
+    const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *st0, int32_t *st1,
     BfsCtl *ctl, unsigned long long timeout_ns) {
-  grid_relabel_bfs(rp, ci, n, dist, seeds, n_seeds, q0, q1, ctl->qsize, &ctl->levels, &ctl->decrease,
-                   &ctl->relabelled, goff, ctl->blk_tot, &ctl->bar, &ctl->err, timeout_ns);
+  grid_relabel_bfs(rp, ci, n, dist, seeds, n_seeds, q0, q1, ctl->pk, &ctl->levels, &ctl->decrease,
+                   &ctl->relabelled, st0, st1, &ctl->bar, &ctl->err, timeout_ns);
 }
 
 // sum(dist) and the count of unreached vertices; the last CTA to finish folds
@@ -191,11 +191,11 @@ int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t
   GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
-  int32_t *q0 = g->bq0, *q1 = g->bq1, *goff = g->goff;
+  int32_t *q0 = g->bq0, *q1 = g->bq1, *st0 = g->goff, *st1 = g->gx;
   BfsCtl *ctl = g->bctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
   void *args[] = {(void *)&rp,      (void *)&ci, (void *)&n,  (void *)&dist, (void *)&seeds,
-                  (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&goff, (void *)&ctl,
+                  (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&st0, (void *)&st1, (void *)&ctl,
                   (void *)&tns};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(std::min(g->bfs_ctas, kMaxGridCtas)),

@@ -347,120 +347,131 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
 
 // Relabel BFS over the whole grid: dist[w] <- min(dist[w], level) from the
 // seeds, expanding only where the label decreased (the pruned SSSP of Sec. 4.1
-// when dist holds d_S).  qsize[0..2] must be zero on entry.  *decrease collects
+// when dist holds d_S).  pk[0..2] must be zero on entry (the frontier of level
+// L by L mod 3: entries << 32 | adjacency entries).  *decrease collects
 // sum(old - new) over relabelled vertices with a finite old label.
-// Each level is edge-balanced like grid_gain_batch: CTA slices of the frontier
-// scan their degrees into goff (phase 1), then every CTA takes an equal slice
-// of the level's adjacency entries (phase 2), so a hub row is shared by all
-// CTAs instead of serialising one warp.  With `work` given, CTA 0 adds the
-// frontier entries and adjacency entries of every level to work[0], work[1].
+// One grid barrier per level, as in grid_gain_batch: a relabelled vertex takes
+// its slot in the next list and the start of its adjacency range with one
+// packed atomicAdd, so every CTA takes an equal slice of the level's adjacency
+// entries right away (a hub row is shared by all CTAs instead of serialising
+// one warp).  q0/q1 are the lists and st0/st1 the range starts by level
+// parity, n entries each.  With `work` given, CTA 0 adds the frontier entries
+// and adjacency entries of every level to work[0], work[1].
 static __device__ __forceinline__ bool grid_relabel_bfs(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
-    const int32_t *seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *qsize, int32_t *levels_out,
-    unsigned long long *decrease, unsigned long long *relabelled, int32_t *__restrict__ goff,
-    int32_t *blk_tot, GridBar *bar, int32_t *err, unsigned long long timeout_ns,
-    unsigned long long *work = nullptr) {
+    const int32_t *seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, unsigned long long *pk, int32_t *levels_out,
+    unsigned long long *decrease, unsigned long long *relabelled, int32_t *st0, int32_t *st1,
+    GridBar *bar, int32_t *err, unsigned long long timeout_ns, unsigned long long *work = nullptr) {
+  constexpr int kT = 1024;  // staging capacity (blockDim.x <= 1024)
   __shared__ unsigned long long sh_bfs[32];
-  __shared__ int s_scan_b[33];
-  __shared__ long long s_boff[kMaxGridCtas + 1];
+  __shared__ int s_go[kT + 1];
+  __shared__ int s_rs[kT];
+  __shared__ int s_x0;
   const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
   const int G = gridDim.x, b = blockIdx.x;
   unsigned long long dec = 0, rel = 0;
-  for (int i = b * T + tid; i < n_seeds; i += G * T) {
-    const int s = ((volatile const int32_t *)seeds)[i];
-    if (s < 0 || s >= n) {
-      atomicExch(err, GC_EINVAL);
-      continue;
+
+  // queue w for level lev: warp-aggregated slot and range start (whole warp)
+  auto enqueue = [&](bool q, int w, int lev) {
+    const unsigned qm = __ballot_sync(0xffffffffu, q);
+    if (!qm) return;
+    const int deg = q ? rp[w + 1] - rp[w] : 0;
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    const int old = atomicMin(&dist[s], 0);
-    if (old > 0) {
-      const int p = atomicAdd(&qsize[0], 1);
-      q0[p] = s;
-      if (old < kInf) dec += (unsigned long long)old;
-      ++rel;
+    const int sum = __shfl_sync(0xffffffffu, incl, 31);
+    const int leader = __ffs(qm) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&pk[lev % 3], ((unsigned long long)__popc(qm) << 32) | (unsigned long long)sum);
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (q) {
+      const int slot = (int)(base >> 32) + __popc(qm & ((1u << lane) - 1u));
+      ((lev & 1) ? q1 : q0)[slot] = w;
+      ((lev & 1) ? st1 : st0)[slot] = (int)(base & 0xffffffffull) + incl - deg;
     }
+  };
+
+  for (int base = b * T; base < n_seeds; base += G * T) {  // warp-uniform trip count
+    const int i = base + tid;
+    bool q = false;
+    int s = 0;
+    if (i < n_seeds) {
+      s = ((volatile const int32_t *)seeds)[i];
+      if (s < 0 || s >= n) {
+        atomicExch(err, GC_EINVAL);
+      } else {
+        const int old = atomicMin(&dist[s], 0);
+        if (old > 0) {
+          q = true;
+          if (old < kInf) dec += (unsigned long long)old;
+          ++rel;
+        }
+      }
+    }
+    enqueue(q, s, 0);
   }
   bool ok = grid_sync(bar, err, timeout_ns);
   for (int L = 0; ok; ++L) {
-    const int F = *(volatile int32_t *)&qsize[L % 3];
+    const unsigned long long pkl = *(volatile unsigned long long *)&pk[L % 3];
+    const int F = (int)(pkl >> 32);
+    const long long E = (long long)(pkl & 0xffffffffull);
     if (F == 0) break;
-    const int32_t *qc = (L & 1) ? q1 : q0;
-    int32_t *qn = (L & 1) ? q0 : q1;
-    int32_t *qn_size = &qsize[(L + 1) % 3];
-    const int nl = L + 1;
-    // phase 1: degree offsets of this CTA's contiguous frontier slice
-    const int P = (F + G - 1) / G;
-    const int lo = min(F, b * P), hi = min(F, lo + P);
-    int carry = 0;
-    for (int base = lo; base < hi; base += T) {
-      const int i = base + tid;
-      const int deg = i < hi ? rp[qc[i] + 1] - rp[qc[i]] : 0;
-      int total;
-      const int off = block_excl_scan(deg, s_scan_b, &total);
-      if (i < hi) goff[i] = carry + off;
-      carry += total;
-    }
-    if (tid == 0) {
-      blk_tot[b] = carry;
-      if (b == 0) qsize[(L + 2) % 3] = 0;
-    }
-    ok = grid_sync(bar, err, timeout_ns);
-    if (!ok) break;
-    // phase 2: an equal slice of the level's adjacency entries per CTA
-    {
-      long long run = 0;
-      for (int base = 0; base < G; base += T) {
-        const int j = base + tid;
-        const int v = j < G ? ((volatile int32_t *)blk_tot)[j] : 0;
-        int total;
-        const int off = block_excl_scan(v, s_scan_b, &total);
-        if (j < G) s_boff[j] = run + off;
-        run += total;
-      }
-      if (tid == 0) s_boff[G] = run;
-      __syncthreads();
-    }
-    const long long E = s_boff[G];
+    if (b == 0 && tid == 0) pk[(L + 2) % 3] = 0;  // the frontier after next (read two levels ago)
     if (work && b == 0 && tid == 0) {
       work[0] += (unsigned long long)F;
       work[1] += (unsigned long long)E;
     }
+    const int32_t *qc = (L & 1) ? q1 : q0;
+    const int32_t *qs = (L & 1) ? st1 : st0;
+    const int nl = L + 1;
     const long long es = E * b / G, ee = E * (b + 1) / G;
-    for (long long e0 = es + (tid & ~31); e0 < ee; e0 += T) {
-      const long long e = e0 + lane;
-      bool push = false;
-      int w = 0;
-      if (e < ee) {
-        int a = 0, z = G - 1;
-        while (a < z) {
-          const int mid = (a + z + 1) >> 1;
-          if (s_boff[mid] <= e) a = mid;
-          else z = mid - 1;
-        }
-        const int local = (int)(e - s_boff[a]);
-        int x = min(F, a * P), y = min(F, a * P + P) - 1;
-        while (x < y) {
-          const int mid = (x + y + 1) >> 1;
-          if (goff[mid] <= local) x = mid;
-          else y = mid - 1;
-        }
-        w = ci[rp[qc[x]] + (local - goff[x])];
-        if (nl < dist[w]) {
-          const int old = atomicMin(&dist[w], nl);
-          if (old > nl) {
-            push = true;
-            if (old < kInf) dec += (unsigned long long)(old - nl);
-            ++rel;
-          }
-        }
+    if (es < ee) {
+      if (tid < 32) {
+        const int x = warp_find_start(qs, F, es);
+        if (tid == 0) s_x0 = x;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, push);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        int pos = 0;
-        if (lane == leader) pos = atomicAdd(qn_size, __popc(m));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (push) qn[pos + __popc(m & ((1u << lane) - 1u))] = w;
+      __syncthreads();
+      int x = s_x0;
+      while (x < F) {
+        const int xi = x + tid;
+        const int cntx = min(T, F - x);
+        if (xi < F) {
+          s_go[tid] = qs[xi];
+          s_rs[tid] = rp[qc[xi]];
+        }
+        if (tid == 0) s_go[cntx] = (x + cntx < F) ? qs[x + cntx] : (int)E;
+        __syncthreads();
+        const long long a0 = max((long long)s_go[0], es), a1 = min((long long)s_go[cntx], ee);
+        for (long long e0 = a0 + (tid & ~31); e0 < a1; e0 += T) {  // warp-uniform trip count
+          const long long e = e0 + lane;
+          bool q = false;
+          int w = 0;
+          if (e < a1) {
+            int l = 0, h = cntx - 1;  // staged entry holding e (every entry's range is non-empty)
+            while (l < h) {
+              const int mid = (l + h + 1) >> 1;
+              if (s_go[mid] <= e) l = mid;
+              else h = mid - 1;
+            }
+            w = ci[s_rs[l] + (int)(e - s_go[l])];
+            if (nl < dist[w]) {
+              const int old = atomicMin(&dist[w], nl);
+              if (old > nl) {
+                q = true;
+                if (old < kInf) dec += (unsigned long long)(old - nl);
+                ++rel;
+              }
+            }
+          }
+          enqueue(q, w, nl);
+        }
+        const int done_end = s_go[cntx];
+        __syncthreads();  // the staged arrays are reused
+        if ((long long)done_end >= ee) break;
+        x += cntx;
       }
     }
     ok = grid_sync(bar, err, timeout_ns);

@@ -73,10 +73,9 @@ struct GridBar {
 // Grid-wide BFS control block (zeroed before each launch).
 struct BfsCtl {
   GridBar bar;
-  int32_t qsize[3];     // frontier sizes by level mod 3
+  unsigned long long pk[3];  // frontier by level mod 3: entries << 32 | adjacency entries
   int32_t err;          // GC_* code set by the device, 0 = fine
   int32_t levels;       // levels completed
-  int32_t pad;
   unsigned long long decrease;  // sum over relabelled vertices of (old - new), old finite
   unsigned long long relabelled;
   int32_t blk_tot[kMaxGridCtas];  // per-CTA adjacency totals of the level
@@ -126,8 +125,9 @@ struct LazyCtl {
   int32_t rounds_done;
   long long best_gain;
   long long theta;      // every candidate outside the active list has ub < theta
-  int32_t qsize[3];     // relabel BFS frontier sizes
-  int32_t pad;
+  int32_t pad;          // fold flag of the batched solver
+  int32_t pad3;
+  unsigned long long pk[3];  // relabel BFS frontiers (see BfsCtl)
   unsigned long long decrease;
   long long steps, evals;
   unsigned long long ns_select, ns_gain, ns_update;  // time in each phase (CTA 0's clock)

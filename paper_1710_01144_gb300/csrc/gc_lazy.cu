@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       picks[r] = lc->best_id;
       pgain[r] = lc->best_gain;
-      lc->qsize[0] = lc->qsize[1] = lc->qsize[2] = 0;
+      lc->pk[0] = lc->pk[1] = lc->pk[2] = 0;
       lc->decrease = 0;
     }
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         if (threadIdx.x == 0) lc->decrease = (unsigned long long)d;
       }
     } else {
-      ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->qsize, nullptr, &lc->decrease,
-                            &lc->upd_relabels, goff, gg->blk_tot, &lc->bar, &lc->err, tns, lc->upd_work);
+      ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->pk, nullptr, &lc->decrease,
+                            &lc->upd_relabels, goff, gx, &lc->bar, &lc->err, tns, lc->upd_work);
     }
     ok = ok && grid_sync(&lc->bar, &lc->err, tns);
     if (!ok) break;

@@ -11,10 +11,10 @@
 //
 // The scratch is a file-scope __device__ array of kStaticScratchBytes (64 MiB).
 // Every GPU that loads the library reserves it until the process exits.  It
-// holds d(., S), two BFS queues and a frontier-offset array, the kernels'
+// holds d(., S), two BFS queues and two range-start lists, the kernels'
 // control words and as many per-CTA gain workspaces (44 bytes per vertex
 // each) as fit; a graph needs at least one workspace, which caps n at about
-// one million vertices (64 bytes per vertex in all).
+// 980,000 vertices (68 bytes per vertex in all).
 //
 // Host code cannot use the array's name as a device address; on the first
 // call on each device (with that device current) the library looks the
@@ -95,7 +95,7 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   // carve the array: control words, d(., S), BFS queues, then workspaces
   const size_t stride = gain_ws_stride(n);
   const size_t a4 = round_up((size_t)n * sizeof(int32_t));
-  const size_t head = round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)) + 3 * a4 +
+  const size_t head = round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)) + 4 * a4 +
                       round_up(((size_t)n + 1) * sizeof(int32_t));
   if (head + stride > kStaticScratchBytes) {
     set_error("gc_marginal_gains_static: n = " + std::to_string(n) + " needs " +
@@ -125,6 +125,8 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   p += a4;
   g.goff = (int32_t *)p;
   p += round_up(((size_t)n + 1) * sizeof(int32_t));
+  g.gx = (int32_t *)p;  // second range-start list of the relabel BFS
+  p += a4;
   g.ws = p;
   g.ws_stride = stride;
   const int fit = (int)((kStaticScratchBytes - head) / stride);
