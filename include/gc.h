@@ -96,9 +96,10 @@ typedef struct gc_opts {
                               negative = none */
   uint32_t flags;          /* GC_OPT_NO_EXPAND_BOUND: do not skip expansions by the
                               neighbour bound (work only; the group is the same) */
-  int32_t spread_max_gain; /* step_mode 3: a step whose largest bound is at most this
-                              evaluates one candidate per CTA (no grid barrier
-                              inside); 0 or negative = always grid-wide */
+  int32_t step_form;       /* step_mode 3: 0 = automatic (wide when the batches of
+                              rounds 0-1 averaged more than 16 BFS levels), 1 = one
+                              grid-wide 64-lane batch per step, 2 = wide steps: up
+                              to 64 candidates per CTA, one CTA-local batch each */
   int32_t local_update_max_gain; /* step_mode 3: a pick whose gain is at most this
                               updates d_S on one CTA; 0 or negative = never */
   int32_t lazy_ctas;       /* step_mode 3: CTAs of the persistent kernel (fewer

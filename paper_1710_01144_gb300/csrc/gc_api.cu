@@ -60,7 +60,7 @@ static void release(gc_graph *g) {
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
-                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx};
+                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -223,6 +223,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   // bound; a second CTA per SM measured slower on R-MAT and grid graphs)
   if ((rc = lazy_occupancy(&occ))) return bail(rc);
   g->lazy_ctas = std::min(kMaxGridCtas, std::min(std::max(1, occ), 1) * g->num_sms);
+  g->wcap = (int32_t)std::min<long long>((long long)n, (long long)g->lazy_ctas * kLanes);
   g->red_blocks = g->num_sms * 4;
   // per-vertex arrays
   const size_t N = (size_t)n;
@@ -238,6 +239,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
       (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
+      (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
+      (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
     return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
@@ -456,7 +459,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const bool persistent = opts.step_mode == 0 || opts.step_mode == 3;
   const int32_t heavy = opts.round1_heavy < 0 ? 0 : (opts.round1_heavy == 0 ? 1024 : opts.round1_heavy);
   // measured on R-MAT graphs: the grid-wide forms win, so both default off
-  const long long spread_max = opts.spread_max_gain <= 0 ? -1 : opts.spread_max_gain;
+  // lazy step form: wide (one 64-lane batch per CTA) on deep graphs, where a
+  // grid-wide batch pays a grid barrier for each of its many levels
+  int step_form = opts.step_form;
   const long long local_max = opts.local_update_max_gain <= 0 ? -1 : opts.local_update_max_gain;
   int64_t lazy_steps = 0, lazy_evals = 0, lazy_launches = 0;
   GainCtl lazy0, lazy1;  // gain counters around the persistent kernel
@@ -481,6 +486,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
       GC_TRY(read_ctl(g));
       lazy0 = *g->h_gctl;
+      if (step_form == 0)  // levels per 64-lane batch so far (rounds 0 and 1)
+        step_form = lazy0.batches && lazy0.levels > kWideLevels * lazy0.batches ? 2 : 1;
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
         cudaEvent_t le0, le1;
@@ -489,8 +496,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         ev_used += 2;
         ev_k64.push_back(2);
         GC_CUDA(cudaEventRecord(le0, g->stream));
-        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill, spread_max,
-                                  local_max, opts.lazy_ctas));
+        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill,
+                                  step_form == 2, local_max, opts.lazy_ctas));
         GC_CUDA(cudaEventRecord(le1, g->stream));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));

@@ -15,6 +15,7 @@ namespace gc {
 constexpr int32_t kInf = 0x3fffffff;  // "unreached" distance (d + 1 cannot overflow)
 constexpr int kLanes = 64;            // candidates per bit-parallel batch (one uint64 word)
 constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
+constexpr int kWideLevels = 16;       // lazy steps go wide above this many BFS levels per batch
 constexpr int kEdgeIlp = 4;           // adjacency entries in flight per thread (CTA gain batch)
 constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS
 constexpr int kRedThreads = 256;      // threads per CTA of reductions / scans
@@ -207,6 +208,10 @@ struct gc_graph {
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
   int32_t *gx = nullptr;       // grid-wide gain batch: entry offsets by level parity, third list [3n]
+  int32_t *wsel = nullptr;     // wide lazy steps: candidates, list positions, gains [wcap]
+  int32_t *wpos = nullptr;
+  long long *wgain = nullptr;
+  int32_t wcap = 0;
   long long *akey = nullptr;   // persistent lazy kernel: ub of list entry i [n]
   int32_t *ast = nullptr;      // persistent lazy kernel: stamp of list entry i [n]
   int32_t *bq0 = nullptr, *bq1 = nullptr;  // grid BFS queues [n]
@@ -308,11 +313,11 @@ int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 int launch_max_nbr(gc_graph *g);
 int launch_active_theta(gc_graph *g);
 // prop: proposal weights (nullptr = plain bound order); fill: lanes it chooses
-// spread_max: largest bound of a step evaluated one candidate per CTA (above
-// it, one grid-wide 64-lane batch); local_max: largest pick gain whose d_S
-// update runs on one CTA (above it, grid-wide)
+// wide: steps of one 64-lane batch per CTA (else one grid-wide 64-lane batch);
+// local_max: largest pick gain whose d_S update runs on one CTA (above it,
+// grid-wide)
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       long long spread_max, long long local_max, int ctas);
+                       bool wide, long long local_max, int ctas);
 int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 

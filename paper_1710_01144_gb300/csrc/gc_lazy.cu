@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   int32_t *goff, GridGainCtl *gg, LazyCtl *lc, GainCtl *gctl, int32_t *bq0, int32_t *bq1,
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
-                  long long spread_max, long long local_max, long long *akey, int32_t *ast,
-                  int32_t *gx) {
+                  int32_t wide, long long local_max, long long *akey, int32_t *ast,
+                  int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   {  // compact copies of the bounds of the (new) active list, and best_id's position
@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
       if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
     }
-    if (blockIdx.x == 0) lazy_cta0_step(act, m, ub, stamp, lc, gg, fold, prop ? score : nullptr, fill, akey, ast);
+    if (blockIdx.x == 0)
+      lazy_cta0_step(act, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill, akey,
+                     ast, wsel, wgain, wpos, wide ? wcap : 0);
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();
@@ -71,16 +73,15 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     const int dec = *(volatile int32_t *)&lc->dec;
     if (dec == 2) break;  // the host lowers theta and relaunches
     if (dec == 0) {
-      // small searches: one candidate per CTA, no barrier inside; large ones:
-      // the whole grid on one 64-lane batch.  Every CTA sees the same bounds.
-      const int ns = *(volatile int32_t *)&lc->n_sel;
-      long long umax = 0;
-      for (int j = 0; j < ns; ++j) umax = max(umax, ub[lc->sel[j]]);
+      // wide steps (deep graphs): one 64-lane batch per CTA, no grid barrier
+      // inside; otherwise the whole grid on one 64-lane batch.
       bool ok;
-      if (umax <= spread_max) {
-        if (blockIdx.x < ns)
-          cta_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel + blockIdx.x, 1, lc->gsel + blockIdx.x, myws, gctl, mx,
-                                    LaneGraphs(), cnt);
+      if (wide) {
+        const int ns = *(volatile int32_t *)&lc->n_sel;
+        const int nb = (ns + kLanes - 1) / kLanes;
+        for (int bi = blockIdx.x; bi < nb; bi += gridDim.x)
+          cta_gain_batch<kModeGain>(rp, ci, n, dS, wsel + bi * kLanes, min(kLanes, ns - bi * kLanes),
+                                    wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt);
         ok = true;
       } else {
         ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
@@ -172,7 +173,13 @@ int launch_active_theta(gc_graph *g) {
 }
 
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       long long spread_max, long long local_max, int ctas) {
+                       bool wide_steps, long long local_max, int ctas) {
+  int grid = std::min(g->lazy_ctas, g->ws_count);
+  if (ctas > 0 && ctas < grid) grid = ctas;
+  int32_t wide = wide_steps ? 1 : 0;
+  int32_t wcap = std::min(g->wcap, grid * kLanes);
+  int32_t *wsel = g->wsel, *wpos = g->wpos;
+  long long *wgain = g->wgain;
   const int32_t *rp = g->rp, *ci = g->ci;
   int32_t n = g->n;
   int32_t *dS = g->dS;
@@ -201,11 +208,9 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
-                  (void *)&ws_stride, (void *)&spread_max, (void *)&local_max, (void *)&akey,
-                  (void *)&ast, (void *)&gx};
+                  (void *)&ws_stride, (void *)&wide, (void *)&local_max, (void *)&akey,
+                  (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap};
   ++g->launches;
-  int grid = std::min(g->lazy_ctas, g->ws_count);
-  if (ctas > 0 && ctas < grid) grid = ctas;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
                                       dim3(kGridGainThreads),
                                       args, 0, g->stream));

@@ -81,15 +81,15 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
 }
 
 // Exact top-`need` of the list entries by key (larger first; ties by list
-// order, i.e. smaller id), written to sel[base..) and, when selpos is given,
-// their list positions to selpos[base..).  key(i, v) returns LLONG_MIN
+// order, i.e. smaller id), written to sel[base..cap) and, when selpos is
+// given, their list positions to selpos[base..cap).  key(i, v) returns LLONG_MIN
 // for entries that are not eligible; kmin/kmax/cnt describe the eligible keys.
 // Histogram passes over [kmin, kmax] fix the threshold value; every key above it
 // is taken, then keys equal to it in list order.  Returns the number taken.
 template <class KeyFn>
 static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
                         long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist,
-                        int32_t *selpos = nullptr, unsigned long long *scanned = nullptr) {
+                        int32_t *selpos = nullptr, unsigned long long *scanned = nullptr, int cap = kLanes) {
   __shared__ int s_scan[33];
   __shared__ int s_b;
   __shared__ long long s_ab;
@@ -167,7 +167,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
     const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
     const int take = gt || (eq && eq_rank < need - above);
     const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
-    if (take && base + pos < kLanes) {
+    if (take && base + pos < cap) {
       sel[base + pos] = v;
       if (selpos) selpos[base + pos] = i;
     }
@@ -182,13 +182,16 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
 // lc->sel[0..n_sel), 1 accept lc->best_id, 2 rebuild the list).  With compact
 // keys (akey/ast non-null: ub and stamp of list entry i at position i, kept in
 // step with ub/stamp), every scan of the list reads contiguous words instead of
-// gathering ub[v] and stamp[v]; lc->selpos/best_pos then hold list positions.  With a
+// gathering ub[v] and stamp[v]; lc->selpos/best_pos then hold list positions.
+// With wcap > 0 (wide steps) a step selects up to wcap candidates into
+// wsel/wpos (their gains come back in wgain) instead of 64 into lc->sel.  With a
 // proposal network (score != nullptr), `fill` of the 64 lanes go to the
 // unevaluated candidates whose bound most exceeds the network's predicted
 // gain: evaluating them tightens the bounds later rounds must beat.
 static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
                                LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill,
-                               long long *akey = nullptr, int32_t *ast = nullptr) {
+                               long long *akey = nullptr, int32_t *ast = nullptr, int32_t *wsel = nullptr,
+                               long long *wgain = nullptr, int32_t *wpos = nullptr, int wcap = 0) {
   __shared__ long long s_v[32];
   __shared__ int s_id[32];
   __shared__ long long s_ll[32];
@@ -200,22 +203,27 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
 
   if (fold) {  // the batch just evaluated: exact gains become the bounds
     const int ns = lc->n_sel;
+    const int32_t *fsel = wcap ? wsel : lc->sel, *fpos = wcap ? wpos : lc->selpos;
+    const long long *fgain = wcap ? wgain : lc->gsel;
     long long bv = -1;
-    int bid = -1, mine = -1, mypos = -1;
-    if (tid < ns) {
-      const int v = lc->sel[tid];
-      const long long gv = lc->gsel[tid];
+    int bid = -1, mypos = -1;
+    for (int i = tid; i < ns; i += T) {
+      const int v = fsel[i];
+      const long long gv = fgain[i];
       ub[v] = gv;
       stamp[v] = r;
+      const int p = akey ? fpos[i] : -1;
       if (akey) {
-        mypos = lc->selpos[tid];
-        akey[mypos] = gv;
-        ast[mypos] = r;
+        akey[p] = gv;
+        ast[p] = r;
       }
-      bv = gv;
-      bid = v;
-      mine = v;
+      if (better_max(gv, v, bv, bid)) {
+        bv = gv;
+        bid = v;
+        mypos = p;
+      }
     }
+    const int mine = bid;
     block_argmax_all(bv, bid, s_v, s_id);
     if (mine >= 0 && mine == bid) s_bpos = mypos;
     __syncthreads();
@@ -260,14 +268,23 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     if (tid == 0) lc->dec = dec;
     return;
   }
-  // the largest bounds (all 64 lanes without a proposal)
-  const int need1 = score ? kLanes - fill : kLanes;
+  // the largest bounds (all 64 lanes without a proposal; wcap in wide steps)
+  const int need1 = wcap ? wcap : (score ? kLanes - fill : kLanes);
   auto by_bound = [=] __device__(int i, int v) -> long long {
     const long long u = akey ? akey[i] : ub[v];
     return (u >= 0 && (akey ? ast[i] : stamp[v]) != r) ? u : LLONG_MIN;
   };
   int32_t *selpos = akey ? lc->selpos : nullptr;
   unsigned long long *scanned = akey ? &lc->sel_scanned : nullptr;
+  if (wcap) {
+    const int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, wsel, 0, s_hist, akey ? wpos : nullptr,
+                               scanned, wcap);
+    if (tid == 0) {
+      lc->n_sel = taken < wcap ? taken : wcap;
+      lc->dec = 0;
+    }
+    return;
+  }
   int taken = cta_topk(act, m, by_bound, umin, umax, cnt, need1, lc->sel, 0, s_hist, selpos, scanned);
   if (score && taken < kLanes && cnt > taken) {
     // mark the bound picks as evaluated in this round (their fold does it again)

@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("max_ctas", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
                 ("step_lanes", ctypes.c_int32), ("step_mode", ctypes.c_int32),
                 ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("spread_max_gain", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("step_form", ctypes.c_int32),
                 ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32)]
 
 
@@ -228,14 +228,14 @@ class Graph:
     def greedy(self, k: int, eval_per_step: int = 0, max_ctas: int = 0, timeout_ms: int = 0,
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
-               spread_max_gain: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0):
+               step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
         o.step_lanes, o.step_mode, o.active_target = step_lanes, step_mode, active_target
         o.round1_heavy = round1_heavy
         o.flags = 0 if expand_bound else GC_OPT_NO_EXPAND_BOUND
-        o.spread_max_gain, o.local_update_max_gain = spread_max_gain, local_update_max_gain
+        o.step_form, o.local_update_max_gain = step_form, local_update_max_gain
         o.lazy_ctas = lazy_ctas
         if timeout_ms:
             o.timeout_ms = timeout_ms

@@ -96,14 +96,15 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
 
 @pytest.mark.parametrize("name,g", small_cases())
 def test_greedy_step_forms(gcm, name, g):
-    """Persistent rounds with every evaluation spread one candidate per CTA and
-    every d_S update on one CTA, and with both always grid-wide."""
+    """Persistent rounds with wide steps (a 64-lane batch per CTA) or grid-wide
+    steps, each with every d_S update on one CTA or always grid-wide, and with
+    the automatic choice."""
     rp, ci = g
     k = min(12, rp.size - 1)
     grp, ft, _ = oracle.greedy_plain(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for spread, local in ((1 << 30, 1 << 30), (-1, -1), (1, 1 << 30), (4096, 4096)):
-            got, f, _ = G.greedy(k, spread_max_gain=spread, local_update_max_gain=local)
+        for form, local in ((2, 1 << 30), (1, -1), (2, -1), (1, 1 << 30), (0, 4096)):
+            got, f, _ = G.greedy(k, step_form=form, local_update_max_gain=local)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
 
@@ -152,10 +153,10 @@ def test_greedy_rmat20_k100_full_size(gcm):
         got, f, st = G.greedy(100)
         np.testing.assert_array_equal(got, grp)
         assert f == ft[-1]
-        for mode, heavy, bound, spread in ((1, -1, False, 0), (2, 64, True, 0), (3, 4096, True, -1),
-                                           (3, 0, False, 1 << 30)):
+        for mode, heavy, bound, form, local in ((1, -1, False, 0, 0), (2, 64, True, 0, 0), (3, 4096, True, 1, -1),
+                                                (3, 0, False, 2, 1 << 30)):
             g2, f2, _ = G.greedy(100, step_mode=mode, round1_heavy=heavy, expand_bound=bound,
-                                 spread_max_gain=spread, local_update_max_gain=spread)
+                                 step_form=form, local_update_max_gain=local)
             np.testing.assert_array_equal(g2, grp)
             assert f2 == ft[-1]
         # farness of the prefixes by the library's own BFS, against the trace
