@@ -30,6 +30,7 @@ static int fail(int code, const std::string &msg) {
 }
 
 constexpr int32_t kRound0GridMax = 256;  // round-0 survivors handled by grid-wide batches
+constexpr int kRound0Pivots = 8;         // round 0: at most this many pivot bounds
 
 #define GC_TRY(expr)              \
   do {                            \
@@ -60,7 +61,8 @@ static void release(gc_graph *g) {
   void *dev[] = {g->dS, g->ub, g->stamp, g->key, g->f0, g->list, g->lgain, g->bq0, g->bq1,
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
-                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain};
+                 g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
+                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -239,6 +241,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
       (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
+      (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
+      (rc = dalloc(&g->lev_max, 1)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
@@ -260,6 +264,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   if ((rc = dalloc(&g->ws, (size_t)want * g->ws_stride))) return bail(rc);
   if (cudaMemsetAsync(g->ws, 0, (size_t)want * g->ws_stride, st) != cudaSuccess ||
       cudaMemsetAsync(g->hist, 0, kHistBins * sizeof(unsigned int), st) != cudaSuccess ||
+      cudaMemsetAsync(g->lev_cnt, 0, N * sizeof(unsigned long long), st) != cudaSuccess ||
       cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), st) != cudaSuccess ||
       cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), st) != cudaSuccess)
     return bail(fail(GC_ECUDA, "memset failed"));
@@ -416,7 +421,23 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   GC_TRY(launch_round0_seed(g));
   GC_TRY(launch_select(g, kSelKey, 0, 0, kTauDevice, 0));
   GC_TRY(read_ctl(g));
-  const int32_t n_surv = g->h_sctl->n_sel;
+  int32_t n_surv = g->h_sctl->n_sel;
+  // Many survivors (deep graphs, where the degree bound is weak): tighten the
+  // bounds with the BFS levels of pivots (triangle inequality, see
+  // k_pivot_bound).  The first pivot is the vertex just searched; each further
+  // pivot is the undecided vertex of smallest bound, searched exactly, so it
+  // may also lower the threshold.
+  for (int piv = 0; n_surv > kRound0GridMax && piv < kRound0Pivots; ++piv) {
+    if (piv > 0) {
+      GC_TRY(launch_argmin_lb(g));
+      GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
+      GC_TRY(launch_round0_pivot(g));
+    }
+    GC_TRY(launch_pivot_bound(g));
+    GC_TRY(launch_select(g, kSelKey, 0, 0, kTauDevice, 0));
+    GC_TRY(read_ctl(g));
+    n_surv = g->h_sctl->n_sel;
+  }
   if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)

@@ -107,6 +107,91 @@ __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__re
   }
 }
 
+// Pivot lower bound for round 0.  For any vertex p and every w,
+// d(v, w) >= |d(p, w) - d(p, v)| (triangle inequality), so with n_l vertices
+// at distance l from p,
+//   f({v}) >= LB_p(v) = sum_l n_l * |l - d(p, v)|,
+// which prefix counts C[x] = sum_{l<x} n_l and prefix sums M[x] = sum_{l<x} l n_l
+// give in O(1) per vertex:  x C[x] - M[x] + (M[D+1] - M[x+1]) - x (n - C[x+1]).
+// The bound only decides which vertices still need an exact search.
+__global__ void __launch_bounds__(kRedThreads) k_level_hist(const int32_t *__restrict__ dist, int32_t n,
+                                                            unsigned long long *cnt, int32_t *maxlev) {
+  int mloc = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int x = dist[v];
+    if (x >= 0 && x < n) {
+      atomicAdd(&cnt[x], 1ull);
+      mloc = max(mloc, x);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mloc = max(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxlev, mloc);
+}
+
+// One CTA: cnt[0..D] -> C[0..D+1] (exclusive prefix counts, in place of cnt
+// shifted by one) and M[0..D+1]; D = *maxlev.  cnt is cleared for the next use.
+__global__ void __launch_bounds__(1024) k_level_prefix(unsigned long long *cnt, const int32_t *maxlev,
+                                                       unsigned long long *C, unsigned long long *M) {
+  __shared__ unsigned long long s_c[1024], s_m[1024];
+  __shared__ unsigned long long carry_c, carry_m;
+  const int D = *maxlev;
+  if (threadIdx.x == 0) {
+    carry_c = 0;
+    carry_m = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base <= D; base += 1024) {
+    const int l = base + threadIdx.x;
+    const unsigned long long c = l <= D ? cnt[l] : 0ull;
+    s_c[threadIdx.x] = c;
+    s_m[threadIdx.x] = c * (unsigned long long)(l <= D ? l : 0);
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
+      unsigned long long a = 0, b = 0;
+      if (threadIdx.x >= o) {
+        a = s_c[threadIdx.x - o];
+        b = s_m[threadIdx.x - o];
+      }
+      __syncthreads();
+      s_c[threadIdx.x] += a;
+      s_m[threadIdx.x] += b;
+      __syncthreads();
+    }
+    if (l <= D) {
+      C[l + 1] = carry_c + s_c[threadIdx.x];
+      M[l + 1] = carry_m + s_m[threadIdx.x];
+      cnt[l] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) {
+      carry_c += s_c[1023];
+      carry_m += s_m[1023];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    C[0] = 0;
+    M[0] = 0;
+  }
+}
+
+// key[v] = -max(LB(v), LB_p(v)) for vertices still undecided (key != INT64_MIN).
+__global__ void __launch_bounds__(kRedThreads) k_pivot_bound(const int32_t *__restrict__ dist, int32_t n,
+                                                             const unsigned long long *__restrict__ C,
+                                                             const unsigned long long *__restrict__ M,
+                                                             const int32_t *maxlev, long long *key) {
+  const int D = *maxlev;
+  const long long Mt = (long long)M[D + 1];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const long long k0 = key[v];
+    const int x = dist[v];
+    if (k0 == LLONG_MIN || x < 0 || x > D) continue;
+    const long long cx = (long long)C[x], cx1 = (long long)C[x + 1];
+    const long long lb = (long long)x * cx - (long long)M[x] + (Mt - (long long)M[x + 1]) - (long long)x * ((long long)n - cx1);
+    if (-lb < k0) key[v] = -lb;
+  }
+}
+
 // mx[u] = max over neighbours w of d_S[w].  d_S only decreases as the group
 // grows, so the value stays an upper bound; a frontier vertex u at level L can
 // claim a neighbour only if that neighbour's d_S exceeds L+1, so mx[u] <= L+1
@@ -219,6 +304,17 @@ int launch_round0_keys(gc_graph *g) {
   ++g->launches;
   k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
                   g->stream>>>(g->rp, g->ci, g->n, g->key, g->two_hop);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_pivot_bound(gc_graph *g) {
+  g->launches += 3;
+  GC_CUDA(cudaMemsetAsync(g->lev_max, 0, sizeof(int32_t), g->stream));
+  k_level_hist<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->dS, g->n, g->lev_cnt, g->lev_max);
+  k_level_prefix<<<1, 1024, 0, g->stream>>>(g->lev_cnt, g->lev_max, g->lev_C, g->lev_M);
+  k_pivot_bound<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->dS, g->n, g->lev_C, g->lev_M, g->lev_max,
+                                                              g->key);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

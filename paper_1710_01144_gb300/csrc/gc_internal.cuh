@@ -208,6 +208,9 @@ struct gc_graph {
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
   int32_t *gx = nullptr;       // grid-wide gain batch: entry offsets by level parity, third list [3n]
+  unsigned long long *lev_cnt = nullptr;  // round-0 pivot bound: level counts [n] (zero between uses)
+  unsigned long long *lev_C = nullptr, *lev_M = nullptr;  // prefix counts / level sums [n + 1]
+  int32_t *lev_max = nullptr;
   int32_t *wsel = nullptr;     // wide lazy steps: candidates, list positions, gains [wcap]
   int32_t *wpos = nullptr;
   long long *wgain = nullptr;
@@ -311,6 +314,11 @@ int launch_degree_keys(gc_graph *g);
 int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 // mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
 int launch_max_nbr(gc_graph *g);
+// round 0: key[v] = -max(LB(v), LB_p(v)) with p the source of the BFS now in d_S
+int launch_pivot_bound(gc_graph *g);
+// round 0: an exactly evaluated pivot (sctl->arg_id, farness sctl->sum) becomes
+// decided; best_f and tau follow the smallest exact farness so far
+int launch_round0_pivot(gc_graph *g);
 int launch_active_theta(gc_graph *g);
 // prop: proposal weights (nullptr = plain bound order); fill: lanes it chooses
 // wide: steps of one 64-lane batch per CTA (else one grid-wide 64-lane batch);

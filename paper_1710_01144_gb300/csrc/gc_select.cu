@@ -452,6 +452,17 @@ __global__ void k_round0_seed(long long *f0, long long *key, SelCtl *ctl, GainCt
   ctl->tau = -f;
 }
 
+__global__ void k_round0_pivot(long long *f0, long long *key, SelCtl *ctl, GainCtl *gctl) {
+  const int v = ctl->arg_id;
+  const long long f = ctl->sum;
+  if (v >= 0) {
+    f0[v] = f;
+    key[v] = LLONG_MIN;
+  }
+  if (f < gctl->best_f) gctl->best_f = f;
+  ctl->tau = -gctl->best_f;
+}
+
 // Start of a lazy round: clear the round's best and the acceptance flag.
 __global__ void k_round_begin(SelCtl *ctl) {
   ctl->best_gain = -1;
@@ -560,6 +571,13 @@ int launch_argmin_lb(gc_graph *g) {
 int launch_round0_seed(gc_graph *g) {
   ++g->launches;
   k_round0_seed<<<1, 1, 0, g->stream>>>(g->f0, g->key, g->sctl, g->gctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_round0_pivot(gc_graph *g) {
+  ++g->launches;
+  k_round0_pivot<<<1, 1, 0, g->stream>>>(g->f0, g->key, g->sctl, g->gctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
