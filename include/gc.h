@@ -67,6 +67,10 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
 #define GC_OPT_CAPTURE 0x2u /* gc_batch_greedy: record the launch sequence in a
                                CUDA graph once and replay it while ks and the
                                options stay the same */
+#define GC_OPT_FULL_ADJACENCY 0x4u /* gc_greedy: scan the full adjacency in rounds
+                               >= 1 instead of the pruned one built after round 0
+                               (rows without neighbours at d_S <= 1); work only,
+                               the group is the same */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */

@@ -62,7 +62,7 @@ static void release(gc_graph *g) {
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
-                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max};
+                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -241,7 +241,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->pgain, N)) || (rc = dalloc(&g->pdec, N)) ||
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
       (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
-      (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
+      (rc = dalloc(&g->rpf, N + 1)) || (rc = dalloc(&g->cif, std::max<size_t>(1, (size_t)nnz))) ||
+      (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
       (rc = dalloc(&g->lev_max, 1)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
@@ -378,6 +379,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   size_t ev_used = 0;
+  bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
                          int lanes) -> int {
@@ -387,7 +389,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     ev_used += 2;
     ev_k64.push_back(1);
     GC_CUDA(cudaEventRecord(e0, g->stream));
-    GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas, lanes));
+    GC_TRY(launch_gains(g, mode, cand, n_cand, n_dev, g->lgain, opts.max_ctas, lanes, pruned));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     return GC_OK;
   };
@@ -399,7 +401,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     ev_used += 2;
     ev_k64.push_back(0);
     GC_CUDA(cudaEventRecord(e0, g->stream));
-    GC_TRY(launch_gains_grid(g, mode, cand, nl, nl_dev, out, tns));
+    GC_TRY(launch_gains_grid(g, mode, cand, nl, nl_dev, out, tns, pruned));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     return GC_OK;
   };
@@ -462,6 +464,11 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(launch_max_nbr(g));
     g->mx = g->mx_buf;
   }
+  // pruned adjacency: drop the entries no later round can use (d_S[w] <= 1)
+  if (!(opts.flags & GC_OPT_FULL_ADJACENCY)) {
+    GC_TRY(launch_prune_csr(g));
+    pruned = true;
+  }
   const double ms_round0 =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   double ms_round1 = 0;
@@ -518,7 +525,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         ev_k64.push_back(2);
         GC_CUDA(cudaEventRecord(le0, g->stream));
         GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill,
-                                  step_form == 2, local_max, opts.lazy_ctas));
+                                  step_form == 2, local_max, opts.lazy_ctas, pruned));
         GC_CUDA(cudaEventRecord(le1, g->stream));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
@@ -595,7 +602,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     gains_picked[r] = g->h_sctl->best_gain;
     GC_TRY(launch_round_end(g));
     GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
-    GC_TRY(launch_bfs_relabel(g, g->dS, &g->sctl->best_id, 1, tns));
+    GC_TRY(launch_bfs_relabel(g, g->dS, &g->sctl->best_id, 1, tns, pruned));
     GC_CUDA(cudaMemcpyAsync(&g->h_bctl->decrease, &g->bctl->decrease, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, g->stream));
     GC_TRY(sync(g));

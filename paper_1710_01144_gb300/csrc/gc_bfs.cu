@@ -34,9 +34,9 @@ __global__ void k_fill_i64(long long *p, long long v, int64_t count) {
 __global__ void __launch_bounds__(kBfsThreads) k_bfs_relabel(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
     const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, int32_t *st0, int32_t *st1,
-    BfsCtl *ctl, unsigned long long timeout_ns) {
+    BfsCtl *ctl, unsigned long long timeout_ns, const int32_t *__restrict__ c3) {
   grid_relabel_bfs(rp, ci, n, dist, seeds, n_seeds, q0, q1, ctl->pk, &ctl->levels, &ctl->decrease,
-                   &ctl->relabelled, st0, st1, &ctl->bar, &ctl->err, timeout_ns);
+                   &ctl->relabelled, st0, st1, &ctl->bar, &ctl->err, timeout_ns, nullptr, c3);
 }
 
 // sum(dist) and the count of unreached vertices; the last CTA to finish folds
@@ -192,6 +192,109 @@ __global__ void __launch_bounds__(kRedThreads) k_pivot_bound(const int32_t *__re
   }
 }
 
+// Pruned adjacency for the rounds after round 0.  A neighbour w of u can be
+// claimed (or relabelled) at level L+1 only if d_S[w] > L+1 >= 1, and d_S only
+// decreases, so entries with d_S[w] <= 1 at the time of the build are useless
+// in every later round.  The pruned row of u keeps the entries with d_S[w] >= 2,
+// those with d_S[w] >= 3 first; c3[u] counts them.  Level 0 scans the whole
+// pruned row, levels >= 1 (where d_S[w] > 2 is needed) only its first c3[u].
+__global__ void __launch_bounds__(kRedThreads) k_prune_count(const int32_t *__restrict__ rp,
+                                                             const int32_t *__restrict__ ci, int32_t n,
+                                                             const int32_t *__restrict__ dS, int32_t *cnt2,
+                                                             int32_t *c3) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = gwarp; u < n; u += nwarps) {
+    int a2 = 0, a3 = 0;
+    for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+      const int d = dS[ci[e]];
+      a2 += d >= 2;
+      a3 += d >= 3;
+    }
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) {
+      cnt2[u] = a2;
+      c3[u] = a3;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_prune_fill(const int32_t *__restrict__ rp,
+                                                            const int32_t *__restrict__ ci, int32_t n,
+                                                            const int32_t *__restrict__ dS,
+                                                            const int32_t *__restrict__ rpf, int32_t *cif) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = gwarp; u < n; u += nwarps) {
+    int pos = rpf[u];
+    for (int pass = 0; pass < 2; ++pass) {  // d_S >= 3 first, then d_S == 2
+      for (int e0 = rp[u]; e0 < rp[u + 1]; e0 += 32) {
+        const int e = e0 + lane;
+        int w = 0;
+        bool keep = false;
+        if (e < rp[u + 1]) {
+          w = ci[e];
+          const int d = dS[w];
+          keep = pass == 0 ? d >= 3 : d == 2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) cif[pos + __popc(m & ((1u << lane) - 1u))] = w;
+        pos += __popc(m);
+      }
+    }
+  }
+}
+
+// Exclusive prefix sum of cnt[0..n) into out[0..n] (out[n] = total), three
+// launches: per-tile sums, a one-CTA scan of the tile sums, per-tile scans.
+constexpr int kScanTile = 4096;
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int32_t *__restrict__ cnt, int32_t n,
+                                                    long long *tile_sum) {
+  __shared__ long long s[32];
+  long long a = 0;
+  const int base = blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += 1024)
+    if (base + i < n) a += cnt[base + i];
+  a = block_sum(a, s);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = a;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tops(long long *tile_sum, int32_t tiles) {
+  __shared__ int s_scan[33];
+  long long carry = 0;
+  for (int base = 0; base < tiles; base += 1024) {
+    const int i = base + threadIdx.x;
+    const long long v = i < tiles ? tile_sum[i] : 0;
+    int tot;
+    // tile sums fit int32 here: the CSR has fewer than 2^31 entries
+    const int ex = block_excl_scan((int)v, s_scan, &tot);
+    if (i < tiles) tile_sum[i] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const int32_t *__restrict__ cnt, int32_t n,
+                                                    const long long *__restrict__ tile_sum, int32_t *out) {
+  __shared__ int s_scan[33];
+  const int base = blockIdx.x * kScanTile;
+  long long carry = tile_sum[blockIdx.x];
+  for (int off = 0; off < kScanTile; off += 1024) {
+    const int i = base + off + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, s_scan, &tot);
+    if (i < n) out[i] = (int32_t)(carry + ex);
+    if (i == n - 1) out[n] = (int32_t)(carry + ex + v);
+    carry += tot;
+    __syncthreads();
+  }
+}
+
 // mx[u] = max over neighbours w of d_S[w].  d_S only decreases as the group
 // grows, so the value stays an upper bound; a frontier vertex u at level L can
 // claim a neighbour only if that neighbour's d_S exceeds L+1, so mx[u] <= L+1
@@ -272,16 +375,17 @@ int launch_fill_i64(gc_graph *g, long long *p, long long v, int64_t count) {
 }
 
 int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t n_seeds,
-                       int64_t timeout_ns) {
+                       int64_t timeout_ns, bool pruned) {
   GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
-  const int32_t *rp = g->rp, *ci = g->ci;
+  const int32_t *rp = pruned ? g->rpf : g->rp, *ci = pruned ? g->cif : g->ci;
+  const int32_t *c3 = pruned ? g->c3 : nullptr;
   int32_t n = g->n;
   int32_t *q0 = g->bq0, *q1 = g->bq1, *st0 = g->goff, *st1 = g->gx;
   BfsCtl *ctl = g->bctl;
   unsigned long long tns = (unsigned long long)timeout_ns;
   void *args[] = {(void *)&rp,      (void *)&ci, (void *)&n,  (void *)&dist, (void *)&seeds,
                   (void *)&n_seeds, (void *)&q0, (void *)&q1, (void *)&st0, (void *)&st1, (void *)&ctl,
-                  (void *)&tns};
+                  (void *)&tns, (void *)&c3};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_relabel, dim3(std::min(g->bfs_ctas, kMaxGridCtas)),
                                       dim3(kBfsThreads), args, 0, g->stream));
@@ -315,6 +419,20 @@ int launch_pivot_bound(gc_graph *g) {
   k_level_prefix<<<1, 1024, 0, g->stream>>>(g->lev_cnt, g->lev_max, g->lev_C, g->lev_M);
   k_pivot_bound<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->dS, g->n, g->lev_C, g->lev_M, g->lev_max,
                                                               g->key);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_prune_csr(gc_graph *g) {
+  const int n = g->n;
+  const int tiles = (n + kScanTile - 1) / kScanTile;
+  const int grid = grid_for((int64_t)n * 32, kRedThreads, g->num_sms * 8);
+  g->launches += 5;
+  k_prune_count<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->io_a, g->c3);
+  k_scan_tiles<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain);
+  k_scan_tops<<<1, 1024, 0, g->stream>>>(g->lgain, tiles);
+  k_scan_apply<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain, g->rpf);
+  k_prune_fill<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->cif);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

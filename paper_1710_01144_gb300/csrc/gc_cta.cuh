@@ -24,13 +24,17 @@ struct GainCounters {
 // are then recorded in nx[(L + 1) & 1][w].  Level L + 1 expands w with the
 // lanes of that word, which the expanding thread reads and clears; so no
 // separate commit pass is needed between levels.
+//
+// With c3 (the pruned adjacency, see k_prune_count), rp/ci are the pruned
+// rows: level 0 scans a whole row, later levels only its first c3[u] entries.
 template <int MODE>
 __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                int32_t n, const int32_t *__restrict__ dS,
                                                const int32_t *__restrict__ cand, int nl,
                                                long long *__restrict__ out, const GainWs &ws, GainCtl *ctl,
                                                const int32_t *__restrict__ mx, const LaneGraphs lg,
-                                               GainCounters &cnt, int voff = 0) {
+                                               GainCounters &cnt, int voff = 0,
+                                               const int32_t *__restrict__ c3 = nullptr) {
   constexpr int T = kGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ int s_cnt[kLanes];
@@ -111,7 +115,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
         m = cur[u - voff];
         cur[u - voff] = 0;
         if (MODE == kModeFarness) m &= s_alive;
-        const int r0 = rp[u], r1 = rp[u + 1];
+        const int r0 = rp[u], r1 = (c3 && L > 0) ? r0 + c3[u] : rp[u + 1];
         // no neighbour of u can still be claimed: skip the scan
         if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
         if (m) {

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kGainThreads, 2)
               const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t n_cand_arg,
               const int32_t *__restrict__ n_cand_dev, long long *__restrict__ out,
               unsigned char *ws_base, size_t ws_stride, GainCtl *ctl, int lanes,
-              const int32_t *__restrict__ mx, const LaneGraphs lg) {
+              const int32_t *__restrict__ mx, const LaneGraphs lg, const int32_t *__restrict__ c3) {
   __shared__ int s_batch;
   __shared__ u64 s_red[32];
   const int tid = threadIdx.x;
@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     __syncthreads();
     if (b >= n_batches) break;
     const int base = b * lanes;
-    cta_gain_batch<MODE>(rp, ci, n, dS, cand + base, min(lanes, n_cand - base), out + base, ws, ctl, mx, lg, cnt);
+    cta_gain_batch<MODE>(rp, ci, n, dS, cand + base, min(lanes, n_cand - base), out + base, ws, ctl, mx, lg, cnt, 0,
+                         c3);
   }
   u64 c_scalar = block_sum(cnt.scalar, s_red);
   u64 c_union = block_sum(cnt.uni, s_red);
@@ -89,7 +90,7 @@ int gain_kernel_occupancy(int *blocks_per_sm) {
 }
 
 int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
-                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes) {
+                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes, bool pruned) {
   if (!n_cand_dev && n_cand <= 0) return GC_OK;
   if (lanes < 1 || lanes > kLanes) lanes = kLanes;
   GC_CUDA(cudaMemsetAsync(&g->gctl->batch_next, 0, sizeof(unsigned int), g->stream));
@@ -100,14 +101,16 @@ int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
     if (ctas > n_batches) ctas = n_batches;
   }
   ++g->launches;
+  const bool pr = pruned && mode == kModeGain;
+  const int32_t *rp = pr ? g->rpf : g->rp, *ci = pr ? g->cif : g->ci, *c3 = pr ? g->c3 : nullptr;
   if (mode == kModeGain)
     k_gains64<kModeGain><<<ctas, kGainThreads, 0, g->stream>>>(
-        g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes, g->mx,
-        LaneGraphs());
+        rp, ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes, g->mx,
+        LaneGraphs(), c3);
   else
     k_gains64<kModeFarness><<<ctas, kGainThreads, 0, g->stream>>>(
         g->rp, g->ci, g->n, g->dS, cand, n_cand, n_cand_dev, out, g->ws, g->ws_stride, g->gctl, lanes, nullptr,
-        g->lane_graphs);
+        g->lane_graphs, nullptr);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

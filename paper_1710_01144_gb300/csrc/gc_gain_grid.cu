@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 2)
                  const int32_t *__restrict__ dS, const int32_t *__restrict__ cand, int32_t nl_arg,
                  const int32_t *__restrict__ nl_dev, long long *__restrict__ out, unsigned char *ws_base,
                  int32_t *gx, int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl,
-                 unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
+                 unsigned long long timeout_ns, const int32_t *__restrict__ mx, const int32_t *__restrict__ c3) {
   grid_gain_batch<MODE>(rp, ci, n, dS, cand, nl_arg, nl_dev, out, ws_base, gx, goff, ctl, gctl, &ctl->bar,
-                        &ctl->err, timeout_ns, mx);
+                        &ctl->err, timeout_ns, mx, c3);
 }
 
 int grid_gain_occupancy(int *blocks_per_sm) {
@@ -42,11 +42,13 @@ int grid_gain_occupancy(int *blocks_per_sm) {
 }
 
 int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,
-                      long long *out, int64_t timeout_ns) {
+                      long long *out, int64_t timeout_ns, bool pruned) {
   if (!nl_dev && nl <= 0) return GC_OK;
   if (nl > kLanes) return GC_EINVAL;
   GC_CUDA(cudaMemsetAsync(g->ggctl, 0, sizeof(GridGainCtl), g->stream));
-  const int32_t *rp = g->rp, *ci = g->ci, *dS = g->dS;
+  const bool pr = pruned && mode == kModeGain;
+  const int32_t *rp = pr ? g->rpf : g->rp, *ci = pr ? g->cif : g->ci, *dS = g->dS;
+  const int32_t *c3 = pr ? g->c3 : nullptr;
   int32_t n = g->n;
   unsigned char *ws = g->ws;
   int32_t *gx = g->gx;
@@ -57,7 +59,7 @@ int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, co
   const int32_t *mx = mode == kModeGain ? g->mx : nullptr;
   void *args[] = {(void *)&rp,  (void *)&ci,   (void *)&n,   (void *)&dS,  (void *)&cand,
                   (void *)&nl,  (void *)&nl_dev, (void *)&out, (void *)&ws, (void *)&gx, (void *)&goff,
-                  (void *)&ctl, (void *)&gctl, (void *)&tns, (void *)&mx};
+                  (void *)&ctl, (void *)&gctl, (void *)&tns, (void *)&mx, (void *)&c3};
   ++g->launches;
   if (mode == kModeGain)
     GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gains_grid<kModeGain>, dim3(g->grid_ctas),

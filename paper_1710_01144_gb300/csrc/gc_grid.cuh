@@ -53,12 +53,15 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict_
 // warp-wide search, stages the entries covering its slice in shared memory
 // and expands them edge by edge.  A vertex with nothing left to claim (gain
 // mode: every neighbour's d_S <= its level + 1) is counted but never queued.
+// With c3 (pruned adjacency, see k_prune_count) rp/ci are the pruned rows and
+// levels >= 1 scan only their first c3[u] entries.
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
                                 const int32_t *nl_dev, long long *out, unsigned char *ws_base, int32_t *gx,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
-                                int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx) {
+                                int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
+                                const int32_t *__restrict__ c3 = nullptr) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
@@ -91,7 +94,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   auto enqueue = [&](bool q, int w, int lev) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    int deg = q ? rp[w + 1] - rp[w] : 0;
+    int deg = q ? ((c3 && lev > 0) ? c3[w] : rp[w + 1] - rp[w]) : 0;
     int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -187,7 +190,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           s_sm[tid] = m;
           s_rs[tid] = rp[u];
           if (s_go[tid] >= es && s_go[tid] < ee) {  // counted once: by the CTA holding the entry's first edge
-            const int deg = rp[u + 1] - s_rs[tid];
+            const int deg = (c3 && L > 0) ? c3[u] : rp[u + 1] - s_rs[tid];
             c_union += (u64)deg;
             c_scalar += (u64)__popcll(m) * (u64)deg;
             c_front += 1;
@@ -356,12 +359,15 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
 // entries right away (a hub row is shared by all CTAs instead of serialising
 // one warp).  q0/q1 are the lists and st0/st1 the range starts by level
 // parity, n entries each.  With `work` given, CTA 0 adds the frontier entries
-// and adjacency entries of every level to work[0], work[1].
+// and adjacency entries of every level to work[0], work[1].  With c3 (pruned
+// adjacency, valid when dist holds d_S) levels >= 1 scan only the first c3[u]
+// entries of the pruned rows rp/ci.
 static __device__ __forceinline__ bool grid_relabel_bfs(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *dist,
     const int32_t *seeds, int32_t n_seeds, int32_t *q0, int32_t *q1, unsigned long long *pk, int32_t *levels_out,
     unsigned long long *decrease, unsigned long long *relabelled, int32_t *st0, int32_t *st1,
-    GridBar *bar, int32_t *err, unsigned long long timeout_ns, unsigned long long *work = nullptr) {
+    GridBar *bar, int32_t *err, unsigned long long timeout_ns, unsigned long long *work = nullptr,
+    const int32_t *__restrict__ c3 = nullptr) {
   constexpr int kT = 1024;  // staging capacity (blockDim.x <= 1024)
   __shared__ unsigned long long sh_bfs[32];
   __shared__ int s_go[kT + 1];
@@ -375,7 +381,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
   auto enqueue = [&](bool q, int w, int lev) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    const int deg = q ? rp[w + 1] - rp[w] : 0;
+    const int deg = q ? ((c3 && lev > 0) ? c3[w] : rp[w + 1] - rp[w]) : 0;
     int incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {

@@ -208,6 +208,7 @@ struct gc_graph {
   int32_t *list = nullptr;     // compacted candidate list [n]
   long long *lgain = nullptr;  // gains/farness of list entries [n]
   int32_t *gx = nullptr;       // grid-wide gain batch: entry offsets by level parity, third list [3n]
+  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr;  // pruned adjacency after round 0 [n+1], [nnz], [n]
   unsigned long long *lev_cnt = nullptr;  // round-0 pivot bound: level counts [n] (zero between uses)
   unsigned long long *lev_C = nullptr, *lev_M = nullptr;  // prefix counts / level sums [n + 1]
   int32_t *lev_max = nullptr;
@@ -266,8 +267,10 @@ int cuda_fail(cudaError_t e, const char *what);
 // Grid-wide relabel BFS: dist[w] <- min(dist[w], level) from the seeds,
 // expanding only where the label decreased.  dist must already hold either
 // kInf (fresh BFS) or the current d_S (pruned update, Sec. 4.1).
+// pruned: use the pruned adjacency (g->rpf, g->cif, g->c3; valid only for
+// d_S updates after it was built from an earlier d_S) instead of the full CSR.
 int launch_bfs_relabel(gc_graph *g, int32_t *dist, const int32_t *seeds, int32_t n_seeds,
-                       int64_t timeout_ns);
+                       int64_t timeout_ns, bool pruned = false);
 int launch_fill_i32(gc_graph *g, int32_t *p, int32_t v, int64_t count);
 int launch_fill_i64(gc_graph *g, long long *p, long long v, int64_t count);
 // sum of dist and count of unreached -> sctl->sum, sctl->count
@@ -283,13 +286,15 @@ enum GainMode { kModeGain = 0, kModeFarness = 1 };
 // n_cand_dev (optional) overrides n_cand with a count held in device memory.
 // lanes: candidates per batch (1..64); fewer lanes spread one step's work
 // over more CTAs.
+// pruned (gain mode only): the pruned adjacency, as for launch_bfs_relabel.
 int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
-                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes = kLanes);
+                 const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes = kLanes,
+                 bool pruned = false);
 size_t gain_ws_stride(int32_t n);
 // One batch of nl <= 64 candidates with every CTA (cooperative launch);
 // nl_dev (optional) gives min(64, *nl_dev) instead.
 int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,
-                      long long *out, int64_t timeout_ns);
+                      long long *out, int64_t timeout_ns, bool pruned = false);
 int grid_gain_occupancy(int *blocks_per_sm);
 int gain_kernel_occupancy(int *blocks_per_sm);
 
@@ -314,6 +319,8 @@ int launch_degree_keys(gc_graph *g);
 int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 // mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
 int launch_max_nbr(gc_graph *g);
+// pruned adjacency (g->rpf, g->cif, g->c3) from the d_S now in g->dS
+int launch_prune_csr(gc_graph *g);
 // round 0: key[v] = -max(LB(v), LB_p(v)) with p the source of the BFS now in d_S
 int launch_pivot_bound(gc_graph *g);
 // round 0: an exactly evaluated pivot (sctl->arg_id, farness sctl->sum) becomes
@@ -325,7 +332,7 @@ int launch_active_theta(gc_graph *g);
 // local_max: largest pick gain whose d_S update runs on one CTA (above it,
 // grid-wide)
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       bool wide, long long local_max, int ctas);
+                       bool wide, long long local_max, int ctas, bool pruned);
 int lazy_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 

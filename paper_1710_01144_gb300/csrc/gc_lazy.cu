@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   unsigned long long tns, const int32_t *__restrict__ mx, const float *__restrict__ prop,
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
                   int32_t wide, long long local_max, long long *akey, int32_t *ast,
-                  int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap) {
+                  int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap,
+                  const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   {  // compact copies of the bounds of the (new) active list, and best_id's position
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     const int r = *(volatile int32_t *)&lc->round;
     if (r >= k) break;
     if (prop && *(volatile int32_t *)&lc->scored_round != r) {
-      lazy_score(act, m, prop, rp, dS, ub, stamp, two_hop, mx, r, lc->last_gain, score);
+      lazy_score(act, m, prop, rp_full, dS, ub, stamp, two_hop, mx, r, lc->last_gain, score);
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
       if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
     }
@@ -81,11 +82,11 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         const int nb = (ns + kLanes - 1) / kLanes;
         for (int bi = blockIdx.x; bi < nb; bi += gridDim.x)
           cta_gain_batch<kModeGain>(rp, ci, n, dS, wsel + bi * kLanes, min(kLanes, ns - bi * kLanes),
-                                    wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt);
+                                    wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt, 0, c3);
         ok = true;
       } else {
         ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
-                                        &lc->bar, &lc->err, tns, mx);
+                                        &lc->bar, &lc->err, tns, mx, c3);
       }
       ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
       if (!ok) break;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       }
     } else {
       ok = grid_relabel_bfs(rp, ci, n, dS, &lc->best_id, 1, bq0, bq1, lc->pk, nullptr, &lc->decrease,
-                            &lc->upd_relabels, goff, gx, &lc->bar, &lc->err, tns, lc->upd_work);
+                            &lc->upd_relabels, goff, gx, &lc->bar, &lc->err, tns, lc->upd_work, c3);
     }
     ok = ok && grid_sync(&lc->bar, &lc->err, tns);
     if (!ok) break;
@@ -173,14 +174,15 @@ int launch_active_theta(gc_graph *g) {
 }
 
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       bool wide_steps, long long local_max, int ctas) {
+                       bool wide_steps, long long local_max, int ctas, bool pruned) {
   int grid = std::min(g->lazy_ctas, g->ws_count);
   if (ctas > 0 && ctas < grid) grid = ctas;
   int32_t wide = wide_steps ? 1 : 0;
   int32_t wcap = std::min(g->wcap, grid * kLanes);
   int32_t *wsel = g->wsel, *wpos = g->wpos;
   long long *wgain = g->wgain;
-  const int32_t *rp = g->rp, *ci = g->ci;
+  const int32_t *rp = pruned ? g->rpf : g->rp, *ci = pruned ? g->cif : g->ci;
+  const int32_t *rp_full = g->rp, *c3 = pruned ? g->c3 : nullptr;
   int32_t n = g->n;
   int32_t *dS = g->dS;
   long long *ub = g->ub;
@@ -209,7 +211,8 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&lc,    (void *)&gctl,  (void *)&q0,   (void *)&q1,   (void *)&tns,
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&wide, (void *)&local_max, (void *)&akey,
-                  (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap};
+                  (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap,
+                  (void *)&rp_full, (void *)&c3};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
                                       dim3(kGridGainThreads),
