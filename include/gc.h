@@ -93,7 +93,8 @@ typedef struct gc_opts {
                               the device) */
   int32_t active_target;   /* step_mode 3: initial size of its candidate list
                               (grown x4 when the list cannot certify a pick);
-                              0 = 4096 */
+                              0 = 2048 for grid-wide steps, max(4096, two wide
+                              steps) for wide ones */
   int32_t round1_heavy;    /* round 1: this many highest-degree candidates are
                               evaluated by the grid-wide kernel before the
                               CTA-per-batch sweep over the rest; 0 = 1024,

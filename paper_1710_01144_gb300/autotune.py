@@ -24,7 +24,7 @@ import numpy as np
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gcgb300", "autotune.json")
 
 BATCH_SPACE = [{"lanes": l, "A": a} for l in (16, 32, 64) for a in (256, 1024, 4096)]
-SINGLE_SPACE = [{"active_target": a, "round1_heavy": h} for a in (1024, 4096) for h in (256, 1024, 4096)]
+SINGLE_SPACE = [{"active_target": a, "round1_heavy": h} for a in (512, 2048, 8192) for h in (256, 1024, 4096)]
 
 
 def _load(path):

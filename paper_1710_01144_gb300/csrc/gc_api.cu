@@ -420,6 +420,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   GC_TRY(launch_round0_keys(g));
   GC_TRY(launch_argmin_lb(g));
   GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
+  int32_t ds_src = g->h_sctl->arg_id;  // the vertex whose BFS distances are in d_S
   GC_TRY(launch_round0_seed(g));
   GC_TRY(launch_select(g, kSelKey, 0, 0, kTauDevice, 0));
   GC_TRY(read_ctl(g));
@@ -433,6 +434,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     if (piv > 0) {
       GC_TRY(launch_argmin_lb(g));
       GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
+      ds_src = g->h_sctl->arg_id;
       GC_TRY(launch_round0_pivot(g));
     }
     GC_TRY(launch_pivot_bound(g));
@@ -456,9 +458,11 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const long long f_s0 = g->h_sctl->arg_val;
   const int64_t round0_evals = (int64_t)g->h_gctl->lanes + 1;
   if (s0 < 0) return fail(GC_EINTERNAL, "round 0 produced no vertex");
-  int64_t f = 0;
-  GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, &f));
-  if (f != f_s0) return fail(GC_EINTERNAL, "farness of s0 disagrees between round 0 and the BFS");
+  int64_t f = f_s0;
+  if (s0 != ds_src) {  // d_S = d(s0, .) unless s0's BFS is the one already in d_S
+    GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, &f));
+    if (f != f_s0) return fail(GC_EINTERNAL, "farness of s0 disagrees between round 0 and the BFS");
+  }
   // neighbour bound for the pruning of useless expansions in every later round
   if (!(opts.flags & GC_OPT_NO_EXPAND_BOUND)) {
     GC_TRY(launch_max_nbr(g));
@@ -511,11 +515,14 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       init.scored_round = -1;
       *g->h_lctl = init;
       GC_CUDA(cudaMemcpyAsync(g->lctl, g->h_lctl, sizeof(LazyCtl), cudaMemcpyHostToDevice, g->stream));
-      int32_t target = opts.active_target > 0 ? opts.active_target : 4096;
       GC_TRY(read_ctl(g));
       lazy0 = *g->h_gctl;
       if (step_form == 0)  // levels per 64-lane batch so far (rounds 0 and 1)
         step_form = lazy0.batches && lazy0.levels > kWideLevels * lazy0.batches ? 2 : 1;
+      // active list: short for 64-candidate steps (its scans are the selection's
+      // cost), at least two wide steps for wide ones
+      int32_t target = opts.active_target > 0 ? opts.active_target
+                                              : (step_form == 2 ? std::max<int32_t>(4096, 2 * g->wcap) : 2048);
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
         cudaEvent_t le0, le1;

@@ -103,8 +103,9 @@ def test_greedy_step_forms(gcm, name, g):
     k = min(12, rp.size - 1)
     grp, ft, _ = oracle.greedy_plain(rp, ci, k)
     with gcm.Graph(rp, ci) as G:
-        for form, local in ((2, 1 << 30), (1, -1), (2, -1), (1, 1 << 30), (0, 4096)):
-            got, f, _ = G.greedy(k, step_form=form, local_update_max_gain=local)
+        for form, local, pruned in ((2, 1 << 30, True), (1, -1, True), (2, -1, False), (1, 1 << 30, False),
+                                    (0, 4096, True)):
+            got, f, _ = G.greedy(k, step_form=form, local_update_max_gain=local, pruned_adjacency=pruned)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
 
@@ -153,10 +154,10 @@ def test_greedy_rmat20_k100_full_size(gcm):
         got, f, st = G.greedy(100)
         np.testing.assert_array_equal(got, grp)
         assert f == ft[-1]
-        for mode, heavy, bound, form, local in ((1, -1, False, 0, 0), (2, 64, True, 0, 0), (3, 4096, True, 1, -1),
-                                                (3, 0, False, 2, 1 << 30)):
+        for mode, heavy, bound, form, local, pruned in ((1, -1, False, 0, 0, True), (2, 64, True, 0, 0, False),
+                                                        (3, 4096, True, 1, -1, True), (3, 0, False, 2, 1 << 30, False)):
             g2, f2, _ = G.greedy(100, step_mode=mode, round1_heavy=heavy, expand_bound=bound,
-                                 step_form=form, local_update_max_gain=local)
+                                 step_form=form, local_update_max_gain=local, pruned_adjacency=pruned)
             np.testing.assert_array_equal(g2, grp)
             assert f2 == ft[-1]
         # farness of the prefixes by the library's own BFS, against the trace
