@@ -366,13 +366,15 @@ def _best_ms(fn, reps):
 def comparison_legs(gc, rp, ci, args, grp0, f0):
     """Plain GPU lazy greedy vs the learned + batched forms, same GPU, same
     groups.  Plain: host-driven lazy steps of 64 candidates in bound order (one
-    CTA per batch), no grid-wide steps, no heavy split, no expansion bound."""
+    CTA per batch), no grid-wide steps, no heavy split, no expansion bound, full
+    adjacency."""
     from paper_1710_01144_gb300 import autotune, graphgen, proposal
 
     out = {}
     with gc.Graph(rp, ci) as G:
         ms, (g, f, _) = _best_ms(lambda: G.greedy(args.k, step_mode=1, eval_per_step=64, step_lanes=64,
-                                                  round1_heavy=-1, expand_bound=False), 3)
+                                                  round1_heavy=-1, expand_bound=False,
+                                                  pruned_adjacency=False), 3)
         assert np.array_equal(g, grp0) and f == f0
         out["plain_gpu_lazy_ms"] = ms
         ms, (g, f, _) = _best_ms(lambda: G.greedy(args.k), 3)

@@ -48,6 +48,7 @@ struct BatchCtl {
   unsigned long long decrease;
   long long iterations;
   long long dbg[4];  // first failed check: phase, graph, expected, found
+  unsigned long long ns_ph[4];  // end of round 0 (P2), round 1 (P5), lazy rounds (P6), check (P7)
   int32_t blk_tot[kMaxGridCtas];
 };
 
@@ -69,6 +70,7 @@ struct BatchArgs {
   int32_t lanes1;         // candidates per round-1 batch
   int32_t max_n;          // vertices of the largest graph (workspace layout)
   int32_t *dS, *mx, *stamp, *q0, *q1, *goff, *st1;
+  int32_t *rpf, *cif, *c3;  // pruned adjacency for rounds >= 1 (built in P3)
   long long *ub, *key, *f0;
   unsigned char *ws;
   size_t ws_stride;
@@ -91,6 +93,81 @@ struct BatchArgs {
 constexpr int kBatchThreads = kGainThreads;
 
 static __device__ __forceinline__ bool bsync(const BatchArgs &a) { return grid_sync(&a.ctl->bar, &a.ctl->err, a.tns); }
+
+// The pruned adjacency of the single-graph path (k_prune_count in gc_bfs.cu)
+// over the union CSR, built inside the solve once d_S = d(s0, .) is known:
+// rows keep the neighbours with d_S >= 2, those with d_S >= 3 first (c3 of
+// them).  Count per vertex into a.q0 (free here), scan across CTAs (each
+// CTA owns a contiguous vertex range), fill.  Three grid barriers.
+static __device__ bool batch_prune(const BatchArgs &a) {
+  __shared__ int s_scan[33];
+  __shared__ long long s_off[kMaxGridCtas + 1];
+  const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x, G = gridDim.x, b = blockIdx.x;
+  const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+  for (int u = gw; u < a.N; u += nw) {
+    int a2 = 0, a3 = 0;
+    for (int e = a.rp[u] + lane; e < a.rp[u + 1]; e += 32) {
+      const int d = a.dS[a.ci[e]];
+      a2 += d >= 2;
+      a3 += d >= 3;
+    }
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) {
+      a.q0[u] = a2;
+      a.c3[u] = a3;
+    }
+  }
+  if (!bsync(a)) return false;
+  const int P = (a.N + G - 1) / G;
+  const int lo = min(a.N, b * P), hi = min(a.N, lo + P);
+  long long mine = 0;
+  for (int v = lo + tid; v < hi; v += T) mine += a.q0[v];
+  mine = block_sum(mine, (long long *)s_off);
+  if (tid == 0) a.ctl->blk_tot[b] = (int32_t)mine;  // < 2^31: the CSR has fewer entries
+  if (!bsync(a)) return false;
+  long long run = 0;
+  for (int base = 0; base < G; base += T) {
+    const int j = base + tid;
+    const int v = j < G ? ((volatile int32_t *)a.ctl->blk_tot)[j] : 0;
+    int total;
+    const int off = block_excl_scan(v, s_scan, &total);
+    if (j < G) s_off[j] = run + off;
+    run += total;
+    __syncthreads();
+  }
+  long long carry = s_off[b];
+  __syncthreads();
+  for (int base = lo; base < hi; base += T) {
+    const int v = base + tid;
+    const int x = v < hi ? a.q0[v] : 0;
+    int total;
+    const int off = block_excl_scan(x, s_scan, &total);
+    if (v < hi) a.rpf[v] = (int32_t)(carry + off);
+    carry += total;
+  }
+  if (b == G - 1 && tid == 0) a.rpf[a.N] = (int32_t)run;
+  if (!bsync(a)) return false;
+  for (int u = gw; u < a.N; u += nw) {
+    int pos = a.rpf[u];
+    for (int pass = 0; pass < 2; ++pass) {  // d_S >= 3 first, then d_S == 2
+      for (int e0 = a.rp[u]; e0 < a.rp[u + 1]; e0 += 32) {
+        const int e = e0 + lane;
+        int w = 0;
+        bool keep = false;
+        if (e < a.rp[u + 1]) {
+          w = a.ci[e];
+          const int d = a.dS[w];
+          keep = pass == 0 ? d >= 3 : d == 2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) a.cif[pos + __popc(m & ((1u << lane) - 1u))] = w;
+        pos += __popc(m);
+      }
+    }
+  }
+  return bsync(a);
+}
 
 // per-graph sum of d over all vertices (warp-aggregated when a warp's vertices
 // share a graph); unreached vertices raise GC_EDISCONNECTED
@@ -258,6 +335,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     __syncthreads();
   }
   if (!bsync(a)) return;
+  if (b == 0 && tid == 0) a.ctl->ns_ph[0] = global_ns() - t_start;
   // ---- P3: d_S = BFS from all s0; farness; neighbour bound ----
   for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
   if (!bsync(a)) return;
@@ -284,6 +362,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     a.ctl->task = 0;
   }
   if (!bsync(a)) return;
+  if (!batch_prune(a)) return;
   for (int g = b * T + tid; g < a.count; g += G * T) {
     const int s0 = a.seeds[g];
     if (a.f0[s0] != a.farness[g]) check_fail(a.ctl, 3, g, a.f0[s0], a.farness[g]);
@@ -309,8 +388,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     if (a.kk[g] < 2) continue;
     const int o = a.off[g], first = (t - a.bstart[g]) * a.lanes1;
     const int nl = min(a.lanes1, a.ng[g] - first);
-    cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, a.iota + o + first, nl, a.ub + o + first, myws, a.gctl,
-                              a.mx, LaneGraphs(), cnt, o);
+    cta_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, a.iota + o + first, nl, a.ub + o + first, myws, a.gctl,
+                              a.mx, LaneGraphs(), cnt, o, a.c3);
   }
   if (!bsync(a)) return;
   for (int v = b * T + tid; v < a.N; v += G * T) a.stamp[v] = 1;
@@ -368,9 +447,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     }
   }
   if (!bsync(a)) return;
-  if (!grid_relabel_bfs(a.rp, a.ci, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
+  if (!grid_relabel_bfs(a.rpf, a.cif, a.N, a.dS, a.seeds, *(volatile int32_t *)&a.ctl->nseeds, a.q0, a.q1,
                         a.ctl->pk, nullptr, &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar,
-                        &a.ctl->err, a.tns))
+                        &a.ctl->err, a.tns, nullptr, a.c3))
     return;
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) {
@@ -429,6 +508,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     __syncthreads();
   }
   if (!bsync(a)) return;
+  if (b == 0 && tid == 0) a.ctl->ns_ph[1] = global_ns() - t_start;
   // ---- P6: lazy rounds; each CTA runs its graphs to completion (no grid
   // barrier: a graph never waits for another graph's step) ----
   {
@@ -449,15 +529,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
         __syncthreads();
         const int dec = *(volatile int32_t *)&lc->dec;
         if (dec == 0) {  // evaluate the selected batch
-          cta_gain_batch<kModeGain>(a.rp, a.ci, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
-                                    LaneGraphs(), cnt, o);
+          cta_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
+                                    LaneGraphs(), cnt, o, a.c3);
           if (tid == 0) lc->pad = 1;  // fold it next step
         } else if (dec == 1) {  // accept: record, then update d_S from the pick
           const int pick = lc->best_id;
           const long long gain = lc->best_gain;
           const int r = lc->round;
           __syncthreads();
-          const long long decr = cta_relabel_bfs(a.rp, a.ci, a.dS, pick, myws.qv0, myws.qv1);
+          const long long decr = cta_relabel_bfs(a.rpf, a.cif, a.dS, pick, myws.qv0, myws.qv1);
           if (tid == 0) {
             if (decr != gain) check_fail(a.ctl, 6, g, gain, decr);
             a.picks[(size_t)g * a.kmax + r] = pick;
@@ -483,6 +563,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
     }
   }
   if (!bsync(a)) return;
+  if (b == 0 && tid == 0) a.ctl->ns_ph[2] = global_ns() - t_start;
   // ---- P7: check every group's farness with one BFS ----
   for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
   if (b == 0) {
@@ -511,6 +592,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArg
   if (!bsync(a)) return;
   for (int g = b * T + tid; g < a.count; g += G * T)
     if (a.farness[g] != a.fa[g]) check_fail(a.ctl, 7, g, a.fa[g], a.farness[g]);
+  if (b == 0 && tid == 0) a.ctl->ns_ph[3] = global_ns() - t_start;
   // work counters
   u64 c_scalar = block_sum(cnt.scalar, s_red);
   u64 c_union = block_sum(cnt.uni, s_red);
@@ -572,6 +654,7 @@ struct gc_batch {
   int32_t *rp = nullptr, *ci = nullptr, *gid = nullptr, *off = nullptr, *ng = nullptr, *iota = nullptr;
   int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr,
           *st1 = nullptr;
+  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr;
   long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
   unsigned char *ws = nullptr;
   size_t ws_stride = 0;
@@ -609,7 +692,7 @@ static void batch_release(gc_batch *b) {
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
-                 b->scount, b->tstart};
+                 b->scount, b->tstart, b->rpf, b->cif, b->c3};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -690,6 +773,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
             balloc(&b->lc, (size_t)count) && balloc(&b->act_n, (size_t)count) && balloc(&b->full, (size_t)count) &&
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
             balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
+            balloc(&b->rpf, Nn + 1) && balloc(&b->cif, std::max<size_t>(1, (size_t)E)) && balloc(&b->c3, Nn) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
   int64_t *d_eoff = nullptr;
@@ -841,6 +925,9 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.q1 = b->q1;
   a.goff = b->goff;
   a.st1 = b->st1;
+  a.rpf = b->rpf;
+  a.cif = b->cif;
+  a.c3 = b->c3;
   a.ub = b->ub;
   a.key = b->key;
   a.f0 = b->f0;
@@ -970,6 +1057,12 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     stats->lanes = (int64_t)b->h_gctl->lanes;
     stats->kernel_launches = 1;
     stats->graph_replay = used_graph ? 1 : 0;
+    // phases of the solve (CTA 0's clock): rounds 0, 1, the lazy rounds, the check
+    const unsigned long long *ph = b->h_ctl->ns_ph;
+    stats->ms_round0 = ph[0] * 1e-6;
+    stats->ms_round1 = (ph[1] - ph[0]) * 1e-6;
+    stats->ms_lazy_gain = (ph[2] - ph[1]) * 1e-6;
+    stats->ms_lazy_update = (ph[3] - ph[2]) * 1e-6;
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return GC_OK;
