@@ -214,7 +214,9 @@ static __device__ int cta_argmin_f0(const BatchArgs &a, int g) {
   return bid;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_solve(const BatchArgs a) {
+// Two CTAs per SM (64 registers, no spills): the CTA-local phases are latency
+// bound and gain from the second resident CTA.
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArgs a) {
   __shared__ long long s_out[kLanes];
   __shared__ int s_task;
   __shared__ int s_scan[33];
