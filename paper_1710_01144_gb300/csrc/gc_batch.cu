@@ -48,7 +48,8 @@ struct BatchCtl {
   unsigned long long decrease;
   long long iterations;
   long long dbg[4];  // first failed check: phase, graph, expected, found
-  unsigned long long ns_ph[4];  // end of round 0 (P2), round 1 (P5), lazy rounds (P6), check (P7)
+  unsigned long long ns_ph[6];  // end of round 0 (P2), round 1 (P5), lazy rounds (P6), check (P7),
+                                // start and end of the round-1 gains (P4)
   int32_t blk_tot[kMaxGridCtas];
 };
 
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     a.packed[g] = 0;  // reused as the round-1 arg-max key
   }
   // ---- P4: round 1 (graph-aligned batches from a dynamic counter) ----
+  if (b == 0 && tid == 0) a.ctl->ns_ph[4] = global_ns() - t_start;
   const int n_tasks = a.bstart[a.count];
   for (;;) {
     if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
@@ -394,6 +396,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
                               a.mx, LaneGraphs(), cnt, o, a.c3);
   }
   if (!bsync(a)) return;
+  if (b == 0 && tid == 0) a.ctl->ns_ph[5] = global_ns() - t_start;
   for (int v = b * T + tid; v < a.N; v += G * T) a.stamp[v] = 1;
   for (int g = b * T + tid; g < a.count; g += G * T) a.ub[a.seeds[g]] = -1;  // s0 is a member
   if (!bsync(a)) return;
@@ -1065,6 +1068,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     stats->ms_round1 = (ph[1] - ph[0]) * 1e-6;
     stats->ms_lazy_gain = (ph[2] - ph[1]) * 1e-6;
     stats->ms_lazy_update = (ph[3] - ph[2]) * 1e-6;
+    stats->ms_gain_kernel = (ph[5] - ph[4]) * 1e-6;  // round-1 gains of every graph (P4)
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return GC_OK;
