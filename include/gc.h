@@ -110,6 +110,10 @@ typedef struct gc_opts {
   int32_t lazy_ctas;       /* step_mode 3: CTAs of the persistent kernel (fewer
                               CTAs make its grid barriers cheaper); 0 = one per
                               SM; clamped to that */
+  int32_t batch_grid_min_n; /* gc_batch_greedy: graphs with at least this many
+                              vertices run their lazy rounds grid-wide, one
+                              graph at a time; the others CTA-locally;
+                              0 = 65536, negative = none */
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */

@@ -88,10 +88,14 @@ struct BatchArgs {
   int32_t *scount, *tstart;  // per-graph survivor counts, task prefix [count+1]
   BatchCtl *ctl;
   GainCtl *gctl;
+  GridGainCtl *gg;    // grid-wide batches of the big graphs' lazy rounds
+  int32_t *gx;        // their scratch: 3 * max_n
+  int32_t grid_min_n; // graphs with at least this many vertices run their lazy rounds grid-wide
   unsigned long long tns;
 };
 
 constexpr int kBatchThreads = kGainThreads;
+constexpr int32_t kBatchGridMinN = 65536;  // lazy rounds grid-wide from this many vertices
 
 static __device__ __forceinline__ bool bsync(const BatchArgs &a) { return grid_sync(&a.ctl->bar, &a.ctl->err, a.tns); }
 
@@ -168,6 +172,75 @@ static __device__ bool batch_prune(const BatchArgs &a) {
     }
   }
   return bsync(a);
+}
+
+// Lazy rounds (Sec. 4.2) of one big graph g by the whole grid: CTA 0 folds,
+// decides and selects 64 candidates (lazy_cta0_step), every CTA evaluates them
+// as one grid-wide 64-lane batch, and each pick updates d_S by the grid
+// relabel BFS, checked against the pick's gain.  A list that cannot certify a
+// pick is replaced by all of g's candidates.  Every CTA runs the same loop.
+static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
+  const int tid = threadIdx.x, b = blockIdx.x;
+  LazyCtl *lc = &a.lc[g];
+  const int o = a.off[g], ng = a.ng[g];
+  bool fold = false;
+  for (;;) {
+    const int r = *(volatile int32_t *)&lc->round;
+    if (r >= a.kk[g]) break;
+    if (b == 0) {
+      const bool full = *(volatile int32_t *)&a.full[g] != 0;
+      const int32_t *act = full ? a.iota + o : a.act + (size_t)g * a.A;
+      const int m = full ? ng : a.act_n[g];
+      if (full && tid == 0) lc->theta = LLONG_MIN;
+      __syncthreads();
+      lazy_cta0_step(act, m, a.ub, a.stamp, lc, a.gg, fold, nullptr, 0);
+    }
+    if (!bsync(a)) return false;
+    const int dec = *(volatile int32_t *)&lc->dec;
+    if (dec == 2) {  // the list cannot certify: use every candidate of the graph
+      if (b == 0 && tid == 0) a.full[g] = 1;
+      fold = false;
+      if (!bsync(a)) return false;
+      continue;
+    }
+    if (dec == 0) {
+      if (!grid_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, lc->sel, 0, &lc->n_sel, lc->gsel, a.ws, a.gx,
+                                      a.goff, a.gg, a.gctl, &a.ctl->bar, &a.ctl->err, a.tns, a.mx, a.c3, o,
+                                      a.max_n))
+        return false;
+      if (b == 0 && tid == 0 && *(volatile int32_t *)&a.gg->err)
+        atomicExch(&a.ctl->err, *(volatile int32_t *)&a.gg->err);
+      if (!bsync(a)) return false;  // workspace clean, gains visible
+      fold = true;
+      continue;
+    }
+    // accept the round's best and update d_S from it
+    fold = false;
+    if (b == 0 && tid == 0) {
+      a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
+      a.ctl->decrease = 0;
+    }
+    if (!bsync(a)) return false;
+    if (!grid_relabel_bfs(a.rpf, a.cif, a.N, a.dS, &lc->best_id, 1, a.q0, a.q1, a.ctl->pk, nullptr,
+                          &a.ctl->decrease, nullptr, a.goff, a.st1, &a.ctl->bar, &a.ctl->err, a.tns, nullptr,
+                          a.c3))
+      return false;
+    if (!bsync(a)) return false;
+    if (b == 0 && tid == 0) {
+      const int pick = lc->best_id;
+      const long long gain = lc->best_gain;
+      if ((long long)a.ctl->decrease != gain) check_fail(a.ctl, 6, g, gain, (long long)a.ctl->decrease);
+      a.picks[(size_t)g * a.kmax + r] = pick;
+      a.pgain[(size_t)g * a.kmax + r] = gain;
+      a.ub[pick] = -1;
+      lc->last_gain = gain;
+      lc->best_id = -1;
+      lc->best_gain = -1;
+      lc->round = r + 1;
+    }
+    if (!bsync(a)) return false;
+  }
+  return true;
 }
 
 // per-graph sum of d over all vertices (warp-aggregated when a warp's vertices
@@ -514,11 +587,15 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   }
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) a.ctl->ns_ph[1] = global_ns() - t_start;
-  // ---- P6: lazy rounds; each CTA runs its graphs to completion (no grid
-  // barrier: a graph never waits for another graph's step) ----
+  // ---- P6a: lazy rounds of the big graphs, one graph at a time by the grid ----
+  for (int g = 0; g < a.count; ++g)
+    if (a.ng[g] >= a.grid_min_n && a.kk[g] > 2 && !batch_grid_lazy(a, g)) return;
+  // ---- P6b: the other graphs' lazy rounds; each CTA runs its graphs to
+  // completion (no grid barrier: a graph never waits for another graph's step) ----
   {
     __shared__ int s_stop;
     for (int g = b; g < a.count; g += G) {
+      if (a.ng[g] >= a.grid_min_n) continue;  // done in P6a
       LazyCtl *lc = &a.lc[g];
       const int o = a.off[g];
       for (;;) {
@@ -659,7 +736,8 @@ struct gc_batch {
   int32_t *rp = nullptr, *ci = nullptr, *gid = nullptr, *off = nullptr, *ng = nullptr, *iota = nullptr;
   int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr,
           *st1 = nullptr;
-  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr;
+  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr, *gx = nullptr;
+  GridGainCtl *gg = nullptr;
   long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
   unsigned char *ws = nullptr;
   size_t ws_stride = 0;
@@ -681,7 +759,7 @@ struct gc_batch {
   cudaGraph_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream the sequence is captured on
   std::vector<int32_t> cap_k;
-  int32_t cap_A = 0, cap_lanes = 0;
+  int32_t cap_A = 0, cap_lanes = 0, cap_grid_min_n = 0;
   std::vector<int32_t> h_picks;
   std::vector<long long> h_pgain, h_far;
   int32_t *h_picks_pinned = nullptr;
@@ -697,7 +775,7 @@ static void batch_release(gc_batch *b) {
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
-                 b->scount, b->tstart, b->rpf, b->cif, b->c3};
+                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -779,6 +857,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
             balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
             balloc(&b->rpf, Nn + 1) && balloc(&b->cif, std::max<size_t>(1, (size_t)E)) && balloc(&b->c3, Nn) &&
+            balloc(&b->gx, 3 * (size_t)std::max<int32_t>(1, b->max_n)) && balloc(&b->gg, 1) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
   int64_t *d_eoff = nullptr;
@@ -908,7 +987,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   }
   std::vector<int32_t> bstart(b->count + 1, 0);
   for (int32_t g = 0; g < b->count; ++g) bstart[g + 1] = bstart[g] + (b->h_n[g] + lanes1 - 1) / lanes1;
-  const bool same = b->exec && !resized && b->cap_k == std::vector<int32_t>(ks, ks + b->count) && b->cap_A == A &&
+  const bool same = b->exec && !resized && b->cap_k == std::vector<int32_t>(ks, ks + b->count) && b->cap_A == A && b->cap_grid_min_n == opts.batch_grid_min_n &&
                     b->cap_lanes == lanes1;
   BatchArgs a;
   a.rp = b->rp;
@@ -933,6 +1012,10 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.rpf = b->rpf;
   a.cif = b->cif;
   a.c3 = b->c3;
+  a.gg = b->gg;
+  a.gx = b->gx;
+  a.grid_min_n = opts.batch_grid_min_n == 0 ? kBatchGridMinN
+                 : (opts.batch_grid_min_n < 0 ? INT32_MAX : opts.batch_grid_min_n);
   a.ub = b->ub;
   a.key = b->key;
   a.f0 = b->f0;
@@ -970,6 +1053,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     if ((e = cudaMemsetAsync(b->lc, 0, (size_t)b->count * sizeof(LazyCtl), st))) return e;
     if ((e = cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), st))) return e;
     if ((e = cudaMemsetAsync(b->gctl, 0, sizeof(GainCtl), st))) return e;
+    if ((e = cudaMemsetAsync(b->gg, 0, sizeof(GridGainCtl), st))) return e;
     void *args[] = {(void *)&a};
     if ((e = cudaLaunchCooperativeKernel((const void *)k_batch_solve, dim3(b->ctas), dim3(kBatchThreads), args, 0,
                                          st)))
@@ -1002,6 +1086,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     b->cap_k.assign(ks, ks + b->count);
     b->cap_A = A;
     b->cap_lanes = lanes1;
+    b->cap_grid_min_n = opts.batch_grid_min_n;
     // capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the graph is then launched on the caller's stream
     cudaError_t e = cudaSuccess;

@@ -54,14 +54,16 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict_
 // and expands them edge by edge.  A vertex with nothing left to claim (gain
 // mode: every neighbour's d_S <= its level + 1) is counted but never queued.
 // With c3 (pruned adjacency, see k_prune_count) rp/ci are the pruned rows and
-// levels >= 1 scan only their first c3[u] entries.
+// levels >= 1 scan only their first c3[u] entries.  With voff/ws_n (one graph
+// of a block-diagonal union) the vertices are [voff, voff + ws_n): workspace 0
+// and gx are laid out for ws_n vertices and indexed by w - voff.
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
                                 const int32_t *nl_dev, long long *out, unsigned char *ws_base, int32_t *gx,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
-                                const int32_t *__restrict__ c3 = nullptr) {
+                                const int32_t *__restrict__ c3 = nullptr, int voff = 0, int ws_n = -1) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
@@ -75,12 +77,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   const int tid = threadIdx.x, lane = tid & 31;
   const int G = gridDim.x, b = blockIdx.x;
   const int nl = nl_dev ? min(kLanes, *(volatile const int32_t *)nl_dev) : nl_arg;
-  const GainWs ws = gain_ws(ws_base, 0, n, 0);
+  if (ws_n < 0) ws_n = n;
+  const GainWs ws = gain_ws(ws_base, 0, ws_n, 0);
   // frontier lists by level mod 3 and range starts by level parity (selected,
   // not indexed, so that nothing lands in local memory)
-  int32_t *const list2 = gx + 2 * (size_t)n;
+  int32_t *const list2 = gx + 2 * (size_t)ws_n;
   auto list_of = [&](int r) -> int32_t * { return r == 0 ? ws.qv0 : (r == 1 ? ws.qv1 : list2); };
-  auto starts_of = [&](int p) -> int32_t * { return p ? gx + (size_t)n : gx; };
+  auto starts_of = [&](int p) -> int32_t * { return p ? gx + (size_t)ws_n : gx; };
   auto words_of = [&](int r) -> LaneWords { return r == 0 ? ws.nx[0] : (r == 1 ? ws.nx[1] : ws.nx[2]); };
   u64 c_scalar = 0, c_union = 0, c_front = 0, c_push = 0;
   if (tid < kLanes) {
@@ -125,7 +128,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       if (j < nl) {
         const u64 bit = 1ull << j;
         bool reach = false;
-        if (c < 0 || c >= n) {
+        if (c < 0 || c >= n || c - voff < 0 || c - voff >= ws_n) {  // outside the graph
           atomicExch(&ctl->err, GC_EINVAL);
         } else if (MODE == kModeGain) {
           const int dc = dS[c];
@@ -138,9 +141,9 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           reach = true;
         }
         if (reach) {
-          if (atomicOr(&ws.vis[c], bit) == 0) ws.touched[atomicAdd(&ctl->touched, 1)] = c;
+          if (atomicOr(&ws.vis[c - voff], bit) == 0) ws.touched[atomicAdd(&ctl->touched, 1)] = c;
           const bool expand = MODE != kModeGain || !mx || mx[c] > 1;
-          if (expand) q = atomicOr(&ws.nx[0][c], bit) == 0;
+          if (expand) q = atomicOr(&ws.nx[0][c - voff], bit) == 0;
         }
       }
       enqueue(q, c, 0);
@@ -162,7 +165,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     if (L > 0) {
       const LaneWords prev = words_of((L + 2) % 3);
       const int32_t *pl = list_of((L + 2) % 3);
-      for (int i = b * T + tid; i < F_prev; i += G * T) prev[pl[i]] = 0;
+      for (int i = b * T + tid; i < F_prev; i += G * T) prev[pl[i] - voff] = 0;
     }
     if (F == 0) break;
     if (b == 0 && tid == 0) ctl->pk[(L + 2) % 3] = 0;  // the frontier after next (read two levels ago)
@@ -184,7 +187,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         const int cntx = min(T, F - x);
         if (xi < F) {
           const int u = qcur_v[xi];
-          u64 m = cur[u];
+          u64 m = cur[u - voff];
           if (MODE == kModeFarness) m &= alive;
           s_go[tid] = qstart[xi];
           s_sm[tid] = m;
@@ -226,11 +229,11 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           for (int k = 0; k < kGridIlp; ++k) {
             // pruned unless w is strictly closer to the lane's candidate than to S
             const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
-            nb[k] = live ? (s_sm[sl[k]] & ~ws.vis[w[k]]) : 0ull;
+            nb[k] = live ? (s_sm[sl[k]] & ~ws.vis[w[k] - voff]) : 0ull;
           }
           u64 ov[kGridIlp];
 #pragma unroll
-          for (int k = 0; k < kGridIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k]], nb[k]) : ~0ull;
+          for (int k = 0; k < kGridIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) {
             u64 won = nb[k] & ~ov[k];
@@ -239,7 +242,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             if (won) {
               // expanded at level nlev only if some neighbour may still be claimed
               const bool expand = MODE != kModeGain || !mx || mx[w[k]] > nlev + 1;
-              if (expand) q = atomicOr(&nxt[w[k]], won) == 0;
+              if (expand) q = atomicOr(&nxt[w[k] - voff], won) == 0;
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
                 const int j = __ffsll((long long)won) - 1;
@@ -293,8 +296,8 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         // next one, which is not expanded
         const LaneWords lw0 = cur, lw1 = nxt;
         const int32_t *l0 = list_of(L % 3), *l1 = list_of((L + 1) % 3);
-        for (int i = b * T + tid; i < F; i += G * T) lw0[l0[i]] = 0;
-        for (int i = b * T + tid; i < Fn; i += G * T) lw1[l1[i]] = 0;
+        for (int i = b * T + tid; i < F; i += G * T) lw0[l0[i] - voff] = 0;
+        for (int i = b * T + tid; i < Fn; i += G * T) lw1[l1[i] - voff] = 0;
         F_prev = 0;
         ++L;
         break;
@@ -343,7 +346,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   }
   // leave the workspace zero for the next launch
   const int nt = *(volatile int32_t *)&ctl->touched;
-  for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i]] = 0;
+  for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i] - voff] = 0;
   if (!ok2 && b == 0 && tid == 0) atomicExch(&gctl->err, GC_ETIMEOUT);
   return ok2;
 }

@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("step_lanes", ctypes.c_int32), ("step_mode", ctypes.c_int32),
                 ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("step_form", ctypes.c_int32),
-                ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32)]
+                ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32),
+                ("batch_grid_min_n", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -351,11 +352,13 @@ class Batch:
     def __exit__(self, *a):
         self.close()
 
-    def greedy(self, ks, active_target: int = 0, lanes: int = 0, capture: bool = False, timeout_ms: int = 0):
+    def greedy(self, ks, active_target: int = 0, lanes: int = 0, capture: bool = False, timeout_ms: int = 0,
+               grid_min_n: int = 0):
         ks = np.ascontiguousarray(ks, dtype=np.int32)
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.active_target, o.step_lanes = active_target, lanes
+        o.batch_grid_min_n = grid_min_n
         o.flags = GC_OPT_CAPTURE if capture else 0
         if timeout_ms:
             o.timeout_ms = timeout_ms
