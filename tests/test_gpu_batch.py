@@ -46,10 +46,11 @@ def test_batch_matches_oracle(gcm):
     graphs, ks = mixed_batch()
     ref = oracle_groups(graphs, ks)
     with gcm.Batch(graphs) as B:
-        for act, lanes in ((0, 0), (2, 16), (64, 64)):
-            groups, far, st = B.greedy(ks, active_target=act, lanes=lanes)
+        # grid_min_n: 1 = every graph's lazy rounds grid-wide, -1 = all CTA-local
+        for act, lanes, gmin in ((0, 0, 0), (2, 16, 1), (64, 64, -1), (0, 0, 1)):
+            groups, far, st = B.greedy(ks, active_target=act, lanes=lanes, grid_min_n=gmin)
             for i, ((g, f), got) in enumerate(zip(ref, groups)):
-                np.testing.assert_array_equal(got, g, err_msg="graph %d (act %d)" % (i, act))
+                np.testing.assert_array_equal(got, g, err_msg="graph %d (act %d, gmin %d)" % (i, act, gmin))
                 assert far[i] == f
 
 
