@@ -229,6 +229,7 @@ static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
     if (b == 0 && tid == 0) {
       const int pick = lc->best_id;
       const long long gain = lc->best_gain;
+      a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
       if ((long long)a.ctl->decrease != gain) check_fail(a.ctl, 6, g, gain, (long long)a.ctl->decrease);
       a.picks[(size_t)g * a.kmax + r] = pick;
       a.pgain[(size_t)g * a.kmax + r] = gain;
@@ -649,7 +650,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   // ---- P7: check every group's farness with one BFS ----
   for (int v = b * T + tid; v < a.N; v += G * T) a.dS[v] = kInf;
   if (b == 0) {
-    if (tid == 0) a.ctl->nseeds = 0;
+    if (tid == 0) {
+      a.ctl->nseeds = 0;
+      a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;  // the grid lazy rounds leave them set
+    }
     __syncthreads();
     for (int g = tid; g < a.count; g += T) {
       long long f = a.pgain[(size_t)g * a.kmax];
