@@ -62,7 +62,7 @@ static void release(gc_graph *g) {
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
-                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3};
+                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -243,7 +243,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
       (rc = dalloc(&g->rpf, N + 1)) || (rc = dalloc(&g->cif, std::max<size_t>(1, (size_t)nnz))) ||
       (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
-      (rc = dalloc(&g->lev_max, 1)) ||
+      (rc = dalloc(&g->lev_max, 1)) || (rc = dalloc(&g->gsel, 1)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
@@ -266,6 +266,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
   if (cudaMemsetAsync(g->ws, 0, (size_t)want * g->ws_stride, st) != cudaSuccess ||
       cudaMemsetAsync(g->hist, 0, kHistBins * sizeof(unsigned int), st) != cudaSuccess ||
       cudaMemsetAsync(g->lev_cnt, 0, N * sizeof(unsigned long long), st) != cudaSuccess ||
+      cudaMemsetAsync(g->gsel, 0, sizeof(GridSelScratch), st) != cudaSuccess ||
       cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), st) != cudaSuccess ||
       cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), st) != cudaSuccess)
     return bail(fail(GC_ECUDA, "memset failed"));

@@ -89,6 +89,7 @@ struct BatchArgs {
   BatchCtl *ctl;
   GainCtl *gctl;
   GridGainCtl *gg;    // grid-wide batches of the big graphs' lazy rounds
+  GridSelScratch *gsel;  // their grid-wide selection
   int32_t *gx;        // their scratch: 3 * max_n
   int32_t grid_min_n; // graphs with at least this many vertices run their lazy rounds grid-wide
   unsigned long long tns;
@@ -174,34 +175,29 @@ static __device__ bool batch_prune(const BatchArgs &a) {
   return bsync(a);
 }
 
-// Lazy rounds (Sec. 4.2) of one big graph g by the whole grid: CTA 0 folds,
-// decides and selects 64 candidates (lazy_cta0_step), every CTA evaluates them
-// as one grid-wide 64-lane batch, and each pick updates d_S by the grid
-// relabel BFS, checked against the pick's gain.  A list that cannot certify a
-// pick is replaced by all of g's candidates.  Every CTA runs the same loop.
+// Lazy rounds (Sec. 4.2) of one big graph g by the whole grid: every CTA
+// takes part in each step's decision and selection (grid_lazy_step) over all
+// of g's candidates, evaluates the 64 selected as one grid-wide 64-lane batch,
+// and each pick updates d_S by the grid relabel BFS, checked against the
+// pick's gain.  Every CTA runs the same loop.
 static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
   const int tid = threadIdx.x, b = blockIdx.x;
   LazyCtl *lc = &a.lc[g];
   const int o = a.off[g], ng = a.ng[g];
+  if (b == 0 && tid == 0) lc->theta = LLONG_MIN;  // the list is every candidate
+  if (!bsync(a)) return false;
   bool fold = false;
   for (;;) {
     const int r = *(volatile int32_t *)&lc->round;
     if (r >= a.kk[g]) break;
-    if (b == 0) {
-      const bool full = *(volatile int32_t *)&a.full[g] != 0;
-      const int32_t *act = full ? a.iota + o : a.act + (size_t)g * a.A;
-      const int m = full ? ng : a.act_n[g];
-      if (full && tid == 0) lc->theta = LLONG_MIN;
-      __syncthreads();
-      lazy_cta0_step(act, m, a.ub, a.stamp, lc, a.gg, fold, nullptr, 0);
-    }
+    int dec;
+    if (!grid_lazy_step(a.iota + o, ng, a.ub, a.stamp, nullptr, nullptr, lc, a.gg, fold, lc->sel, lc->selpos,
+                        lc->gsel, kLanes, a.gsel, &a.ctl->bar, &a.ctl->err, a.tns, &dec))
+      return false;
     if (!bsync(a)) return false;
-    const int dec = *(volatile int32_t *)&lc->dec;
-    if (dec == 2) {  // the list cannot certify: use every candidate of the graph
-      if (b == 0 && tid == 0) a.full[g] = 1;
-      fold = false;
-      if (!bsync(a)) return false;
-      continue;
+    if (dec == 2) {  // cannot happen with every candidate listed
+      if (b == 0 && tid == 0) check_fail(a.ctl, 6, g, 1, 2);
+      return false;
     }
     if (dec == 0) {
       if (!grid_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, lc->sel, 0, &lc->n_sel, lc->gsel, a.ws, a.gx,
@@ -742,6 +738,7 @@ struct gc_batch {
           *st1 = nullptr;
   int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr, *gx = nullptr;
   GridGainCtl *gg = nullptr;
+  GridSelScratch *gsel = nullptr;
   long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
   unsigned char *ws = nullptr;
   size_t ws_stride = 0;
@@ -779,7 +776,7 @@ static void batch_release(gc_batch *b) {
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
-                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg};
+                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg, b->gsel};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -861,7 +858,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
             balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
             balloc(&b->rpf, Nn + 1) && balloc(&b->cif, std::max<size_t>(1, (size_t)E)) && balloc(&b->c3, Nn) &&
-            balloc(&b->gx, 3 * (size_t)std::max<int32_t>(1, b->max_n)) && balloc(&b->gg, 1) &&
+            balloc(&b->gx, 3 * (size_t)std::max<int32_t>(1, b->max_n)) && balloc(&b->gg, 1) && balloc(&b->gsel, 1) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
   int64_t *d_eoff = nullptr;
@@ -1017,6 +1014,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.cif = b->cif;
   a.c3 = b->c3;
   a.gg = b->gg;
+  a.gsel = b->gsel;
   a.gx = b->gx;
   a.grid_min_n = opts.batch_grid_min_n == 0 ? kBatchGridMinN
                  : (opts.batch_grid_min_n < 0 ? INT32_MAX : opts.batch_grid_min_n);
@@ -1058,6 +1056,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     if ((e = cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), st))) return e;
     if ((e = cudaMemsetAsync(b->gctl, 0, sizeof(GainCtl), st))) return e;
     if ((e = cudaMemsetAsync(b->gg, 0, sizeof(GridGainCtl), st))) return e;
+    if ((e = cudaMemsetAsync(b->gsel, 0, sizeof(GridSelScratch), st))) return e;
     void *args[] = {(void *)&a};
     if ((e = cudaLaunchCooperativeKernel((const void *)k_batch_solve, dim3(b->ctas), dim3(kBatchThreads), args, 0,
                                          st)))

@@ -15,6 +15,7 @@ namespace gc {
 constexpr int32_t kInf = 0x3fffffff;  // "unreached" distance (d + 1 cannot overflow)
 constexpr int kLanes = 64;            // candidates per bit-parallel batch (one uint64 word)
 constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
+constexpr int kCta0SelectMax = 4096;  // lazy selection by CTA 0 up to this list length, grid-wide above
 constexpr int kWideLevels = 16;       // lazy steps go wide above this many BFS levels per batch
 constexpr int kEdgeIlp = 4;           // adjacency entries in flight per thread (CTA gain batch)
 constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS
@@ -62,6 +63,20 @@ __device__ __forceinline__ GainWs gain_ws(unsigned char *base, size_t stride, in
   w.touched = (int32_t *)(p + a32 + 2 * a4);
   return w;
 }
+
+// Scratch of the grid-wide lazy step (gc_lazy.cuh, grid_lazy_step): per-CTA
+// partials of the decision scan and of the selection counts, and three
+// threshold histograms that are all zero between steps.
+constexpr int kSelBins = 1024;
+struct GridSelScratch {
+  long long umax[1024];
+  int32_t vmax[1024];
+  long long umin[1024];
+  long long cnt[1024];
+  int32_t gt[1024];
+  int32_t eq[1024];
+  unsigned int hist[3][kSelBins];
+};
 
 // Bounded grid barrier used by cooperative kernels: one arrival word whose
 // bit 31 flips once per episode (`gen` is padding).  Every wait gives up
@@ -212,6 +227,7 @@ struct gc_graph {
   unsigned long long *lev_cnt = nullptr;  // round-0 pivot bound: level counts [n] (zero between uses)
   unsigned long long *lev_C = nullptr, *lev_M = nullptr;  // prefix counts / level sums [n + 1]
   int32_t *lev_max = nullptr;
+  gc::GridSelScratch *gsel = nullptr;  // grid-wide lazy selection scratch (histograms zero at rest)
   int32_t *wsel = nullptr;     // wide lazy steps: candidates, list positions, gains [wcap]
   int32_t *wpos = nullptr;
   long long *wgain = nullptr;

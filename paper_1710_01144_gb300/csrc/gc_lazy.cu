@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
                   int32_t wide, long long local_max, long long *akey, int32_t *ast,
                   int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap,
-                  const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3) {
+                  const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3, GridSelScratch *gsel) {
   __shared__ unsigned long long s_red[32];
   const int m = *m_dev;
   {  // compact copies of the bounds of the (new) active list, and best_id's position
@@ -62,9 +62,19 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
       if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
     }
-    if (blockIdx.x == 0)
-      lazy_cta0_step(act, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill, akey,
-                     ast, wsel, wgain, wpos, wide ? wcap : 0);
+    // CTA 0 selects for short lists (a few scans of m entries cost less than
+    // the grid barriers of the grid-wide selection), with proposal lanes and in
+    // wide steps; otherwise every CTA takes part
+    if (prop || wide || m <= kCta0SelectMax) {
+      if (blockIdx.x == 0)
+        lazy_cta0_step(act, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
+                       akey, ast, wsel, wgain, wpos, wide ? wcap : 0);
+    } else {  // every CTA takes part in the selection
+      int dec_local;
+      if (!grid_lazy_step(act, m, ub, stamp, akey, ast, lc, gg, fold, lc->sel, lc->selpos, lc->gsel, kLanes, gsel,
+                          &lc->bar, &lc->err, tns, &dec_local))
+        break;
+    }
     if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();
@@ -183,6 +193,7 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   long long *wgain = g->wgain;
   const int32_t *rp = pruned ? g->rpf : g->rp, *ci = pruned ? g->cif : g->ci;
   const int32_t *rp_full = g->rp, *c3 = pruned ? g->c3 : nullptr;
+  GridSelScratch *gsel = g->gsel;
   int32_t n = g->n;
   int32_t *dS = g->dS;
   long long *ub = g->ub;
@@ -212,7 +223,7 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&wide, (void *)&local_max, (void *)&akey,
                   (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap,
-                  (void *)&rp_full, (void *)&c3};
+                  (void *)&rp_full, (void *)&c3, (void *)&gsel};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
                                       dim3(kGridGainThreads),

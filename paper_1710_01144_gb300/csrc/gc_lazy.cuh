@@ -331,6 +331,276 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
   }
 }
 
+// One step of the lazy loop (Sec. 4.2) by every CTA of the grid: the lazy
+// state lives in *lc, the list is act[0..m) (ids in increasing order), its
+// bounds are akey/ast at list positions (compact copies) or ub/stamp by
+// vertex (akey == nullptr).  CTA b owns the list slice [b P, b P + P).
+//   1. fold: the gains of the last evaluated batch (sel/selpos/gsel, n_sel of
+//      them) become bounds; each CTA applies those in its slice and every CTA
+//      computes the round's best exact gain the same way;
+//   2. scan: per-CTA (largest unevaluated bound, its id), smallest bound, count;
+//   3. decision, taken identically by every CTA: accept the best (dec 1), ask
+//      for a longer list (dec 2: no unevaluated entry, or the best is below
+//      theta), or evaluate (dec 0);
+//   4. threshold: histogram passes over [umin, umax] (1024 bins, summed over
+//      CTAs in global memory) find the key of the need-th largest entry;
+//   5. selection: entries above it and, in list order, enough equal to it.
+// Returns false if a barrier gave up; *dec_out gets the decision.  The caller
+// synchronises the grid before using the selection.
+static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+                                      long long *akey, int32_t *ast, LazyCtl *lc, GridGainCtl *gg, bool fold,
+                                      int32_t *sel, int32_t *selpos, const long long *gsel, int cap,
+                                      GridSelScratch *sc, GridBar *bar, int32_t *err, unsigned long long tns,
+                                      int *dec_out) {
+  __shared__ long long s_v[32];
+  __shared__ int s_id[32];
+  __shared__ long long s_ll[32];
+  __shared__ unsigned int s_hist[kSelBins];
+  __shared__ int s_scan[33];
+  __shared__ int s_b;
+  __shared__ long long s_ab;
+  const int tid = threadIdx.x, T = blockDim.x, G = gridDim.x, b = blockIdx.x;
+  const int r = *(volatile int32_t *)&lc->round;
+  const int P = (m + G - 1) / G;
+  const int lo = min(m, b * P), hi = min(m, lo + P);
+  auto key_of = [&](int i) -> long long {
+    const int v = act[i];
+    const long long u = akey ? akey[i] : ub[v];
+    const int st = akey ? ast[i] : stamp[v];
+    return (u >= 0 && st != r) ? u : LLONG_MIN;
+  };
+
+  // ---- 1. fold ----
+  long long gb = *(volatile long long *)&lc->best_gain;
+  int vb = *(volatile int32_t *)&lc->best_id;
+  int bpos = *(volatile int32_t *)&lc->best_pos;
+  if (fold) {
+    const int ns = *(volatile int32_t *)&lc->n_sel;
+    long long fv = -1;
+    int fid = -1, fpos = -1;
+    for (int j = tid; j < ns; j += T) {
+      const int v = sel[j], p = selpos[j];
+      const long long gv = gsel[j];
+      if (p >= lo && p < hi) {  // this CTA's slice: the bound becomes exact
+        ub[v] = gv;
+        stamp[v] = r;
+        if (akey) {
+          akey[p] = gv;
+          ast[p] = r;
+        }
+      }
+      if (better_max(gv, v, fv, fid)) {
+        fv = gv;
+        fid = v;
+        fpos = p;
+      }
+    }
+    const int mine = fid;
+    block_argmax_all(fv, fid, s_v, s_id);
+    if (mine >= 0 && mine == fid) s_b = fpos;
+    __syncthreads();
+    if (fid >= 0 && better_max(fv, fid, gb, vb)) {
+      gb = fv;
+      vb = fid;
+      bpos = s_b;
+    }
+    if (b == 0 && tid == 0) {
+      lc->best_gain = gb;
+      lc->best_id = vb;
+      lc->best_pos = bpos;
+      lc->steps += 1;
+      lc->evals += ns;
+    }
+    __syncthreads();
+  }
+  // ---- 2. scan of this CTA's slice ----
+  long long umax = LLONG_MIN, umin = LLONG_MAX, cnt = 0;
+  int vmax = -1;
+  for (int i = lo + tid; i < hi; i += T) {
+    const long long k = key_of(i);
+    if (k == LLONG_MIN) continue;
+    const int v = act[i];
+    if (better_max(k, v, umax, vmax)) {
+      umax = k;
+      vmax = v;
+    }
+    umin = min(umin, k);
+    ++cnt;
+  }
+  block_argmax_all(umax, vmax, s_v, s_id);
+  umin = block_min_ll(umin, s_ll);
+  cnt = block_sum(cnt, s_ll);
+  if (tid == 0) {
+    sc->umax[b] = umax;
+    sc->vmax[b] = vmax;
+    sc->umin[b] = umin;
+    sc->cnt[b] = cnt;
+  }
+  if (!grid_sync(bar, err, tns)) return false;
+  // ---- 3. decision (every CTA the same) ----
+  umax = LLONG_MIN;
+  vmax = -1;
+  umin = LLONG_MAX;
+  cnt = 0;
+  for (int c = tid; c < G; c += T) {
+    const long long u = ((volatile long long *)sc->umax)[c];
+    const int v = ((volatile int32_t *)sc->vmax)[c];
+    if (v >= 0 && better_max(u, v, umax, vmax)) {
+      umax = u;
+      vmax = v;
+    }
+    umin = min(umin, ((volatile long long *)sc->umin)[c]);
+    cnt += ((volatile long long *)sc->cnt)[c];
+  }
+  block_argmax_all(umax, vmax, s_v, s_id);
+  umin = block_min_ll(umin, s_ll);
+  cnt = block_sum(cnt, s_ll);
+  const long long theta = *(volatile long long *)&lc->theta;
+  int dec;
+  if (vb >= 0 && (cnt == 0 || better_max(gb, vb, umax, vmax))) dec = gb >= theta ? 1 : 2;
+  else if (cnt == 0) dec = 2;
+  else dec = 0;
+  *dec_out = dec;
+  if (dec != 0) {
+    if (b == 0 && tid == 0) lc->dec = dec;
+    return true;
+  }
+  // ---- 4. threshold: key of the need-th largest eligible entry ----
+  const int need = (int)((long long)cap < cnt ? (long long)cap : cnt);
+  long long tau = umin, above = 0;  // above = eligible keys > tau
+  int last_hist = -1;
+  if (cnt > need) {
+    unsigned long long lo2 = (unsigned long long)umin, hi2 = (unsigned long long)umax;
+    long long want = need, acc = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+      const int hb = pass % 3;
+      unsigned int *gh = sc->hist[hb];
+      const unsigned long long span = hi2 - lo2 + 1ull;
+      const unsigned long long width = span / kSelBins + ((span % kSelBins) ? 1ull : 0ull);
+      for (int i = tid; i < kSelBins; i += T) s_hist[i] = 0;
+      if (b == 0)  // the next pass's buffer (read two passes ago by everyone)
+        for (int i = tid; i < kSelBins; i += T) sc->hist[(pass + 1) % 3][i] = 0;
+      __syncthreads();
+      for (int i = lo + tid; i < hi; i += T) {
+        const long long k = key_of(i);
+        if (k == LLONG_MIN) continue;
+        const unsigned long long uu = (unsigned long long)k;
+        if (uu - lo2 > hi2 - lo2) continue;  // outside [lo2, hi2]
+        atomicAdd(&s_hist[(uu - lo2) / width], 1u);
+      }
+      __syncthreads();
+      for (int i = tid; i < kSelBins; i += T)
+        if (s_hist[i]) atomicAdd(&gh[i], s_hist[i]);
+      if (!grid_sync(bar, err, tns)) return false;
+      last_hist = hb;
+      // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
+      const int b0 = kSelBins - 1 - 2 * tid, b1 = b0 - 1;
+      const int h0 = tid < kSelBins / 2 ? (int)((volatile unsigned int *)gh)[b0] : 0;
+      const int h1 = tid < kSelBins / 2 ? (int)((volatile unsigned int *)gh)[b1] : 0;
+      if (tid == 0) {
+        s_b = 0;
+        s_ab = 0;
+      }
+      int total;
+      const long long a0 = block_excl_scan(h0 + h1, s_scan, &total);
+      if (tid < kSelBins / 2) {
+        if (a0 < want && a0 + h0 >= want) {
+          s_b = b0;
+          s_ab = a0;
+        } else if (a0 + h0 < want && a0 + h0 + h1 >= want) {
+          s_b = b1;
+          s_ab = a0 + h0;
+        }
+      }
+      __syncthreads();
+      const int bb = s_b;
+      const long long ab = s_ab;
+      __syncthreads();
+      const unsigned long long bin_lo = lo2 + width * (unsigned long long)bb;
+      if (width == 1ull) {
+        tau = (long long)bin_lo;
+        above = acc + ab;
+        break;
+      }
+      acc += ab;
+      want -= ab;
+      const unsigned long long room = hi2 - bin_lo;
+      lo2 = bin_lo;
+      hi2 = bin_lo + (width - 1ull < room ? width - 1ull : room);
+    }
+  }
+  // ---- 5. selection: counts per slice, then positions in list order ----
+  int n_gt = 0, n_eq = 0;
+  for (int i = lo + tid; i < hi; i += T) {
+    const long long k = key_of(i);
+    if (k == LLONG_MIN) continue;
+    n_gt += k > tau;
+    n_eq += k == tau;
+  }
+  n_gt = (int)block_sum((long long)n_gt, s_ll);
+  n_eq = (int)block_sum((long long)n_eq, s_ll);
+  if (tid == 0) {
+    sc->gt[b] = n_gt;
+    sc->eq[b] = n_eq;
+  }
+  if (!grid_sync(bar, err, tns)) return false;
+  if (b == 0 && last_hist >= 0)  // every histogram has been read: all three zero for the next step
+    for (int i = tid; i < 3 * kSelBins; i += T) (&sc->hist[0][0])[i] = 0;
+  long long gt_off = 0, eq_off = 0, gt_tot = 0;
+  for (int c = tid; c < G; c += T) {
+    const long long g1 = ((volatile int32_t *)sc->gt)[c], e1 = ((volatile int32_t *)sc->eq)[c];
+    gt_tot += g1;
+    if (c < b) {
+      gt_off += g1;
+      eq_off += e1;
+    }
+  }
+  gt_off = block_sum(gt_off, s_ll);
+  eq_off = block_sum(eq_off, s_ll);
+  gt_tot = block_sum(gt_tot, s_ll);
+  (void)above;
+  const long long quota = (long long)need - gt_tot;  // entries equal to tau still to take, in list order
+  int gt_seen = 0, eq_seen = 0;
+  for (int base = lo; base < hi; base += T) {
+    const int i = base + tid;
+    int gt = 0, eq = 0;
+    if (i < hi) {
+      const long long k = key_of(i);
+      if (k != LLONG_MIN) {
+        gt = k > tau;
+        eq = k == tau;
+      }
+    }
+    int tg, te;
+    const int rg = block_excl_scan(gt, s_scan, &tg);
+    const int re = block_excl_scan(eq, s_scan, &te);
+    long long pos = -1;
+    if (gt) pos = gt_off + gt_seen + rg;
+    else if (eq && eq_off + eq_seen + re < quota) pos = gt_tot + eq_off + eq_seen + re;
+    if (pos >= 0 && pos < cap) {
+      sel[pos] = act[i];
+      selpos[pos] = i;
+    }
+    gt_seen += tg;
+    eq_seen += te;
+  }
+  if (b == 0 && tid == 0) {
+    lc->n_sel = need;
+    lc->dec = 0;
+    if (gg) {
+      gg->pk[0] = 0;
+      gg->pk[1] = 0;
+      gg->pk[2] = 0;
+      gg->touched = 0;
+    }
+  }
+  if (b == 0 && gg && tid < kLanes) {
+    gg->gain[tid] = 0;
+    gg->cnt[tid] = 0;
+  }
+  return true;
+}
+
 // Proposal scores of the active list for this round (every CTA, one warp per
 // candidate): score[i] = network output on the candidate's features.
 static __device__ void lazy_score(const int32_t *__restrict__ act, int32_t m, const float *__restrict__ prop,
