@@ -72,6 +72,7 @@ struct BatchArgs {
   int32_t max_n;          // vertices of the largest graph (workspace layout)
   int32_t *dS, *mx, *stamp, *q0, *q1, *goff, *st1;
   int32_t *rpf, *cif, *c3;  // pruned adjacency for rounds >= 1 (built in P3)
+  int32_t *dS1;             // d(s0, .) as of P3, never written after: round 1 reads it read-only
   long long *ub, *key, *f0;
   unsigned char *ws;
   size_t ws_stride;
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       }
       const int g = lo, o = a.off[g], first = (t - a.tstart[g]) * kLanes;
       const int nl = min(kLanes, a.scount[g] - first);
-      cta_gain_batch<kModeFarness>(a.rp, a.ci, a.N, a.dS, a.slist + o + first, nl, s_out, myws, a.gctl, nullptr,
+      cta_gain_batch<kModeFarness, true, false>(a.rp, a.ci, a.N, a.dS, a.slist + o + first, nl, s_out, myws, a.gctl, nullptr,
                                    lg, cnt, o);
       if (tid < nl) a.f0[a.slist[o + first + tid]] = s_out[tid];
       __syncthreads();
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     return;
   if (!bsync(a)) return;
   seg_sum_dist(a, a.farness);
+  for (int v = b * T + tid; v < a.N; v += G * T) a.dS1[v] = a.dS[v];  // round 1's read-only d_S
   {
     const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
     for (int v = gw; v < a.N; v += nw) {
@@ -462,8 +464,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     if (a.kk[g] < 2) continue;
     const int o = a.off[g], first = (t - a.bstart[g]) * a.lanes1;
     const int nl = min(a.lanes1, a.ng[g] - first);
-    cta_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, a.iota + o + first, nl, a.ub + o + first, myws, a.gctl,
-                              a.mx, LaneGraphs(), cnt, o, a.c3);
+    cta_gain_batch<kModeGain, true, true>(a.rpf, a.cif, a.N, a.dS1, a.iota + o + first, nl, a.ub + o + first, myws,
+                                          a.gctl, a.mx, LaneGraphs(), cnt, o, a.c3);
   }
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) a.ctl->ns_ph[5] = global_ns() - t_start;
@@ -608,8 +610,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
         __syncthreads();
         const int dec = *(volatile int32_t *)&lc->dec;
         if (dec == 0) {  // evaluate the selected batch
-          cta_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws, a.gctl, a.mx,
-                                    LaneGraphs(), cnt, o, a.c3);
+          cta_gain_batch<kModeGain, true, false>(a.rpf, a.cif, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws,
+                                                 a.gctl, a.mx, LaneGraphs(), cnt, o, a.c3);
           if (tid == 0) lc->pad = 1;  // fold it next step
         } else if (dec == 1) {  // accept: record, then update d_S from the pick
           const int pick = lc->best_id;
@@ -736,7 +738,7 @@ struct gc_batch {
   int32_t *rp = nullptr, *ci = nullptr, *gid = nullptr, *off = nullptr, *ng = nullptr, *iota = nullptr;
   int32_t *dS = nullptr, *mx = nullptr, *stamp = nullptr, *q0 = nullptr, *q1 = nullptr, *goff = nullptr,
           *st1 = nullptr;
-  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr, *gx = nullptr;
+  int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr, *gx = nullptr, *dS1 = nullptr;
   GridGainCtl *gg = nullptr;
   GridSelScratch *gsel = nullptr;
   long long *ub = nullptr, *key = nullptr, *f0 = nullptr;
@@ -776,7 +778,7 @@ static void batch_release(gc_batch *b) {
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
-                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg, b->gsel};
+                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg, b->gsel, b->dS1};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -858,6 +860,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
             balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
             balloc(&b->rpf, Nn + 1) && balloc(&b->cif, std::max<size_t>(1, (size_t)E)) && balloc(&b->c3, Nn) &&
+            balloc(&b->dS1, Nn) &&
             balloc(&b->gx, 3 * (size_t)std::max<int32_t>(1, b->max_n)) && balloc(&b->gg, 1) && balloc(&b->gsel, 1) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
@@ -1013,6 +1016,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.rpf = b->rpf;
   a.cif = b->cif;
   a.c3 = b->c3;
+  a.dS1 = b->dS1;
   a.gg = b->gg;
   a.gsel = b->gsel;
   a.gx = b->gx;

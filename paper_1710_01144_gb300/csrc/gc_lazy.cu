@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         const int ns = *(volatile int32_t *)&lc->n_sel;
         const int nb = (ns + kLanes - 1) / kLanes;
         for (int bi = blockIdx.x; bi < nb; bi += gridDim.x)
-          cta_gain_batch<kModeGain>(rp, ci, n, dS, wsel + bi * kLanes, min(kLanes, ns - bi * kLanes),
+          cta_gain_batch<kModeGain, true, false>(rp, ci, n, dS, wsel + bi * kLanes, min(kLanes, ns - bi * kLanes),
                                     wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt, 0, c3);
         ok = true;
       } else {
