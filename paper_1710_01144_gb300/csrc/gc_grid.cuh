@@ -3,6 +3,11 @@
 // relabel BFS that maintains d_S (see gc_bfs.cu).  Both synchronise through a
 // caller-supplied bounded grid barrier, so they can run as phases of a larger
 // persistent kernel (gc_lazy.cu).
+// The adjacency (rp, ci, c3) and the neighbour bound mx are read through the
+// read-only data path: callers never change them while a kernel that runs
+// these functions can read them (inside a persistent kernel they are written
+// before, in an earlier phase, and never after).  d_S and the lane words are
+// read with ordinary loads: they change between phases.
 #pragma once
 
 #include "gc_device.cuh"
@@ -97,7 +102,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   auto enqueue = [&](bool q, int w, int lev) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    int deg = q ? ((c3 && lev > 0) ? c3[w] : rp[w + 1] - rp[w]) : 0;
+    int deg = q ? ((c3 && lev > 0) ? __ldg(c3 + w) : __ldg(rp + w + 1) - __ldg(rp + w)) : 0;
     int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -142,7 +147,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         }
         if (reach) {
           if (atomicOr(&ws.vis[c - voff], bit) == 0) ws.touched[atomicAdd(&ctl->touched, 1)] = c;
-          const bool expand = MODE != kModeGain || !mx || mx[c] > 1;
+          const bool expand = MODE != kModeGain || !mx || __ldg(mx + c) > 1;
           if (expand) q = atomicOr(&ws.nx[0][c - voff], bit) == 0;
         }
       }
@@ -191,9 +196,9 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           if (MODE == kModeFarness) m &= alive;
           s_go[tid] = qstart[xi];
           s_sm[tid] = m;
-          s_rs[tid] = rp[u];
+          s_rs[tid] = __ldg(rp + u);
           if (s_go[tid] >= es && s_go[tid] < ee) {  // counted once: by the CTA holding the entry's first edge
-            const int deg = (c3 && L > 0) ? c3[u] : rp[u + 1] - s_rs[tid];
+            const int deg = (c3 && L > 0) ? __ldg(c3 + u) : __ldg(rp + u + 1) - s_rs[tid];
             c_union += (u64)deg;
             c_scalar += (u64)__popcll(m) * (u64)deg;
             c_front += 1;
@@ -218,7 +223,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 else h = mid - 1;
               }
               sl[k] = l;
-              w[k] = ci[s_rs[l] + (int)(e - s_go[l])];
+              w[k] = __ldg(ci + s_rs[l] + (int)(e - s_go[l]));
             }
           }
           int dw[kGridIlp];
@@ -241,7 +246,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             bool q = false;
             if (won) {
               // expanded at level nlev only if some neighbour may still be claimed
-              const bool expand = MODE != kModeGain || !mx || mx[w[k]] > nlev + 1;
+              const bool expand = MODE != kModeGain || !mx || __ldg(mx + w[k]) > nlev + 1;
               if (expand) q = atomicOr(&nxt[w[k] - voff], won) == 0;
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
@@ -384,7 +389,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
   auto enqueue = [&](bool q, int w, int lev) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    const int deg = q ? ((c3 && lev > 0) ? c3[w] : rp[w + 1] - rp[w]) : 0;
+    const int deg = q ? ((c3 && lev > 0) ? __ldg(c3 + w) : __ldg(rp + w + 1) - __ldg(rp + w)) : 0;
     int incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -449,7 +454,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
         const int cntx = min(T, F - x);
         if (xi < F) {
           s_go[tid] = qs[xi];
-          s_rs[tid] = rp[qc[xi]];
+          s_rs[tid] = __ldg(rp + qc[xi]);
         }
         if (tid == 0) s_go[cntx] = (x + cntx < F) ? qs[x + cntx] : (int)E;
         __syncthreads();
@@ -465,7 +470,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
               if (s_go[mid] <= e) l = mid;
               else h = mid - 1;
             }
-            w = ci[s_rs[l] + (int)(e - s_go[l])];
+            w = __ldg(ci + s_rs[l] + (int)(e - s_go[l]));
             if (nl < dist[w]) {
               const int old = atomicMin(&dist[w], nl);
               if (old > nl) {
