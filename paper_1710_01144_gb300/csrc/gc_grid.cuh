@@ -19,6 +19,13 @@ typedef unsigned long long u64;
 
 constexpr int kGridIlp = 2;  // adjacency entries in flight per thread (grid forms)
 
+// Length of the row that vertex w scans when expanded at level lev: the whole
+// row at level 0, the first c3[w] entries of a pruned row later.
+static __device__ __forceinline__ int row_len(const int32_t *__restrict__ rp, const int32_t *__restrict__ c3, int w,
+                                              int lev) {
+  return (c3 && lev > 0) ? __ldg(c3 + w) : __ldg(rp + w + 1) - __ldg(rp + w);
+}
+
 // Largest x in [0, F) with start[x] <= e, for one warp; start is
 // non-decreasing and start[0] <= e.  A 32-ary search: about log32(F) rounds
 // of one coalesced probe each.
@@ -99,10 +106,12 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
 
   // Queue w for level lev (its lanes are already in claim word lev mod 3):
   // warp-aggregated slot and range start.  Every lane of the warp calls it.
-  auto enqueue = [&](bool q, int w, int lev) {
+  // deg: the row length w will scan at level lev (loaded by the caller with
+  // its other per-neighbour data, so that no load waits here)
+  auto enqueue = [&](bool q, int w, int lev, int deg) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    int deg = q ? ((c3 && lev > 0) ? __ldg(c3 + w) : __ldg(rp + w + 1) - __ldg(rp + w)) : 0;
+    if (!q) deg = 0;
     int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -151,7 +160,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           if (expand) q = atomicOr(&ws.nx[0][c - voff], bit) == 0;
         }
       }
-      enqueue(q, c, 0);
+      enqueue(q, c, 0, q ? row_len(rp, c3, c, 0) : 0);
     }
   }
   bool ok = grid_sync(bar, err, timeout_ns);
@@ -226,16 +235,25 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
               w[k] = __ldg(ci + s_rs[l] + (int)(e - s_go[l]));
             }
           }
-          int dw[kGridIlp];
+          // everything indexed by the neighbour is loaded at once: d_S, the
+          // neighbour bound and the row length it would scan next level
+          int dw[kGridIlp], mxw[kGridIlp], lw[kGridIlp];
 #pragma unroll
-          for (int k = 0; k < kGridIlp; ++k) dw[k] = (MODE == kModeGain && w[k] >= 0) ? dS[w[k]] : 0;
+          for (int k = 0; k < kGridIlp; ++k) {
+            const bool ok = w[k] >= 0;
+            dw[k] = (MODE == kModeGain && ok) ? dS[w[k]] : 0;
+            mxw[k] = (MODE == kModeGain && mx && ok) ? __ldg(mx + w[k]) : INT_MAX;
+            lw[k] = ok ? row_len(rp, c3, w[k], nlev) : 0;
+          }
           u64 nb[kGridIlp];
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) {
             // pruned unless w is strictly closer to the lane's candidate than to S
             const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
-            nb[k] = live ? (s_sm[sl[k]] & ~ws.vis[w[k] - voff]) : 0ull;
+            nb[k] = live ? s_sm[sl[k]] : 0ull;
           }
+          // claim with the atomicOr itself (no pre-read of the visited word:
+          // the searches are few, so latency counts more than atomic traffic)
           u64 ov[kGridIlp];
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
@@ -246,7 +264,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             bool q = false;
             if (won) {
               // expanded at level nlev only if some neighbour may still be claimed
-              const bool expand = MODE != kModeGain || !mx || __ldg(mx + w[k]) > nlev + 1;
+              const bool expand = mxw[k] > nlev + 1;
               if (expand) q = atomicOr(&nxt[w[k] - voff], won) == 0;
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
@@ -256,7 +274,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1u);
               } while (won);
             }
-            enqueue(q, w[k], nlev);
+            enqueue(q, w[k], nlev, lw[k]);
             const unsigned fm = __ballot_sync(0xffffffffu, fresh);
             if (fm) {
               const int leader = __ffs(fm) - 1;
@@ -386,10 +404,10 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
   unsigned long long dec = 0, rel = 0;
 
   // queue w for level lev: warp-aggregated slot and range start (whole warp)
-  auto enqueue = [&](bool q, int w, int lev) {
+  auto enqueue = [&](bool q, int w, int lev, int deg) {
     const unsigned qm = __ballot_sync(0xffffffffu, q);
     if (!qm) return;
-    const int deg = q ? ((c3 && lev > 0) ? __ldg(c3 + w) : __ldg(rp + w + 1) - __ldg(rp + w)) : 0;
+    if (!q) deg = 0;
     int incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -425,7 +443,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
         }
       }
     }
-    enqueue(q, s, 0);
+    enqueue(q, s, 0, q ? row_len(rp, c3, s, 0) : 0);
   }
   bool ok = grid_sync(bar, err, timeout_ns);
   for (int L = 0; ok; ++L) {
@@ -462,7 +480,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
         for (long long e0 = a0 + (tid & ~31); e0 < a1; e0 += T) {  // warp-uniform trip count
           const long long e = e0 + lane;
           bool q = false;
-          int w = 0;
+          int w = 0, lw = 0;
           if (e < a1) {
             int l = 0, h = cntx - 1;  // staged entry holding e (every entry's range is non-empty)
             while (l < h) {
@@ -471,7 +489,9 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
               else h = mid - 1;
             }
             w = __ldg(ci + s_rs[l] + (int)(e - s_go[l]));
-            if (nl < dist[w]) {
+            const int dcur = dist[w];
+            lw = row_len(rp, c3, w, nl);  // with the label: no load waits in enqueue
+            if (nl < dcur) {
               const int old = atomicMin(&dist[w], nl);
               if (old > nl) {
                 q = true;
@@ -480,7 +500,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
               }
             }
           }
-          enqueue(q, w, nl);
+          enqueue(q, w, nl, lw);
         }
         const int done_end = s_go[cntx];
         __syncthreads();  // the staged arrays are reused
