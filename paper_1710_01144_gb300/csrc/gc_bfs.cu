@@ -221,29 +221,68 @@ __global__ void __launch_bounds__(kRedThreads) k_prune_count(const int32_t *__re
   }
 }
 
+constexpr int kPruneHeavyRow = 2048;  // rows longer than this are filled by a whole CTA
+
+// One pass per row, two cursors: entries with d_S >= 3 go to the front of the
+// pruned row, entries with d_S == 2 after the c3[u] of them.  A warp per row;
+// rows longer than kPruneHeavyRow are left to k_prune_fill_heavy.
 __global__ void __launch_bounds__(kRedThreads) k_prune_fill(const int32_t *__restrict__ rp,
                                                             const int32_t *__restrict__ ci, int32_t n,
                                                             const int32_t *__restrict__ dS,
-                                                            const int32_t *__restrict__ rpf, int32_t *cif) {
+                                                            const int32_t *__restrict__ rpf,
+                                                            const int32_t *__restrict__ c3, int32_t *cif) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int u = gwarp; u < n; u += nwarps) {
-    int pos = rpf[u];
-    for (int pass = 0; pass < 2; ++pass) {  // d_S >= 3 first, then d_S == 2
-      for (int e0 = rp[u]; e0 < rp[u + 1]; e0 += 32) {
-        const int e = e0 + lane;
-        int w = 0;
-        bool keep = false;
-        if (e < rp[u + 1]) {
-          w = ci[e];
-          const int d = dS[w];
-          keep = pass == 0 ? d >= 3 : d == 2;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) cif[pos + __popc(m & ((1u << lane) - 1u))] = w;
-        pos += __popc(m);
+    const int r0 = rp[u], r1 = rp[u + 1];
+    if (r1 - r0 > kPruneHeavyRow) continue;
+    int p3 = rpf[u], p2 = p3 + c3[u];
+    for (int e0 = r0; e0 < r1; e0 += 32) {
+      const int e = e0 + lane;
+      int w = 0, d = 0;
+      if (e < r1) {
+        w = ci[e];
+        d = dS[w];
       }
+      const unsigned m3 = __ballot_sync(0xffffffffu, e < r1 && d >= 3);
+      const unsigned m2 = __ballot_sync(0xffffffffu, e < r1 && d == 2);
+      const unsigned below = (1u << lane) - 1u;
+      if (e < r1 && d >= 3) cif[p3 + __popc(m3 & below)] = w;
+      if (e < r1 && d == 2) cif[p2 + __popc(m2 & below)] = w;
+      p3 += __popc(m3);
+      p2 += __popc(m2);
+    }
+  }
+}
+
+// The long rows of k_prune_fill: each CTA takes whole rows, 1024 entries at a
+// time, with block scans for the two cursors.
+__global__ void __launch_bounds__(1024) k_prune_fill_heavy(const int32_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ ci, int32_t n,
+                                                          const int32_t *__restrict__ dS,
+                                                          const int32_t *__restrict__ rpf,
+                                                          const int32_t *__restrict__ c3, int32_t *cif) {
+  __shared__ int s_scan[33];
+  for (int u = blockIdx.x; u < n; u += gridDim.x) {
+    const int r0 = rp[u], r1 = rp[u + 1];
+    if (r1 - r0 <= kPruneHeavyRow) continue;
+    int p3 = rpf[u], p2 = p3 + c3[u];
+    for (int e0 = r0; e0 < r1; e0 += 1024) {
+      const int e = e0 + threadIdx.x;
+      int w = 0, d = 0;
+      if (e < r1) {
+        w = ci[e];
+        d = dS[w];
+      }
+      const int f3 = e < r1 && d >= 3, f2 = e < r1 && d == 2;
+      int t3, t2;
+      const int x3 = block_excl_scan(f3, s_scan, &t3);
+      const int x2 = block_excl_scan(f2, s_scan, &t2);
+      if (f3) cif[p3 + x3] = w;
+      if (f2) cif[p2 + x2] = w;
+      p3 += t3;
+      p2 += t2;
     }
   }
 }
@@ -427,12 +466,13 @@ int launch_prune_csr(gc_graph *g) {
   const int n = g->n;
   const int tiles = (n + kScanTile - 1) / kScanTile;
   const int grid = grid_for((int64_t)n * 32, kRedThreads, g->num_sms * 8);
-  g->launches += 5;
+  g->launches += 6;
   k_prune_count<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->io_a, g->c3);
   k_scan_tiles<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain);
   k_scan_tops<<<1, 1024, 0, g->stream>>>(g->lgain, tiles);
   k_scan_apply<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain, g->rpf);
-  k_prune_fill<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->cif);
+  k_prune_fill<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif);
+  k_prune_fill_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
