@@ -62,7 +62,7 @@ static void release(gc_graph *g) {
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
-                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel};
+                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -242,7 +242,8 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->mx_buf, N)) || (rc = dalloc(&g->two_hop, N)) || (rc = dalloc(&g->score, N)) ||
       (rc = dalloc(&g->akey, N)) || (rc = dalloc(&g->ast, N)) || (rc = dalloc(&g->gx, 3 * N)) ||
       (rc = dalloc(&g->rpf, N + 1)) || (rc = dalloc(&g->cif, std::max<size_t>(1, (size_t)nnz))) ||
-      (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
+      (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->heavy, N)) ||
+      (rc = dalloc(&g->n_heavy, 1)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
       (rc = dalloc(&g->lev_max, 1)) || (rc = dalloc(&g->gsel, 1)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
@@ -270,6 +271,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), st) != cudaSuccess ||
       cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), st) != cudaSuccess)
     return bail(fail(GC_ECUDA, "memset failed"));
+  if ((rc = launch_heavy_rows(g))) return bail(rc);
   if (flags & GC_VALIDATE) {
     if ((rc = launch_validate(g))) return bail(rc == GC_EINVAL ? fail(GC_EINVAL, "CSR validation failed") : rc);
     int32_t zero = 0;

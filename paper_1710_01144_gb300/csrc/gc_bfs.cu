@@ -82,6 +82,19 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_dist(const int32_t *__restr
 // most c2 = min(sum_{w in N(v)} (deg(w) - 1), n - 1 - deg(v)) vertices sit at
 // distance 2 (every neighbour has v among its own neighbours); everything else
 // is at least 3 away.  key[v] = -(deg + 2 c2 + 3 (n - 1 - deg - c2)).
+// Row-wise kernels give a warp to each row up to kHeavyRow entries; longer
+// rows (hubs) go to a whole CTA in a companion kernel, so that no warp walks a
+// hub's row alone while the rest of the grid has finished.  The companions
+// walk the list of long rows built once per graph (k_heavy_rows).
+constexpr int kHeavyRow = 2048;
+
+// heavy[0..*nh) = the rows with more than kHeavyRow entries (any order)
+__global__ void __launch_bounds__(kRedThreads) k_heavy_rows(const int32_t *__restrict__ rp, int32_t n,
+                                                            int32_t *heavy, int32_t *nh) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (rp[v + 1] - rp[v] > kHeavyRow) heavy[atomicAdd(nh, 1)] = v;
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__restrict__ rp,
                                                              const int32_t *__restrict__ ci,
                                                              int32_t n, long long *key, long long *two_hop) {
@@ -90,6 +103,7 @@ __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__re
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int v = gwarp; v < n; v += nwarps) {
     const int beg = rp[v], end = rp[v + 1];
+    if (end - beg > kHeavyRow) continue;  // k_round0_keys_heavy
     long long x = 0;
     for (int e = beg + lane; e < end; e += 32) {
       const int w = ci[e];
@@ -97,6 +111,30 @@ __global__ void __launch_bounds__(kRedThreads) k_round0_keys(const int32_t *__re
     }
     x = warp_sum(x);
     if (lane == 0) {
+      const long long deg = end - beg;
+      long long rest = (long long)n - 1 - deg;
+      if (rest < 0) rest = 0;
+      const long long c2 = x < rest ? x : rest;
+      key[v] = -(deg + 2 * c2 + 3 * (rest - c2));
+      if (two_hop) two_hop[v] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_round0_keys_heavy(const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci, int32_t n,
+                                                           long long *key, long long *two_hop, const int32_t *__restrict__ heavy, const int32_t *__restrict__ nh) {
+  __shared__ long long s_red[32];
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int v = heavy[i];
+    const int beg = rp[v], end = rp[v + 1];
+    long long x = 0;
+    for (int e = beg + threadIdx.x; e < end; e += 1024) {
+      const int w = ci[e];
+      x += (long long)(rp[w + 1] - rp[w] - 1);
+    }
+    x = block_sum(x, s_red);
+    if (threadIdx.x == 0) {
       const long long deg = end - beg;
       long long rest = (long long)n - 1 - deg;
       if (rest < 0) rest = 0;
@@ -206,8 +244,10 @@ __global__ void __launch_bounds__(kRedThreads) k_prune_count(const int32_t *__re
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int u = gwarp; u < n; u += nwarps) {
+    const int r0 = rp[u], r1 = rp[u + 1];
+    if (r1 - r0 > kHeavyRow) continue;  // k_prune_count_heavy
     int a2 = 0, a3 = 0;
-    for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+    for (int e = r0 + lane; e < r1; e += 32) {
       const int d = dS[ci[e]];
       a2 += d >= 2;
       a3 += d >= 3;
@@ -221,11 +261,33 @@ __global__ void __launch_bounds__(kRedThreads) k_prune_count(const int32_t *__re
   }
 }
 
-constexpr int kPruneHeavyRow = 2048;  // rows longer than this are filled by a whole CTA
+// The long rows of k_prune_count, a CTA per row.
+__global__ void __launch_bounds__(1024) k_prune_count_heavy(const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci, int32_t n,
+                                                           const int32_t *__restrict__ dS, int32_t *cnt2,
+                                                           int32_t *c3, const int32_t *__restrict__ heavy, const int32_t *__restrict__ nh) {
+  __shared__ long long s_red[32];
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int u = heavy[i];
+    const int r0 = rp[u], r1 = rp[u + 1];
+    long long a2 = 0, a3 = 0;
+    for (int e = r0 + threadIdx.x; e < r1; e += 1024) {
+      const int d = dS[ci[e]];
+      a2 += d >= 2;
+      a3 += d >= 3;
+    }
+    a2 = block_sum(a2, s_red);
+    a3 = block_sum(a3, s_red);
+    if (threadIdx.x == 0) {
+      cnt2[u] = (int32_t)a2;
+      c3[u] = (int32_t)a3;
+    }
+  }
+}
 
 // One pass per row, two cursors: entries with d_S >= 3 go to the front of the
 // pruned row, entries with d_S == 2 after the c3[u] of them.  A warp per row;
-// rows longer than kPruneHeavyRow are left to k_prune_fill_heavy.
+// rows longer than kHeavyRow are left to k_prune_fill_heavy.
 __global__ void __launch_bounds__(kRedThreads) k_prune_fill(const int32_t *__restrict__ rp,
                                                             const int32_t *__restrict__ ci, int32_t n,
                                                             const int32_t *__restrict__ dS,
@@ -236,7 +298,7 @@ __global__ void __launch_bounds__(kRedThreads) k_prune_fill(const int32_t *__res
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int u = gwarp; u < n; u += nwarps) {
     const int r0 = rp[u], r1 = rp[u + 1];
-    if (r1 - r0 > kPruneHeavyRow) continue;
+    if (r1 - r0 > kHeavyRow) continue;
     int p3 = rpf[u], p2 = p3 + c3[u];
     for (int e0 = r0; e0 < r1; e0 += 32) {
       const int e = e0 + lane;
@@ -262,11 +324,11 @@ __global__ void __launch_bounds__(1024) k_prune_fill_heavy(const int32_t *__rest
                                                           const int32_t *__restrict__ ci, int32_t n,
                                                           const int32_t *__restrict__ dS,
                                                           const int32_t *__restrict__ rpf,
-                                                          const int32_t *__restrict__ c3, int32_t *cif) {
+                                                          const int32_t *__restrict__ c3, int32_t *cif, const int32_t *__restrict__ heavy, const int32_t *__restrict__ nh) {
   __shared__ int s_scan[33];
-  for (int u = blockIdx.x; u < n; u += gridDim.x) {
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int u = heavy[i];
     const int r0 = rp[u], r1 = rp[u + 1];
-    if (r1 - r0 <= kPruneHeavyRow) continue;
     int p3 = rpf[u], p2 = p3 + c3[u];
     for (int e0 = r0; e0 < r1; e0 += 1024) {
       const int e = e0 + threadIdx.x;
@@ -346,11 +408,34 @@ __global__ void __launch_bounds__(kRedThreads) k_max_nbr(const int32_t *__restri
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int v = gwarp; v < n; v += nwarps) {
+    if (rp[v + 1] - rp[v] > kHeavyRow) continue;  // k_max_nbr_heavy
     int m = 0;
     for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) m = max(m, dS[ci[e]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) mx[v] = m;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_max_nbr_heavy(const int32_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci, int32_t n,
+                                                       const int32_t *__restrict__ dS, int32_t *mx, const int32_t *__restrict__ heavy, const int32_t *__restrict__ nh) {
+  __shared__ int s_m[32];
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int v = heavy[i];
+    int m = 0;
+    for (int e = rp[v] + threadIdx.x; e < rp[v + 1]; e += 1024) m = max(m, dS[ci[e]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      m = s_m[threadIdx.x];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (threadIdx.x == 0) mx[v] = m;
+    }
   }
 }
 
@@ -447,6 +532,9 @@ int launch_round0_keys(gc_graph *g) {
   ++g->launches;
   k_round0_keys<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0,
                   g->stream>>>(g->rp, g->ci, g->n, g->key, g->two_hop);
+  ++g->launches;
+  k_round0_keys_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, g->n, g->key, g->two_hop,
+                                                              g->heavy, g->n_heavy);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
@@ -466,13 +554,24 @@ int launch_prune_csr(gc_graph *g) {
   const int n = g->n;
   const int tiles = (n + kScanTile - 1) / kScanTile;
   const int grid = grid_for((int64_t)n * 32, kRedThreads, g->num_sms * 8);
-  g->launches += 6;
+  g->launches += 7;
   k_prune_count<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->io_a, g->c3);
+  k_prune_count_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->io_a, g->c3, g->heavy,
+                                                              g->n_heavy);
   k_scan_tiles<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain);
   k_scan_tops<<<1, 1024, 0, g->stream>>>(g->lgain, tiles);
   k_scan_apply<<<tiles, 1024, 0, g->stream>>>(g->io_a, n, g->lgain, g->rpf);
   k_prune_fill<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif);
-  k_prune_fill_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif);
+  k_prune_fill_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif,
+                                                             g->heavy, g->n_heavy);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_heavy_rows(gc_graph *g) {
+  ++g->launches;
+  GC_CUDA(cudaMemsetAsync(g->n_heavy, 0, sizeof(int32_t), g->stream));
+  k_heavy_rows<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->rp, g->n, g->heavy, g->n_heavy);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
@@ -481,6 +580,9 @@ int launch_max_nbr(gc_graph *g) {
   ++g->launches;
   k_max_nbr<<<grid_for((int64_t)g->n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0, g->stream>>>(
       g->rp, g->ci, g->n, g->dS, g->mx_buf);
+  ++g->launches;
+  k_max_nbr_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, g->n, g->dS, g->mx_buf, g->heavy,
+                                                          g->n_heavy);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -224,6 +224,7 @@ struct gc_graph {
   long long *lgain = nullptr;  // gains/farness of list entries [n]
   int32_t *gx = nullptr;       // grid-wide gain batch: entry offsets by level parity, third list [3n]
   int32_t *rpf = nullptr, *cif = nullptr, *c3 = nullptr;  // pruned adjacency after round 0 [n+1], [nnz], [n]
+  int32_t *heavy = nullptr, *n_heavy = nullptr;           // rows with more than 2048 entries (built at load)
   unsigned long long *lev_cnt = nullptr;  // round-0 pivot bound: level counts [n] (zero between uses)
   unsigned long long *lev_C = nullptr, *lev_M = nullptr;  // prefix counts / level sums [n + 1]
   int32_t *lev_max = nullptr;
@@ -335,6 +336,8 @@ int launch_degree_keys(gc_graph *g);
 int launch_record(gc_graph *g, int32_t round, long long prev_gain);
 // mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
 int launch_max_nbr(gc_graph *g);
+// the list of long rows used by the row-wise kernels' CTA-per-row companions
+int launch_heavy_rows(gc_graph *g);
 // pruned adjacency (g->rpf, g->cif, g->c3) from the d_S now in g->dS
 int launch_prune_csr(gc_graph *g);
 // round 0: key[v] = -max(LB(v), LB_p(v)) with p the source of the BFS now in d_S
