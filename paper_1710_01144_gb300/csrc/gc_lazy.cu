@@ -38,40 +38,14 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap,
                   const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3, GridSelScratch *gsel) {
   __shared__ unsigned long long s_red[32];
-  extern __shared__ __align__(16) unsigned char s_list[];  // kLazyListSmem bytes
   const int m = *m_dev;
-  // CTA 0 keeps a list of at most kCta0SelectMax entries in shared memory (ids,
-  // bounds, stamps): it alone selects from such a list, so every scan of a
-  // step reads shared memory instead of L2.  Longer lists keep compact copies
-  // in global memory (akey/ast), read by the grid-wide selection.
-  const bool local = m <= kCta0SelectMax;
-  const int32_t *lact = act;
-  long long *lkey = akey;
-  int32_t *lst = ast;
-  {  // the copies of the bounds of the (new) active list, and best_id's position
+  {  // compact copies of the bounds of the (new) active list, and best_id's position
     const int b0 = *(volatile int32_t *)&lc->best_id;
-    if (local) {
-      if (blockIdx.x == 0) {
-        long long *sk = reinterpret_cast<long long *>(s_list);
-        int32_t *sa = reinterpret_cast<int32_t *>(sk + kCta0SelectMax), *ss = sa + kCta0SelectMax;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-          const int v = act[i];
-          sa[i] = v;
-          sk[i] = ub[v];
-          ss[i] = stamp[v];
-          if (v == b0) lc->best_pos = i;
-        }
-        lact = sa;
-        lkey = sk;
-        lst = ss;
-      }
-    } else {
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int v = act[i];
-        akey[i] = ub[v];
-        ast[i] = stamp[v];
-        if (v == b0) lc->best_pos = i;
-      }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+      const int v = act[i];
+      akey[i] = ub[v];
+      ast[i] = stamp[v];
+      if (v == b0) lc->best_pos = i;
     }
   }
   if (!grid_sync(&lc->bar, &lc->err, tns)) return;
@@ -93,8 +67,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     // wide steps; otherwise every CTA takes part
     if (prop || wide || m <= kCta0SelectMax) {
       if (blockIdx.x == 0)
-        lazy_cta0_step(lact, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
-                       lkey, lst, wsel, wgain, wpos, wide ? wcap : 0);
+        lazy_cta0_step(act, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
+                       akey, ast, wsel, wgain, wpos, wide ? wcap : 0);
     } else {  // every CTA takes part in the selection
       int dec_local;
       if (!grid_lazy_step(act, m, ub, stamp, akey, ast, lc, gg, fold, lc->sel, lc->selpos, lc->gsel, kLanes, gsel,
@@ -160,7 +134,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       lc->last_gain = lc->best_gain;
       ub[lc->best_id] = -1;  // a member: never a candidate again
       const int bp = lc->best_pos;
-      if (bp >= 0 && bp < m && lact[bp] == lc->best_id) lkey[bp] = -1;
+      if (bp >= 0 && bp < m && act[bp] == lc->best_id) akey[bp] = -1;
       lc->best_id = -1;
       lc->best_gain = -1;
       lc->rounds_done += 1;
@@ -198,9 +172,7 @@ __global__ void k_active_theta(SelCtl *sc, LazyCtl *lc) {
 }
 
 int lazy_occupancy(int *blocks_per_sm) {
-  GC_CUDA(cudaFuncSetAttribute(k_lazy_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, kLazyListSmem));
-  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lazy_rounds, kGridGainThreads,
-                                                        kLazyListSmem));
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lazy_rounds, kGridGainThreads, 0));
   return GC_OK;
 }
 
@@ -253,8 +225,9 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap,
                   (void *)&rp_full, (void *)&c3, (void *)&gsel};
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid), dim3(kGridGainThreads), args,
-                                      kLazyListSmem, g->stream));
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
+                                      dim3(kGridGainThreads),
+                                      args, 0, g->stream));
   return GC_OK;
 }
 
