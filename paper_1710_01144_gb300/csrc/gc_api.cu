@@ -108,10 +108,13 @@ static int device_errors(gc_graph *g) {
   cudaMemsetAsync(g->ws, 0, (size_t)g->ws_count * g->ws_stride, g->stream);
   cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream);
   cudaStreamSynchronize(g->stream);
-  const char *what = e == GC_ETIMEOUT ? "device-side wait timed out"
+  std::string what = e == GC_ETIMEOUT ? "device-side wait timed out"
                      : e == GC_EDISCONNECTED ? "graph is disconnected"
                      : e == GC_EINVAL ? "invalid vertex id on the device"
                                       : "device-side consistency check failed";
+  if (e == GC_EDISCONNECTED && g->h_gctl->err == GC_EDISCONNECTED)
+    what += ": the search from vertex " + std::to_string(g->h_gctl->short_vertex) + " reached " +
+            std::to_string(g->h_gctl->short_count) + " of " + std::to_string(g->n) + " vertices";
   return fail(e, what);
 }
 
@@ -123,7 +126,10 @@ static int distances_from(gc_graph *g, const int32_t *seeds_dev, int32_t n_seeds
   GC_TRY(launch_sum_dist(g, g->dS));
   GC_TRY(read_ctl(g));
   if (g->h_bctl->err) return device_errors(g);
-  if (g->h_sctl->count != 0) return fail(GC_EDISCONNECTED, "graph is disconnected");
+  if (g->h_sctl->count != 0)
+    return fail(GC_EDISCONNECTED, "graph is disconnected: the BFS from " + std::to_string(n_seeds) +
+                                      " seed(s) left " + std::to_string(g->h_sctl->count) + " of " +
+                                      std::to_string(g->n) + " vertices unreached");
   if (farness) *farness = g->h_sctl->sum;
   return GC_OK;
 }

@@ -228,6 +228,8 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       r = -1;  // cut: cannot beat the best farness
     } else if (s_cnt[tid] != s_nlane[tid]) {
       r = -1;
+      ctl->short_vertex = c;
+      ctl->short_count = s_cnt[tid];
       atomicExch(&ctl->err, GC_EDISCONNECTED);
     } else {
       r = (long long)s_gain[tid];

@@ -360,6 +360,8 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       r = -1;
     } else if ((long long)((volatile u64 *)ctl->cnt)[tid] != n) {
       r = -1;
+      gctl->short_vertex = c;
+      gctl->short_count = (long long)((volatile u64 *)ctl->cnt)[tid];
       atomicExch(&gctl->err, GC_EDISCONNECTED);
     } else {
       r = (long long)((volatile u64 *)ctl->gain)[tid];

@@ -112,6 +112,9 @@ struct GainCtl {
   unsigned long long lanes;         // candidate lanes processed
   // the same counters, added by the CTA-batched kernel (k_gains64) alone
   unsigned long long k_front, k_union, k_push, k_lanes;
+  // farness mode, GC_EDISCONNECTED: a candidate whose search ended short and
+  // the vertices it reached (for the error message)
+  long long short_vertex, short_count;
 };
 
 // Grid-wide gain kernel control block (zeroed before each launch).
