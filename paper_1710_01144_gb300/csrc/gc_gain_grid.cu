@@ -14,8 +14,10 @@
 //      slice in shared memory (start, row, mask) and expands them edge by edge,
 //      claiming (neighbour, lane) pairs with atomicOr on the visited word as the
 //      CTA-per-batch kernel does; pushes are aggregated per warp.  In farness
-//      mode per-lane sums and counts are folded globally, and after the barrier
-//      every CTA applies the same BFScut test to its copy of the live-lane mask.
+//      mode per-lane sums and counts of each level are folded into a buffer of
+//      that distance (three, by distance mod 3); after the barrier every CTA
+//      adds the same buffer to its running totals and applies the same BFScut
+//      test to its copy of the live-lane mask.
 // Per-lane gains accumulate in shared memory and reach global memory once per
 // CTA (gain mode) or once per level (farness mode, where the cut needs them).
 #include "gc_grid.cuh"

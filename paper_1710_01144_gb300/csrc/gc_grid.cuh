@@ -84,6 +84,10 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   __shared__ u64 s_sm[T];
   __shared__ int s_x0;
   __shared__ u64 s_red[32];
+  // farness mode: running per-lane distance sums and counts, the same in every
+  // CTA (each adds the same per-level totals), so that every CTA takes the
+  // same BFScut decisions
+  __shared__ u64 s_tg[kLanes], s_tc[kLanes];
   (void)goff;
 
   const int tid = threadIdx.x, lane = tid & 31;
@@ -151,7 +155,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             reach = true;
           }
         } else {
-          ctl->cnt[j] = 1;
+          ctl->dcnt[0][j] = 1;
           reach = true;
         }
         if (reach) {
@@ -166,8 +170,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   bool ok = grid_sync(bar, err, timeout_ns);
   // invalid candidate ids leave their lanes empty
   if (ok && MODE == kModeFarness) {
+    if (tid < kLanes) {
+      s_tg[tid] = 0;
+      s_tc[tid] = tid < nl ? ((volatile u64 *)ctl->dcnt[0])[tid] : 0ull;
+    }
+    __syncthreads();
     for (int j = 0; j < nl; ++j)
-      if (((volatile unsigned long long *)ctl->cnt)[j] == 0) alive &= ~(1ull << j);
+      if (s_tc[j] == 0) alive &= ~(1ull << j);
   }
 
   int L = 0, F_prev = 0;
@@ -183,6 +192,11 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     }
     if (F == 0) break;
     if (b == 0 && tid == 0) ctl->pk[(L + 2) % 3] = 0;  // the frontier after next (read two levels ago)
+    if (MODE == kModeFarness && b == 0 && tid < kLanes) {
+      // the totals of distance L + 2 (read by every CTA after the barrier of level L - 2)
+      ctl->dgain[(L + 2) % 3][tid] = 0;
+      ctl->dcnt[(L + 2) % 3][tid] = 0;
+    }
     const int32_t *qcur_v = list_of(L % 3);
     const int32_t *qstart = starts_of(L & 1);
     const LaneWords cur = words_of(L % 3), nxt = words_of((L + 1) % 3);
@@ -293,9 +307,9 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     }
     if (MODE == kModeFarness) {
       __syncthreads();
-      if (tid < kLanes) {
-        if (s_gain[tid]) atomicAdd(&ctl->gain[tid], s_gain[tid]);
-        if (s_cnt[tid]) atomicAdd(&ctl->cnt[tid], (u64)s_cnt[tid]);
+      if (tid < kLanes) {  // the vertices claimed at distance L + 1
+        if (s_gain[tid]) atomicAdd(&ctl->dgain[(L + 1) % 3][tid], s_gain[tid]);
+        if (s_cnt[tid]) atomicAdd(&ctl->dcnt[(L + 1) % 3][tid], (u64)s_cnt[tid]);
         s_gain[tid] = 0;
         s_cnt[tid] = 0;
       }
@@ -306,12 +320,20 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     if (MODE == kModeFarness) {
       // the same BFScut test in every CTA: all vertices within L+1 are
       // counted, the rest are at least L+2 away
+      // (the running totals come from the per-distance buffers, which no CTA
+      // changes until the next barrier: the cumulative sums would already be
+      // growing with the next level in faster CTAs)
       const int Fn = (int)(*(volatile unsigned long long *)&ctl->pk[(L + 1) % 3] >> 32);
       const long long best = *(volatile long long *)&gctl->best_f;
+      if (tid < nl) {
+        s_tg[tid] += ((volatile u64 *)ctl->dgain[(L + 1) % 3])[tid];
+        s_tc[tid] += ((volatile u64 *)ctl->dcnt[(L + 1) % 3])[tid];
+      }
+      __syncthreads();
       for (int j = 0; j < nl; ++j) {
         if (!((alive >> j) & 1ull)) continue;
-        const long long s = (long long)((volatile u64 *)ctl->gain)[j];
-        const long long c = (long long)((volatile u64 *)ctl->cnt)[j];
+        const long long s = (long long)s_tg[j];
+        const long long c = (long long)s_tc[j];
         if (Fn > 0 && s + (long long)(L + 2) * ((long long)n - c) > best) alive &= ~(1ull << j);
       }
       if (alive == 0) {
@@ -358,13 +380,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       r = (long long)((volatile u64 *)ctl->gain)[tid];
     } else if (!((alive >> tid) & 1ull)) {
       r = -1;
-    } else if ((long long)((volatile u64 *)ctl->cnt)[tid] != n) {
+    } else if ((long long)s_tc[tid] != n) {
       r = -1;
       gctl->short_vertex = c;
-      gctl->short_count = (long long)((volatile u64 *)ctl->cnt)[tid];
+      gctl->short_count = (long long)s_tc[tid];
       atomicExch(&gctl->err, GC_EDISCONNECTED);
     } else {
-      r = (long long)((volatile u64 *)ctl->gain)[tid];
+      r = (long long)s_tg[tid];
       atomicMin(&gctl->best_f, r);
     }
     out[tid] = r;

@@ -128,9 +128,14 @@ struct GridGainCtl {
   // frontier of level L, by L mod 3: entries (high 32 bits) and adjacency
   // entries (low 32 bits), both taken by one atomicAdd per push
   unsigned long long pk[3];
-  unsigned long long gain[kLanes];  // per-lane gain (gain mode) / distance sum (farness)
-  unsigned long long cnt[kLanes];   // farness mode: per-lane visited count
+  unsigned long long gain[kLanes];  // gain mode: per-lane gain
+  unsigned long long cnt[kLanes];   // (unused in farness mode, see dgain/dcnt)
   int32_t blk_tot[kMaxGridCtas];    // per-CTA adjacency totals of the level
+  // farness mode: per-lane distance sums and counts of the vertices claimed at
+  // distance d, in dgain/dcnt[d mod 3] (written during one level, read by every
+  // CTA after its barrier, cleared two levels later)
+  unsigned long long dgain[3][kLanes];
+  unsigned long long dcnt[3][kLanes];
 };
 
 // Persistent lazy-rounds kernel control block (gc_lazy.cu).

@@ -94,6 +94,23 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
             assert st["rounds"] == k
 
 
+@pytest.mark.parametrize("n", [37, 64, 101])
+def test_round0_deep_graphs_repeated(gcm, n):
+    """Round 0 (top-1 closeness) on paths and cycles, many times over: the
+    grid-wide BFScut batches run dozens of levels, one barrier each, and every
+    CTA must take the same cut decisions at every level (a lane that some CTAs
+    cut and others keep ends short of n and reads as a disconnected graph).
+    Closed forms: f({v}) on a path = v(v+1)/2 + (n-1-v)(n-v)/2, minimised at
+    (n-1)//2; on a cycle every vertex has floor(n^2/4), so s0 = 0."""
+    v = (n - 1) // 2
+    cases = [(sg.path(n), v, v * (v + 1) // 2 + (n - 1 - v) * (n - v) // 2), (sg.cycle(n), 0, n * n // 4)]
+    for (rp, ci), s0, f0 in cases:
+        with gcm.Graph(rp, ci) as G:
+            for _ in range(40):
+                grp, f, _ = G.greedy(1)
+                assert int(grp[0]) == s0 and f == f0
+
+
 @pytest.mark.parametrize("name,g", small_cases())
 def test_greedy_step_forms(gcm, name, g):
     """Persistent rounds with wide steps (a 64-lane batch per CTA) or grid-wide
