@@ -50,7 +50,7 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict_
 // One batch of nl <= 64 candidates advanced by every CTA of the grid, with one
 // grid barrier per BFS level.  ctl must hold zeros in pk, touched, gain and
 // cnt on entry; the workspace's lane words must be zero and are zero again
-// when the last CTA passes the caller's next barrier.  gx holds 3n int32
+// when the function returns (in every CTA).  gx holds 3n int32
 // (entry offsets by level parity, a third frontier list).  Returns false if a
 // barrier gave up (the error code is in *err / gctl->err).
 //
@@ -69,13 +69,20 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict_
 // levels >= 1 scan only their first c3[u] entries.  With voff/ws_n (one graph
 // of a block-diagonal union) the vertices are [voff, voff + ws_n): workspace 0
 // and gx are laid out for ws_n vertices and indexed by w - voff.
+// `phase` (gain mode only) splits off level 0, which one warp does: kBatchLevel0
+// runs just that part in the calling CTA and returns without a barrier (a
+// persistent kernel's selecting CTA does it right after choosing the batch);
+// kBatchRest then runs the rest in every CTA, after a grid barrier the caller
+// placed between the two.  kBatchAll does both with a barrier of its own.
+constexpr int kBatchAll = 0, kBatchLevel0 = 1, kBatchRest = 2;
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
                                 const int32_t *nl_dev, long long *out, unsigned char *ws_base, int32_t *gx,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
-                                const int32_t *__restrict__ c3 = nullptr, int voff = 0, int ws_n = -1) {
+                                const int32_t *__restrict__ c3 = nullptr, int voff = 0, int ws_n = -1,
+                                int phase = kBatchAll) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
@@ -136,8 +143,9 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     c_push += (lane == leader) ? (u64)__popc(qm) : 0ull;
   };
 
-  // ---- level 0 (warp 0 of CTA 0): lanes reach their candidates ----
-  if (b == 0 && tid < 32) {
+  if (MODE != kModeGain) phase = kBatchAll;
+  // ---- level 0 (warp 0 of CTA 0, or of the calling CTA): lanes reach their candidates ----
+  if (phase != kBatchRest && (b == 0 || phase == kBatchLevel0) && tid < 32) {
     // lane t handles lanes t and t + 32 of the batch, one after the other
     for (int h = 0; h < 2; ++h) {
       const int j = lane + 32 * h;
@@ -166,8 +174,15 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       }
       enqueue(q, c, 0, q ? row_len(rp, c3, c, 0) : 0);
     }
+    if (phase == kBatchLevel0) {
+      if (c_push) atomicAdd(&gctl->pushes, c_push);
+      return true;
+    }
   }
-  bool ok = grid_sync(bar, err, timeout_ns);
+  if (phase == kBatchLevel0) return true;
+  bool ok = true;
+  if (phase == kBatchRest) __syncthreads();  // s_gain and s_cnt are zero
+  else ok = grid_sync(bar, err, timeout_ns);
   // invalid candidate ids leave their lanes empty
   if (ok && MODE == kModeFarness) {
     if (tid < kLanes) {
@@ -355,6 +370,12 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     __syncthreads();
     if (tid < kLanes && s_gain[tid]) atomicAdd(&ctl->gain[tid], s_gain[tid]);
   }
+  // leave the workspace zero: the touched list is complete once the last
+  // level's barrier has passed, and the barrier below publishes the clearing
+  {
+    const int nt = *(volatile int32_t *)&ctl->touched;
+    for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i] - voff] = 0;
+  }
   c_scalar = block_sum(c_scalar, s_red);
   c_union = block_sum(c_union, s_red);
   c_front = block_sum(c_front, s_red);
@@ -391,9 +412,6 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     }
     out[tid] = r;
   }
-  // leave the workspace zero for the next launch
-  const int nt = *(volatile int32_t *)&ctl->touched;
-  for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i] - voff] = 0;
   if (!ok2 && b == 0 && tid == 0) atomicExch(&gctl->err, GC_ETIMEOUT);
   return ok2;
 }

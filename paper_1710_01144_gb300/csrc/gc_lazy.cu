@@ -38,14 +38,40 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap,
                   const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3, GridSelScratch *gsel) {
   __shared__ unsigned long long s_red[32];
+  extern __shared__ __align__(16) unsigned char s_list[];  // kLazyListSmem bytes
   const int m = *m_dev;
-  {  // compact copies of the bounds of the (new) active list, and best_id's position
+  // CTA 0 keeps a list of at most kCta0SelectMax entries in shared memory (ids,
+  // bounds, stamps): it alone selects from such a list, so every scan of a
+  // step reads shared memory instead of L2.  Longer lists keep compact copies
+  // in global memory (akey/ast), read by the grid-wide selection.
+  const bool local = m <= kCta0SelectMax;
+  const int32_t *lact = act;
+  long long *lkey = akey;
+  int32_t *lst = ast;
+  {  // the copies of the bounds of the (new) active list, and best_id's position
     const int b0 = *(volatile int32_t *)&lc->best_id;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-      const int v = act[i];
-      akey[i] = ub[v];
-      ast[i] = stamp[v];
-      if (v == b0) lc->best_pos = i;
+    if (local) {
+      if (blockIdx.x == 0) {
+        long long *sk = reinterpret_cast<long long *>(s_list);
+        int32_t *sa = reinterpret_cast<int32_t *>(sk + kCta0SelectMax), *ss = sa + kCta0SelectMax;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          const int v = act[i];
+          sa[i] = v;
+          sk[i] = ub[v];
+          ss[i] = stamp[v];
+          if (v == b0) lc->best_pos = i;
+        }
+        lact = sa;
+        lkey = sk;
+        lst = ss;
+      }
+    } else {
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = act[i];
+        akey[i] = ub[v];
+        ast[i] = stamp[v];
+        if (v == b0) lc->best_pos = i;
+      }
     }
   }
   if (!grid_sync(&lc->bar, &lc->err, tns)) return;
@@ -54,21 +80,39 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
   GainCounters cnt;
   unsigned long long t0 = timer ? global_ns() : 0, t1;
   bool fold = false;
+  // CTA 0 selects for short lists (a few scans of m entries cost less than the
+  // grid barriers of the grid-wide selection), with proposal lanes and in wide
+  // steps; otherwise every CTA takes part.  With CTA 0 selecting 64-lane grid
+  // batches it also runs level 0 of the batch and the accept bookkeeping before
+  // the step's barrier, and fewer barriers are needed per step and per round.
+  const bool cta0_sel = prop || wide || m <= kCta0SelectMax;
+  const bool lean = cta0_sel && !prop && !wide;
+  int r = *(volatile int32_t *)&lc->round;  // every CTA counts the rounds itself
   for (;;) {
-    const int r = *(volatile int32_t *)&lc->round;
     if (r >= k) break;
     if (prop && *(volatile int32_t *)&lc->scored_round != r) {
       lazy_score(act, m, prop, rp_full, dS, ub, stamp, two_hop, mx, r, lc->last_gain, score);
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
       if (blockIdx.x == 0 && threadIdx.x == 0) lc->scored_round = r;
     }
-    // CTA 0 selects for short lists (a few scans of m entries cost less than
-    // the grid barriers of the grid-wide selection), with proposal lanes and in
-    // wide steps; otherwise every CTA takes part
-    if (prop || wide || m <= kCta0SelectMax) {
-      if (blockIdx.x == 0)
-        lazy_cta0_step(act, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
-                       akey, ast, wsel, wgain, wpos, wide ? wcap : 0);
+    if (cta0_sel) {
+      if (blockIdx.x == 0) {
+        lazy_cta0_step(lact, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
+                       lkey, lst, wsel, wgain, wpos, wide ? wcap : 0);
+        if (lean) {
+          __syncthreads();  // lc->dec, lc->sel and the reset batch control block
+          const int d = *(volatile int32_t *)&lc->dec;
+          if (d == 0) {
+            grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
+                                       &lc->bar, &lc->err, tns, mx, c3, 0, -1, kBatchLevel0);
+          } else if (d == 1 && threadIdx.x == 0) {
+            picks[r] = lc->best_id;
+            pgain[r] = lc->best_gain;
+            lc->pk[0] = lc->pk[1] = lc->pk[2] = 0;
+            lc->decrease = 0;
+          }
+        }
+      }
     } else {  // every CTA takes part in the selection
       int dec_local;
       if (!grid_lazy_step(act, m, ub, stamp, akey, ast, lc, gg, fold, lc->sel, lc->selpos, lc->gsel, kLanes, gsel,
@@ -93,12 +137,14 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         for (int bi = blockIdx.x; bi < nb; bi += gridDim.x)
           cta_gain_batch<kModeGain, true, false>(rp, ci, n, dS, wsel + bi * kLanes, min(kLanes, ns - bi * kLanes),
                                     wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt, 0, c3);
-        ok = true;
+        ok = grid_sync(&lc->bar, &lc->err, tns);  // gains visible to CTA 0
       } else {
         ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
-                                        &lc->bar, &lc->err, tns, mx, c3);
+                                        &lc->bar, &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll);
+        // the gains are in lc->gsel, written by CTA 0: only a grid-wide fold
+        // needs them published
+        if (!lean) ok = ok && grid_sync(&lc->bar, &lc->err, tns);
       }
-      ok = ok && grid_sync(&lc->bar, &lc->err, tns);  // workspace clean, gains visible
       if (!ok) break;
       if (timer) {
         t1 = global_ns();
@@ -110,13 +156,15 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     }
     // accept the round's best: record it and update d_S from it
     fold = false;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      picks[r] = lc->best_id;
-      pgain[r] = lc->best_gain;
-      lc->pk[0] = lc->pk[1] = lc->pk[2] = 0;
-      lc->decrease = 0;
+    if (!lean) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        picks[r] = lc->best_id;
+        pgain[r] = lc->best_gain;
+        lc->pk[0] = lc->pk[1] = lc->pk[2] = 0;
+        lc->decrease = 0;
+      }
+      if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     }
-    if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     bool ok = true;
     if (*(volatile long long *)&lc->best_gain <= local_max) {  // small region: CTA 0 alone
       if (blockIdx.x == 0) {
@@ -134,13 +182,17 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       lc->last_gain = lc->best_gain;
       ub[lc->best_id] = -1;  // a member: never a candidate again
       const int bp = lc->best_pos;
-      if (bp >= 0 && bp < m && act[bp] == lc->best_id) akey[bp] = -1;
+      if (bp >= 0 && bp < m && lact[bp] == lc->best_id) lkey[bp] = -1;
       lc->best_id = -1;
       lc->best_gain = -1;
       lc->rounds_done += 1;
       lc->round = r + 1;
     }
-    if (!grid_sync(&lc->bar, &lc->err, tns)) break;
+    ++r;
+    // the other CTAs read none of the bookkeeping before the next step's
+    // barrier unless they select or score too; CTA 0's own threads do
+    if (lean) __syncthreads();
+    else if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();
       lc->ns_update += t1 - t0;
@@ -172,7 +224,9 @@ __global__ void k_active_theta(SelCtl *sc, LazyCtl *lc) {
 }
 
 int lazy_occupancy(int *blocks_per_sm) {
-  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lazy_rounds, kGridGainThreads, 0));
+  GC_CUDA(cudaFuncSetAttribute(k_lazy_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, kLazyListSmem));
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_lazy_rounds, kGridGainThreads,
+                                                        kLazyListSmem));
   return GC_OK;
 }
 
@@ -225,9 +279,8 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap,
                   (void *)&rp_full, (void *)&c3, (void *)&gsel};
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid),
-                                      dim3(kGridGainThreads),
-                                      args, 0, g->stream));
+  GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid), dim3(kGridGainThreads), args,
+                                      kLazyListSmem, g->stream));
   return GC_OK;
 }
 

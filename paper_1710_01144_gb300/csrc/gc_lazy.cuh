@@ -150,31 +150,43 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
       __syncthreads();
     }
   }
-  int taken = 0, eq_seen = 0;
-  for (int b = 0; b < m && taken < need; b += T) {
-    if (scanned && tid == 0) *scanned += (unsigned long long)min(T, m - b);
-    const int i = b + tid;
-    int gt = 0, eq = 0, v = -1;
-    if (i < m) {
-      v = act[i];
+  // Selection in list order.  Thread t owns the contiguous entries [t C, t C + C):
+  // one pass counts its keys above and equal to tau, two block scans give the
+  // counts before its first entry, a second pass writes its taken entries at
+  // rank (entries above tau before it) + min(entries equal before it, eq_take).
+  const int eq_take = (int)(need - above);  // equal keys taken, the first ones in list order
+  const int C = (m + T - 1) / T;
+  const int i0 = min(m, tid * C), i1 = min(m, i0 + C);
+  int ngt = 0, neq = 0;
+  for (int i = i0; i < i1; ++i) {
+    const long long k = key(i, act[i]);
+    if (k == LLONG_MIN) continue;
+    ngt += k > tau;
+    neq += k == tau;
+  }
+  if (scanned && tid == 0) *scanned += (unsigned long long)m;
+  int tot_gt, tot_eq;
+  int gt_before = block_excl_scan(ngt, s_scan, &tot_gt);
+  int eq_before = block_excl_scan(neq, s_scan, &tot_eq);
+  if (ngt > 0 || (neq > 0 && eq_before < eq_take)) {
+    for (int i = i0; i < i1; ++i) {
+      const int v = act[i];
       const long long k = key(i, v);
-      if (k != LLONG_MIN) {
-        gt = k > tau;
-        eq = k == tau;
+      if (k == LLONG_MIN) continue;
+      const bool gt = k > tau, eq = k == tau;
+      if (gt || (eq && eq_before < eq_take)) {
+        const int pos = gt_before + min(eq_before, eq_take);
+        if (base + pos < cap) {
+          sel[base + pos] = v;
+          if (selpos) selpos[base + pos] = i;
+        }
       }
+      gt_before += gt;
+      eq_before += eq;
     }
-    int tot_eq, tot_take;
-    const int eq_rank = eq_seen + block_excl_scan(eq, s_scan, &tot_eq);
-    const int take = gt || (eq && eq_rank < need - above);
-    const int pos = taken + block_excl_scan(take, s_scan, &tot_take);
-    if (take && base + pos < cap) {
-      sel[base + pos] = v;
-      if (selpos) selpos[base + pos] = i;
-    }
-    eq_seen += tot_eq;
-    taken += tot_take;
   }
   __syncthreads();
+  const int taken = tot_gt + min(tot_eq, eq_take);
   return taken < need ? taken : need;
 }
 
