@@ -265,36 +265,45 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             }
           }
           // everything indexed by the neighbour is loaded at once: d_S, the
-          // neighbour bound and the row length it would scan next level
+          // neighbour bound, the row length it would scan next level and its
+          // visited word (from L2: it holds every lane that reached w before
+          // this level)
           int dw[kGridIlp], mxw[kGridIlp], lw[kGridIlp];
+          u64 vp[kGridIlp];
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) {
             const bool ok = w[k] >= 0;
             dw[k] = (MODE == kModeGain && ok) ? dS[w[k]] : 0;
             mxw[k] = (MODE == kModeGain && mx && ok) ? __ldg(mx + w[k]) : INT_MAX;
             lw[k] = ok ? row_len(rp, c3, w[k], nlev) : 0;
+            vp[k] = ok ? __ldcg(&ws.vis[w[k] - voff]) : 0ull;
           }
           u64 nb[kGridIlp];
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) {
-            // pruned unless w is strictly closer to the lane's candidate than to S
+            // pruned unless w is strictly closer to the lane's candidate than
+            // to S; lanes that reached w at an earlier level are left out
             const bool live = w[k] >= 0 && (MODE != kModeGain || dw[k] > nlev);
-            nb[k] = live ? s_sm[sl[k]] : 0ull;
+            nb[k] = live ? (s_sm[sl[k]] & ~vp[k]) : 0ull;
           }
-          // claim with the atomicOr itself (no pre-read of the visited word:
-          // the searches are few, so latency counts more than atomic traffic)
-          u64 ov[kGridIlp];
+          // Both claims at once.  The visited word decides which lanes this
+          // thread wins (its gains) and whether w is new to the batch.  The
+          // claim word of level nlev receives all of nb: every bit of it is a
+          // lane that reaches w at this level (won here or by a concurrent
+          // claim), and the thread that finds the word empty queues w.  w is
+          // expanded at level nlev only if some neighbour may still be claimed.
+          u64 ov[kGridIlp], on[kGridIlp];
 #pragma unroll
-          for (int k = 0; k < kGridIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
+          for (int k = 0; k < kGridIlp; ++k) {
+            ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
+            on[k] = (nb[k] && mxw[k] > nlev + 1) ? atomicOr(&nxt[w[k] - voff], nb[k]) : ~0ull;
+          }
 #pragma unroll
           for (int k = 0; k < kGridIlp; ++k) {
             u64 won = nb[k] & ~ov[k];
             const bool fresh = won && ov[k] == 0;
-            bool q = false;
+            const bool q = on[k] == 0ull;
             if (won) {
-              // expanded at level nlev only if some neighbour may still be claimed
-              const bool expand = mxw[k] > nlev + 1;
-              if (expand) q = atomicOr(&nxt[w[k] - voff], won) == 0;
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {
                 const int j = __ffsll((long long)won) - 1;
