@@ -334,7 +334,7 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
     const int32_t len = std::min<int32_t>(g->n, n_cand - off);
     GC_CUDA(cudaMemcpyAsync(g->list, cand + off, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice,
                             g->stream));
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     GC_TRY(gain_event(g, 0, &e0));
     GC_TRY(gain_event(g, 1, &e1));
     GC_CUDA(cudaEventRecord(e0, g->stream));
@@ -392,7 +392,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
                          int lanes) -> int {
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     GC_TRY(gain_event(g, ev_used, &e0));
     GC_TRY(gain_event(g, ev_used + 1, &e1));
     ev_used += 2;
@@ -404,7 +404,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   };
   auto grid_timed = [&](int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,
                         long long *out) -> int {
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     GC_TRY(gain_event(g, ev_used, &e0));
     GC_TRY(gain_event(g, ev_used + 1, &e1));
     ev_used += 2;
@@ -534,7 +534,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
                                               : (step_form == 2 ? std::max<int32_t>(4096, 2 * g->wcap) : 2048);
       for (;;) {
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
-        cudaEvent_t le0, le1;
+        cudaEvent_t le0 = nullptr, le1 = nullptr;
         GC_TRY(gain_event(g, ev_used, &le0));
         GC_TRY(gain_event(g, ev_used + 1, &le1));
         ev_used += 2;
