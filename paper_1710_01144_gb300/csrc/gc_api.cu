@@ -62,7 +62,8 @@ static void release(gc_graph *g) {
                  g->blk, g->partial, g->hist, g->io_a, g->io_b, g->bctl, g->gctl, g->sctl,
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
-                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy};
+                 g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
+                 g->g3};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -250,7 +251,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->rpf, N + 1)) || (rc = dalloc(&g->cif, std::max<size_t>(1, (size_t)nnz))) ||
       (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->heavy, N)) ||
       (rc = dalloc(&g->n_heavy, 1)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
-      (rc = dalloc(&g->lev_max, 1)) || (rc = dalloc(&g->gsel, 1)) ||
+      (rc = dalloc(&g->lev_max, 1)) || (rc = dalloc(&g->gsel, 1)) || (rc = dalloc(&g->g3, 1)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
@@ -488,16 +489,23 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   out_group[0] = s0;
 
   // ---- rounds 1..k-1: lazy greedy with exact pruned gains ----
-  if (k > 1) {
-    GC_TRY(launch_fill_i64(g, g->ub, LLONG_MAX, g->n));
-    GC_TRY(launch_fill_i64(g, g->ub + s0, -1, 1));
-    GC_TRY(launch_fill_i32(g, g->stamp, 0, g->n));
-  }
   // later rounds: few candidates per step, spread over CTAs in small batches
   const int32_t step_want = opts.eval_per_step > 0 ? opts.eval_per_step : 128;
   const int step_lanes = (opts.step_lanes > 0 && opts.step_lanes <= kLanes) ? opts.step_lanes : 8;
   const bool grid_steps = opts.step_mode == 2;
   const bool persistent = opts.step_mode == 0 || opts.step_mode == 3;
+  // round-1 bounds (k_round1_bound, from the pruned adjacency's counts): round
+  // 1 then runs in the persistent kernel like every later round
+  const bool round1_bound = persistent && pruned && !(opts.flags & GC_OPT_NO_ROUND1_BOUND);
+  if (k > 1) {
+    if (round1_bound) {
+      GC_TRY(launch_round1_bound(g));
+    } else {
+      GC_TRY(launch_fill_i64(g, g->ub, LLONG_MAX, g->n));
+      GC_TRY(launch_fill_i64(g, g->ub + s0, -1, 1));
+      GC_TRY(launch_fill_i32(g, g->stamp, 0, g->n));
+    }
+  }
   const int32_t heavy = opts.round1_heavy < 0 ? 0 : (opts.round1_heavy == 0 ? 1024 : opts.round1_heavy);
   // measured on R-MAT graphs: the grid-wide forms win, so both default off
   // lazy step form: wide (one 64-lane batch per CTA) on deep graphs, where a
@@ -512,7 +520,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
   gains_picked[0] = f;
   for (int32_t r = 1; r < k; ++r) {
-    if (r >= 2 && persistent) {
+    if (r >= (round1_bound ? 1 : 2) && persistent) {
       // rounds r..k-1 on the device: persistent kernel over an active list
       LazyCtl init;
       memset(&init, 0, sizeof(init));

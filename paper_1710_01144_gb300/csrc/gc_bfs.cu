@@ -439,6 +439,88 @@ __global__ void __launch_bounds__(1024) k_max_nbr_heavy(const int32_t *__restric
   }
 }
 
+// Round-1 upper bounds.  With S = {s0} and d_S = d(s0, .), every candidate v
+// satisfies
+//   Delta(v|S) <= d_S[v] + sum_{w in N(v)} ((d_S[w] - 1)^+ + c3[w]) + G3,
+//   G3 = sum_u (d_S[u] - 3)^+,
+// because a vertex u at distance 1 from v gains at most d_S[u] - 1; one at
+// distance 2 gains at most (d_S[u] - 2)^+ = [d_S[u] >= 3] + (d_S[u] - 3)^+,
+// and each such u with d_S[u] >= 3 is a neighbour of some w in N(v), counted
+// by c3[w] (neighbours of w with d_S >= 3); farther vertices gain at most
+// (d_S[u] - 3)^+; and the (d_S - 3)^+ terms of all of them sum to at most G3.
+// A neighbour w with d_S[w] <= 1 adds nothing (its own term is 0 and its
+// neighbours have d_S <= 2), so the pruned rows (d_S[w] >= 2) suffice.  The
+// bounds replace the +infinity of round 1 (Sec. 4.2 gives none), so the lazy
+// rule of round 1 evaluates only the candidates whose bound reaches the best
+// exact gain.  ub[v] <- the bound (members of S: -1), stamp[v] <- 0.
+__global__ void __launch_bounds__(kRedThreads) k_excess3(const int32_t *__restrict__ dS, int32_t n,
+                                                         unsigned long long *g3) {
+  __shared__ long long sh[32];
+  long long s = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = dS[i];
+    if (d > 3) s += d - 3;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0 && s) atomicAdd(g3, (unsigned long long)s);
+}
+
+// A warp per row; rows longer than kHeavyRow (full adjacency) are left to
+// k_round1_bound_heavy.
+__global__ void __launch_bounds__(kRedThreads) k_round1_bound(const int32_t *__restrict__ rpf,
+                                                              const int32_t *__restrict__ cif,
+                                                              const int32_t *__restrict__ rp, int32_t n,
+                                                              const int32_t *__restrict__ dS,
+                                                              const int32_t *__restrict__ c3,
+                                                              const unsigned long long *__restrict__ g3,
+                                                              long long *ub, int32_t *stamp) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const long long G3 = (long long)*g3;
+  for (int v = gwarp; v < n; v += nwarps) {
+    if (rp[v + 1] - rp[v] > kHeavyRow) continue;  // k_round1_bound_heavy
+    long long s = 0;
+    for (int e = rpf[v] + lane; e < rpf[v + 1]; e += 32) {
+      const int w = cif[e];
+      s += (long long)max(dS[w] - 1, 0) + (long long)c3[w];
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      const int dv = dS[v];
+      ub[v] = dv == 0 ? -1ll : (long long)dv + s + G3;
+      stamp[v] = 0;
+    }
+  }
+}
+
+// The long rows of k_round1_bound, a CTA per row.
+__global__ void __launch_bounds__(1024) k_round1_bound_heavy(const int32_t *__restrict__ rpf,
+                                                            const int32_t *__restrict__ cif,
+                                                            const int32_t *__restrict__ dS,
+                                                            const int32_t *__restrict__ c3,
+                                                            const unsigned long long *__restrict__ g3,
+                                                            long long *ub, int32_t *stamp,
+                                                            const int32_t *__restrict__ heavy,
+                                                            const int32_t *__restrict__ nh) {
+  __shared__ long long s_red[32];
+  const long long G3 = (long long)*g3;
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int v = heavy[i];
+    long long s = 0;
+    for (int e = rpf[v] + threadIdx.x; e < rpf[v + 1]; e += 1024) {
+      const int w = cif[e];
+      s += (long long)max(dS[w] - 1, 0) + (long long)c3[w];
+    }
+    s = block_sum(s, s_red);
+    if (threadIdx.x == 0) {
+      const int dv = dS[v];
+      ub[v] = dv == 0 ? -1ll : (long long)dv + s + G3;
+      stamp[v] = 0;
+    }
+  }
+}
+
 // CSR validation, part 1: row_ptr monotone within [0, nnz].
 __global__ void k_validate_rowptr(const int32_t *__restrict__ rp, int32_t n, int64_t nnz,
                                   SelCtl *ctl) {
@@ -564,6 +646,19 @@ int launch_prune_csr(gc_graph *g) {
   k_prune_fill<<<grid, kRedThreads, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif);
   k_prune_fill_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rp, g->ci, n, g->dS, g->rpf, g->c3, g->cif,
                                                              g->heavy, g->n_heavy);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_round1_bound(gc_graph *g) {
+  const int n = g->n;
+  g->launches += 3;
+  GC_CUDA(cudaMemsetAsync(g->g3, 0, sizeof(unsigned long long), g->stream));
+  k_excess3<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->dS, n, g->g3);
+  k_round1_bound<<<grid_for((int64_t)n * 32, kRedThreads, g->num_sms * 8), kRedThreads, 0, g->stream>>>(
+      g->rpf, g->cif, g->rp, n, g->dS, g->c3, g->g3, g->ub, g->stamp);
+  k_round1_bound_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rpf, g->cif, g->dS, g->c3, g->g3, g->ub,
+                                                               g->stamp, g->heavy, g->n_heavy);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -30,6 +30,7 @@ GC_VALIDATE = 0x4
 GC_OPT_NO_EXPAND_BOUND = 0x1
 GC_OPT_CAPTURE = 0x2
 GC_OPT_FULL_ADJACENCY = 0x4
+GC_OPT_NO_ROUND1_BOUND = 0x8
 
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
@@ -231,13 +232,14 @@ class Graph:
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
                step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0,
-               pruned_adjacency: bool = True):
+               pruned_adjacency: bool = True, round1_bound: bool = True):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
         o.step_lanes, o.step_mode, o.active_target = step_lanes, step_mode, active_target
         o.round1_heavy = round1_heavy
-        o.flags = (0 if expand_bound else GC_OPT_NO_EXPAND_BOUND) | (0 if pruned_adjacency else GC_OPT_FULL_ADJACENCY)
+        o.flags = ((0 if expand_bound else GC_OPT_NO_EXPAND_BOUND) | (0 if pruned_adjacency else GC_OPT_FULL_ADJACENCY)
+                   | (0 if round1_bound else GC_OPT_NO_ROUND1_BOUND))
         o.step_form, o.local_update_max_gain = step_form, local_update_max_gain
         o.lazy_ctas = lazy_ctas
         if timeout_ms:

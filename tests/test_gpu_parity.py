@@ -94,6 +94,24 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
             assert st["rounds"] == k
 
 
+@pytest.mark.parametrize("name,g", small_cases() + [("rmat13", graphgen.rmat(13, 16.0, seed=4))])
+def test_round1_bound_same_group(gcm, name, g):
+    """Round 1 started in the persistent kernel with the two-hop bounds returns
+    the oracle's group, as the every-vertex round 1 does; on R-MAT it evaluates
+    far fewer candidates."""
+    rp, ci = g
+    k = min(12, rp.size - 1)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, k)
+    with gcm.Graph(rp, ci) as G:
+        a, fa, sa = G.greedy(k)
+        b, fb, sb = G.greedy(k, round1_bound=False)
+    np.testing.assert_array_equal(a, grp)
+    np.testing.assert_array_equal(b, grp)
+    assert fa == fb == ft[-1]
+    if name == "rmat13":
+        assert sa["evals"] * 2 < sb["evals"]
+
+
 @pytest.mark.parametrize("n", [37, 64, 101])
 def test_round0_deep_graphs_repeated(gcm, n):
     """Round 0 (top-1 closeness) on paths and cycles, many times over: the
