@@ -302,11 +302,13 @@ def run_gc(args):
                     "share_of_step": ms / sum(times)}
 
         # the largest kernel by device time (the persistent lazy kernel), then
-        # the round-1 gain kernel
+        # the CTA-per-batch gain kernel when it ran (round 1 without bounds)
         roof_lazy = roof("k_lazy_rounds", lazy_kernel_bytes(tot), tot["ms_lazy_kernel"], tot["lazy_launches"])
-        roof_g64 = roof("k_gains64", algorithmic_bytes(tot["gain64_frontier"], tot["gain64_edges"],
-                                                       tot["gain64_pushes"], tot["gain64_lanes"]),
-                        tot["ms_gain64"], tot["gain64_launches"])
+        roof_g64 = None
+        if tot["gain64_launches"] > 0:
+            roof_g64 = roof("k_gains64", algorithmic_bytes(tot["gain64_frontier"], tot["gain64_edges"],
+                                                           tot["gain64_pushes"], tot["gain64_lanes"]),
+                            tot["ms_gain64"], tot["gain64_launches"])
         line = {
             "metric": METRIC,
             "value": job_value(ws, t_step),
