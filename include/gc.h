@@ -72,8 +72,8 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
                                (rows without neighbours at d_S <= 1); work only,
                                the group is the same */
 #define GC_OPT_NO_ROUND1_BOUND 0x8u /* gc_greedy: evaluate every vertex in round 1
-                               instead of starting the persistent lazy rounds at
-                               round 1 with two-hop upper bounds; work only */
+                               instead of only those whose two-hop upper bound
+                               reaches the best exact gain; work only */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
@@ -134,8 +134,7 @@ typedef struct gc_stats {
   int64_t lanes;           /* candidate lanes processed (all launches) */
   int64_t round0_evals;    /* candidates evaluated (exactly or cut) in round 0 */
   double ms_round0;        /* time of round 0 (top-1 closeness + d_S) */
-  double ms_round1;        /* time of a host-driven round 1 (0 when round 1
-                              runs in the persistent kernel) */
+  double ms_round1;        /* time of round 1 */
   double ms_total;         /* time of the whole call */
   double ms_gain_kernel;   /* summed duration of gain-kernel launches (host-driven
                               steps; the persistent kernel's phases are below) */

@@ -495,7 +495,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const bool grid_steps = opts.step_mode == 2;
   const bool persistent = opts.step_mode == 0 || opts.step_mode == 3;
   // round-1 bounds (k_round1_bound, from the pruned adjacency's counts): round
-  // 1 then runs in the persistent kernel like every later round
+  // 1 evaluates the 64 largest bounds, then only the candidates whose bound
+  // reaches the best exact gain found, instead of every vertex
   const bool round1_bound = persistent && pruned && !(opts.flags & GC_OPT_NO_ROUND1_BOUND);
   if (k > 1) {
     if (round1_bound) {
@@ -520,7 +521,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   std::vector<long long> gains_picked(k, 0), decreases(k, 0);
   gains_picked[0] = f;
   for (int32_t r = 1; r < k; ++r) {
-    if (r >= (round1_bound ? 1 : 2) && persistent) {
+    if (r >= 2 && persistent) {
       // rounds r..k-1 on the device: persistent kernel over an active list
       LazyCtl init;
       memset(&init, 0, sizeof(init));
@@ -588,7 +589,20 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     }
     GC_TRY(launch_round_begin(g));
     for (int step = 0;; ++step) {
-      if (r == 1) {  // no bounds yet: all of V \ S
+      if (r == 1 && round1_bound) {
+        if (step == 0) {
+          // the 64 largest bounds first, as one grid-wide batch: their best
+          // exact gain is the level every other candidate's bound must reach
+          GC_TRY(launch_select(g, kSelLazy, r, kLanes, kTauHistogram, 0));
+          GC_TRY(launch_clamp_nsel(g, kLanes));
+          GC_TRY(grid_timed(kModeGain, g->list, 0, &g->sctl->n_sel, g->lgain));
+        } else {
+          // every unevaluated candidate whose bound reaches the best exact
+          // gain so far, in 64-lane batches, one CTA each
+          GC_TRY(launch_select(g, kSelLazy, r, 0, kTauHost, g->h_sctl->best_gain));
+          GC_TRY(gains_timed(kModeGain, g->list, 0, &g->sctl->n_sel, kLanes));
+        }
+      } else if (r == 1) {  // no bounds: all of V \ S
         if (heavy > 0) {
           // the highest-degree candidates have the largest searches: one
           // grid-wide batch per 64 of them, so no CTA is left with a hub batch

@@ -96,9 +96,10 @@ def test_greedy_equals_plain_oracle(gcm, name, g):
 
 @pytest.mark.parametrize("name,g", small_cases() + [("rmat13", graphgen.rmat(13, 16.0, seed=4))])
 def test_round1_bound_same_group(gcm, name, g):
-    """Round 1 started in the persistent kernel with the two-hop bounds returns
-    the oracle's group, as the every-vertex round 1 does; on R-MAT it evaluates
-    far fewer candidates."""
+    """Round 1 with the two-hop bounds (the 64 largest first, then every
+    candidate whose bound reaches the best exact gain) returns the oracle's
+    group, as the every-vertex round 1 does; on R-MAT it evaluates far fewer
+    candidates."""
     rp, ci = g
     k = min(12, rp.size - 1)
     grp, ft, _ = oracle.greedy_plain(rp, ci, k)
