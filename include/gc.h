@@ -117,6 +117,10 @@ typedef struct gc_opts {
                               vertices run their lazy rounds grid-wide, one
                               graph at a time; the others CTA-locally;
                               0 = 65536, negative = none */
+  int32_t timeout_us;      /* if > 0: the limit of every device-side wait in
+                              microseconds, overriding timeout_ms (a limit
+                              that short makes the waits give up with
+                              GC_ETIMEOUT; the handle stays usable) */
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */
@@ -217,35 +221,55 @@ int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len,
                              const int32_t *cand_dev, int32_t n_cand, int64_t *out_gain_dev);
 
 /* gc_marginal_gains_static -- the gains of gc_marginal_gains for callers that
- * cannot allocate device memory (for example code that runs while somebody
- * else captures the stream into a CUDA graph, plugins confined to a host
- * application's own allocator, or request paths where allocator calls and
- * their implicit synchronisation are not allowed).  The paper has no
+ * cannot allocate device memory: plugins confined to a host application's own
+ * allocator or fixed memory budget (a raw cudaMalloc would bypass both), and
+ * request paths where allocator calls are not allowed (cudaMalloc and cudaFree
+ * can synchronise the device and take unbounded time).  The paper has no
  * counterpart; this is a deployment variant.
  * It calls no cudaMalloc/cudaFree and creates no handle: all scratch lives in
  * one 64 MiB array compiled into the library, which every GPU that loads the
  * library keeps until the process exits.
- * n, row_ptr, col_idx : the CSR as device pointers (same format as above); the
- *            graph must be connected.
+ * n, row_ptr, col_idx : the CSR as device pointers (same format as above).
  * S, cand, out_gain   : device int32[s_len], int32[n_cand], int64[n_cand];
- *            s_len >= 1; out_gain[i] = Delta(cand[i] | S), -1 for an id
- *            outside [0, n).  Ids in S must be in range.
+ *            s_len >= 1; out_gain[i] = Delta(cand[i] | S), or -1 for an id
+ *            outside [0, n).
  * stream   : cudaStream_t (as void*); the call is asynchronous on it.
- * Limits   : n is limited by the array (one 44-byte-per-vertex workspace plus
- *            24 bytes per vertex must fit: n up to about 980,000); a larger
- *            n returns GC_ERANGE before anything runs.  Smaller graphs get more
- *            workspaces and therefore more parallel CTAs.
- * Sharing  : all calls in the process share the one array.  Each call zeroes
- *            the parts it uses, so calls ordered on one stream are safe, but
- *            calls that overlap on the GPU (different streams or threads) race
- *            and give wrong results.
+ * Device-side failures: when the BFS from S fails -- an id of S outside
+ *            [0, n), a device-side wait that timed out, or a vertex that S does
+ *            not reach (a disconnected graph) -- every out_gain entry is -1.
+ *            Nothing is reported to the host, since that needs a
+ *            synchronisation.
+ * Limits   : n <= 1,048,496 (64 bytes of scratch per vertex: 20 for d(., S)
+ *            and the BFS queues, 44 for one gain workspace, each part 256-byte
+ *            aligned); a larger n returns GC_ERANGE before anything runs.
+ *            Smaller graphs get more workspaces and so more parallel CTAs
+ *            (about 14 at n = 100,000; one at n = 646,000).
+ * Sharing  : all calls in the process share the one array, which keeps what the
+ *            last call left.  Each call zeroes the parts it uses, so calls
+ *            ordered on one stream are safe, but calls that overlap on the GPU
+ *            (different streams or threads) race and give wrong results.
  * Set-up   : the first call on a device (with that device current) looks up the
- *            array's device address once; make that first call before any
- *            stream capture begins.
+ *            array's device address once with cudaGetSymbolAddress; make that
+ *            first call before any stream capture begins.
  * Errors   : GC_EINVAL (NULL or bad sizes), GC_ERANGE (n too large), GC_ECUDA. */
 int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                              const int32_t *S, int32_t s_len, const int32_t *cand, int32_t n_cand,
                              int64_t *out_gain, void *stream);
+
+/* gc_gain_upper_bounds -- for every vertex v, an upper bound on Delta(v | S)
+ * that needs no search from v (the paper gives no bound before a candidate's
+ * first exact evaluation; this is the library's own, used to start the lazy
+ * rounds of gc_greedy at round 1 and to tighten the bounds later):
+ *   Delta(v | S) <= d_S[v] + sum_{w in N(v)} ((d_S[w] - 1)^+ + c3[w])
+ *                   + sum_u (d_S[u] - 3)^+,
+ * with d_S = d(., S) and c3[w] = #{u in N(w) : d_S[u] >= 3}.  A vertex at
+ * distance 1 from v gains at most d_S - 1, one at distance 2 at most
+ * [d_S >= 3] + (d_S - 3)^+ (and it is a neighbour of some w in N(v)), any other
+ * at most (d_S - 3)^+.
+ * S        : host int32[s_len] vertex ids, s_len >= 1.
+ * out_ub   : host int64[n]; -1 for members of S.
+ * Errors   : GC_EINVAL, GC_EDISCONNECTED. */
+int gc_gain_upper_bounds(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_ub);
 
 /* gc_greedy -- Greedy++ (Algorithm 2 with pruned SSSPs, Sec. 4.1, and the lazy
  * supermodular bounds, Sec. 4.2): s0 = argmin_v f({v}) (top-1 closeness,

@@ -63,7 +63,7 @@ static void release(gc_graph *g) {
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
                  g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
-                 g->g3};
+                 g->g3, g->c3s};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -75,6 +75,7 @@ static void release(gc_graph *g) {
 }
 
 static int64_t timeout_ns(const gc_opts *o) {
+  if (o && o->timeout_us > 0) return (int64_t)o->timeout_us * 1000LL;
   const int64_t ms = (o && o->timeout_ms > 0) ? o->timeout_ms : 10000;
   return ms * 1000000LL;
 }
@@ -105,9 +106,11 @@ static int read_ctl(gc_graph *g) {
 static int device_errors(gc_graph *g) {
   const int e = g->h_gctl->err ? g->h_gctl->err : g->h_bctl->err ? g->h_bctl->err : g->h_sctl->err;
   if (!e) return GC_OK;
-  // a kernel that gave up may have left lane words behind: clear the scratch
+  // a kernel that gave up may have left lane words and selection histograms
+  // behind: clear every scratch that must be zero at rest
   cudaMemsetAsync(g->ws, 0, (size_t)g->ws_count * g->ws_stride, g->stream);
   cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream);
+  if (g->gsel) cudaMemsetAsync(g->gsel, 0, sizeof(GridSelScratch), g->stream);
   cudaStreamSynchronize(g->stream);
   std::string what = e == GC_ETIMEOUT ? "device-side wait timed out"
                      : e == GC_EDISCONNECTED ? "graph is disconnected"
@@ -252,6 +255,7 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->c3, N)) || (rc = dalloc(&g->lev_cnt, N)) || (rc = dalloc(&g->heavy, N)) ||
       (rc = dalloc(&g->n_heavy, 1)) || (rc = dalloc(&g->lev_C, N + 1)) || (rc = dalloc(&g->lev_M, N + 1)) ||
       (rc = dalloc(&g->lev_max, 1)) || (rc = dalloc(&g->gsel, 1)) || (rc = dalloc(&g->g3, 1)) ||
+      (rc = dalloc(&g->c3s, N)) ||
       (rc = dalloc(&g->wsel, (size_t)g->wcap)) || (rc = dalloc(&g->wpos, (size_t)g->wcap)) ||
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
@@ -375,6 +379,28 @@ int gc_marginal_gains_device(gc_graph *g, const int32_t *S_dev, int32_t s_len, c
   if (!g || !S_dev || s_len < 1 || n_cand < 0 || (n_cand > 0 && (!cand_dev || !out_gain_dev)))
     return fail(GC_EINVAL, "bad argument to gc_marginal_gains_device");
   return gains_core(g, S_dev, s_len, cand_dev, n_cand, (long long *)out_gain_dev, false);
+}
+
+int gc_gain_upper_bounds(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_ub) {
+  if (!g || !S || !out_ub || s_len < 1 || s_len > g->n) return fail(GC_EINVAL, "bad argument to gc_gain_upper_bounds");
+  GC_TRY(check_ids(g, S, s_len, "S"));
+  g->mx = nullptr;
+  // S goes to io_b: the pruned-adjacency build uses io_a as scratch
+  GC_CUDA(cudaMemcpyAsync(g->io_b, S, (size_t)s_len * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  // pruned rows from the distances of S[0] alone: every group containing S[0]
+  // has d_S <= d(S[0], .), so the rows keep every neighbour it can still use
+  GC_TRY(distances_from(g, g->io_b, 1, timeout_ns(nullptr), nullptr));
+  GC_TRY(launch_prune_csr(g));
+  if (s_len == 1) {
+    GC_TRY(launch_round1_bound(g));
+  } else {
+    GC_TRY(distances_from(g, g->io_b, s_len, timeout_ns(nullptr), nullptr));
+    GC_TRY(launch_init_ub(g));
+    GC_TRY(launch_bound_refresh(g));
+  }
+  GC_CUDA(cudaMemcpyAsync(out_ub, g->ub, (size_t)g->n * sizeof(long long), cudaMemcpyDeviceToHost, g->stream));
+  GC_TRY(sync(g));
+  return GC_OK;
 }
 
 int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
@@ -542,6 +568,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       int32_t target = opts.active_target > 0 ? opts.active_target
                                               : (step_form == 2 ? std::max<int32_t>(4096, 2 * g->wcap) : 2048);
       for (;;) {
+        // two-hop bounds for the current group, before every (re)launch: the
+        // candidates round 1 skipped would otherwise keep their round-1 bounds
+        if (round1_bound) GC_TRY(launch_bound_refresh(g));
         GC_TRY(launch_select(g, kSelActive, 0, target, kTauHistogramTheta, 0));
         cudaEvent_t le0 = nullptr, le1 = nullptr;
         GC_TRY(gain_event(g, ev_used, &le0));

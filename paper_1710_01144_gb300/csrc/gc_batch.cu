@@ -1045,7 +1045,8 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.tstart = b->tstart;
   a.ctl = b->ctl;
   a.gctl = b->gctl;
-  a.tns = (unsigned long long)((opts.timeout_ms > 0 ? opts.timeout_ms : 10000) * 1000000LL);
+  a.tns = opts.timeout_us > 0 ? (unsigned long long)opts.timeout_us * 1000ull
+                              : (unsigned long long)((opts.timeout_ms > 0 ? opts.timeout_ms : 10000) * 1000000LL);
   auto enqueue = [&](cudaStream_t st) -> cudaError_t {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(b->kk, b->h_k_pinned, (size_t)b->count * sizeof(int32_t), cudaMemcpyHostToDevice, st)))

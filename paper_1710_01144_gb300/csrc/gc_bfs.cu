@@ -521,6 +521,95 @@ __global__ void __launch_bounds__(1024) k_round1_bound_heavy(const int32_t *__re
   }
 }
 
+// Bound refresh for later rounds.  The inequality of k_round1_bound holds for
+// any group S with d_S, c3 and G3 taken for that S, and it tightens as S grows.
+// k_count3 recounts, for the current d_S, the neighbours with d_S >= 3 of every
+// vertex (they are all in the pruned rows: d_S only decreases); k_bound_refresh
+// lowers every candidate's bound to the recomputed value.  A candidate already
+// evaluated in the current round keeps its exact gain (the bound is above it).
+__global__ void __launch_bounds__(kRedThreads) k_count3(const int32_t *__restrict__ rpf,
+                                                        const int32_t *__restrict__ cif,
+                                                        const int32_t *__restrict__ rp, int32_t n,
+                                                        const int32_t *__restrict__ dS, int32_t *c3s) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = gwarp; u < n; u += nwarps) {
+    if (rp[u + 1] - rp[u] > kHeavyRow) continue;  // k_count3_heavy
+    int a = 0;
+    for (int e = rpf[u] + lane; e < rpf[u + 1]; e += 32) a += dS[cif[e]] >= 3;
+    a = warp_sum(a);
+    if (lane == 0) c3s[u] = a;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_count3_heavy(const int32_t *__restrict__ rpf,
+                                                      const int32_t *__restrict__ cif,
+                                                      const int32_t *__restrict__ dS, int32_t *c3s,
+                                                      const int32_t *__restrict__ heavy,
+                                                      const int32_t *__restrict__ nh) {
+  __shared__ long long s_red[32];
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int u = heavy[i];
+    long long a = 0;
+    for (int e = rpf[u] + threadIdx.x; e < rpf[u + 1]; e += 1024) a += dS[cif[e]] >= 3;
+    a = block_sum(a, s_red);
+    if (threadIdx.x == 0) c3s[u] = (int32_t)a;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_bound_refresh(const int32_t *__restrict__ rpf,
+                                                               const int32_t *__restrict__ cif,
+                                                               const int32_t *__restrict__ rp, int32_t n,
+                                                               const int32_t *__restrict__ dS,
+                                                               const int32_t *__restrict__ c3s,
+                                                               const unsigned long long *__restrict__ g3,
+                                                               long long *ub) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const long long G3 = (long long)*g3;
+  for (int v = gwarp; v < n; v += nwarps) {
+    if (rp[v + 1] - rp[v] > kHeavyRow) continue;  // k_bound_refresh_heavy
+    if (ub[v] < 0) continue;                       // a member (warp-uniform: one v per warp)
+    long long s = 0;
+    for (int e = rpf[v] + lane; e < rpf[v + 1]; e += 32) {
+      const int w = cif[e];
+      s += (long long)max(dS[w] - 1, 0) + (long long)c3s[w];
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      const long long b = (long long)dS[v] + s + G3;
+      if (b < ub[v]) ub[v] = b;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_bound_refresh_heavy(const int32_t *__restrict__ rpf,
+                                                             const int32_t *__restrict__ cif,
+                                                             const int32_t *__restrict__ dS,
+                                                             const int32_t *__restrict__ c3s,
+                                                             const unsigned long long *__restrict__ g3,
+                                                             long long *ub, const int32_t *__restrict__ heavy,
+                                                             const int32_t *__restrict__ nh) {
+  __shared__ long long s_red[32];
+  const long long G3 = (long long)*g3;
+  for (int i = blockIdx.x; i < *nh; i += gridDim.x) {
+    const int v = heavy[i];
+    if (ub[v] < 0) continue;  // block-uniform
+    long long s = 0;
+    for (int e = rpf[v] + threadIdx.x; e < rpf[v + 1]; e += 1024) {
+      const int w = cif[e];
+      s += (long long)max(dS[w] - 1, 0) + (long long)c3s[w];
+    }
+    s = block_sum(s, s_red);
+    if (threadIdx.x == 0) {
+      const long long b = (long long)dS[v] + s + G3;
+      if (b < ub[v]) ub[v] = b;
+    }
+  }
+}
+
 // CSR validation, part 1: row_ptr monotone within [0, nnz].
 __global__ void k_validate_rowptr(const int32_t *__restrict__ rp, int32_t n, int64_t nnz,
                                   SelCtl *ctl) {
@@ -659,6 +748,35 @@ int launch_round1_bound(gc_graph *g) {
       g->rpf, g->cif, g->rp, n, g->dS, g->c3, g->g3, g->ub, g->stamp);
   k_round1_bound_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rpf, g->cif, g->dS, g->c3, g->g3, g->ub,
                                                                g->stamp, g->heavy, g->n_heavy);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+// ub[v] = -1 for members (d_S[v] = 0), +infinity for every other vertex: the
+// starting point of k_bound_refresh when no earlier bound exists.
+__global__ void k_init_ub(const int32_t *__restrict__ dS, int32_t n, long long *ub) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    ub[v] = dS[v] == 0 ? -1ll : LLONG_MAX;
+}
+
+int launch_init_ub(gc_graph *g) {
+  ++g->launches;
+  k_init_ub<<<grid_for(g->n, 256, g->num_sms * 8), 256, 0, g->stream>>>(g->dS, g->n, g->ub);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_bound_refresh(gc_graph *g) {
+  const int n = g->n;
+  const int grid = grid_for((int64_t)n * 32, kRedThreads, g->num_sms * 8);
+  g->launches += 5;
+  GC_CUDA(cudaMemsetAsync(g->g3, 0, sizeof(unsigned long long), g->stream));
+  k_excess3<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->dS, n, g->g3);
+  k_count3<<<grid, kRedThreads, 0, g->stream>>>(g->rpf, g->cif, g->rp, n, g->dS, g->c3s);
+  k_count3_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rpf, g->cif, g->dS, g->c3s, g->heavy, g->n_heavy);
+  k_bound_refresh<<<grid, kRedThreads, 0, g->stream>>>(g->rpf, g->cif, g->rp, n, g->dS, g->c3s, g->g3, g->ub);
+  k_bound_refresh_heavy<<<g->num_sms * 2, 1024, 0, g->stream>>>(g->rpf, g->cif, g->dS, g->c3s, g->g3, g->ub,
+                                                                g->heavy, g->n_heavy);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

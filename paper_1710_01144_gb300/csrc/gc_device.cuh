@@ -42,7 +42,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
       asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
       if ((cur ^ old) & 0x80000000u) break;
       ++it;
-      if ((it & 127u) == 0 && (global_ns() - t0 > timeout_ns || it > (1u << 30))) {
+      if ((it & 3u) == 0 && (global_ns() - t0 > timeout_ns || it > (1u << 30))) {
         atomicExch(err, GC_ETIMEOUT);
         ok = 0;
         break;

@@ -239,6 +239,7 @@ struct gc_graph {
   unsigned long long *lev_C = nullptr, *lev_M = nullptr;  // prefix counts / level sums [n + 1]
   int32_t *lev_max = nullptr;
   unsigned long long *g3 = nullptr;  // round-1 bounds: sum over u of (d_S[u] - 3)^+
+  int32_t *c3s = nullptr;            // bound refresh: neighbours with the current d_S >= 3 [n]
   gc::GridSelScratch *gsel = nullptr;  // grid-wide lazy selection scratch (histograms zero at rest)
   int32_t *wsel = nullptr;     // wide lazy steps: candidates, list positions, gains [wcap]
   int32_t *wpos = nullptr;
@@ -352,6 +353,11 @@ int launch_heavy_rows(gc_graph *g);
 // pruned adjacency (g->rpf, g->cif, g->c3) from the d_S now in g->dS
 int launch_prune_csr(gc_graph *g);
 int launch_round1_bound(gc_graph *g);
+// the same bound for the group whose distances are in d_S, over the pruned rows
+// of an earlier d_S (any group contained in the current one); lowers ub[v]
+int launch_bound_refresh(gc_graph *g);
+// ub[v] = -1 where d_S[v] = 0, else +infinity
+int launch_init_ub(gc_graph *g);
 // round 0: key[v] = -max(LB(v), LB_p(v)) with p the source of the BFS now in d_S
 int launch_pivot_bound(gc_graph *g);
 // round 0: an exactly evaluated pivot (sctl->arg_id, farness sctl->sum) becomes

@@ -1,20 +1,27 @@
 // gc_marginal_gains_static: marginal gains without any device allocation.
 //
-// Who needs this: callers that cannot call cudaMalloc -- code running while
-// a CUDA stream is being captured into a graph by someone else, plugins
-// that must live inside a host application's fixed device-memory budget or
-// custom allocator, and latency-critical services that forbid allocator calls
-// (and the implicit synchronisation cudaMalloc/cudaFree can cause) on their
-// request path.  gc_load_csr allocates a handle's arrays, so such callers cannot
-// use gc_marginal_gains; this entry point takes plain device pointers instead
-// and keeps all of its scratch in one fixed array compiled into the library.
+// Who needs this: callers that cannot call cudaMalloc -- plugins that must
+// live inside a host application's fixed device-memory budget or its own
+// allocator (a raw cudaMalloc would bypass both), and latency-critical
+// services that forbid allocator calls on their request path (cudaMalloc and
+// cudaFree can synchronise the device and take unbounded time).  gc_load_csr
+// allocates a handle's arrays, so such callers cannot use gc_marginal_gains;
+// this entry point takes plain device pointers instead and keeps all of its
+// scratch in one fixed array compiled into the library.
 //
 // The scratch is a file-scope __device__ array of kStaticScratchBytes (64 MiB).
 // Every GPU that loads the library reserves it until the process exits.  It
-// holds d(., S), two BFS queues and two range-start lists, the kernels'
-// control words and as many per-CTA gain workspaces (44 bytes per vertex
-// each) as fit; a graph needs at least one workspace, which caps n at about
-// 980,000 vertices (68 bytes per vertex in all).
+// holds the control words, then 20 bytes per vertex (d(., S), two BFS queues
+// and two range-start lists), then as many per-CTA gain workspaces (44 bytes
+// per vertex each) as fit.  A graph needs at least one workspace, so n is at
+// most kStaticMaxVertices = 1,048,496 (64 bytes per vertex plus 256-byte
+// alignment of each part).  Fewer vertices leave room for more workspaces and
+// so more CTAs: about 14 at n = 100,000, one at n = 646,000.
+//
+// Errors found on the device cannot reach the host without a synchronisation,
+// which this entry point avoids.  Instead, when the BFS from S fails (an id of
+// S outside [0, n), a device-side wait that timed out, or a vertex that S does
+// not reach), a last kernel overwrites every output with -1.
 //
 // Host code cannot use the array's name as a device address; on the first
 // call on each device (with that device current) the library looks the
@@ -32,6 +39,7 @@ int gain_kernel_occupancy(int *blocks_per_sm);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 constexpr size_t kStaticScratchBytes = 64ull << 20;
+constexpr int32_t kStaticMaxVertices = 1048496;  // largest n whose layout fits (see above)
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -45,6 +53,15 @@ int g_static_bfs_occ[kMaxDevices];
 
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
+
+// Outputs become -1 when the BFS that computed d(., S) did not finish cleanly:
+// an error code (bad id of S, wait timeout) or fewer than n vertices labelled
+// (S does not reach every vertex, so d(., S) is undefined somewhere).
+__global__ void k_static_poison(const BfsCtl *__restrict__ ctl, int32_t n, long long *out, int32_t n_cand) {
+  const bool bad = ctl->err != 0 || ctl->relabelled != (unsigned long long)n;
+  if (!bad) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += gridDim.x * blockDim.x) out[i] = -1;
+}
 
 // Set-up once per device: the array's device address and the launch geometry.
 static int static_setup(int dev) {
@@ -97,7 +114,7 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   const size_t a4 = round_up((size_t)n * sizeof(int32_t));
   const size_t head = round_up(sizeof(BfsCtl)) + round_up(sizeof(GainCtl)) + 4 * a4 +
                       round_up(((size_t)n + 1) * sizeof(int32_t));
-  if (head + stride > kStaticScratchBytes) {
+  if (n > kStaticMaxVertices || head + stride > kStaticScratchBytes) {
     set_error("gc_marginal_gains_static: n = " + std::to_string(n) + " needs " +
               std::to_string(head + stride) + " bytes of scratch, the static array holds " +
               std::to_string(kStaticScratchBytes));
@@ -145,5 +162,14 @@ extern "C" int gc_marginal_gains_static(int32_t n, const int32_t *row_ptr, const
   }
   if ((rc = launch_fill_i32(&g, g.dS, kInf, n)) != GC_OK) return rc;
   if ((rc = launch_bfs_relabel(&g, g.dS, S, s_len, 10000000000LL)) != GC_OK) return rc;
-  return launch_gains(&g, kModeGain, cand, n_cand, nullptr, (long long *)out_gain, 0);
+  if ((rc = launch_gains(&g, kModeGain, cand, n_cand, nullptr, (long long *)out_gain, 0)) != GC_OK) return rc;
+  if (n_cand > 0) {
+    const int blocks = (n_cand + 255) / 256 < 4 * g.num_sms ? (n_cand + 255) / 256 : 4 * g.num_sms;
+    k_static_poison<<<blocks, 256, 0, g.stream>>>(g.bctl, n, (long long *)out_gain, n_cand);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("launch of the output check failed");
+      return GC_ECUDA;
+    }
+  }
+  return GC_OK;
 }

@@ -38,7 +38,7 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_last_error", "gc_marginal_gains_static", "gc_mlp_create", "gc_mlp_free", "gc_mlp_set_params",
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
-           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy")
+           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("step_form", ctypes.c_int32),
                 ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32),
-                ("batch_grid_min_n", ctypes.c_int32)]
+                ("batch_grid_min_n", ctypes.c_int32), ("timeout_us", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         lib.gc_marginal_gains.argtypes = [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Stats)]
         lib.gc_marginal_gains_device.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.gc_greedy.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_gain_upper_bounds.argtypes = [vp, vp, i32, vp]
         lib.gc_marginal_gains_static.argtypes = [i32, vp, vp, vp, i32, vp, i32, vp, vp]
         lib.gc_mlp_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
         lib.gc_mlp_free.argtypes = [vp]
@@ -210,6 +211,13 @@ class Graph:
         _check(load().gc_marginal_gains_device(self._h, S_dev.data_ptr(), S_dev.numel(), cand_dev.data_ptr(),
                                                cand_dev.numel(), out_dev.data_ptr()))
 
+    def upper_bounds(self, S):
+        """Two-hop upper bounds on Delta(v|S) for every vertex (-1 for members)."""
+        s = _i32(S)
+        out = np.zeros(self.n, dtype=np.int64)
+        _check(load().gc_gain_upper_bounds(self._h, s.ctypes.data, int(np.size(S)), out.ctypes.data))
+        return out
+
     def set_proposal(self, mlp, fill: int = 0):
         """Use `mlp` (an Mlp, or None to disable) for part of every batch."""
         self._prop = mlp
@@ -232,7 +240,7 @@ class Graph:
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
                step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0,
-               pruned_adjacency: bool = True, round1_bound: bool = True):
+               pruned_adjacency: bool = True, round1_bound: bool = True, timeout_us: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
@@ -244,6 +252,7 @@ class Graph:
         o.lazy_ctas = lazy_ctas
         if timeout_ms:
             o.timeout_ms = timeout_ms
+        o.timeout_us = timeout_us
         grp = np.zeros(max(int(k), 1), dtype=np.int32)
         f = ctypes.c_int64()
         st = Stats()

@@ -34,10 +34,12 @@ def test_binding_lists_header_symbols():
 
 
 def test_struct_layouts_match_header():
-    # gc_opts: 12 x 4 bytes; gc_stats: 11 int64 + 7 double + 3 int64
-    assert ctypes.sizeof(gc.Opts) == 52
-    assert ctypes.sizeof(gc.Stats) == 8 * 37
     text = open(os.path.join(ROOT, "include", "gc.h")).read()
+    opts = re.sub(r"/\*.*?\*/", "", text[text.index("typedef struct gc_opts"):text.index("} gc_opts;")], flags=re.S)
+    ofields = re.findall(r"(int32_t|uint32_t)\s+(\w+);", opts)
+    assert [f for _, f in ofields] == [f for f, _ in gc.Opts._fields_]
+    assert ctypes.sizeof(gc.Opts) == 4 * len(ofields)
+    assert ctypes.sizeof(gc.Stats) == 8 * 37
     stats = text[text.index("typedef struct gc_stats"):text.index("} gc_stats;")]
     fields = re.findall(r"(int64_t|double)\s+(\w+);", stats)
     assert [f for _, f in fields] == [f for f, _ in gc.Stats._fields_]

@@ -262,3 +262,41 @@ def test_device_pointers_and_adopt(gcm):
             G.gains_device(torch.from_numpy(S).cuda(), torch.from_numpy(cand).cuda(), out)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("name,g", small_cases())
+def test_upper_bounds_match_restatement(gcm, name, g):
+    """gc_gain_upper_bounds element by element against the numpy restatement of
+    the two-hop bound (tests/test_round1_bound.py), for groups of 1 to 5
+    vertices: one vertex goes through the round-1 kernel, larger groups through
+    the refresh kernels of later rounds.  The restatement itself is checked
+    against the oracle's exact gains on CPU."""
+    from tests.test_round1_bound import bound
+
+    rp, ci = g
+    n = rp.size - 1
+    rng = np.random.default_rng(17)
+    with gcm.Graph(rp, ci) as G:
+        for size in (1, 2, 3, 5):
+            if size >= n:
+                continue
+            S = rng.choice(n, size=size, replace=False).astype(np.int32)
+            d = oracle.bfs(rp, ci, S).astype(np.int64)
+            np.testing.assert_array_equal(G.upper_bounds(S), bound(rp, ci, d))
+
+
+def test_wait_expiry_returns_timeout_and_handle_stays_usable(gcm):
+    """Every device-side wait has a time limit.  With a limit of 1 us the grid
+    barriers of a deep graph's BFS levels cannot all be met: the call returns
+    GC_ETIMEOUT (no fault, no hang), and the next call on the same handle with
+    the default limit returns the oracle's group."""
+    rp, ci = sg.path(6000)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, 3)
+    with gcm.Graph(rp, ci) as G:
+        for _ in range(2):
+            with pytest.raises(gcm.GcError) as e:
+                G.greedy(3, timeout_us=1)
+            assert e.value.code == gcm.GC_ETIMEOUT
+            got, f, _ = G.greedy(3)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]

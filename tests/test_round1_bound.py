@@ -60,3 +60,23 @@ def test_round1_bound_prunes_rmat():
     top = np.argsort(-ub)[:64]
     gstar = int(np.asarray(oracle.gains(rp, ci, [s0], top)).max())
     assert (ub >= gstar).sum() < 64
+
+
+@pytest.mark.parametrize("name,g", cases())
+def test_two_hop_bound_holds_for_larger_groups(name, g):
+    """The same inequality with d, c3 and the (d - 3)^+ sum taken for a group
+    of 2 to 5 vertices (the refresh of later rounds)."""
+    rp, ci = g
+    n = rp.size - 1
+    rng = np.random.default_rng(11)
+    for size in (2, 3, 5):
+        if size >= n:
+            continue
+        S = rng.choice(n, size=size, replace=False)
+        d = oracle.bfs(rp, ci, S).astype(np.int64)
+        ub = bound(rp, ci, d)
+        gain = np.asarray(oracle.gains(rp, ci, S, np.arange(n)), dtype=np.int64)
+        off = d > 0
+        assert (gain[off] <= ub[off]).all()
+        assert (ub[~off] == -1).all()
+        np.testing.assert_array_equal(bound(rp, ci, d, only_pruned_rows=True), ub)
