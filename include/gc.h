@@ -117,6 +117,11 @@ typedef struct gc_opts {
                               vertices run their lazy rounds grid-wide, one
                               graph at a time; the others CTA-locally;
                               0 = 65536, negative = none */
+  int32_t round0_lanes;    /* gc_greedy round 0 on shallow graphs (the BFS from
+                              the lowest-bound vertex has at most 32 levels):
+                              candidates per wide bottom-up batch, 64, 128, 256
+                              or 512; 0 = automatic; negative = the 64-lane
+                              batches used for deep graphs */
   int32_t timeout_us;      /* if > 0: the limit of every device-side wait in
                               microseconds, overriding timeout_ms (a limit
                               that short makes the waits give up with
@@ -168,6 +173,10 @@ typedef struct gc_stats {
   int64_t lazy_upd_edges;    /* d_S updates: adjacency entries scanned */
   int64_t lazy_upd_relabels; /* d_S updates: labels lowered */
   int64_t lazy_sel_scanned;  /* selection: active-list entries read */
+  /* gc_greedy round 0: the wide bottom-up kernel (shallow graphs) */
+  double ms_round0_wide;     /* its duration (CUDA events on the launch stream) */
+  int64_t r0_batches;        /* its batches */
+  int64_t r0_levels;         /* bottom-up levels summed over batches */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

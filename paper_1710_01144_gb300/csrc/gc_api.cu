@@ -31,6 +31,7 @@ static int fail(int code, const std::string &msg) {
 
 constexpr int32_t kRound0GridMax = 256;  // round-0 survivors handled by grid-wide batches
 constexpr int kRound0Pivots = 8;         // round 0: at most this many pivot bounds
+constexpr int32_t kShallowLevels = 32;   // round 0: wide bottom-up batches up to this BFS depth
 
 #define GC_TRY(expr)              \
   do {                            \
@@ -63,7 +64,7 @@ static void release(gc_graph *g) {
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
                  g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
-                 g->g3, g->c3s};
+                 g->g3, g->c3s, g->r0_vis};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -111,6 +112,12 @@ static int device_errors(gc_graph *g) {
   cudaMemsetAsync(g->ws, 0, (size_t)g->ws_count * g->ws_stride, g->stream);
   cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream);
   if (g->gsel) cudaMemsetAsync(g->gsel, 0, sizeof(GridSelScratch), g->stream);
+  if (g->r0_vis) {  // the wide round-0 kernel's words: reallocated (zeroed) on next use
+    cudaStreamSynchronize(g->stream);
+    cudaFree(g->r0_vis);
+    g->r0_vis = nullptr;
+    g->r0_w = 0;
+  }
   cudaStreamSynchronize(g->stream);
   std::string what = e == GC_ETIMEOUT ? "device-side wait timed out"
                      : e == GC_EDISCONNECTED ? "graph is disconnected"
@@ -415,6 +422,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   size_t ev_used = 0;
+  int64_t r0_stats[2] = {0, 0};  // wide round-0 kernel: batches, bottom-up levels
   bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
@@ -461,12 +469,22 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   GC_TRY(launch_select(g, kSelKey, 0, 0, kTauDevice, 0));
   GC_TRY(read_ctl(g));
   int32_t n_surv = g->h_sctl->n_sel;
+  // Shallow graphs (the BFS just run has few levels, as in social networks):
+  // the survivors go to the wide bottom-up kernel, whose batches of up to 512
+  // candidates read the graph once per level for all of them.  Pivot bounds
+  // (triangle inequality) are weak there and are skipped.
+  const int32_t ecc_a = g->h_bctl->levels;
+  int r0_w = 0;
+  if (opts.round0_lanes >= 0 && ecc_a <= kShallowLevels && n_surv > 0) {
+    const int want = opts.round0_lanes > 0 ? opts.round0_lanes : (n_surv > 256 ? 512 : n_surv > 128 ? 256 : n_surv > 64 ? 128 : 64);
+    r0_w = want >= 512 ? 8 : want >= 256 ? 4 : want >= 128 ? 2 : 1;
+  }
   // Many survivors (deep graphs, where the degree bound is weak): tighten the
   // bounds with the BFS levels of pivots (triangle inequality, see
   // k_pivot_bound).  The first pivot is the vertex just searched; each further
   // pivot is the undecided vertex of smallest bound, searched exactly, so it
   // may also lower the threshold.
-  for (int piv = 0; n_surv > kRound0GridMax && piv < kRound0Pivots; ++piv) {
+  for (int piv = 0; r0_w == 0 && n_surv > kRound0GridMax && piv < kRound0Pivots; ++piv) {
     if (piv > 0) {
       GC_TRY(launch_argmin_lb(g));
       GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
@@ -478,7 +496,24 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(read_ctl(g));
     n_surv = g->h_sctl->n_sel;
   }
-  if (n_surv <= kRound0GridMax) {
+  int64_t r0_wide_lanes = 0;
+  if (r0_w > 0) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GC_TRY(gain_event(g, ev_used, &e0));
+    GC_TRY(gain_event(g, ev_used + 1, &e1));
+    ev_used += 2;
+    ev_k64.push_back(3);
+    GC_CUDA(cudaEventRecord(e0, g->stream));
+    GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w, tns));
+    GC_CUDA(cudaEventRecord(e1, g->stream));
+    R0Ctl r0c;
+    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 3 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, g->stream));
+    GC_TRY(sync(g));
+    r0_wide_lanes = (int64_t)r0c.lanes;
+    r0_stats[0] = (int64_t)r0c.batches;
+    r0_stats[1] = (int64_t)r0c.levels;
+  } else if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)
       GC_TRY(grid_timed(kModeFarness, g->list + off, std::min<int32_t>(kLanes, n_surv - off), nullptr,
@@ -492,7 +527,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   GC_TRY(device_errors(g));
   const int32_t s0 = g->h_sctl->arg_id;
   const long long f_s0 = g->h_sctl->arg_val;
-  const int64_t round0_evals = (int64_t)g->h_gctl->lanes + 1;
+  const int64_t round0_evals = (int64_t)g->h_gctl->lanes + r0_wide_lanes + 1;
   if (s0 < 0) return fail(GC_EINTERNAL, "round 0 produced no vertex");
   int64_t f = f_s0;
   if (s0 != ds_src) {  // d_S = d(s0, .) unless s0's BFS is the one already in d_S
@@ -711,6 +746,10 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         ++stats->lazy_launches;
         continue;
       }
+      if (kind == 3) {
+        stats->ms_round0_wide += ms;
+        continue;
+      }
       stats->ms_gain_kernel += ms;
       ++stats->gain_launches;
       if (kind == 1) {
@@ -730,6 +769,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lazy_upd_edges = (int64_t)g->h_lctl->upd_work[1];
     stats->lazy_upd_relabels = (int64_t)g->h_lctl->upd_relabels;
     stats->lazy_sel_scanned = (int64_t)g->h_lctl->sel_scanned;
+    stats->r0_batches = r0_stats[0];
+    stats->r0_levels = r0_stats[1];
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_dist(const int32_t *__restr
 // rows (hubs) go to a whole CTA in a companion kernel, so that no warp walks a
 // hub's row alone while the rest of the grid has finished.  The companions
 // walk the list of long rows built once per graph (k_heavy_rows).
-constexpr int kHeavyRow = 2048;
 
 // heavy[0..*nh) = the rows with more than kHeavyRow entries (any order)
 __global__ void __launch_bounds__(kRedThreads) k_heavy_rows(const int32_t *__restrict__ rp, int32_t n,

@@ -25,6 +25,8 @@ constexpr int kRedThreads = 256;      // threads per CTA of reductions / scans
 constexpr int kHistBins = 2048;       // bins of the selection histogram
 constexpr int kGridGainThreads = 512; // threads per CTA of the grid-wide gain kernel
 constexpr int kMaxGridCtas = 1024;    // cap on CTAs of cooperative launches
+constexpr int kHeavyRow = 2048;       // rows longer than this are split over CTAs / warps
+constexpr int kR0MaxLanes = 512;      // lanes of the widest round-0 batch
 
 // ----------------------------------------------------------- control words --
 // Lane words of a gain workspace: one 32-byte record per vertex w holding its
@@ -169,6 +171,23 @@ struct LazyCtl {
   unsigned long long sel_scanned;  // selection: active-list entries read
 };
 
+// Control block of the wide round-0 kernel (gc_round0.cu), zeroed before each
+// launch except best_f.
+struct R0Ctl {
+  GridBar bar;
+  int32_t phase;    // 0: survivor list, 1: deferred candidates, 2: done
+  int32_t nb;       // lanes of the current batch
+  int32_t cursor;   // next survivor-list position
+  int32_t dcursor;  // next deferred position
+  int32_t n_defer;  // deferred candidates
+  int32_t pad;
+  long long best_f;  // best exact farness (written by CTA 0 between batches)
+  int32_t cand[kR0MaxLanes];  // the batch: candidate ids and their list positions
+  int32_t pos[kR0MaxLanes];
+  unsigned long long tot[3][kR0MaxLanes];  // claims per lane at distance d, in tot[d mod 3]
+  unsigned long long batches, levels, lanes;  // work counters
+};
+
 // Selection / reduction control block (lives across a whole greedy call).
 struct SelCtl {
   // threshold search (keys are compared as int64; differences in uint64)
@@ -274,6 +293,16 @@ struct gc_graph {
   int grid_ctas = 0;       // resident CTAs of the grid-wide gain kernel
   int lazy_ctas = 0;       // resident CTAs of the persistent lazy kernel
   int red_blocks = 0;      // grid size of reductions
+  // wide round-0 kernel (one allocation, made on first use): lane words
+  // vis/buf[3] of r0_w 64-bit words per vertex, frontier bitmaps, heavy-row
+  // chunk index and accumulators, deferred candidates, control block
+  unsigned long long *r0_vis = nullptr, *r0_buf[3] = {nullptr, nullptr, nullptr}, *r0_hacc = nullptr;
+  uint32_t *r0_fb[3] = {nullptr, nullptr, nullptr};
+  int32_t *r0_hcp = nullptr, *r0_defer = nullptr;
+  gc::R0Ctl *r0_ctl = nullptr;
+  int r0_w = 0;
+  int32_t r0_nh = 0;
+  size_t r0_bytes = 0;
   int32_t *dec = nullptr;                  // scratch word
   int64_t launches = 0;                    // kernels launched through this handle
   gc::LaneGraphs lane_graphs;              // set for block-diagonal graph batches
@@ -371,6 +400,11 @@ int launch_active_theta(gc_graph *g);
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
                        bool wide, long long local_max, int ctas, bool pruned);
 int lazy_occupancy(int *blocks_per_sm);
+// round 0 on shallow graphs: f({v}) or -1 (cut / bound above the best) into
+// lgain[i] for list[0..m), B = 64 W lanes per batch (W in {1, 2, 4, 8}); a batch
+// whose live lanes drop below defer_below after distance 2 defers them
+int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
+                       int64_t timeout_ns);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 }  // namespace gc

@@ -1,0 +1,703 @@
+// Round 0 on shallow graphs: f({v}) for many round-0 survivors at once, with
+// the BFScut of Sec. 3.1 (Algorithm 3 with k = 1), by a bit-parallel
+// multi-source BFS of B = 64 W lanes per batch that runs on the whole GPU.
+//
+// Why a separate kernel.  On small-world graphs (R-MAT, social networks) the
+// round-0 degree bound leaves the vertices next to the hubs: their two-hop
+// counts are large.  Each of them reaches most of the graph at distance 2, so
+// its search scans the hub rows before its cut can fire.  Batches of 64 lanes
+// on one CTA re-read those rows once per batch (the scale-24 R-MAT graph: 867
+// batches, 210G adjacency entries, 23 s).  Here one batch holds up to 512
+// candidates and every level after the first is expanded bottom-up: each
+// vertex with lanes still missing ORs the lane words of its neighbours that are
+// in the current frontier (a 1-bit-per-vertex bitmap decides which words to
+// read) until no missing lane is left.  One pass over the adjacency then serves
+// every lane of the batch, and the pass is a coalesced stream over the CSR.
+//
+// Level 0 -> 1 (the candidates' own rows) is top-down: atomicOr of the lane
+// bit into the neighbour's visited and claim words.  Rows longer than
+// kHeavyRow entries are split into chunks of kHeavyRow that any warp can
+// take; their partial ORs meet in a per-row accumulator that a second phase
+// applies.  Rows of up to 32 entries are scanned by one thread, longer light
+// rows by a whole warp.
+//
+// Lane words: vis[w] (the lanes that reached w) and three claim buffers used in
+// rotation: the frontier of distance d is buf[d mod 3] with bitmap fb[d mod 3];
+// while distance d + 1 is claimed, the buffer of distance d - 1 is cleared.
+// Claim buffers and bitmaps are zero between batches; vis is cleared at the
+// end of every batch.
+//
+// Per-lane counts of each level come from warp ballots (one ballot per lane
+// bit over 32 vertices), summed per CTA in shared memory and per level in
+// global memory.  After each level every CTA applies the same BFScut test to
+// its own copy of the lane state, from the same global totals:
+//   lane j, all vertices within distance d counted (cnt_j of them, distance
+//   sum sum_j):  f({v_j}) >= sum_j + (d + 1) (n - cnt_j);  cut if > best.
+// best only decreases (completed lanes), so every CTA keeps the same copy.
+//
+// Survivors are taken in list order while their lower bound is at most the
+// best farness so far.  A batch whose live lanes fall below `defer_below`
+// after the distance-2 cut hands them to a deferred list and ends, so that a
+// few surviving lanes do not pay full passes over the graph alone; the
+// deferred candidates run afterwards in full batches of their own.
+#include <limits.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "gc_device.cuh"
+#include "gc_internal.cuh"
+
+namespace gc {
+
+typedef unsigned long long u64;
+
+constexpr int kR0Threads = 512;
+
+// Lane words and bitmaps change from level to level and are written by other
+// SMs, so they are read at L2 (ld.global.cg): a line left in this SM's L1
+// from an earlier level could be stale, and a stale visited word written back
+// would drop lanes that other CTAs set.
+template <int W>
+__device__ __forceinline__ void ld_words(const u64 *p, u64 (&x)[W]) {
+  if (W == 1) {
+    x[0] = __ldcg(p);
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+      const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p + k));
+      x[k] = v.x;
+      x[k + (W > 1 ? 1 : 0)] = v.y;
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void st_words(u64 *p, const u64 (&x)[W]) {
+  if (W == 1) {
+    *p = x[0];
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+      ulonglong2 v;
+      v.x = x[k];
+      v.y = x[k + (W > 1 ? 1 : 0)];
+      *reinterpret_cast<ulonglong2 *>(p + k) = v;
+    }
+  }
+}
+
+__device__ __forceinline__ u64 warp_or64(u64 x) {
+  const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
+  const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
+  return ((u64)hi << 32) | lo;
+}
+
+__device__ __forceinline__ long long r0_block_min(long long v, long long *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = LLONG_MAX;
+  for (int w = 0; w < nw; ++w) v = min(v, sh[w]);
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ bool in_frontier(const uint32_t *fb, int u) { return (__ldcg(fb + (u >> 5)) >> (u & 31)) & 1u; }
+
+// Zero the claim words of every vertex marked in bitmap fb, and the bitmap.
+template <int W>
+__device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw) {
+  const int T = blockDim.x;
+  for (int x = blockIdx.x * T + threadIdx.x; x < nbw; x += gridDim.x * T) {
+    uint32_t bits = __ldcg(fb + x);
+    if (!bits) continue;
+    fb[x] = 0;
+    const u64 z[W] = {};
+    do {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      st_words<W>(buf + (size_t)(32 * x + b) * W, z);
+    } while (bits);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kR0Threads, 1)
+    k_round0_wide(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
+                  const int32_t *__restrict__ list, int32_t m, const long long *__restrict__ key, long long *lgain,
+                  int32_t *defer, R0Ctl *ctl, GainCtl *gctl, u64 *vis, u64 *buf_a, u64 *buf_b, u64 *buf_c,
+                  uint32_t *fb_a, uint32_t *fb_b, uint32_t *fb_c, const int32_t *__restrict__ heavy, int32_t nh,
+                  const int32_t *__restrict__ hcp, u64 *hacc, int32_t defer_below, unsigned long long tns) {
+  constexpr int B = 64 * W;
+  constexpr int T = kR0Threads;
+  __shared__ int s_cand[B], s_pos[B];
+  __shared__ long long s_sum[B], s_cnt[B], s_fin[B];
+  __shared__ unsigned int s_lc[B];
+  __shared__ int s_eoff[B + 1];
+  __shared__ u64 s_alive[W];
+  __shared__ int s_scan[33];
+  __shared__ long long s_red[32];
+  const int tid = threadIdx.x, lane = tid & 31, G = gridDim.x, b = blockIdx.x;
+  const int gw = b * (T / 32) + (tid >> 5), nwarps = G * (T / 32);
+  const int nbw = (n + 31) >> 5;
+  int32_t *err = &gctl->err;
+  u64 *bufs[3] = {buf_a, buf_b, buf_c};
+  uint32_t *fbs[3] = {fb_a, fb_b, fb_c};
+  const int C = nh > 0 ? hcp[nh] : 0;  // heavy-row chunks
+  u64 w_batches = 0, w_levels = 0, w_lanes = 0;
+
+  for (;;) {
+    // ---------- batch selection (warp 0 of CTA 0) ----------
+    if (b == 0 && tid < 32) {
+      const long long bf = ctl->best_f;
+      int phase = ctl->phase, nb = 0;
+      while (phase < 2 && nb < B) {
+        const int end = phase == 0 ? m : ctl->n_defer;
+        int cur = phase == 0 ? ctl->cursor : ctl->dcursor;
+        while (cur < end && nb < B) {
+          const int i = cur + lane;
+          int v = -1, pos = -1;
+          bool ok = false;
+          if (i < end) {
+            if (phase == 0) {
+              v = list[i];
+              pos = i;
+            } else {
+              v = defer[2 * i];
+              pos = defer[2 * i + 1];
+            }
+            ok = -key[v] <= bf;  // lower bound at most the best farness so far
+          }
+          const unsigned okm = __ballot_sync(0xffffffffu, ok);
+          const int room = B - nb;
+          // entries consumed: all up to the room-th accepted one
+          int take_upto = 32;  // lanes [0, take_upto) are consumed
+          if (__popc(okm) > room) {
+            unsigned mm = okm;
+            for (int r = 0; r < room; ++r) mm &= mm - 1;
+            take_upto = __ffs(mm) - 1;  // the first accepted entry that does not fit
+          }
+          if (i < end && lane < take_upto) {
+            if (ok) {
+              const int slot = nb + __popc(okm & ((1u << lane) - 1u));
+              ctl->cand[slot] = v;
+              ctl->pos[slot] = pos;
+            } else {
+              lgain[pos] = -1;  // cannot beat the best farness: never searched
+            }
+          }
+          nb += __popc(okm & (take_upto == 32 ? 0xffffffffu : ((1u << take_upto) - 1u)));
+          cur += min(take_upto, end - cur);
+          __syncwarp();
+        }
+        if (lane == 0) {
+          if (phase == 0) ctl->cursor = cur;
+          else ctl->dcursor = cur;
+        }
+        if (nb < B && cur >= end) ++phase;  // this list is exhausted
+        else break;
+      }
+      if (lane == 0) {
+        ctl->phase = phase;
+        ctl->nb = nb;
+      }
+      for (int i = lane; i < 3 * B; i += 32) ctl->tot[i / B][i % B] = 0;  // rows are kR0MaxLanes apart
+    }
+    if (!grid_sync(&ctl->bar, err, tns)) break;
+    const int nb = *(volatile int32_t *)&ctl->nb;
+    if (nb == 0) break;
+    const int phase = *(volatile int32_t *)&ctl->phase;
+    long long bf = *(volatile long long *)&ctl->best_f;
+    // ---------- lane state (every CTA keeps the same copy) ----------
+    for (int j = tid; j < B; j += T) {
+      const int c = j < nb ? ((volatile int32_t *)ctl->cand)[j] : -1;
+      s_cand[j] = c;
+      s_pos[j] = j < nb ? ((volatile int32_t *)ctl->pos)[j] : -1;
+      s_sum[j] = 0;
+      s_cnt[j] = 1;  // the candidate itself
+      s_fin[j] = -1;
+      s_lc[j] = 0;
+    }
+    if (tid < W) {
+      const int lo = 64 * tid;
+      s_alive[tid] = nb >= lo + 64 ? ~0ull : (nb > lo ? ((1ull << (nb - lo)) - 1ull) : 0ull);
+    }
+    __syncthreads();
+    // ---------- distance 1: the candidates' rows, top-down ----------
+    {
+      const int j = tid;
+      const int deg = (j < nb) ? __ldg(rp + s_cand[j] + 1) - __ldg(rp + s_cand[j]) : 0;
+      int total;
+      const int ex = block_excl_scan(j < B ? deg : 0, s_scan, &total);
+      if (j < B) s_eoff[j] = ex;
+      if (j == 0) s_eoff[B] = total;
+      __syncthreads();
+      if (b == 0 && j < nb) {  // level 0: each lane reaches its candidate
+        const int c = s_cand[j];
+        atomicOr(&vis[(size_t)c * W + (j >> 6)], 1ull << (j & 63));
+      }
+      const int E = s_eoff[B];
+      u64 *nx1 = bufs[1];
+      uint32_t *fb1 = fbs[1];
+      for (int e = b * T + tid; e < E; e += G * T) {
+        int lo = 0, hi = nb - 1;  // lane holding e (largest lo with s_eoff[lo] <= e)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_eoff[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        const int c = s_cand[lo];
+        const int w = __ldg(ci + __ldg(rp + c) + (e - s_eoff[lo]));
+        const u64 bit = 1ull << (lo & 63);
+        const size_t at = (size_t)w * W + (lo >> 6);
+        const u64 old = atomicOr(&vis[at], bit);
+        if (!(old & bit)) {
+          atomicOr(&nx1[at], bit);
+          atomicOr(&fb1[w >> 5], 1u << (w & 31));
+          atomicAdd(&s_lc[lo], 1u);
+        }
+      }
+      __syncthreads();
+      for (int j2 = tid; j2 < nb; j2 += T)
+        if (s_lc[j2]) {
+          atomicAdd(&ctl->tot[1][j2], (u64)s_lc[j2]);
+          s_lc[j2] = 0;
+        }
+    }
+    bool ok = grid_sync(&ctl->bar, err, tns);
+    if (!ok) break;
+    ++w_batches;
+    w_lanes += (u64)nb;
+    int d = 1;  // the distance whose claims were just counted
+    bool any_alive = true;
+    for (;;) {
+      // ---------- fold the counts of distance d; BFScut (same in every CTA) ----------
+      const volatile u64 *tot = (const volatile u64 *)ctl->tot[d % 3];
+      long long fmin = LLONG_MAX;
+      for (int j = tid; j < nb; j += T) {
+        if (!((s_alive[j >> 6] >> (j & 63)) & 1ull)) continue;
+        const long long c = (long long)tot[j];
+        s_cnt[j] += c;
+        s_sum[j] += (long long)d * c;
+        if (c == 0 || s_cnt[j] == n) {  // search complete
+          if (s_cnt[j] == n) {
+            s_fin[j] = s_sum[j];
+            fmin = min(fmin, s_sum[j]);
+          } else {
+            s_fin[j] = -2;  // ended short of n: the graph is disconnected
+          }
+        }
+      }
+      fmin = r0_block_min(fmin, s_red);
+      bf = min(bf, fmin);
+      for (int j = tid; j < nb; j += T) {
+        if (!((s_alive[j >> 6] >> (j & 63)) & 1ull)) continue;
+        bool drop = false;
+        long long out = 0;
+        bool write = false;
+        if (s_fin[j] != -1) {
+          drop = true;
+          write = true;
+          out = s_fin[j] >= 0 ? s_fin[j] : -1;
+          if (s_fin[j] == -2 && b == 0) {
+            gctl->short_vertex = s_cand[j];
+            gctl->short_count = s_cnt[j];
+            atomicExch(&gctl->err, GC_EDISCONNECTED);
+          }
+        } else if (s_sum[j] + (long long)(d + 1) * ((long long)n - s_cnt[j]) > bf) {
+          drop = true;  // cut: cannot beat the best farness
+          write = true;
+          out = -1;
+        }
+        if (drop) atomicAnd(&s_alive[j >> 6], ~(1ull << (j & 63)));
+        if (write && b == 0) lgain[s_pos[j]] = out;
+      }
+      __syncthreads();
+      if (b == 0)  // the next level's totals (read two folds ago by every CTA)
+        for (int j = tid; j < B; j += T) ctl->tot[(d + 1) % 3][j] = 0;
+      int alive_cnt = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) alive_cnt += __popcll(s_alive[k]);
+      if (alive_cnt > 0 && phase == 0 && d >= 2 && alive_cnt < defer_below) {
+        // few live lanes: run them later in full batches of their own
+        if (b == 0) {
+          int j = 0;
+          if (tid == 0) {
+            int at = ctl->n_defer;
+            for (j = 0; j < nb; ++j)
+              if ((s_alive[j >> 6] >> (j & 63)) & 1ull) {
+                defer[2 * at] = s_cand[j];
+                defer[2 * at + 1] = s_pos[j];
+                ++at;
+              }
+            ctl->n_defer = at;
+          }
+        }
+        alive_cnt = 0;
+      }
+      __syncthreads();
+      if (alive_cnt == 0) {
+        any_alive = false;
+        break;
+      }
+      ++w_levels;
+      // ---------- claims of distance d + 1, bottom-up ----------
+      u64 al[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) al[k] = s_alive[k];
+      const u64 *cur = bufs[d % 3];
+      const uint32_t *fbc = fbs[d % 3];
+      u64 *nxt = bufs[(d + 1) % 3];
+      uint32_t *fbn = fbs[(d + 1) % 3];
+      clear_frontier<W>(bufs[(d + 2) % 3], fbs[(d + 2) % 3], nbw);  // distance d - 1
+      unsigned int lc[2 * W];
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k) lc[k] = 0;
+      for (int base = gw * 32; base < n; base += nwarps * 32) {
+        const int w = base + lane;
+        int r0 = 0, r1 = 0;
+        u64 miss[W], vw[W];
+        bool want = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) miss[k] = vw[k] = 0;
+        if (w < n) {
+          r0 = __ldg(rp + w);
+          r1 = __ldg(rp + w + 1);
+          if (r1 - r0 <= kHeavyRow) {
+            ld_words<W>(vis + (size_t)w * W, vw);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              miss[k] = al[k] & ~vw[k];
+              want |= miss[k] != 0;
+            }
+          }
+        }
+        const unsigned wm = __ballot_sync(0xffffffffu, want);
+        if (!wm) continue;
+        u64 acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        const bool own = want && (r1 - r0) <= 32;
+        if (own) {
+          for (int e = r0; e < r1; ++e) {
+            const int u = __ldg(ci + e);
+            if (in_frontier(fbc, u)) {
+              u64 f[W];
+              ld_words<W>(cur + (size_t)u * W, f);
+              bool done = true;
+#pragma unroll
+              for (int k = 0; k < W; ++k) {
+                acc[k] |= f[k];
+                done &= (acc[k] & miss[k]) == miss[k];
+              }
+              if (done) break;
+            }
+          }
+        }
+        unsigned mm = __ballot_sync(0xffffffffu, want && !own);
+        while (mm) {  // longer light rows: the whole warp on one vertex
+          const int t = __ffs(mm) - 1;
+          mm &= mm - 1;
+          const int a0 = __shfl_sync(0xffffffffu, r0, t), a1 = __shfl_sync(0xffffffffu, r1, t);
+          u64 ms[W], ac[W];
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            ms[k] = __shfl_sync(0xffffffffu, miss[k], t);
+            ac[k] = 0;
+          }
+          for (int e0 = a0; e0 < a1; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < a1) {
+              const int u = __ldg(ci + e);
+              if (in_frontier(fbc, u)) {
+                u64 f[W];
+                ld_words<W>(cur + (size_t)u * W, f);
+#pragma unroll
+                for (int k = 0; k < W; ++k) ac[k] |= f[k];
+              }
+            }
+            bool done = true;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              ac[k] = warp_or64(ac[k]);
+              done &= (ac[k] & ms[k]) == ms[k];
+            }
+            if (done) break;
+          }
+          if (lane == t) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc[k] = ac[k];
+          }
+        }
+        u64 nw[W];
+        bool has = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          nw[k] = acc[k] & miss[k];
+          has |= nw[k] != 0;
+        }
+        if (has) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) vw[k] |= nw[k];
+          st_words<W>(vis + (size_t)w * W, vw);
+          st_words<W>(nxt + (size_t)w * W, nw);
+        }
+        const unsigned hm = __ballot_sync(0xffffffffu, has);
+        if (lane == 0 && hm) fbn[base >> 5] = hm;  // this warp owns the bitmap word
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          if (!__any_sync(0xffffffffu, nw[k] != 0)) continue;
+#pragma unroll 8
+          for (int bt = 0; bt < 64; ++bt) {
+            const unsigned bm = __ballot_sync(0xffffffffu, (nw[k] >> bt) & 1ull);
+            if (lane == (bt & 31)) lc[2 * k + (bt >> 5)] += __popc(bm);
+          }
+        }
+      }
+      // heavy rows: chunks of kHeavyRow entries, partial ORs into hacc
+      for (int c = gw; c < C; c += nwarps) {
+        int lo = 0, hi = nh - 1;  // heavy row holding chunk c
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (hcp[mid] <= c) lo = mid;
+          else hi = mid - 1;
+        }
+        const int h = heavy[lo];
+        const int a0 = __ldg(rp + h) + (c - hcp[lo]) * kHeavyRow;
+        const int a1 = min(__ldg(rp + h + 1), a0 + kHeavyRow);
+        u64 vh[W], ms[W], ac[W];
+        ld_words<W>(vis + (size_t)h * W, vh);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          ms[k] = al[k] & ~vh[k];
+          any |= ms[k] != 0;
+          ac[k] = 0;
+        }
+        if (!any) continue;
+        for (int e0 = a0; e0 < a1; e0 += 32) {
+          const int e = e0 + lane;
+          if (e < a1) {
+            const int u = __ldg(ci + e);
+            if (in_frontier(fbc, u)) {
+              u64 f[W];
+              ld_words<W>(cur + (size_t)u * W, f);
+#pragma unroll
+              for (int k = 0; k < W; ++k) ac[k] |= f[k];
+            }
+          }
+          if (((e0 - a0) & 255) == 224 || e0 + 32 >= a1) {  // every 256 entries: stop once nothing is missing
+            bool done = true;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              ac[k] = warp_or64(ac[k]);
+              done &= (ac[k] & ms[k]) == ms[k];
+            }
+            if (done) break;
+          }
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < W; ++k)
+            if (ac[k] & ms[k]) atomicOr(&hacc[(size_t)lo * W + k], ac[k] & ms[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k)
+        if (lc[k]) atomicAdd(&s_lc[64 * (k >> 1) + 32 * (k & 1) + lane], lc[k]);
+      ok = grid_sync(&ctl->bar, err, tns);
+      if (!ok) break;
+      // heavy rows: apply the accumulated lanes
+      for (int i = b * T + tid; i < nh; i += G * T) {
+        u64 a[W];
+        ld_words<W>(hacc + (size_t)i * W, a);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) any |= a[k] != 0;
+        if (!any) continue;
+        const u64 z[W] = {};
+        st_words<W>(hacc + (size_t)i * W, z);
+        const int h = heavy[i];
+        u64 vh[W], nw[W];
+        ld_words<W>(vis + (size_t)h * W, vh);
+        bool has = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          nw[k] = a[k] & al[k] & ~vh[k];
+          has |= nw[k] != 0;
+          vh[k] |= nw[k];
+        }
+        if (!has) continue;
+        st_words<W>(vis + (size_t)h * W, vh);
+        st_words<W>(nxt + (size_t)h * W, nw);
+        atomicOr(&fbn[h >> 5], 1u << (h & 31));
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          u64 x = nw[k];
+          while (x) {
+            const int bt = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            atomicAdd(&s_lc[64 * k + bt], 1u);
+          }
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < nb; j += T)
+        if (s_lc[j]) {
+          atomicAdd(&ctl->tot[(d + 1) % 3][j], (u64)s_lc[j]);
+          s_lc[j] = 0;
+        }
+      ok = grid_sync(&ctl->bar, err, tns);
+      if (!ok) break;
+      ++d;
+    }
+    if (!ok) break;
+    (void)any_alive;
+    // ---------- batch end: every lane word back to zero ----------
+    clear_frontier<W>(bufs[d % 3], fbs[d % 3], nbw);
+    clear_frontier<W>(bufs[(d + 2) % 3], fbs[(d + 2) % 3], nbw);
+    {
+      const size_t words = (size_t)n * W;
+      for (size_t i = ((size_t)b * T + tid) * 2; i < words; i += (size_t)G * T * 2) {
+        if (i + 1 < words) *reinterpret_cast<ulonglong2 *>(vis + i) = make_ulonglong2(0ull, 0ull);
+        else vis[i] = 0;
+      }
+    }
+    if (b == 0 && tid == 0) ctl->best_f = bf;
+    if (!grid_sync(&ctl->bar, err, tns)) break;
+  }
+  if (b == 0 && tid == 0) {
+    if (ctl->best_f < gctl->best_f) gctl->best_f = ctl->best_f;
+    ctl->batches += w_batches;
+    ctl->levels += w_levels;
+    ctl->lanes += w_lanes;
+  }
+}
+
+int round0_wide_occupancy(int W, int *blocks_per_sm) {
+  cudaError_t e;
+  switch (W) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<1>, kR0Threads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<2>, kR0Threads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<4>, kR0Threads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<8>, kR0Threads, 0); break;
+  }
+  GC_CUDA(e);
+  return GC_OK;
+}
+
+__global__ void k_heavy_chunks(const int32_t *__restrict__ rp, const int32_t *__restrict__ heavy,
+                               const int32_t *__restrict__ nh_dev, int32_t *hcp) {
+  // one CTA: hcp[i] = sum over heavy rows before i of ceil(deg / kHeavyRow)
+  __shared__ int s_scan[33];
+  const int nh = *nh_dev;
+  int carry = 0;
+  for (int base = 0; base < nh; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int c = 0;
+    if (i < nh) {
+      const int h = heavy[i];
+      c = (rp[h + 1] - rp[h] + kHeavyRow - 1) / kHeavyRow;
+    }
+    int total;
+    const int ex = block_excl_scan(c, s_scan, &total);
+    if (i < nh) hcp[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) hcp[nh] = carry;
+}
+
+// Allocate (once per handle and lane width) the lane words, bitmaps and heavy
+// chunk index of the wide round-0 kernel; everything starts at zero.
+static int round0_workspace(gc_graph *g, int W) {
+  if (g->r0_w >= W && g->r0_vis) return GC_OK;
+  if (g->r0_vis) {
+    cudaFree(g->r0_vis);
+    g->r0_vis = nullptr;
+  }
+  int32_t nh = 0;
+  GC_CUDA(cudaMemcpyAsync(&nh, g->n_heavy, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+  GC_CUDA(cudaStreamSynchronize(g->stream));
+  const size_t n = (size_t)g->n, nbw = ((n + 31) / 32 + 63) & ~(size_t)63;
+  const size_t words = ws_align(n * W * 8);
+  const size_t bitmap = ws_align(nbw * 4);
+  const size_t bytes = 4 * words + 3 * bitmap + ws_align(((size_t)nh + 1) * 4) + ws_align((size_t)nh * W * 8 + 8) +
+                      ws_align(2 * n * 4) + ws_align(sizeof(R0Ctl));
+  unsigned char *p = nullptr;
+  cudaError_t e = cudaMalloc((void **)&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMalloc (round-0 lane words)");
+  }
+  GC_CUDA(cudaMemsetAsync(p, 0, bytes, g->stream));
+  g->r0_vis = (unsigned long long *)p;
+  g->r0_bytes = bytes;
+  g->r0_w = W;
+  g->r0_nh = nh;
+  unsigned char *q = p + words;
+  for (int i = 0; i < 3; ++i) {
+    g->r0_buf[i] = (unsigned long long *)q;
+    q += words;
+  }
+  for (int i = 0; i < 3; ++i) {
+    g->r0_fb[i] = (uint32_t *)q;
+    q += bitmap;
+  }
+  g->r0_hcp = (int32_t *)q;
+  q += ws_align(((size_t)nh + 1) * 4);
+  g->r0_hacc = (unsigned long long *)q;
+  q += ws_align((size_t)nh * W * 8 + 8);
+  g->r0_defer = (int32_t *)q;
+  q += ws_align(2 * n * 4);
+  g->r0_ctl = (R0Ctl *)q;
+  ++g->launches;
+  k_heavy_chunks<<<1, 1024, 0, g->stream>>>(g->rp, g->heavy, g->n_heavy, g->r0_hcp);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
+                       int64_t timeout_ns) {
+  if (m <= 0) return GC_OK;
+  if (W != 1 && W != 2 && W != 4 && W != 8) return GC_EINVAL;
+  int rc = round0_workspace(g, W);
+  if (rc != GC_OK) return rc;
+  // the control block: batch cursors, best farness, per-level lane totals
+  GC_CUDA(cudaMemsetAsync(g->r0_ctl, 0, sizeof(R0Ctl), g->stream));
+  GC_CUDA(cudaMemcpyAsync(&g->r0_ctl->best_f, &g->gctl->best_f, sizeof(long long), cudaMemcpyDeviceToDevice,
+                          g->stream));
+  int occ = 0;
+  if ((rc = round0_wide_occupancy(W, &occ)) != GC_OK) return rc;
+  const int grid = std::min(kMaxGridCtas, std::max(1, occ) * g->num_sms);
+  const int32_t *rp = g->rp, *ci = g->ci, *key_list = list;
+  int32_t n = g->n;
+  const long long *key = g->key;
+  int32_t *defer = g->r0_defer;
+  R0Ctl *ctl = g->r0_ctl;
+  GainCtl *gctl = g->gctl;
+  // a workspace allocated for a wider W serves a narrower one: its words are
+  // laid out with stride W of this launch, inside the larger buffers
+  unsigned long long *vis = g->r0_vis, *b0 = g->r0_buf[0], *b1 = g->r0_buf[1], *b2 = g->r0_buf[2];
+  uint32_t *f0 = g->r0_fb[0], *f1 = g->r0_fb[1], *f2 = g->r0_fb[2];
+  const int32_t *heavy = g->heavy, *hcp = g->r0_hcp;
+  int32_t nh = g->r0_nh;
+  unsigned long long *hacc = g->r0_hacc;
+  unsigned long long tns = (unsigned long long)timeout_ns;
+  void *args[] = {(void *)&rp,   (void *)&ci,   (void *)&n,    (void *)&key_list, (void *)&m,     (void *)&key,
+                  (void *)&lgain, (void *)&defer, (void *)&ctl, (void *)&gctl,     (void *)&vis,   (void *)&b0,
+                  (void *)&b1,   (void *)&b2,   (void *)&f0,   (void *)&f1,       (void *)&f2,    (void *)&heavy,
+                  (void *)&nh,   (void *)&hcp,  (void *)&hacc, (void *)&defer_below, (void *)&tns};
+  const void *fn = W == 1 ? (const void *)k_round0_wide<1>
+                 : W == 2 ? (const void *)k_round0_wide<2>
+                 : W == 4 ? (const void *)k_round0_wide<4>
+                          : (const void *)k_round0_wide<8>;
+  ++g->launches;
+  GC_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kR0Threads), args, 0, g->stream));
+  return GC_OK;
+}
+
+}  // namespace gc

@@ -55,7 +55,8 @@ class Opts(ctypes.Structure):
                 ("active_target", ctypes.c_int32), ("round1_heavy", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("step_form", ctypes.c_int32),
                 ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32),
-                ("batch_grid_min_n", ctypes.c_int32), ("timeout_us", ctypes.c_int32)]
+                ("batch_grid_min_n", ctypes.c_int32), ("round0_lanes", ctypes.c_int32),
+                ("timeout_us", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -69,7 +70,8 @@ class Stats(ctypes.Structure):
         "gain64_frontier", "gain64_edges", "gain64_pushes", "gain64_lanes",
         "lazy_frontier", "lazy_edges", "lazy_pushes", "lazy_lanes", "lazy_launches")] + [
         ("ms_lazy_kernel", ctypes.c_double)] + [(n, ctypes.c_int64) for n in (
-        "lazy_upd_frontier", "lazy_upd_edges", "lazy_upd_relabels", "lazy_sel_scanned")]
+        "lazy_upd_frontier", "lazy_upd_edges", "lazy_upd_relabels", "lazy_sel_scanned")] + [
+        ("ms_round0_wide", ctypes.c_double), ("r0_batches", ctypes.c_int64), ("r0_levels", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -240,7 +242,8 @@ class Graph:
                use_proposal: bool = False, step_lanes: int = 0, step_mode: int = 0,
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
                step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0,
-               pruned_adjacency: bool = True, round1_bound: bool = True, timeout_us: int = 0):
+               pruned_adjacency: bool = True, round1_bound: bool = True, timeout_us: int = 0,
+               round0_lanes: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
@@ -253,6 +256,7 @@ class Graph:
         if timeout_ms:
             o.timeout_ms = timeout_ms
         o.timeout_us = timeout_us
+        o.round0_lanes = round0_lanes
         grp = np.zeros(max(int(k), 1), dtype=np.int32)
         f = ctypes.c_int64()
         st = Stats()

@@ -300,3 +300,31 @@ def test_wait_expiry_returns_timeout_and_handle_stays_usable(gcm):
             got, f, _ = G.greedy(3)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
+
+
+def round0_cases():
+    return [("ba20000m1", graphgen.barabasi_albert(20000, 1, 5)), ("gnp400", sg.gnp_connected(400, 0.02, 3)),
+            ("ba3000m2", graphgen.barabasi_albert(3000, 2, 3)), ("tree", sg.tree_random(900, 3)),
+            ("rmat12", graphgen.rmat(12, 16.0, seed=1)), ("star70", sg.star(70)), ("k9", sg.complete(9))]
+
+
+@pytest.mark.parametrize("name,g", round0_cases())
+@pytest.mark.parametrize("lanes", [64, 128, 256, 512, -1])
+def test_round0_wide_lane_widths(gcm, name, g, lanes):
+    """Round 0 (top-1 closeness, BFScut) by the wide bottom-up kernel at every
+    batch width, and by the 64-lane path (-1): the same s0 and farness as the
+    oracle, then the same group.  The 20,000-vertex tree leaves every vertex a
+    survivor of the degree bound, so many batches and deferred lanes run."""
+    rp, ci = g
+    s0, f0, _ = oracle.top1_closeness(rp, ci)
+    k = 4
+    grp, ft, _, _ = oracle.greedypp(rp, ci, k)
+    assert grp[0] == s0 and ft[0] == f0
+    with gcm.Graph(rp, ci) as G:
+        got, f, st = G.greedy(k, round0_lanes=lanes)
+        np.testing.assert_array_equal(got, grp)
+        assert f == ft[-1]
+        if lanes > 0 and name == "ba20000m1":
+            assert st["r0_batches"] >= 2
+        got1, f1, _ = G.greedy(1, round0_lanes=lanes)
+        assert got1[0] == s0 and f1 == f0
