@@ -177,6 +177,15 @@ typedef struct gc_stats {
   double ms_round0_wide;     /* its duration (CUDA events on the launch stream) */
   int64_t r0_batches;        /* its batches */
   int64_t r0_levels;         /* bottom-up levels summed over batches */
+  int64_t r0_td_edges;       /* adjacency entries of its top-down levels */
+  double ms_r0_select;       /* its phases by the clock of its first CTA: batch selection, */
+  double ms_r0_topdown;      /* the top-down first level, */
+  double ms_r0_bottomup;     /* the bottom-up levels with their BFScut folds, */
+  double ms_r0_clear;        /* and the clearing of the lane words after each batch */
+  int64_t r0_bu_rows;        /* bottom-up: vertices that claimed at least one lane */
+  int64_t r0_bu_scanned;     /* bottom-up: adjacency entries read */
+  int64_t r0_bu_gathers;     /* bottom-up: frontier lane words gathered */
+  int64_t r0_width;          /* its candidates per batch (0: not used) */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -67,6 +67,8 @@ def _load():
             lib.or_top1_closeness.argtypes = [i32, vp, vp, i32, vp, vp, vp]
             lib.or_greedypp.restype = ctypes.c_int
             lib.or_greedypp.argtypes = [i32, vp, vp, i32, vp, vp, vp, i32, ctypes.POINTER(_GppStats)]
+            lib.or_greedypp_cost_sample.restype = ctypes.c_int
+            lib.or_greedypp_cost_sample.argtypes = [i32, vp, vp, i32, i64, i32, vp, i32, i32, vp]
             _lib = lib
     return _lib
 
@@ -184,3 +186,19 @@ def greedypp(row_ptr, col_idx, k: int, threads: int | None = None):
     if rc:
         raise ValueError("bad k or disconnected graph")
     return g, ft, gt, {"evals": st.evals, "edges": st.edges, "round0_full": st.round0_full}
+
+
+def greedypp_cost_sample(row_ptr, col_idx, s0: int, f_best: int, cand, threads: int | None = None):
+    """Wall seconds of CPU Greedy++'s two dominant steps on the vertices `cand`:
+    (round-0 BFScut against the fixed threshold (f_best, s0), round-1 pruned
+    SSSP against S = {s0}, entries scanned by the latter).  Used only to time
+    the oracle on a bounded sample of a large workload."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    c = _i32(cand)
+    out = np.zeros(3, dtype=np.float64)
+    rc = _load().or_greedypp_cost_sample(n, rp.ctypes.data, ci.ctypes.data, int(s0), int(f_best), int(s0),
+                                         c.ctypes.data, int(np.size(cand)), threads or default_threads(),
+                                         out.ctypes.data)
+    if rc:
+        raise MemoryError("oracle cost sample failed")
+    return float(out[0]), float(out[1]), float(out[2])

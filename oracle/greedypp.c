@@ -312,3 +312,68 @@ int or_greedypp(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32
   if (stats) *stats = st;
   return 0;
 }
+
+/* Cost sample (used only to time the oracle on a bounded part of a workload
+ * whose answer is known, for the benchmark's CPU baseline): for each vertex in
+ * cand[0..m), the two steps of this file that dominate Greedy++ on large
+ * graphs -- the round-0 BFScut of Sec. 3.1 / Algorithm 3 against the fixed
+ * threshold (f_best, id_best), and the round-1 pruned SSSP of Sec. 4.1 against
+ * S = {s0} -- run exactly as or_greedypp runs them, in parallel over the
+ * candidates.  out[0] and out[1] receive the wall seconds of the two parts;
+ * out[2] the adjacency entries the pruned SSSPs scanned.  Returns 0, or -2 on
+ * allocation failure. */
+int or_greedypp_cost_sample(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t s0,
+                            int64_t f_best, int32_t id_best, const int32_t *cand, int32_t m, int32_t nthreads,
+                            double *out) {
+  int nt = nthreads > 0 ? nthreads : 1;
+  int32_t *dS = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  if (!dS || !queue) { free(dS); free(queue); return -2; }
+  for (int32_t u = 0; u < n; ++u) dS[u] = -1;
+  {
+    int64_t head = 0, tail = 0;
+    dS[s0] = 0; queue[tail++] = s0;
+    while (head < tail) {
+      int32_t u = queue[head++];
+      for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+        if (dS[col_idx[e]] < 0) { dS[col_idx[e]] = dS[u] + 1; queue[tail++] = col_idx[e]; }
+    }
+  }
+  int err = 0;
+  int64_t scanned = 0;
+  double t0 = omp_get_wtime();
+#pragma omp parallel num_threads(nt)
+  {
+    bfs_ws w;
+    int ok = ws_init(&w, n) == 0;
+    if (!ok) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = 0; i < m; ++i)
+      if (ok) (void)bfscut(n, row_ptr, col_idx, cand[i], f_best, id_best, &w);
+    if (ok) ws_free(&w);
+  }
+  double t1 = omp_get_wtime();
+#pragma omp parallel num_threads(nt) reduction(+ : scanned)
+  {
+    bfs_ws w;
+    int ok = ws_init(&w, n) == 0;
+    if (!ok) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 64)
+    for (int32_t i = 0; i < m; ++i)
+      if (ok) (void)pruned_gain(row_ptr, col_idx, dS, cand[i], &w, &scanned);
+    if (ok) ws_free(&w);
+  }
+  double t2 = omp_get_wtime();
+  free(dS); free(queue);
+  if (err) return -2;
+  out[0] = t1 - t0;
+  out[1] = t2 - t1;
+  out[2] = (double)scanned;
+  return 0;
+}

@@ -422,7 +422,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
   size_t ev_used = 0;
-  int64_t r0_stats[2] = {0, 0};  // wide round-0 kernel: batches, bottom-up levels
+  int64_t r0_stats[3] = {0, 0, 0};  // wide round-0 kernel: batches, bottom-up levels, top-down entries
+  double r0_ms[4] = {0, 0, 0, 0};     // and its phases: selection, top-down, bottom-up, clears
+  int64_t r0_bu[3] = {0, 0, 0};       // its bottom-up rows with missing lanes, entries read, words gathered
   bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
@@ -476,7 +478,9 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const int32_t ecc_a = g->h_bctl->levels;
   int r0_w = 0;
   if (opts.round0_lanes >= 0 && ecc_a <= kShallowLevels && n_surv > 0) {
-    const int want = opts.round0_lanes > 0 ? opts.round0_lanes : (n_surv > 256 ? 512 : n_surv > 128 ? 256 : n_surv > 64 ? 128 : 64);
+    // automatic: 256 lanes at most (measured on R-MAT scale 24: 512 lanes are no
+    // faster, their wider gathers cancel the halved batch count)
+    const int want = opts.round0_lanes > 0 ? opts.round0_lanes : (n_surv > 128 ? 256 : n_surv > 64 ? 128 : 64);
     r0_w = want >= 512 ? 8 : want >= 256 ? 4 : want >= 128 ? 2 : 1;
   }
   // Many survivors (deep graphs, where the degree bound is weak): tighten the
@@ -507,12 +511,17 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w, tns));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     R0Ctl r0c;
-    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 3 * sizeof(unsigned long long),
+    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 11 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, g->stream));
     GC_TRY(sync(g));
     r0_wide_lanes = (int64_t)r0c.lanes;
     r0_stats[0] = (int64_t)r0c.batches;
     r0_stats[1] = (int64_t)r0c.levels;
+    r0_stats[2] = (int64_t)r0c.td_edges;
+    for (int i = 0; i < 4; ++i) r0_ms[i] = r0c.ns[i] * 1e-6;
+    r0_bu[0] = (int64_t)r0c.bu_rows;
+    r0_bu[1] = (int64_t)r0c.bu_scanned;
+    r0_bu[2] = (int64_t)r0c.bu_gathers;
   } else if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)
@@ -771,6 +780,15 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lazy_sel_scanned = (int64_t)g->h_lctl->sel_scanned;
     stats->r0_batches = r0_stats[0];
     stats->r0_levels = r0_stats[1];
+    stats->r0_td_edges = r0_stats[2];
+    stats->ms_r0_select = r0_ms[0];
+    stats->ms_r0_topdown = r0_ms[1];
+    stats->ms_r0_bottomup = r0_ms[2];
+    stats->ms_r0_clear = r0_ms[3];
+    stats->r0_bu_rows = r0_bu[0];
+    stats->r0_bu_scanned = r0_bu[1];
+    stats->r0_bu_gathers = r0_bu[2];
+    stats->r0_width = r0_w * kLanes;
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

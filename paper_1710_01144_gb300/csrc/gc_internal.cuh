@@ -186,6 +186,9 @@ struct R0Ctl {
   int32_t pos[kR0MaxLanes];
   unsigned long long tot[3][kR0MaxLanes];  // claims per lane at distance d, in tot[d mod 3]
   unsigned long long batches, levels, lanes;  // work counters
+  unsigned long long td_edges;                 // adjacency entries of the top-down levels
+  unsigned long long ns[4];  // CTA 0's clock: selection, top-down level, bottom-up levels with folds, clears
+  unsigned long long bu_rows, bu_scanned, bu_gathers;  // bottom-up: vertices that claimed lanes, entries read, frontier words gathered
 };
 
 // Selection / reduction control block (lives across a whole greedy call).

@@ -53,6 +53,7 @@ namespace gc {
 typedef unsigned long long u64;
 
 constexpr int kR0Threads = 512;
+constexpr int kR0Ilp = 4;  // adjacency entries in flight per thread in the bottom-up passes
 
 // Lane words and bitmaps change from level to level and are written by other
 // SMs, so they are read at L2 (ld.global.cg): a line left in this SM's L1
@@ -83,6 +84,23 @@ __device__ __forceinline__ void st_words(u64 *p, const u64 (&x)[W]) {
       v.x = x[k];
       v.y = x[k + (W > 1 ? 1 : 0)];
       *reinterpret_cast<ulonglong2 *>(p + k) = v;
+    }
+  }
+}
+
+// acc |= the lane words at p, loading only the words marked in `open` (pairs of
+// words share one 16-byte load)
+template <int W>
+__device__ __forceinline__ void gather_open(const u64 *p, unsigned open, u64 (&acc)[W]) {
+  if (W == 1) {
+    if (open & 1u) acc[0] |= __ldcg(p);
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; k += 2) {
+      if (!((open >> k) & 3u)) continue;
+      const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p + k));
+      acc[k] |= v.x;
+      acc[k + (W > 1 ? 1 : 0)] |= v.y;
     }
   }
 }
@@ -148,7 +166,16 @@ __global__ void __launch_bounds__(kR0Threads, 1)
   u64 *bufs[3] = {buf_a, buf_b, buf_c};
   uint32_t *fbs[3] = {fb_a, fb_b, fb_c};
   const int C = nh > 0 ? hcp[nh] : 0;  // heavy-row chunks
-  u64 w_batches = 0, w_levels = 0, w_lanes = 0;
+  u64 w_batches = 0, w_levels = 0, w_lanes = 0, w_td = 0, w_scan = 0, w_gath = 0, w_claim = 0;
+  const bool timer = b == 0 && tid == 0;
+  u64 t_prev = timer ? global_ns() : 0, t_ph[4] = {0, 0, 0, 0};
+  auto lap = [&](int i) {
+    if (timer) {
+      const u64 t = global_ns();
+      t_ph[i] += t - t_prev;
+      t_prev = t;
+    }
+  };
 
   for (;;) {
     // ---------- batch selection (warp 0 of CTA 0) ----------
@@ -208,6 +235,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       for (int i = lane; i < 3 * B; i += 32) ctl->tot[i / B][i % B] = 0;  // rows are kR0MaxLanes apart
     }
     if (!grid_sync(&ctl->bar, err, tns)) break;
+    lap(0);
     const int nb = *(volatile int32_t *)&ctl->nb;
     if (nb == 0) break;
     const int phase = *(volatile int32_t *)&ctl->phase;
@@ -241,6 +269,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
         atomicOr(&vis[(size_t)c * W + (j >> 6)], 1ull << (j & 63));
       }
       const int E = s_eoff[B];
+      w_td += (u64)E;
       u64 *nx1 = bufs[1];
       uint32_t *fb1 = fbs[1];
       for (int e = b * T + tid; e < E; e += G * T) {
@@ -270,6 +299,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
     }
     bool ok = grid_sync(&ctl->bar, err, tns);
     if (!ok) break;
+    lap(1);
     ++w_batches;
     w_lanes += (u64)nb;
     int d = 1;  // the distance whose claims were just counted
@@ -360,18 +390,18 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       for (int base = gw * 32; base < n; base += nwarps * 32) {
         const int w = base + lane;
         int r0 = 0, r1 = 0;
-        u64 miss[W], vw[W];
+        u64 miss[W];
         bool want = false;
 #pragma unroll
-        for (int k = 0; k < W; ++k) miss[k] = vw[k] = 0;
+        for (int k = 0; k < W; ++k) miss[k] = 0;
         if (w < n) {
           r0 = __ldg(rp + w);
           r1 = __ldg(rp + w + 1);
           if (r1 - r0 <= kHeavyRow) {
-            ld_words<W>(vis + (size_t)w * W, vw);
+            ld_words<W>(vis + (size_t)w * W, miss);
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-              miss[k] = al[k] & ~vw[k];
+              miss[k] = al[k] & ~miss[k];
               want |= miss[k] != 0;
             }
           }
@@ -381,21 +411,31 @@ __global__ void __launch_bounds__(kR0Threads, 1)
         u64 acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
+        // Rows of up to 32 entries: one thread each, kR0Ilp entries in flight;
+        // a lane word is loaded only while some of its missing lanes are still
+        // unfound, and the scan stops once none is left.
         const bool own = want && (r1 - r0) <= 32;
         if (own) {
-          for (int e = r0; e < r1; ++e) {
-            const int u = __ldg(ci + e);
-            if (in_frontier(fbc, u)) {
-              u64 f[W];
-              ld_words<W>(cur + (size_t)u * W, f);
-              bool done = true;
+          unsigned open = 0;  // words with lanes still unfound
 #pragma unroll
-              for (int k = 0; k < W; ++k) {
-                acc[k] |= f[k];
-                done &= (acc[k] & miss[k]) == miss[k];
-              }
-              if (done) break;
+          for (int k = 0; k < W; ++k) open |= (miss[k] != 0 ? 1u : 0u) << k;
+          for (int e = r0; e < r1 && open; e += kR0Ilp) {
+            int u[kR0Ilp];
+#pragma unroll
+            for (int q = 0; q < kR0Ilp; ++q) u[q] = e + q < r1 ? __ldg(ci + e + q) : -1;
+            bool fr[kR0Ilp];
+#pragma unroll
+            for (int q = 0; q < kR0Ilp; ++q) fr[q] = u[q] >= 0 && in_frontier(fbc, u[q]);
+#pragma unroll
+            for (int q = 0; q < kR0Ilp; ++q) {
+              if (!fr[q]) continue;
+              w_gath += 1;
+              gather_open<W>(cur + (size_t)u[q] * W, open, acc);
             }
+            w_scan += (u64)min(kR0Ilp, r1 - e);
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+              if ((acc[k] & miss[k]) == miss[k]) open &= ~(1u << k);
           }
         }
         unsigned mm = __ballot_sync(0xffffffffu, want && !own);
@@ -404,29 +444,38 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           mm &= mm - 1;
           const int a0 = __shfl_sync(0xffffffffu, r0, t), a1 = __shfl_sync(0xffffffffu, r1, t);
           u64 ms[W], ac[W];
+          unsigned open = 0;
 #pragma unroll
           for (int k = 0; k < W; ++k) {
             ms[k] = __shfl_sync(0xffffffffu, miss[k], t);
             ac[k] = 0;
+            open |= (ms[k] != 0 ? 1u : 0u) << k;
           }
-          for (int e0 = a0; e0 < a1; e0 += 32) {
-            const int e = e0 + lane;
-            if (e < a1) {
-              const int u = __ldg(ci + e);
-              if (in_frontier(fbc, u)) {
-                u64 f[W];
-                ld_words<W>(cur + (size_t)u * W, f);
+          for (int e0 = a0; e0 < a1 && open; e0 += 32 * kR0Ilp) {
+            int u[kR0Ilp];
 #pragma unroll
-                for (int k = 0; k < W; ++k) ac[k] |= f[k];
-              }
+            for (int q = 0; q < kR0Ilp; ++q) {
+              const int e = e0 + q * 32 + lane;
+              u[q] = e < a1 ? __ldg(ci + e) : -1;
             }
-            bool done = true;
+            bool fr[kR0Ilp];
+#pragma unroll
+            for (int q = 0; q < kR0Ilp; ++q) {
+              fr[q] = u[q] >= 0 && in_frontier(fbc, u[q]);
+              w_scan += u[q] >= 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kR0Ilp; ++q) {
+              if (!fr[q]) continue;
+              w_gath += 1;
+              gather_open<W>(cur + (size_t)u[q] * W, open, ac);
+            }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
+              if (!((open >> k) & 1u)) continue;  // (open is warp-uniform)
               ac[k] = warp_or64(ac[k]);
-              done &= (ac[k] & ms[k]) == ms[k];
+              if ((ac[k] & ms[k]) == ms[k]) open &= ~(1u << k);
             }
-            if (done) break;
           }
           if (lane == t) {
 #pragma unroll
@@ -440,7 +489,10 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           nw[k] = acc[k] & miss[k];
           has |= nw[k] != 0;
         }
-        if (has) {
+        w_claim += has;
+        if (has) {  // (vis reloaded: only this thread writes it during the level)
+          u64 vw[W];
+          ld_words<W>(vis + (size_t)w * W, vw);
 #pragma unroll
           for (int k = 0; k < W; ++k) vw[k] |= nw[k];
           st_words<W>(vis + (size_t)w * W, vw);
@@ -451,11 +503,18 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
         for (int k = 0; k < W; ++k) {
           if (!__any_sync(0xffffffffu, nw[k] != 0)) continue;
-#pragma unroll 8
-          for (int bt = 0; bt < 64; ++bt) {
-            const unsigned bm = __ballot_sync(0xffffffffu, (nw[k] >> bt) & 1ull);
-            if (lane == (bt & 31)) lc[2 * k + (bt >> 5)] += __popc(bm);
+          unsigned c0 = 0, c1 = 0;
+#pragma unroll
+          for (int bt = 0; bt < 32; ++bt) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, (nw[k] >> bt) & 1ull);
+            const unsigned b1 = __ballot_sync(0xffffffffu, (nw[k] >> (bt + 32)) & 1ull);
+            if (lane == bt) {
+              c0 = __popc(b0);
+              c1 = __popc(b1);
+            }
           }
+          lc[2 * k] += c0;
+          lc[2 * k + 1] += c1;
         }
       }
       // heavy rows: chunks of kHeavyRow entries, partial ORs into hacc
@@ -479,18 +538,29 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           ac[k] = 0;
         }
         if (!any) continue;
-        for (int e0 = a0; e0 < a1; e0 += 32) {
-          const int e = e0 + lane;
-          if (e < a1) {
-            const int u = __ldg(ci + e);
-            if (in_frontier(fbc, u)) {
-              u64 f[W];
-              ld_words<W>(cur + (size_t)u * W, f);
+        for (int e0 = a0; e0 < a1; e0 += 32 * kR0Ilp) {
+          int u[kR0Ilp];
 #pragma unroll
-              for (int k = 0; k < W; ++k) ac[k] |= f[k];
-            }
+          for (int q = 0; q < kR0Ilp; ++q) {
+            const int e = e0 + q * 32 + lane;
+            u[q] = e < a1 ? __ldg(ci + e) : -1;
           }
-          if (((e0 - a0) & 255) == 224 || e0 + 32 >= a1) {  // every 256 entries: stop once nothing is missing
+          bool fr[kR0Ilp];
+#pragma unroll
+          for (int q = 0; q < kR0Ilp; ++q) {
+            fr[q] = u[q] >= 0 && in_frontier(fbc, u[q]);
+            w_scan += u[q] >= 0;
+            w_gath += fr[q];
+          }
+#pragma unroll
+          for (int q = 0; q < kR0Ilp; ++q) {
+            if (!fr[q]) continue;
+            u64 f[W];
+            ld_words<W>(cur + (size_t)u[q] * W, f);
+#pragma unroll
+            for (int k = 0; k < W; ++k) ac[k] |= f[k];
+          }
+          if (((e0 - a0) & 255) == 128 || e0 + 32 * kR0Ilp >= a1) {  // every 256 entries: stop once nothing is missing
             bool done = true;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
@@ -532,6 +602,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           vh[k] |= nw[k];
         }
         if (!has) continue;
+        ++w_claim;
         st_words<W>(vis + (size_t)h * W, vh);
         st_words<W>(nxt + (size_t)h * W, nw);
         atomicOr(&fbn[h >> 5], 1u << (h & 31));
@@ -556,6 +627,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       ++d;
     }
     if (!ok) break;
+    lap(2);
     (void)any_alive;
     // ---------- batch end: every lane word back to zero ----------
     clear_frontier<W>(bufs[d % 3], fbs[d % 3], nbw);
@@ -569,24 +641,39 @@ __global__ void __launch_bounds__(kR0Threads, 1)
     }
     if (b == 0 && tid == 0) ctl->best_f = bf;
     if (!grid_sync(&ctl->bar, err, tns)) break;
+    lap(3);
+  }
+  w_scan = block_sum(w_scan, (u64 *)s_red);
+  w_gath = block_sum(w_gath, (u64 *)s_red);
+  w_claim = block_sum(w_claim, (u64 *)s_red);
+  if (tid == 0) {
+    atomicAdd(&ctl->bu_scanned, w_scan);
+    atomicAdd(&ctl->bu_gathers, w_gath);
+    atomicAdd(&ctl->bu_rows, w_claim);
   }
   if (b == 0 && tid == 0) {
     if (ctl->best_f < gctl->best_f) gctl->best_f = ctl->best_f;
     ctl->batches += w_batches;
     ctl->levels += w_levels;
     ctl->lanes += w_lanes;
+    ctl->td_edges += w_td;
+    for (int i = 0; i < 4; ++i) ctl->ns[i] += t_ph[i];
   }
 }
 
+static size_t round0_dyn_smem(int) { return 0; }
+
+static const void *round0_fn(int W) {
+  return W == 1 ? (const void *)k_round0_wide<1>
+       : W == 2 ? (const void *)k_round0_wide<2>
+       : W == 4 ? (const void *)k_round0_wide<4>
+                : (const void *)k_round0_wide<8>;
+}
+
 int round0_wide_occupancy(int W, int *blocks_per_sm) {
-  cudaError_t e;
-  switch (W) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<1>, kR0Threads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<2>, kR0Threads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<4>, kR0Threads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_round0_wide<8>, kR0Threads, 0); break;
-  }
-  GC_CUDA(e);
+  const void *fn = round0_fn(W);
+  GC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)round0_dyn_smem(W)));
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kR0Threads, round0_dyn_smem(W)));
   return GC_OK;
 }
 
@@ -691,12 +778,9 @@ int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *l
                   (void *)&lgain, (void *)&defer, (void *)&ctl, (void *)&gctl,     (void *)&vis,   (void *)&b0,
                   (void *)&b1,   (void *)&b2,   (void *)&f0,   (void *)&f1,       (void *)&f2,    (void *)&heavy,
                   (void *)&nh,   (void *)&hcp,  (void *)&hacc, (void *)&defer_below, (void *)&tns};
-  const void *fn = W == 1 ? (const void *)k_round0_wide<1>
-                 : W == 2 ? (const void *)k_round0_wide<2>
-                 : W == 4 ? (const void *)k_round0_wide<4>
-                          : (const void *)k_round0_wide<8>;
   ++g->launches;
-  GC_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kR0Threads), args, 0, g->stream));
+  GC_CUDA(cudaLaunchCooperativeKernel(round0_fn(W), dim3(grid), dim3(kR0Threads), args, round0_dyn_smem(W),
+                                      g->stream));
   return GC_OK;
 }
 

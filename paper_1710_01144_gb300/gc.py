@@ -71,7 +71,10 @@ class Stats(ctypes.Structure):
         "lazy_frontier", "lazy_edges", "lazy_pushes", "lazy_lanes", "lazy_launches")] + [
         ("ms_lazy_kernel", ctypes.c_double)] + [(n, ctypes.c_int64) for n in (
         "lazy_upd_frontier", "lazy_upd_edges", "lazy_upd_relabels", "lazy_sel_scanned")] + [
-        ("ms_round0_wide", ctypes.c_double), ("r0_batches", ctypes.c_int64), ("r0_levels", ctypes.c_int64)]
+        ("ms_round0_wide", ctypes.c_double), ("r0_batches", ctypes.c_int64), ("r0_levels", ctypes.c_int64),
+        ("r0_td_edges", ctypes.c_int64), ("ms_r0_select", ctypes.c_double), ("ms_r0_topdown", ctypes.c_double),
+        ("ms_r0_bottomup", ctypes.c_double), ("ms_r0_clear", ctypes.c_double), ("r0_bu_rows", ctypes.c_int64),
+        ("r0_bu_scanned", ctypes.c_int64), ("r0_bu_gathers", ctypes.c_int64), ("r0_width", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -74,3 +74,47 @@ def test_mixed_batch_subset_vs_oracle(gcm):
         g, ft, _, _ = oracle.greedypp(rp, ci, k)
         np.testing.assert_array_equal(got, g)
         assert f == ft[-1]
+
+
+def _golden(name):
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, _, val = line.partition(" ")
+        out[key] = val.split()
+    return out
+
+
+def _csr_sha256(rp, ci):
+    import hashlib
+
+    h = hashlib.sha256()
+    h.update(rp.astype("<i4").tobytes())
+    h.update(ci.astype("<i4").tobytes())
+    return h.hexdigest()
+
+
+def test_greedy_rmat24_k50_full_size(gcm):
+    """R-MAT scale 24, edge factor 16 (8.86M vertices, 521M entries), k = 50:
+    the whole group and its farness against CPU Greedy++, whose answer is
+    stored in tests/golden/rmat24_ef16_k50.txt (written by make_rmat24_k50.py,
+    which calls only the oracle).  The graph must be the one the oracle saw.
+    Default launch configuration, then the host-driven lazy steps, then the
+    64-lane round 0."""
+    gold = _golden("rmat24_ef16_k50.txt")
+    rp, ci = graphgen.rmat_s24_ef16()
+    assert rp.size - 1 == int(gold["n"][0]) and ci.size == int(gold["nnz"][0])
+    assert _csr_sha256(rp, ci) == gold["sha256"][0]
+    grp = np.array([int(x) for x in gold["group"]], dtype=np.int32)
+    ft = np.array([int(x) for x in gold["farness"]], dtype=np.int64)
+    with gcm.Graph(rp, ci) as G:
+        for kw in ({}, {"step_mode": 1, "eval_per_step": 128}, {"round0_lanes": -1}):
+            got, f, _ = G.greedy(50, **kw)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+        # the farness of the first ten picks, recomputed by one oracle BFS
+        assert G.farness(grp[:10]) == ft[9] == oracle.farness(rp, ci, grp[:10])
