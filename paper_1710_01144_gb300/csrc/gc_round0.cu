@@ -56,17 +56,18 @@ constexpr int kR0Threads = 512;
 constexpr int kR0Ilp = 4;  // adjacency entries in flight per thread in the bottom-up passes
 
 // Lane words and bitmaps change from level to level and are written by other
-// SMs, so they are read at L2 (ld.global.cg): a line left in this SM's L1
-// from an earlier level could be stale, and a stale visited word written back
-// would drop lanes that other CTAs set.
+// SMs; they are read with ordinary loads after the grid barrier, whose
+// release/acquire pair orders every write before it (other CTAs included)
+// before every read after it, so hot lines (hub frontier words, bitmap words)
+// can be served by L1 within a level.
 template <int W>
 __device__ __forceinline__ void ld_words(const u64 *p, u64 (&x)[W]) {
   if (W == 1) {
-    x[0] = __ldcg(p);
+    x[0] = *p;
   } else {
 #pragma unroll
     for (int k = 0; k < W; k += 2) {
-      const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p + k));
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p + k);
       x[k] = v.x;
       x[k + (W > 1 ? 1 : 0)] = v.y;
     }
@@ -93,12 +94,12 @@ __device__ __forceinline__ void st_words(u64 *p, const u64 (&x)[W]) {
 template <int W>
 __device__ __forceinline__ void gather_open(const u64 *p, unsigned open, u64 (&acc)[W]) {
   if (W == 1) {
-    if (open & 1u) acc[0] |= __ldcg(p);
+    if (open & 1u) acc[0] |= *p;
   } else {
 #pragma unroll
     for (int k = 0; k < W; k += 2) {
       if (!((open >> k) & 3u)) continue;
-      const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p + k));
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p + k);
       acc[k] |= v.x;
       acc[k + (W > 1 ? 1 : 0)] |= v.y;
     }
@@ -124,14 +125,14 @@ __device__ __forceinline__ long long r0_block_min(long long v, long long *sh) {
   return v;
 }
 
-__device__ __forceinline__ bool in_frontier(const uint32_t *fb, int u) { return (__ldcg(fb + (u >> 5)) >> (u & 31)) & 1u; }
+__device__ __forceinline__ bool in_frontier(const uint32_t *fb, int u) { return (fb[u >> 5] >> (u & 31)) & 1u; }
 
 // Zero the claim words of every vertex marked in bitmap fb, and the bitmap.
 template <int W>
 __device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw) {
   const int T = blockDim.x;
   for (int x = blockIdx.x * T + threadIdx.x; x < nbw; x += gridDim.x * T) {
-    uint32_t bits = __ldcg(fb + x);
+    uint32_t bits = fb[x];
     if (!bits) continue;
     fb[x] = 0;
     const u64 z[W] = {};
