@@ -391,6 +391,19 @@ int64_t gc_batch_vertices(const gc_batch *b);
 int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts, int32_t *groups, int64_t *farness,
                     gc_stats *stats);
 
+/* gc_greedy_batch -- the batched solve of gc_batch_greedy over graphs already
+ * loaded with gc_load_csr (all on the current device).  gs[count] handles;
+ * ks[count] group sizes (1 <= ks[g] <= n of graph g); opts as for
+ * gc_batch_greedy; out_groups[g] (host int32[ks[g]]) receives graph g's group
+ * in pick order, out_farness (host int64[count]) each group's farness.  Each
+ * group equals gc_greedy's on that graph alone.  Every call gathers the
+ * handles' CSRs into one union on the device (one device-to-device copy of
+ * each CSR plus the batch's scratch): repeated solves of the same graphs are
+ * cheaper through gc_batch_load + gc_batch_greedy.  The handles are not
+ * changed.  Synchronous.  Errors: as gc_batch_greedy. */
+int gc_greedy_batch(gc_graph *const *gs, const int32_t *ks, int32_t count, const gc_opts *opts,
+                    int32_t *const *out_groups, int64_t *out_farness, gc_stats *stats);
+
 /* gc_last_error -- thread-local description of the last failure ("" if none). */
 const char *gc_last_error(void);
 

@@ -273,10 +273,11 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       cudaMallocHost((void **)&g->h_lctl, sizeof(LazyCtl)) != cudaSuccess)
     return bail(fail(GC_ENOMEM, "pinned host allocation failed"));
   // gain-kernel workspaces: one per resident CTA, within 40% of free memory
+  // and 16 GB (large shallow graphs use the wide round-0 kernel, not these)
   g->ws_stride = gain_ws_stride(n);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return bail(fail(GC_ECUDA, "cudaMemGetInfo"));
-  const size_t budget = free_b / 10 * 4;
+  const size_t budget = std::min<size_t>(free_b / 10 * 4, (size_t)16 << 30);
   int want = g->gain_ctas;
   if ((size_t)want * g->ws_stride > budget) want = (int)std::max<size_t>(1, budget / g->ws_stride);
   g->gain_ctas = want;

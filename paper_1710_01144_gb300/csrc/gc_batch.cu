@@ -801,11 +801,12 @@ static bool balloc(T **p, size_t count) {
   return true;
 }
 
-extern "C" {
-
-int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *const *col_idxs, const int32_t *ns,
-                  uint32_t flags, void *stream, gc_batch **out) {
-  (void)flags;
+// The union CSR of `count` graphs.  Host arrays (nnzs == nullptr: the entry
+// counts are read from row_ptrs[g][ns[g]]), or device arrays of existing
+// handles (nnzs given; the handles were checked when they were loaded).  The
+// copies use cudaMemcpyDefault, which takes either kind of pointer.
+static int batch_load_impl(int32_t count, const int32_t *const *row_ptrs, const int32_t *const *col_idxs,
+                           const int32_t *ns, const int64_t *nnzs, void *stream, gc_batch **out) {
   if (!out || count < 1 || !row_ptrs || !col_idxs || !ns) {
     set_error("bad argument to gc_batch_load");
     return GC_EINVAL;
@@ -819,7 +820,8 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
   std::vector<int64_t> eoff(count + 1);
   int64_t N = 0, E = 0;
   for (int32_t g = 0; g < count; ++g) {
-    if (ns[g] < 1 || !row_ptrs[g] || row_ptrs[g][0] != 0 || (row_ptrs[g][ns[g]] > 0 && !col_idxs[g])) {
+    const int64_t e = nnzs ? nnzs[g] : (ns[g] >= 1 && row_ptrs[g] ? row_ptrs[g][ns[g]] : -1);
+    if (ns[g] < 1 || !row_ptrs[g] || e < 0 || (!nnzs && row_ptrs[g][0] != 0) || (e > 0 && !col_idxs[g])) {
       batch_release(b);
       set_error("gc_batch_load: graph " + std::to_string(g) + " is malformed");
       return GC_EINVAL;
@@ -827,7 +829,7 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
     b->h_off[g] = (int32_t)N;
     eoff[g] = E;
     N += ns[g];
-    E += row_ptrs[g][ns[g]];
+    E += e;
     b->max_n = std::max(b->max_n, ns[g]);
     if (N >= INT32_MAX || E >= INT32_MAX) {
       batch_release(b);
@@ -879,10 +881,10 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
   bool cp = true;
   for (int32_t g = 0; g < count; ++g) {
     cp = cp && cudaMemcpyAsync(b->rp + b->h_off[g], row_ptrs[g], (size_t)ns[g] * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, st) == cudaSuccess;
+                               cudaMemcpyDefault, st) == cudaSuccess;
     const int64_t e = eoff[g + 1] - eoff[g];
     if (e) cp = cp && cudaMemcpyAsync(b->ci + eoff[g], col_idxs[g], (size_t)e * sizeof(int32_t),
-                                      cudaMemcpyHostToDevice, st) == cudaSuccess;
+                                      cudaMemcpyDefault, st) == cudaSuccess;
   }
   const int32_t last = (int32_t)E;
   cp = cp && cudaMemcpyAsync(b->rp + N, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -905,6 +907,14 @@ int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *
   }
   *out = b;
   return GC_OK;
+}
+
+extern "C" {
+
+int gc_batch_load(int32_t count, const int32_t *const *row_ptrs, const int32_t *const *col_idxs, const int32_t *ns,
+                  uint32_t flags, void *stream, gc_batch **out) {
+  (void)flags;
+  return batch_load_impl(count, row_ptrs, col_idxs, ns, nullptr, stream, out);
 }
 
 int gc_batch_free(gc_batch *b) {
@@ -1163,6 +1173,53 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     stats->ms_lazy_update = (ph[3] - ph[2]) * 1e-6;
     stats->ms_gain_kernel = (ph[5] - ph[4]) * 1e-6;  // round-1 gains of every graph (P4)
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return GC_OK;
+}
+
+// gc_greedy_batch: the batched solve over graphs already loaded as handles.
+// Their device CSRs are gathered into one union (device-to-device copies), the
+// union is solved by gc_batch_greedy, and each group is handed back through its
+// own output pointer.
+int gc_greedy_batch(gc_graph *const *gs, const int32_t *ks, int32_t count, const gc_opts *opts,
+                    int32_t *const *out_groups, int64_t *out_farness, gc_stats *stats) {
+  if (!gs || !ks || count < 1 || !out_groups || !out_farness) {
+    set_error("bad argument to gc_greedy_batch");
+    return GC_EINVAL;
+  }
+  std::vector<const int32_t *> rps(count), cis(count);
+  std::vector<int32_t> ns(count);
+  std::vector<int64_t> nnz(count);
+  int64_t ksum = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    if (!gs[g] || !out_groups[g] || gs[g]->device != gs[0]->device) {
+      set_error("gc_greedy_batch: graph " + std::to_string(g) +
+                " is NULL, has no output array, or lives on another device");
+      return GC_EINVAL;
+    }
+    rps[g] = gs[g]->rp;
+    cis[g] = gs[g]->ci;
+    ns[g] = gs[g]->n;
+    nnz[g] = gs[g]->nnz;
+    ksum += ks[g] > 0 ? ks[g] : 0;
+  }
+  // the handles' own streams may still be writing their CSRs (adopted arrays)
+  for (int32_t g = 0; g < count; ++g)
+    if (cudaStreamSynchronize(gs[g]->stream) != cudaSuccess) {
+      set_error("gc_greedy_batch: a handle's stream failed");
+      return GC_ECUDA;
+    }
+  gc_batch *b = nullptr;
+  int rc = batch_load_impl(count, rps.data(), cis.data(), ns.data(), nnz.data(), gs[0]->stream, &b);
+  if (rc != GC_OK) return rc;
+  std::vector<int32_t> flat((size_t)std::max<int64_t>(1, ksum));
+  rc = gc_batch_greedy(b, ks, opts, flat.data(), out_farness, stats);
+  gc_batch_free(b);
+  if (rc != GC_OK) return rc;
+  size_t pos = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    memcpy(out_groups[g], flat.data() + pos, (size_t)ks[g] * sizeof(int32_t));
+    pos += (size_t)ks[g];
   }
   return GC_OK;
 }

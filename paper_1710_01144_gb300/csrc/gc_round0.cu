@@ -144,6 +144,48 @@ __device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw) 
   }
 }
 
+// The end of a vertex chunk in a bottom-up pass: lane w (if `want`) has found
+// the missing lanes `nw` among its frontier neighbours; record them in its
+// visited and next-frontier words and the next bitmap, and add them to this
+// thread's per-lane counts (lc[2k + h] counts lane 64k + 32h + (thread lane))
+// through one warp ballot per lane bit.
+template <int W>
+__device__ __forceinline__ void claim_words(int w, int base, int lane, bool want, const u64 (&nw)[W], u64 *vis,
+                                            u64 *nxt, uint32_t *fbn, unsigned int (&lc)[2 * W],
+                                            unsigned int &claims) {
+  bool has = false;
+#pragma unroll
+  for (int k = 0; k < W; ++k) has |= want && nw[k] != 0;
+  if (has) {  // only this thread writes w's words during the level
+    u64 vw[W];
+    ld_words<W>(vis + (size_t)w * W, vw);
+#pragma unroll
+    for (int k = 0; k < W; ++k) vw[k] |= nw[k];
+    st_words<W>(vis + (size_t)w * W, vw);
+    st_words<W>(nxt + (size_t)w * W, nw);
+    ++claims;
+  }
+  const unsigned hm = __ballot_sync(0xffffffffu, has);
+  if (lane == 0 && hm) atomicOr(&fbn[base >> 5], hm);  // both passes may mark this word
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const u64 x = has ? nw[k] : 0ull;
+    if (!__any_sync(0xffffffffu, x != 0)) continue;
+    unsigned c0 = 0, c1 = 0;
+#pragma unroll
+    for (int bt = 0; bt < 32; ++bt) {
+      const unsigned b0 = __ballot_sync(0xffffffffu, (x >> bt) & 1ull);
+      const unsigned b1 = __ballot_sync(0xffffffffu, (x >> (bt + 32)) & 1ull);
+      if (lane == bt) {
+        c0 = __popc(b0);
+        c1 = __popc(b1);
+      }
+    }
+    lc[2 * k] += c0;
+    lc[2 * k + 1] += c1;
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kR0Threads, 1)
     k_round0_wide(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
@@ -377,9 +419,6 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       }
       ++w_levels;
       // ---------- claims of distance d + 1, bottom-up ----------
-      u64 al[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) al[k] = s_alive[k];
       const u64 *cur = bufs[d % 3];
       const uint32_t *fbc = fbs[d % 3];
       u64 *nxt = bufs[(d + 1) % 3];
@@ -388,35 +427,32 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       unsigned int lc[2 * W];
 #pragma unroll
       for (int k = 0; k < 2 * W; ++k) lc[k] = 0;
+      unsigned int l_scan = 0, l_gath = 0, l_claim = 0;
+      // Pass A: rows of at most 32 entries, one thread each, kR0Ilp entries in
+      // flight; a lane word is loaded only while some of its missing lanes are
+      // unfound, and the scan stops once none is left.
       for (int base = gw * 32; base < n; base += nwarps * 32) {
         const int w = base + lane;
         int r0 = 0, r1 = 0;
         u64 miss[W];
         bool want = false;
-#pragma unroll
-        for (int k = 0; k < W; ++k) miss[k] = 0;
         if (w < n) {
           r0 = __ldg(rp + w);
           r1 = __ldg(rp + w + 1);
-          if (r1 - r0 <= kHeavyRow) {
-            ld_words<W>(vis + (size_t)w * W, miss);
+        }
+        if (r1 - r0 <= 32 && r1 > r0) {
+          ld_words<W>(vis + (size_t)w * W, miss);
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-              miss[k] = al[k] & ~miss[k];
-              want |= miss[k] != 0;
-            }
+          for (int k = 0; k < W; ++k) {
+            miss[k] = s_alive[k] & ~miss[k];
+            want |= miss[k] != 0;
           }
         }
-        const unsigned wm = __ballot_sync(0xffffffffu, want);
-        if (!wm) continue;
+        if (!__any_sync(0xffffffffu, want)) continue;
         u64 acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
-        // Rows of up to 32 entries: one thread each, kR0Ilp entries in flight;
-        // a lane word is loaded only while some of its missing lanes are still
-        // unfound, and the scan stops once none is left.
-        const bool own = want && (r1 - r0) <= 32;
-        if (own) {
+        if (want) {
           unsigned open = 0;  // words with lanes still unfound
 #pragma unroll
           for (int k = 0; k < W; ++k) open |= (miss[k] != 0 ? 1u : 0u) << k;
@@ -430,17 +466,44 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
             for (int q = 0; q < kR0Ilp; ++q) {
               if (!fr[q]) continue;
-              w_gath += 1;
+              ++l_gath;
               gather_open<W>(cur + (size_t)u[q] * W, open, acc);
             }
-            w_scan += (u64)min(kR0Ilp, r1 - e);
+            l_scan += (unsigned)min(kR0Ilp, r1 - e);
 #pragma unroll
             for (int k = 0; k < W; ++k)
               if ((acc[k] & miss[k]) == miss[k]) open &= ~(1u << k);
           }
+#pragma unroll
+          for (int k = 0; k < W; ++k) acc[k] &= miss[k];
         }
-        unsigned mm = __ballot_sync(0xffffffffu, want && !own);
-        while (mm) {  // longer light rows: the whole warp on one vertex
+        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim);
+      }
+      // Pass B: rows of 33 .. kHeavyRow entries, the whole warp on one vertex
+      // at a time (coalesced column loads, kR0Ilp per lane in flight).
+      for (int base = gw * 32; base < n; base += nwarps * 32) {
+        const int w = base + lane;
+        int r0 = 0, r1 = 0;
+        u64 miss[W];
+        bool want = false;
+        if (w < n) {
+          r0 = __ldg(rp + w);
+          r1 = __ldg(rp + w + 1);
+        }
+        if (r1 - r0 > 32 && r1 - r0 <= kHeavyRow) {
+          ld_words<W>(vis + (size_t)w * W, miss);
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            miss[k] = s_alive[k] & ~miss[k];
+            want |= miss[k] != 0;
+          }
+        }
+        unsigned mm = __ballot_sync(0xffffffffu, want);
+        if (!mm) continue;
+        u64 acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[k] = 0;
+        while (mm) {
           const int t = __ffs(mm) - 1;
           mm &= mm - 1;
           const int a0 = __shfl_sync(0xffffffffu, r0, t), a1 = __shfl_sync(0xffffffffu, r1, t);
@@ -463,12 +526,12 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
             for (int q = 0; q < kR0Ilp; ++q) {
               fr[q] = u[q] >= 0 && in_frontier(fbc, u[q]);
-              w_scan += u[q] >= 0;
+              l_scan += u[q] >= 0;
             }
 #pragma unroll
             for (int q = 0; q < kR0Ilp; ++q) {
               if (!fr[q]) continue;
-              w_gath += 1;
+              ++l_gath;
               gather_open<W>(cur + (size_t)u[q] * W, open, ac);
             }
 #pragma unroll
@@ -480,44 +543,14 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           }
           if (lane == t) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) acc[k] = ac[k];
+            for (int k = 0; k < W; ++k) acc[k] = ac[k] & ms[k];
           }
         }
-        u64 nw[W];
-        bool has = false;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          nw[k] = acc[k] & miss[k];
-          has |= nw[k] != 0;
-        }
-        w_claim += has;
-        if (has) {  // (vis reloaded: only this thread writes it during the level)
-          u64 vw[W];
-          ld_words<W>(vis + (size_t)w * W, vw);
-#pragma unroll
-          for (int k = 0; k < W; ++k) vw[k] |= nw[k];
-          st_words<W>(vis + (size_t)w * W, vw);
-          st_words<W>(nxt + (size_t)w * W, nw);
-        }
-        const unsigned hm = __ballot_sync(0xffffffffu, has);
-        if (lane == 0 && hm) fbn[base >> 5] = hm;  // this warp owns the bitmap word
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          if (!__any_sync(0xffffffffu, nw[k] != 0)) continue;
-          unsigned c0 = 0, c1 = 0;
-#pragma unroll
-          for (int bt = 0; bt < 32; ++bt) {
-            const unsigned b0 = __ballot_sync(0xffffffffu, (nw[k] >> bt) & 1ull);
-            const unsigned b1 = __ballot_sync(0xffffffffu, (nw[k] >> (bt + 32)) & 1ull);
-            if (lane == bt) {
-              c0 = __popc(b0);
-              c1 = __popc(b1);
-            }
-          }
-          lc[2 * k] += c0;
-          lc[2 * k + 1] += c1;
-        }
+        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim);
       }
+      u64 al[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) al[k] = s_alive[k];
       // heavy rows: chunks of kHeavyRow entries, partial ORs into hacc
       for (int c = gw; c < C; c += nwarps) {
         int lo = 0, hi = nh - 1;  // heavy row holding chunk c
@@ -550,8 +583,8 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
           for (int q = 0; q < kR0Ilp; ++q) {
             fr[q] = u[q] >= 0 && in_frontier(fbc, u[q]);
-            w_scan += u[q] >= 0;
-            w_gath += fr[q];
+            l_scan += u[q] >= 0;
+            l_gath += fr[q];
           }
 #pragma unroll
           for (int q = 0; q < kR0Ilp; ++q) {
@@ -580,6 +613,8 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
       for (int k = 0; k < 2 * W; ++k)
         if (lc[k]) atomicAdd(&s_lc[64 * (k >> 1) + 32 * (k & 1) + lane], lc[k]);
+      w_scan += l_scan;
+      w_gath += l_gath;
       ok = grid_sync(&ctl->bar, err, tns);
       if (!ok) break;
       // heavy rows: apply the accumulated lanes
@@ -603,7 +638,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           vh[k] |= nw[k];
         }
         if (!has) continue;
-        ++w_claim;
+        ++l_claim;
         st_words<W>(vis + (size_t)h * W, vh);
         st_words<W>(nxt + (size_t)h * W, nw);
         atomicOr(&fbn[h >> 5], 1u << (h & 31));
@@ -617,6 +652,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           }
         }
       }
+      w_claim += l_claim;
       __syncthreads();
       for (int j = tid; j < nb; j += T)
         if (s_lc[j]) {

@@ -38,7 +38,7 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_last_error", "gc_marginal_gains_static", "gc_mlp_create", "gc_mlp_free", "gc_mlp_set_params",
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
-           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds")
+           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH):
         lib.gc_batch_vertices.argtypes = [vp]
         lib.gc_batch_vertices.restype = i64
         lib.gc_batch_greedy.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_greedy_batch.argtypes = [vp, vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded",
@@ -390,3 +391,22 @@ class Batch:
             out.append(groups[pos:pos + k].copy())
             pos += k
         return out, far, st.as_dict()
+
+
+def greedy_batch(graphs, ks, active_target: int = 0, lanes: int = 0, timeout_ms: int = 0):
+    """gc_greedy_batch over existing Graph handles: (groups, farness, stats)."""
+    lib = load()
+    cnt = len(graphs)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    hs = (ctypes.c_void_p * cnt)(*[G._h.value for G in graphs])
+    outs = [np.zeros(max(int(k), 1), dtype=np.int32) for k in ks]
+    optr = (ctypes.c_void_p * cnt)(*[o.ctypes.data for o in outs])
+    far = np.zeros(cnt, dtype=np.int64)
+    o = Opts()
+    lib.gc_opts_default(ctypes.byref(o))
+    o.active_target, o.step_lanes = active_target, lanes
+    if timeout_ms:
+        o.timeout_ms = timeout_ms
+    st = Stats()
+    _check(lib.gc_greedy_batch(hs, ks.ctypes.data, cnt, ctypes.byref(o), optr, far.ctypes.data, ctypes.byref(st)))
+    return [out[:k] for out, k in zip(outs, ks)], far, st.as_dict()

@@ -98,3 +98,37 @@ def test_autotune_batch(gcm, tmp_path):
         assert len(entry["trials"]) == 2
         again, _ = autotune.tune_batch(B, ks, sizes, cache=cache, space=space)  # from the cache
         assert again == best
+
+
+def test_greedy_batch_over_handles(gcm):
+    """gc_greedy_batch: the batched solve over graphs already loaded as handles
+    (host-copied and adopted device arrays mixed); each group equals the
+    oracle's, and the handles still answer on their own afterwards."""
+    import torch
+
+    graphs, ks = mixed_batch()
+    ref = oracle_groups(graphs, ks)
+    handles, keep = [], []
+    for i, (rp, ci) in enumerate(graphs):
+        if i % 3 == 2:  # adopted device arrays
+            trp, tci = torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda()
+            keep.append((trp, tci))
+            handles.append(gcm.Graph(trp, tci, adopt=True))
+        else:
+            handles.append(gcm.Graph(rp, ci))
+    try:
+        for _ in range(2):
+            groups, far, _ = gcm.greedy_batch(handles, ks)
+            for (g, f), got, fv in zip(ref, groups, far):
+                np.testing.assert_array_equal(got, g)
+                assert fv == f
+        got, f, _ = handles[3].greedy(ks[3])
+        np.testing.assert_array_equal(got, ref[3][0])
+        bad = list(ks)
+        bad[4] = graphs[4][0].size  # k > n
+        with pytest.raises(gcm.GcError) as e:
+            gcm.greedy_batch(handles, bad)
+        assert e.value.code == gcm.GC_EINVAL
+    finally:
+        for G in handles:
+            G.close()
