@@ -352,16 +352,22 @@ int gc_mlp_train(gc_mlp *mlp, const float *X, const float *y, int32_t m, int32_t
 int gc_candidate_features(const int32_t *row_ptr, const int32_t *dS, const int64_t *ub, const int32_t *stamp,
                           const int64_t *two_hop, const int32_t *mx, const int32_t *cand, int32_t m, int32_t round,
                           int64_t prev_gain, float *X, void *stream);
-/* gc_set_proposal -- let gc_greedy (opts.use_proposal = 1, persistent rounds)
- * give `fill` of every 64-candidate batch (0 = 16) to the unevaluated
- * candidates whose stale bound most exceeds the network's predicted gain, the
- * rest to the largest bounds.  The network must outlive its use; NULL
- * disables.  Errors: GC_EINVAL (fill outside [0, 63]). */
+/* gc_set_proposal -- let gc_greedy (opts.use_proposal = 1) use the network:
+ * round 1's first exact batch becomes the 64 of the 1024 largest two-hop
+ * bounds with the largest predicted gain (instead of the 64 largest bounds);
+ * its best exact gain is the level every other round-1 candidate's bound must
+ * reach.  With fill > 0, `fill` of every 64-candidate batch of the persistent
+ * lazy rounds also go to the unevaluated candidates whose stale bound most
+ * exceeds the predicted gain, the rest to the largest bounds.  The network
+ * must outlive its use; NULL disables.  Errors: GC_EINVAL (fill outside
+ * [0, 63]). */
 int gc_set_proposal(gc_graph *g, const gc_mlp *mlp, int32_t fill);
-/* gc_set_recorder -- while set (cap > 0), gc_greedy's host-driven lazy steps
- * (opts.step_mode 1 or 2) append, for every candidate evaluated in rounds >= 2,
- * its features at selection time to X[cap][8] and log1p(exact gain) to y[cap]
- * (device arrays owned by the caller); gc_recorded returns the row count. */
+/* gc_set_recorder -- while set (cap > 0), gc_greedy appends training samples
+ * for the proposal: each candidate's features at selection time to X[cap][8]
+ * and log1p(exact gain) to y[cap] (device arrays owned by the caller), for
+ * the host-driven lazy steps of rounds >= 2 (opts.step_mode 1 or 2) and, with
+ * the round-1 bounds, for the 1024 largest round-1 bounds (all evaluated
+ * exactly in such a recording call); gc_recorded returns the row count. */
 int gc_set_recorder(gc_graph *g, float *X, float *y, int32_t cap);
 int64_t gc_recorded(gc_graph *g);
 

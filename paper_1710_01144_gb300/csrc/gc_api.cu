@@ -32,6 +32,7 @@ static int fail(int code, const std::string &msg) {
 constexpr int32_t kRound0GridMax = 256;  // round-0 survivors handled by grid-wide batches
 constexpr int kRound0Pivots = 8;         // round 0: at most this many pivot bounds
 constexpr int32_t kShallowLevels = 32;   // round 0: wide bottom-up batches up to this BFS depth
+constexpr int32_t kR1Propose = 1024;     // round 1: candidates the proposal chooses the first batch from
 
 #define GC_TRY(expr)              \
   do {                            \
@@ -623,7 +624,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         ev_used += 2;
         ev_k64.push_back(2);
         GC_CUDA(cudaEventRecord(le0, g->stream));
-        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal ? g->prop_params : nullptr, g->prop_fill,
+        GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal && g->prop_fill > 0 ? g->prop_params : nullptr,
+                                  g->prop_fill,
                                   step_form == 2, local_max, opts.lazy_ctas, pruned));
         GC_CUDA(cudaEventRecord(le1, g->stream));
         ++lazy_launches;
@@ -664,11 +666,31 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     GC_TRY(launch_round_begin(g));
     for (int step = 0;; ++step) {
       if (r == 1 && round1_bound) {
-        if (step == 0) {
-          // the 64 largest bounds first, as one grid-wide batch: their best
-          // exact gain is the level every other candidate's bound must reach
-          GC_TRY(launch_select(g, kSelLazy, r, kLanes, kTauHistogram, 0));
-          GC_TRY(launch_clamp_nsel(g, kLanes));
+        if (step == 0 && g->rec_X && g->rec_cap > 0) {
+          // recording run (training data for the proposal): the 1024 largest
+          // bounds, every one evaluated exactly and recorded with the
+          // features it had when it was chosen
+          GC_TRY(launch_select(g, kSelLazy, r, kR1Propose, kTauHistogram, 0));
+          GC_TRY(launch_clamp_nsel(g, kR1Propose));
+          GC_TRY(read_ctl(g));
+          const int32_t m1 = g->h_sctl->n_sel;
+          for (int32_t off = 0; off < m1; off += kLanes)
+            GC_TRY(grid_timed(kModeGain, g->list + off, std::min<int32_t>(kLanes, m1 - off), nullptr,
+                              g->lgain + off));
+          GC_TRY(launch_record(g, r, gains_picked[0]));
+        } else if (step == 0) {
+          // the first batch: its best exact gain is the level every other
+          // candidate's bound must reach.  Without the proposal, the 64
+          // largest bounds; with it, the 64 of the 1024 largest bounds whose
+          // predicted gain is largest
+          if (opts.use_proposal) {
+            GC_TRY(launch_select(g, kSelLazy, r, kR1Propose, kTauHistogram, 0));
+            GC_TRY(launch_clamp_nsel(g, kR1Propose));
+            GC_TRY(launch_round1_propose(g, gains_picked[0]));
+          } else {
+            GC_TRY(launch_select(g, kSelLazy, r, kLanes, kTauHistogram, 0));
+            GC_TRY(launch_clamp_nsel(g, kLanes));
+          }
           GC_TRY(grid_timed(kModeGain, g->list, 0, &g->sctl->n_sel, g->lgain));
         } else {
           // every unevaluated candidate whose bound reaches the best exact

@@ -378,6 +378,9 @@ int launch_clamp_nsel(gc_graph *g, int32_t cap);
 int launch_degree_keys(gc_graph *g);
 // features of list entries + log1p(gain) targets appended to the recorder
 int launch_record(gc_graph *g, int32_t round, long long prev_gain);
+// round 1 with the proposal: of the candidates in g->list (n_sel of them, the
+// largest bounds, at most 1024), keep the 64 with the largest predicted gain
+int launch_round1_propose(gc_graph *g, long long prev_gain);
 // mx[u] = max_{w in N(u)} d_S[w] into g->mx_buf (an upper bound for every later d_S)
 int launch_max_nbr(gc_graph *g);
 // the list of long rows used by the row-wise kernels' CTA-per-row companions

@@ -3,6 +3,7 @@
 // Adam, and a minibatch training loop -- all hand-written float32 kernels on
 // CUDA cores (the network is 4801 parameters; there is no dense contraction
 // large enough for tensor cores to matter).
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -213,6 +214,71 @@ int launch_record(gc_graph *g, int32_t round, long long prev_gain) {
   return GC_OK;
 }
 
+// Round-1 proposal (one CTA): the candidates list[0 .. *n_sel) (at most
+// kProposeMax, the largest two-hop bounds) are scored by the network -- one
+// warp per candidate, weights in shared memory -- and the kLanes with the
+// largest predicted gain (ties: larger bound, then smaller id) are written
+// back to list[0 .. 64) with *n_sel = min(64, count).  Only which candidates
+// the first exact batch of round 1 holds changes; every other candidate is
+// still compared with that batch's best exact gain by its bound.
+constexpr int kProposeMax = 1024;
+__global__ void __launch_bounds__(1024) k_round1_propose(int32_t *list, int32_t *n_sel, const float *__restrict__ W,
+                                                        const int32_t *__restrict__ rp, const int32_t *__restrict__ dS,
+                                                        const long long *__restrict__ ub,
+                                                        const int32_t *__restrict__ stamp,
+                                                        const long long *__restrict__ two_hop,
+                                                        const int32_t *__restrict__ mx, long long prev_gain) {
+  __shared__ float sw[kMlpParams];
+  __shared__ float sh[32][kMlpHidden];
+  __shared__ float s_key[kProposeMax];
+  __shared__ long long s_ub[kProposeMax];
+  __shared__ int s_id[kProposeMax];
+  const int m = min(*n_sel, kProposeMax);
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = W[i];
+  for (int i = threadIdx.x; i < kProposeMax; i += blockDim.x) {
+    s_id[i] = i < m ? list[i] : INT_MAX;
+    s_ub[i] = i < m ? ub[s_id[i]] : LLONG_MIN;
+    s_key[i] = -INFINITY;
+  }
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = wid; i < m; i += blockDim.x >> 5) {
+    float f[kMlpIn];
+    cand_features(s_id[i], rp, dS, ub, stamp, two_hop, mx, 1, prev_gain, f);
+    const float o = mlp_forward_warp(sw, f, sh[wid]);
+    if (lane == 0) s_key[i] = o;
+  }
+  __syncthreads();
+  // bitonic sort of (key desc, ub desc, id asc) over kProposeMax entries
+  for (int size = 2; size <= kProposeMax; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int i = threadIdx.x, j = i ^ stride;
+      if (j > i && i < kProposeMax) {
+        const bool up = (i & size) == 0;  // this pair sorts "first = better"
+        const bool ib = s_key[i] > s_key[j] || (s_key[i] == s_key[j] &&
+                        (s_ub[i] > s_ub[j] || (s_ub[i] == s_ub[j] && s_id[i] < s_id[j])));
+        if (ib != up) {
+          const float tk = s_key[i]; s_key[i] = s_key[j]; s_key[j] = tk;
+          const long long tu = s_ub[i]; s_ub[i] = s_ub[j]; s_ub[j] = tu;
+          const int ti = s_id[i]; s_id[i] = s_id[j]; s_id[j] = ti;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < kLanes && threadIdx.x < m) list[threadIdx.x] = s_id[threadIdx.x];
+  if (threadIdx.x == 0) *n_sel = min(m, kLanes);
+}
+
+int launch_round1_propose(gc_graph *g, long long prev_gain) {
+  if (!g->prop_params) return GC_EINVAL;
+  ++g->launches;
+  k_round1_propose<<<1, 1024, 0, g->stream>>>(g->list, &g->sctl->n_sel, g->prop_params, g->rp, g->dS, g->ub,
+                                              g->stamp, g->two_hop, g->mx, prev_gain);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
 int launch_features(gc_graph *g, const int32_t *list, int32_t m, const int32_t *m_dev, int32_t round,
                     long long prev_gain, float *X) {
   ++g->launches;
@@ -413,7 +479,7 @@ int gc_set_proposal(gc_graph *g, const gc_mlp *h, int32_t fill) {
     return GC_EINVAL;
   }
   g->prop_params = h ? h->params : nullptr;
-  g->prop_fill = h ? (fill ? fill : 16) : 0;
+  g->prop_fill = h ? fill : 0;  // 0: round 1's first batch only
   return GC_OK;
 }
 

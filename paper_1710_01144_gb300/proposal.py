@@ -17,8 +17,11 @@ def init_params(seed: int = 0) -> np.ndarray:
     return np.concatenate([w1.ravel(), np.zeros(64), w2.ravel(), np.zeros(64), w3, np.zeros(1)]).astype(np.float32)
 
 
-def record(graphs, k: int, cap: int = 400_000):
-    """(X, y) CUDA tensors of recorded samples from plain host-driven runs."""
+def record(graphs, k: int, cap: int = 400_000, lazy_rounds: bool = True):
+    """(X, y) CUDA tensors of recorded samples: per graph, the 1024 largest
+    round-1 two-hop bounds with their exact gains (a default-mode call) and,
+    with lazy_rounds, every candidate of the host-driven lazy steps of rounds
+    >= 2."""
     import torch
 
     Xs, ys = [], []
@@ -27,7 +30,9 @@ def record(graphs, k: int, cap: int = 400_000):
         y = torch.zeros(cap, dtype=torch.float32, device="cuda")
         with gc.Graph(rp, ci) as G:
             G.set_recorder(X, y)
-            G.greedy(k, step_mode=1, eval_per_step=64, step_lanes=8)
+            G.greedy(min(k, 2))
+            if lazy_rounds:
+                G.greedy(k, step_mode=1, eval_per_step=64, step_lanes=8)
             m = G.recorded()
             G.set_recorder(None, None)
         Xs.append(X[:m].clone())

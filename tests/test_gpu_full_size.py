@@ -118,3 +118,34 @@ def test_greedy_rmat24_k50_full_size(gcm):
             assert f == ft[-1]
         # the farness of the first ten picks, recomputed by one oracle BFS
         assert G.farness(grp[:10]) == ft[9] == oracle.farness(rp, ci, grp[:10])
+
+
+def test_mixed_batch_all_256_vs_oracle(gcm):
+    """The whole 256-graph mixed workload (25M vertices) in one batched launch,
+    replayed from a captured CUDA graph, against CPU Greedy++'s answers stored
+    in tests/golden/batch256_groups.txt (written by make_batch256.py, which
+    calls only the oracle)."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch256_groups.txt")
+    gold = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        d = {f[j]: f[j + 1] for j in range(3, 13, 2)}
+        gold.append((int(d["n"]), int(d["nnz"]), int(d["k"]), d["sha256"], int(d["farness"]),
+                     np.array([int(x) for x in f[f.index("group") + 1:]], dtype=np.int32)))
+    assert len(gold) == 256
+    items = graphgen.batch_params(256, seed=1)
+    graphs = [graphgen.batch_graph(it) for it in items]
+    for (rp, ci), (n, nnz, k, sha, _, _) in zip(graphs, gold):
+        assert rp.size - 1 == n and ci.size == nnz and _csr_sha256(rp, ci)[:32] == sha
+    ks = [g[2] for g in gold]
+    with gcm.Batch(graphs) as B:
+        for _ in range(2):  # record, then replay the captured graph
+            groups, far, st = B.greedy(ks, capture=True)
+            for i, (got, g) in enumerate(zip(groups, gold)):
+                np.testing.assert_array_equal(got, g[5], err_msg="graph %d" % i)
+                assert far[i] == g[4]
+        assert st["graph_replay"] == 1
