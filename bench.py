@@ -234,15 +234,15 @@ def round0_kernel_bytes(t, n) -> float:
     """Algorithmic bytes of the wide round-0 kernel (bottom-up bit-parallel
     BFScut, B = r0_width lanes, B/8 bytes per lane word): per bottom-up level,
     every vertex's row pointers (8 B) and visited word (B/8 B); 4 B per
-    adjacency entry read; per vertex that claims lanes its visited and claim
-    words written (2 B/8 B) and, once the batch moves on, its claim word
-    cleared (B/8 B); per top-down adjacency entry 4 B plus the visited and claim
-    words it sets (2 x 8 B); per batch the dense clear of the visited words
-    (n B/8 B).  Gathered frontier words are not counted: each is a re-read of a
-    word already counted when it was written (most of them hit L2)."""
+    adjacency entry read; per vertex whose claim is written, its visited and
+    claim words (2 B/8 B) and the later clear of the claim word (B/8 B); per
+    top-down adjacency entry 4 B plus the two 8-byte words it sets and their
+    later clear (32 B); per batch that wrote bottom-up levels the dense clear
+    of the visited words (n B/8 B).  Gathered frontier words are not counted:
+    each re-reads a word already counted when it was written (most hit L2)."""
     wb = t["r0_width"] / 8.0 if t["r0_width"] else 0.0
     return (t["r0_levels"] * n * (8.0 + wb) + 4.0 * t["r0_bu_scanned"] + 3.0 * wb * t["r0_bu_rows"] +
-            20.0 * t["r0_td_edges"] + t["r0_batches"] * n * wb)
+            36.0 * t["r0_td_edges"] + t["r0_dense_clears"] * n * wb)
 
 
 def golden_for(scale: int, k: int):

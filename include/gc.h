@@ -71,6 +71,9 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
                                >= 1 instead of the pruned one built after round 0
                                (rows without neighbours at d_S <= 1); work only,
                                the group is the same */
+#define GC_OPT_R0_FULL_LEVELS 0x10u /* gc_greedy round 0 (wide batches): write every
+                               bottom-up level's lane words instead of counting
+                               distance 2 only in first-pass batches; work only */
 #define GC_OPT_NO_ROUND1_BOUND 0x8u /* gc_greedy: evaluate every vertex in round 1
                                instead of only those whose two-hop upper bound
                                reaches the best exact gain; work only */
@@ -182,10 +185,11 @@ typedef struct gc_stats {
   double ms_r0_topdown;      /* the top-down first level, */
   double ms_r0_bottomup;     /* the bottom-up levels with their BFScut folds, */
   double ms_r0_clear;        /* and the clearing of the lane words after each batch */
-  int64_t r0_bu_rows;        /* bottom-up: vertices that claimed at least one lane */
+  int64_t r0_bu_rows;        /* bottom-up: vertices whose words a claim wrote */
   int64_t r0_bu_scanned;     /* bottom-up: adjacency entries read */
   int64_t r0_bu_gathers;     /* bottom-up: frontier lane words gathered */
   int64_t r0_width;          /* its candidates per batch (0: not used) */
+  int64_t r0_dense_clears;   /* its batches that cleared every visited word */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -426,7 +426,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   size_t ev_used = 0;
   int64_t r0_stats[3] = {0, 0, 0};  // wide round-0 kernel: batches, bottom-up levels, top-down entries
   double r0_ms[4] = {0, 0, 0, 0};     // and its phases: selection, top-down, bottom-up, clears
-  int64_t r0_bu[3] = {0, 0, 0};       // its bottom-up rows with missing lanes, entries read, words gathered
+  int64_t r0_bu[4] = {0, 0, 0, 0};    // its bottom-up claiming rows, entries read, words gathered, dense clears
   bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
@@ -510,10 +510,11 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     ev_used += 2;
     ev_k64.push_back(3);
     GC_CUDA(cudaEventRecord(e0, g->stream));
-    GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w, tns));
+    GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w, !(opts.flags & GC_OPT_R0_FULL_LEVELS),
+                              tns));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     R0Ctl r0c;
-    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 11 * sizeof(unsigned long long),
+    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 14 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, g->stream));
     GC_TRY(sync(g));
     r0_wide_lanes = (int64_t)r0c.lanes;
@@ -524,6 +525,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     r0_bu[0] = (int64_t)r0c.bu_rows;
     r0_bu[1] = (int64_t)r0c.bu_scanned;
     r0_bu[2] = (int64_t)r0c.bu_gathers;
+    r0_bu[3] = (int64_t)r0c.dense_clears;
   } else if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)
@@ -812,6 +814,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->r0_bu_scanned = r0_bu[1];
     stats->r0_bu_gathers = r0_bu[2];
     stats->r0_width = r0_w * kLanes;
+    stats->r0_dense_clears = r0_bu[3];
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

@@ -180,7 +180,7 @@ struct R0Ctl {
   int32_t cursor;   // next survivor-list position
   int32_t dcursor;  // next deferred position
   int32_t n_defer;  // deferred candidates
-  int32_t pad;
+  int32_t count_only;  // this batch: distance 2 counted without writing lane words (see gc_round0.cu)
   long long best_f;  // best exact farness (written by CTA 0 between batches)
   int32_t cand[kR0MaxLanes];  // the batch: candidate ids and their list positions
   int32_t pos[kR0MaxLanes];
@@ -189,6 +189,8 @@ struct R0Ctl {
   unsigned long long td_edges;                 // adjacency entries of the top-down levels
   unsigned long long ns[4];  // CTA 0's clock: selection, top-down level, bottom-up levels with folds, clears
   unsigned long long bu_rows, bu_scanned, bu_gathers;  // bottom-up: vertices that claimed lanes, entries read, frontier words gathered
+  unsigned long long co_lanes, co_surv;  // lanes of count-only batches, and those of them deferred
+  unsigned long long dense_clears;       // batches that cleared every visited word
 };
 
 // Selection / reduction control block (lives across a whole greedy call).
@@ -408,9 +410,10 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
 int lazy_occupancy(int *blocks_per_sm);
 // round 0 on shallow graphs: f({v}) or -1 (cut / bound above the best) into
 // lgain[i] for list[0..m), B = 64 W lanes per batch (W in {1, 2, 4, 8}); a batch
-// whose live lanes drop below defer_below after distance 2 defers them
+// whose live lanes drop below defer_below after distance 2 defers them;
+// count_only lets first-pass batches count distance 2 without writing it
 int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
-                       int64_t timeout_ns);
+                       bool count_only, int64_t timeout_ns);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 }  // namespace gc

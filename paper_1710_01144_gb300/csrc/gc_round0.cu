@@ -127,14 +127,15 @@ __device__ __forceinline__ long long r0_block_min(long long v, long long *sh) {
 
 __device__ __forceinline__ bool in_frontier(const uint32_t *fb, int u) { return (fb[u >> 5] >> (u & 31)) & 1u; }
 
-// Zero the claim words of every vertex marked in bitmap fb, and the bitmap.
+// Zero the words of every vertex marked in bitmap fb, and (clear_bitmap) the
+// bitmap.
 template <int W>
-__device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw) {
+__device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw, bool clear_bitmap = true) {
   const int T = blockDim.x;
   for (int x = blockIdx.x * T + threadIdx.x; x < nbw; x += gridDim.x * T) {
     uint32_t bits = fb[x];
     if (!bits) continue;
-    fb[x] = 0;
+    if (clear_bitmap) fb[x] = 0;
     const u64 z[W] = {};
     do {
       const int b = __ffs(bits) - 1;
@@ -152,11 +153,11 @@ __device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw) 
 template <int W>
 __device__ __forceinline__ void claim_words(int w, int base, int lane, bool want, const u64 (&nw)[W], u64 *vis,
                                             u64 *nxt, uint32_t *fbn, unsigned int (&lc)[2 * W],
-                                            unsigned int &claims) {
+                                            unsigned int &claims, bool write) {
   bool has = false;
 #pragma unroll
   for (int k = 0; k < W; ++k) has |= want && nw[k] != 0;
-  if (has) {  // only this thread writes w's words during the level
+  if (has && write) {  // only this thread writes w's words during the level
     u64 vw[W];
     ld_words<W>(vis + (size_t)w * W, vw);
 #pragma unroll
@@ -166,7 +167,7 @@ __device__ __forceinline__ void claim_words(int w, int base, int lane, bool want
     ++claims;
   }
   const unsigned hm = __ballot_sync(0xffffffffu, has);
-  if (lane == 0 && hm) atomicOr(&fbn[base >> 5], hm);  // both passes may mark this word
+  if (write && lane == 0 && hm) atomicOr(&fbn[base >> 5], hm);  // both passes may mark this word
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     const u64 x = has ? nw[k] : 0ull;
@@ -187,12 +188,13 @@ __device__ __forceinline__ void claim_words(int w, int base, int lane, bool want
 }
 
 template <int W>
-__global__ void __launch_bounds__(kR0Threads, 1)
+__global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
     k_round0_wide(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
                   const int32_t *__restrict__ list, int32_t m, const long long *__restrict__ key, long long *lgain,
                   int32_t *defer, R0Ctl *ctl, GainCtl *gctl, u64 *vis, u64 *buf_a, u64 *buf_b, u64 *buf_c,
                   uint32_t *fb_a, uint32_t *fb_b, uint32_t *fb_c, const int32_t *__restrict__ heavy, int32_t nh,
-                  const int32_t *__restrict__ hcp, u64 *hacc, int32_t defer_below, unsigned long long tns) {
+                  const int32_t *__restrict__ hcp, u64 *hacc, int32_t defer_below, int32_t allow_count_only,
+                  unsigned long long tns) {
   constexpr int B = 64 * W;
   constexpr int T = kR0Threads;
   __shared__ int s_cand[B], s_pos[B];
@@ -274,6 +276,9 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       if (lane == 0) {
         ctl->phase = phase;
         ctl->nb = nb;
+        // count distance 2 only while at most a quarter of such lanes survive
+        // their distance-2 cut (the survivors are rerun in full batches)
+        ctl->count_only = allow_count_only && phase == 0 && 4 * ctl->co_surv <= ctl->co_lanes + 64;
       }
       for (int i = lane; i < 3 * B; i += 32) ctl->tot[i / B][i % B] = 0;  // rows are kR0MaxLanes apart
     }
@@ -282,6 +287,8 @@ __global__ void __launch_bounds__(kR0Threads, 1)
     const int nb = *(volatile int32_t *)&ctl->nb;
     if (nb == 0) break;
     const int phase = *(volatile int32_t *)&ctl->phase;
+    const bool co = *(volatile int32_t *)&ctl->count_only != 0;
+    bool wrote = false;  // a bottom-up level wrote visited words (else they are sparse)
     long long bf = *(volatile long long *)&ctl->best_f;
     // ---------- lane state (every CTA keeps the same copy) ----------
     for (int j = tid; j < B; j += T) {
@@ -395,23 +402,23 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       int alive_cnt = 0;
 #pragma unroll
       for (int k = 0; k < W; ++k) alive_cnt += __popcll(s_alive[k]);
-      if (alive_cnt > 0 && phase == 0 && d >= 2 && alive_cnt < defer_below) {
-        // few live lanes: run them later in full batches of their own
-        if (b == 0) {
-          int j = 0;
-          if (tid == 0) {
-            int at = ctl->n_defer;
-            for (j = 0; j < nb; ++j)
-              if ((s_alive[j >> 6] >> (j & 63)) & 1ull) {
-                defer[2 * at] = s_cand[j];
-                defer[2 * at + 1] = s_pos[j];
-                ++at;
-              }
-            ctl->n_defer = at;
-          }
+      if (alive_cnt > 0 && phase == 0 && d >= 2 && (co || alive_cnt < defer_below)) {
+        // few live lanes, or a count-only batch (no distance-2 frontier was
+        // written): run them later in full batches of their own
+        if (b == 0 && tid == 0) {
+          int at = ctl->n_defer;
+          for (int j = 0; j < nb; ++j)
+            if ((s_alive[j >> 6] >> (j & 63)) & 1ull) {
+              defer[2 * at] = s_cand[j];
+              defer[2 * at + 1] = s_pos[j];
+              ++at;
+            }
+          ctl->n_defer = at;
         }
+        if (co && b == 0 && tid == 0) ctl->co_surv += (unsigned long long)alive_cnt;
         alive_cnt = 0;
       }
+      if (co && d == 2 && b == 0 && tid == 0) ctl->co_lanes += (unsigned long long)nb;
       __syncthreads();
       if (alive_cnt == 0) {
         any_alive = false;
@@ -419,6 +426,10 @@ __global__ void __launch_bounds__(kR0Threads, 1)
       }
       ++w_levels;
       // ---------- claims of distance d + 1, bottom-up ----------
+      // (a count-only batch counts distance 2 and writes nothing: its lanes
+      // end or are deferred at the next fold)
+      const bool write_lv = !(co && d == 1);
+      wrote |= write_lv;
       const u64 *cur = bufs[d % 3];
       const uint32_t *fbc = fbs[d % 3];
       u64 *nxt = bufs[(d + 1) % 3];
@@ -477,7 +488,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
 #pragma unroll
           for (int k = 0; k < W; ++k) acc[k] &= miss[k];
         }
-        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim);
+        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim, write_lv);
       }
       // Pass B: rows of 33 .. kHeavyRow entries, the whole warp on one vertex
       // at a time (coalesced column loads, kR0Ilp per lane in flight).
@@ -546,7 +557,7 @@ __global__ void __launch_bounds__(kR0Threads, 1)
             for (int k = 0; k < W; ++k) acc[k] = ac[k] & ms[k];
           }
         }
-        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim);
+        claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim, write_lv);
       }
       u64 al[W];
 #pragma unroll
@@ -638,10 +649,12 @@ __global__ void __launch_bounds__(kR0Threads, 1)
           vh[k] |= nw[k];
         }
         if (!has) continue;
-        ++l_claim;
-        st_words<W>(vis + (size_t)h * W, vh);
-        st_words<W>(nxt + (size_t)h * W, nw);
-        atomicOr(&fbn[h >> 5], 1u << (h & 31));
+        if (write_lv) {
+          ++l_claim;
+          st_words<W>(vis + (size_t)h * W, vh);
+          st_words<W>(nxt + (size_t)h * W, nw);
+          atomicOr(&fbn[h >> 5], 1u << (h & 31));
+        }
 #pragma unroll
         for (int k = 0; k < W; ++k) {
           u64 x = nw[k];
@@ -667,14 +680,27 @@ __global__ void __launch_bounds__(kR0Threads, 1)
     lap(2);
     (void)any_alive;
     // ---------- batch end: every lane word back to zero ----------
+    if (!wrote) {
+      // only the candidates and the distance-1 frontier (bitmap 1) carry
+      // visited bits: clear those words, then the frontier
+      if (b == 0)
+        for (int j = tid; j < nb; j += T) {
+          const u64 z[W] = {};
+          st_words<W>(vis + (size_t)s_cand[j] * W, z);
+        }
+      clear_frontier<W>(vis, fbs[1], nbw, false);
+      __syncthreads();
+      if (!grid_sync(&ctl->bar, err, tns)) break;
+    }
     clear_frontier<W>(bufs[d % 3], fbs[d % 3], nbw);
     clear_frontier<W>(bufs[(d + 2) % 3], fbs[(d + 2) % 3], nbw);
-    {
+    if (wrote) {
       const size_t words = (size_t)n * W;
       for (size_t i = ((size_t)b * T + tid) * 2; i < words; i += (size_t)G * T * 2) {
         if (i + 1 < words) *reinterpret_cast<ulonglong2 *>(vis + i) = make_ulonglong2(0ull, 0ull);
         else vis[i] = 0;
       }
+      if (b == 0 && tid == 0) ++ctl->dense_clears;
     }
     if (b == 0 && tid == 0) ctl->best_f = bf;
     if (!grid_sync(&ctl->bar, err, tns)) break;
@@ -785,7 +811,7 @@ static int round0_workspace(gc_graph *g, int W) {
 }
 
 int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
-                       int64_t timeout_ns) {
+                       bool count_only, int64_t timeout_ns) {
   if (m <= 0) return GC_OK;
   if (W != 1 && W != 2 && W != 4 && W != 8) return GC_EINVAL;
   int rc = round0_workspace(g, W);
@@ -811,10 +837,12 @@ int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *l
   int32_t nh = g->r0_nh;
   unsigned long long *hacc = g->r0_hacc;
   unsigned long long tns = (unsigned long long)timeout_ns;
+  int32_t allow_co = count_only ? 1 : 0;
   void *args[] = {(void *)&rp,   (void *)&ci,   (void *)&n,    (void *)&key_list, (void *)&m,     (void *)&key,
                   (void *)&lgain, (void *)&defer, (void *)&ctl, (void *)&gctl,     (void *)&vis,   (void *)&b0,
                   (void *)&b1,   (void *)&b2,   (void *)&f0,   (void *)&f1,       (void *)&f2,    (void *)&heavy,
-                  (void *)&nh,   (void *)&hcp,  (void *)&hacc, (void *)&defer_below, (void *)&tns};
+                  (void *)&nh,   (void *)&hcp,  (void *)&hacc, (void *)&defer_below, (void *)&allow_co,
+                  (void *)&tns};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel(round0_fn(W), dim3(grid), dim3(kR0Threads), args, round0_dyn_smem(W),
                                       g->stream));
