@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -484,6 +485,19 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     // faster, their wider gathers cancel the halved batch count)
     const int want = opts.round0_lanes > 0 ? opts.round0_lanes : (n_surv > 128 ? 256 : n_surv > 64 ? 128 : 64);
     r0_w = want >= 512 ? 8 : want >= 256 ? 4 : want >= 128 ? 2 : 1;
+    if (opts.round0_lanes == 0) {
+      // The wide batches pay about one pass over the adjacency per batch;
+      // the 64-lane top-down searches pay about the survivors' two-hop counts
+      // (their scans to distance 2, where most searches are cut).  Take the
+      // wide batches only when those counts are the larger: survivors next to
+      // hubs (R-MAT), not flat graphs whose every vertex survives (BA).
+      GC_TRY(launch_sum_two_hop(g, (unsigned long long *)g->g3));
+      unsigned long long two_hop_sum = 0;
+      GC_CUDA(cudaMemcpyAsync(&two_hop_sum, g->g3, sizeof(two_hop_sum), cudaMemcpyDeviceToHost, g->stream));
+      GC_TRY(sync(g));
+      const double passes = std::ceil((double)n_surv / (64.0 * r0_w));
+      if ((double)two_hop_sum < passes * (double)g->nnz) r0_w = 0;
+    }
   }
   // Many survivors (deep graphs, where the degree bound is weak): tighten the
   // bounds with the BFS levels of pivots (triangle inequality, see

@@ -751,6 +751,27 @@ int launch_round1_bound(gc_graph *g) {
   return GC_OK;
 }
 
+// Round-0 work estimate: the sum over list[0..m) of two_hop[v] (sum over the
+// neighbours of v of deg - 1), the adjacency entries a search from v scans to
+// reach distance 2.  Accumulated into *out (zeroed by the caller).
+__global__ void k_sum_two_hop(const int32_t *__restrict__ list, const int32_t *m_dev,
+                              const long long *__restrict__ two_hop, unsigned long long *out) {
+  __shared__ long long sh[32];
+  const int m = *m_dev;
+  long long s = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) s += two_hop[list[i]];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0 && s) atomicAdd(out, (unsigned long long)s);
+}
+
+int launch_sum_two_hop(gc_graph *g, unsigned long long *out) {
+  ++g->launches;
+  GC_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long), g->stream));
+  k_sum_two_hop<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->list, &g->sctl->n_sel, g->two_hop, out);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
 // ub[v] = -1 for members (d_S[v] = 0), +infinity for every other vertex: the
 // starting point of k_bound_refresh when no earlier bound exists.
 __global__ void k_init_ub(const int32_t *__restrict__ dS, int32_t n, long long *ub) {

@@ -395,6 +395,8 @@ int launch_round1_bound(gc_graph *g);
 int launch_bound_refresh(gc_graph *g);
 // ub[v] = -1 where d_S[v] = 0, else +infinity
 int launch_init_ub(gc_graph *g);
+// *out = sum of two_hop[v] over the selected list g->list[0 .. sctl->n_sel)
+int launch_sum_two_hop(gc_graph *g, unsigned long long *out);
 // round 0: key[v] = -max(LB(v), LB_p(v)) with p the source of the BFS now in d_S
 int launch_pivot_bound(gc_graph *g);
 // round 0: an exactly evaluated pivot (sctl->arg_id, farness sctl->sum) becomes
