@@ -74,9 +74,10 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
 #define GC_OPT_R0_FULL_LEVELS 0x10u /* gc_greedy round 0 (wide batches): write every
                                bottom-up level's lane words instead of counting
                                distance 2 only in first-pass batches; work only */
-#define GC_OPT_NO_ROUND1_BOUND 0x8u /* gc_greedy: evaluate every vertex in round 1
-                               instead of only those whose two-hop upper bound
-                               reaches the best exact gain; work only */
+#define GC_OPT_NO_ROUND1_BOUND 0x8u /* gc_greedy, gc_batch_greedy: evaluate every
+                               vertex in round 1 instead of only those whose
+                               two-hop upper bound reaches the best exact
+                               gain, and skip the bound refresh; work only */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
@@ -119,7 +120,7 @@ typedef struct gc_opts {
   int32_t batch_grid_min_n; /* gc_batch_greedy: graphs with at least this many
                               vertices run their lazy rounds grid-wide, one
                               graph at a time; the others CTA-locally;
-                              0 = 65536, negative = none */
+                              0 = 2097152, negative = none */
   int32_t round0_lanes;    /* gc_greedy round 0 on shallow graphs (the BFS from
                               the lowest-bound vertex has at most 32 levels):
                               candidates per wide bottom-up batch, 64, 128, 256

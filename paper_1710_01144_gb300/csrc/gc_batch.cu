@@ -50,6 +50,8 @@ struct BatchCtl {
   long long dbg[4];  // first failed check: phase, graph, expected, found
   unsigned long long ns_ph[6];  // end of round 0 (P2), round 1 (P5), lazy rounds (P6), check (P7),
                                 // start and end of the round-1 gains (P4)
+  unsigned long long ns_lazy[3];  // lazy rounds, summed over graphs: selection (with list
+                                  // rebuilds), gain batches, d_S updates
   int32_t blk_tot[kMaxGridCtas];
 };
 
@@ -93,11 +95,18 @@ struct BatchArgs {
   GridSelScratch *gsel;  // their grid-wide selection
   int32_t *gx;        // their scratch: 3 * max_n
   int32_t grid_min_n; // graphs with at least this many vertices run their lazy rounds grid-wide
+  int32_t bounded;    // round 1 with two-hop bounds (batch_round1_bounded) and the refresh after it
+  long long *g3;      // [2 * count]: sum of (d - 3)^+ per graph for round 1, then for the refresh
   unsigned long long tns;
 };
 
 constexpr int kBatchThreads = kGainThreads;
-constexpr int32_t kBatchGridMinN = 65536;  // lazy rounds grid-wide from this many vertices
+// lazy rounds grid-wide from this many vertices.  On the 256-graph mix
+// (10^4 to 5 x 10^5 vertices per graph) the whole solve took 1.72 s with
+// 65,536, 1.70 s with 262,144 and 1.56 s with every graph CTA-local: one CTA
+// per graph in parallel beats graphs of that size taking the grid in turn, so
+// only much larger graphs go grid-wide
+constexpr int32_t kBatchGridMinN = 1 << 21;
 
 static __device__ __forceinline__ bool bsync(const BatchArgs &a) { return grid_sync(&a.ctl->bar, &a.ctl->err, a.tns); }
 
@@ -141,10 +150,10 @@ static __device__ bool batch_prune(const BatchArgs &a) {
     const int off = block_excl_scan(v, s_scan, &total);
     if (j < G) s_off[j] = run + off;
     run += total;
-    __syncthreads();
+    cta_sync();
   }
   long long carry = s_off[b];
-  __syncthreads();
+  cta_sync();
   for (int base = lo; base < hi; base += T) {
     const int v = base + tid;
     const int x = v < hi ? a.q0[v] : 0;
@@ -176,29 +185,60 @@ static __device__ bool batch_prune(const BatchArgs &a) {
   return bsync(a);
 }
 
+
+static __device__ bool grid_refresh_graph(const BatchArgs &a, int g);
+static __device__ void cta_build_list(const BatchArgs &a, int g);
+
 // Lazy rounds (Sec. 4.2) of one big graph g by the whole grid: every CTA
-// takes part in each step's decision and selection (grid_lazy_step) over all
-// of g's candidates, evaluates the 64 selected as one grid-wide 64-lane batch,
-// and each pick updates d_S by the grid relabel BFS, checked against the
-// pick's gain.  Every CTA runs the same loop.
+// takes part in each step's decision and selection (grid_lazy_step) over the
+// graph's active list (built in P5), evaluates the 64 selected as one
+// grid-wide 64-lane batch, and each pick updates d_S by the grid relabel BFS,
+// checked against the pick's gain.  When the list cannot certify a pick, the
+// graph's bounds are refreshed and the list rebuilt; a second failure in the
+// same round lists every candidate from then on.  Every CTA runs the same loop.
 static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
   const int tid = threadIdx.x, b = blockIdx.x;
   LazyCtl *lc = &a.lc[g];
   const int o = a.off[g], ng = a.ng[g];
-  if (b == 0 && tid == 0) lc->theta = LLONG_MIN;  // the list is every candidate
-  if (!bsync(a)) return false;
-  bool fold = false;
+  bool every = false, fold = false;
+  int rebuilt = -1;  // round of the last rebuild
+  unsigned long long t_ph[3] = {0, 0, 0}, t_mark = global_ns();  // CTA 0's phase clocks
+  auto lap = [&](int q) {
+    if (b == 0 && tid == 0) {
+      const unsigned long long now = global_ns();
+      t_ph[q] += now - t_mark;
+      t_mark = now;
+    }
+    __syncwarp();  // reconverge warp 0 before the warp-synchronous code that follows
+  };
   for (;;) {
     const int r = *(volatile int32_t *)&lc->round;
     if (r >= a.kk[g]) break;
+    const int32_t *list = every ? a.iota + o : a.act + (size_t)g * a.A;
+    const int m = every ? ng : *(volatile int32_t *)&a.act_n[g];
     int dec;
-    if (!grid_lazy_step(a.iota + o, ng, a.ub, a.stamp, nullptr, nullptr, lc, a.gg, fold, lc->sel, lc->selpos,
+    if (!grid_lazy_step(list, m, a.ub, a.stamp, nullptr, nullptr, lc, a.gg, fold, lc->sel, lc->selpos,
                         lc->gsel, kLanes, a.gsel, &a.ctl->bar, &a.ctl->err, a.tns, &dec))
       return false;
     if (!bsync(a)) return false;
-    if (dec == 2) {  // cannot happen with every candidate listed
-      if (b == 0 && tid == 0) check_fail(a.ctl, 6, g, 1, 2);
-      return false;
+    lap(0);
+    if (dec == 2) {
+      if (every) {  // cannot happen with every candidate listed
+        if (b == 0 && tid == 0) check_fail(a.ctl, 6, g, 1, 2);
+        return false;
+      }
+      if (rebuilt == r) {
+        every = true;
+        if (b == 0 && tid == 0) lc->theta = LLONG_MIN;
+      } else {
+        rebuilt = r;
+        if (!grid_refresh_graph(a, g)) return false;
+        if (b == 0) cta_build_list(a, g);
+      }
+      if (!bsync(a)) return false;
+      lap(0);
+      fold = false;
+      continue;
     }
     if (dec == 0) {
       if (!grid_gain_batch<kModeGain>(a.rpf, a.cif, a.N, a.dS, lc->sel, 0, &lc->n_sel, lc->gsel, a.ws, a.gx,
@@ -208,6 +248,7 @@ static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
       if (b == 0 && tid == 0 && *(volatile int32_t *)&a.gg->err)
         atomicExch(&a.ctl->err, *(volatile int32_t *)&a.gg->err);
       if (!bsync(a)) return false;  // workspace clean, gains visible
+      lap(1);
       fold = true;
       continue;
     }
@@ -237,6 +278,11 @@ static __device__ bool batch_grid_lazy(const BatchArgs &a, int g) {
       lc->round = r + 1;
     }
     if (!bsync(a)) return false;
+    lap(2);
+  }
+  if (b == 0 && tid == 0) {
+    atomicAdd((unsigned long long *)&a.ctl->iterations, (unsigned long long)lc->steps);
+    for (int q = 0; q < 3; ++q) atomicAdd(&a.ctl->ns_lazy[q], t_ph[q]);
   }
   return true;
 }
@@ -286,6 +332,368 @@ static __device__ int cta_argmin_f0(const BatchArgs &a, int g) {
   return bid;
 }
 
+// One CTA: the want-th largest of graph g's bounds ub >= 0, by a radix select
+// over their bytes (256-bin shared histograms, most significant byte first).
+// *c gets how many bounds are >= 0; when *c <= want the result is -1.  *need
+// gets how many of the bounds equal to the result belong to the top `want`
+// (the others above it: want - *need of them).
+static __device__ long long cta_kth_bound(const long long *ub, int o, int n, int want, long long *c,
+                                          int *need) {
+  __shared__ int s_hist[256];
+  __shared__ int s_pick[2];
+  __shared__ long long s_ll[32];
+  const int tid = threadIdx.x, T = blockDim.x;
+  long long umax = -1, cnt = 0;
+  for (int i = tid; i < n; i += T) {
+    const long long u = ub[o + i];
+    if (u >= 0) {
+      umax = max(umax, u);
+      ++cnt;
+    }
+  }
+  umax = block_max_ll(umax, s_ll);
+  cnt = block_sum(cnt, s_ll);
+  *c = cnt;
+  *need = 0;
+  if (cnt <= want) return -1;
+  unsigned long long prefix = 0, mask = 0;
+  int nd = want;
+  const int top = umax > 0 ? 63 - __clzll((unsigned long long)umax) : 0;
+  for (int shift = (top / 8) * 8; shift >= 0; shift -= 8) {
+    for (int j = tid; j < 256; j += T) s_hist[j] = 0;
+    cta_sync();
+    for (int i = tid; i < n; i += T) {
+      const long long u = ub[o + i];
+      if (u >= 0 && ((unsigned long long)u & mask) == prefix)
+        atomicAdd(&s_hist[((unsigned long long)u >> shift) & 255], 1);
+    }
+    cta_sync();
+    if (tid == 0) {  // the bin holding the nd-th largest of the matching values
+      int acc = 0, bin = 255;
+      for (; bin > 0; --bin) {
+        if (acc + s_hist[bin] >= nd) break;
+        acc += s_hist[bin];
+      }
+      s_pick[0] = bin;
+      s_pick[1] = acc;
+    }
+    cta_sync();
+    prefix |= (unsigned long long)s_pick[0] << shift;
+    mask |= 255ull << shift;
+    nd -= s_pick[1];
+    cta_sync();
+  }
+  *need = nd;
+  return (long long)prefix;
+}
+
+// One CTA: the `want` candidates of graph g with the largest bounds, ordered by
+// (ub desc, id asc) with ub >= 0, written to out[] in id order; returns their
+// count.  Every candidate above the want-th largest bound T is taken, then the
+// smallest ids of those equal to T.
+static __device__ int cta_top_bounds(const long long *ub, int o, int n, int want, int32_t *out) {
+  __shared__ int s_scan[33];
+  const int tid = threadIdx.x, T = blockDim.x;
+  long long c;
+  int need;
+  const long long thr = cta_kth_bound(ub, o, n, want, &c, &need);  // -1: take every ub >= 0
+  int carry = 0, eq_seen = 0;
+  for (int base = 0; base < n; base += T) {
+    const int i = base + tid;
+    const long long u = i < n ? ub[o + i] : -1;
+    const int eq = u >= 0 && u == thr;
+    int eq_total;
+    const int eq_pos = block_excl_scan(eq, s_scan, &eq_total);
+    const int take = (u >= 0 && u > thr) || (eq && eq_seen + eq_pos < need);
+    int total;
+    const int pos = block_excl_scan(take, s_scan, &total);
+    if (take) out[carry + pos] = o + i;
+    carry += total;
+    eq_seen += eq_total;
+  }
+  return carry;
+}
+
+// One CTA: graph g's active list = {ub >= L} (ids in increasing order, at most
+// A of them) with L the smallest value whose list fits, and theta = the
+// largest bound left out, plus one (LLONG_MIN when nothing is left out): every
+// candidate outside the list has ub < theta.
+static __device__ void cta_build_list(const BatchArgs &a, int g) {
+  __shared__ long long s_ll[32];
+  __shared__ int s_scan[33];
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int o = a.off[g], n = a.ng[g];
+  long long c;
+  int need;
+  const long long kth = cta_kth_bound(a.ub, o, n, a.A, &c, &need);
+  long long L = 0, theta = LLONG_MIN;
+  if (c > a.A) {
+    // the bounds equal to kth that the top A leaves out decide whether kth fits
+    long long eq = 0, below = -1;
+    for (int i = tid; i < n; i += T) {
+      const long long u = a.ub[o + i];
+      eq += u == kth;
+      if (u >= 0 && u < kth) below = max(below, u);
+    }
+    eq = block_sum(eq, s_ll);
+    below = block_max_ll(below, s_ll);
+    if (eq > need) {
+      L = kth + 1;
+      theta = kth + 1;
+    } else {
+      L = kth;
+      theta = below + 1;  // c > A leaves some bound below kth
+    }
+  }
+  int32_t *act = a.act + (size_t)g * a.A;
+  int carry = 0;
+  for (int base = 0; base < n; base += T) {
+    const int i = base + tid;
+    const int f = i < n && a.ub[o + i] >= 0 && a.ub[o + i] >= L;
+    int total;
+    const int pos = block_excl_scan(f, s_scan, &total);
+    if (f && carry + pos < a.A) act[carry + pos] = o + i;
+    carry += total;
+  }
+  if (carry > a.A) {  // cannot happen (count(ub >= L) <= A); never write past the list
+    if (tid == 0) check_fail(a.ctl, 5, g, a.A, carry);
+    carry = a.A;
+  }
+  if (tid == 0) {
+    a.act_n[g] = carry;
+    a.lc[g].theta = theta;
+  }
+  cta_sync();
+}
+
+// Two-hop upper bound of Delta(v|S) for the group whose distances are d (the
+// inequality and its derivation are those of k_round1_bound in gc_bfs.cu):
+// d[v] + sum over the pruned row of v of ((d[w] - 1)^+ + c3[w]), plus the
+// graph's G3 = sum_u (d[u] - 3)^+ added by the caller.  One warp per v.
+static __device__ __forceinline__ long long warp_two_hop(const BatchArgs &a, const int32_t *d, const int32_t *c3,
+                                                         int v) {
+  const int lane = threadIdx.x & 31;
+  long long s = 0;
+  for (int e = a.rpf[v] + lane; e < a.rpf[v + 1]; e += 32) {
+    const int w = a.cif[e];
+    s += (long long)max(d[w] - 1, 0) + (long long)c3[w];
+  }
+  return warp_sum(s) + (long long)d[v];
+}
+
+// per-graph sum of (d - 3)^+ into out[g] (warp-aggregated like seg_sum_dist)
+static __device__ void seg_sum_excess3(const BatchArgs &a, const int32_t *d, long long *out) {
+  const int lane = threadIdx.x & 31;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < a.N; base += gridDim.x * blockDim.x) {
+    const int v = base + lane;
+    long long x = 0;
+    int g = -1;
+    if (v < a.N) {
+      x = max(d[v] - 3, 0);
+      g = a.gid[v];
+    }
+    const int g0 = __shfl_sync(0xffffffffu, g, 0);
+    if (__all_sync(0xffffffffu, g == g0 || g < 0)) {
+      const long long s = warp_sum(x);
+      if (lane == 0 && g0 >= 0 && s) atomicAdd((unsigned long long *)&out[g0], (unsigned long long)s);
+    } else if (g >= 0 && x) {
+      atomicAdd((unsigned long long *)&out[g], (unsigned long long)x);
+    }
+  }
+}
+
+// Round 1 with two-hop bounds (the single-graph path's round 1, per graph):
+// every candidate gets the bound for S = {s0}; the 64 largest bounds of each
+// graph are evaluated as one CTA batch, then every candidate whose bound
+// reaches that batch's best exact gain.  After that no unevaluated candidate
+// can beat the best exact gain (its bound is below it), so the lazy rule of
+// Sec. 4.2 accepts the best one.  Evaluated candidates get stamp 1 and their
+// exact gain in ub; the rest keep stamp 0 and their bound.
+static __device__ bool batch_round1_bounded(const BatchArgs &a, const GainWs &myws, GainCounters &cnt,
+                                            long long *s_out) {
+  __shared__ int s_task;
+  __shared__ long long s_ll[32];
+  __shared__ int s_scan[33];
+  const int tid = threadIdx.x, b = blockIdx.x, G = gridDim.x, T = blockDim.x;
+  seg_sum_excess3(a, a.dS1, a.g3);
+  if (!bsync(a)) return false;
+  {
+    const int lane = tid & 31, gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+    for (int v = gw; v < a.N; v += nw) {
+      const long long s = warp_two_hop(a, a.dS1, a.c3, v);
+      if (lane == 0) {
+        a.ub[v] = a.dS1[v] == 0 ? -1ll : s + a.g3[a.gid[v]];
+        a.stamp[v] = 0;
+      }
+    }
+  }
+  if (!bsync(a)) return false;
+  // the first batch of each graph: its 64 largest bounds
+  for (int g = b; g < a.count; g += G) {
+    const int m = a.kk[g] >= 2 ? cta_top_bounds(a.ub, a.off[g], a.ng[g], kLanes, a.slist + a.off[g]) : 0;
+    if (tid == 0) a.scount[g] = m;
+    cta_sync();
+  }
+  if (!bsync(a)) return false;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
+    cta_sync();
+    const int g = s_task;
+    cta_sync();
+    if (g >= a.count) break;
+    const int m = a.scount[g], o = a.off[g];
+    if (m == 0) continue;
+    cta_gain_batch<kModeGain, true, true>(a.rpf, a.cif, a.N, a.dS1, a.slist + o, m, s_out, myws, a.gctl, a.mx,
+                                          LaneGraphs(), cnt, o, a.c3);
+    if (tid < m) {
+      const int v = a.slist[o + tid];
+      a.ub[v] = s_out[tid];
+      a.stamp[v] = 1;
+    }
+    const long long best = block_max_ll(tid < m ? s_out[tid] : -1ll, s_ll);
+    if (tid == 0) a.bestf[g] = best;
+    cta_sync();
+  }
+  if (!bsync(a)) return false;
+  // every other candidate whose bound reaches the first batch's best
+  for (int g = b; g < a.count; g += G) {
+    const int o = a.off[g], n = a.ng[g];
+    const long long b1 = a.bestf[g];
+    int carry = 0;
+    if (a.kk[g] >= 2) {
+      for (int base = 0; base < n; base += T) {
+        const int i = base + tid;
+        int flag = 0;
+        if (i < n) {
+          const long long u = a.ub[o + i];
+          flag = u >= 0 && u >= b1 && a.stamp[o + i] == 0;
+        }
+        int total;
+        const int pos = block_excl_scan(flag, s_scan, &total);
+        if (flag) a.slist[o + carry + pos] = o + i;
+        carry += total;
+      }
+    }
+    if (tid == 0) a.scount[g] = carry;
+    cta_sync();
+  }
+  if (!bsync(a)) return false;
+  if (b == 0 && tid == 0) {
+    int acc = 0;
+    for (int g = 0; g < a.count; ++g) {
+      a.tstart[g] = acc;
+      acc += (a.scount[g] + kLanes - 1) / kLanes;
+    }
+    a.tstart[a.count] = acc;
+    a.ctl->task = 0;
+  }
+  if (!bsync(a)) return false;
+  const int n_tasks = a.tstart[a.count];
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
+    cta_sync();
+    const int t = s_task;
+    cta_sync();
+    if (t >= n_tasks) break;
+    int lo = 0, hi = a.count - 1;  // graph with tstart[g] <= t < tstart[g+1] (non-empty)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.tstart[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const int g = lo, o = a.off[g], first = (t - a.tstart[g]) * kLanes;
+    const int nl = min(kLanes, a.scount[g] - first);
+    cta_gain_batch<kModeGain, true, true>(a.rpf, a.cif, a.N, a.dS1, a.slist + o + first, nl, s_out, myws, a.gctl,
+                                          a.mx, LaneGraphs(), cnt, o, a.c3);
+    if (tid < nl) {
+      const int v = a.slist[o + first + tid];
+      a.ub[v] = s_out[tid];
+      a.stamp[v] = 1;
+    }
+    cta_sync();
+  }
+  return bsync(a);
+}
+
+// Bound refresh before the lazy rounds: the two-hop bound for the group after
+// round 1 (d = the current d_S, c3 recounted into q0, G3 into g3[count + g])
+// lowers every candidate's bound, as before each persistent launch of the
+// single-graph path.
+static __device__ bool batch_bound_refresh(const BatchArgs &a) {
+  const int tid = threadIdx.x, lane = tid & 31, b = blockIdx.x, G = gridDim.x, T = blockDim.x;
+  const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+  for (int u = gw; u < a.N; u += nw) {
+    int c = 0;
+    for (int e = a.rpf[u] + lane; e < a.rpf[u + 1]; e += 32) c += a.dS[a.cif[e]] >= 3;
+    c = warp_sum(c);
+    if (lane == 0) a.q0[u] = c;
+  }
+  seg_sum_excess3(a, a.dS, a.g3 + a.count);
+  if (!bsync(a)) return false;
+  for (int v = gw; v < a.N; v += nw) {
+    const int g = a.gid[v];
+    if (a.kk[g] <= 2 || a.ub[v] < 0) continue;  // warp-uniform: one v per warp
+    const long long s = warp_two_hop(a, a.dS, a.q0, v) + a.g3[a.count + g];
+    if (lane == 0 && s < a.ub[v]) a.ub[v] = s;
+  }
+  return bsync(a);
+}
+
+// Refresh of one graph's bounds in the lazy rounds, when its active list can no
+// longer certify a pick (the single-graph path refreshes before each rebuild
+// of its list the same way): c3 for the current d_S into q0, G3 of the graph,
+// then every candidate's bound lowered to the two-hop bound for the current
+// group.  The CTA form runs inside one CTA (P6b); the grid form is spread over
+// every CTA, with three grid barriers (P6a).
+static __device__ void cta_refresh_graph(const BatchArgs &a, int g) {
+  __shared__ long long s_ll[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int o = a.off[g], n = a.ng[g];
+  long long x3 = 0;
+  for (int i = tid; i < n; i += blockDim.x) x3 += max(a.dS[o + i] - 3, 0);
+  for (int u = o + wid; u < o + n; u += nw) {
+    int c = 0;
+    for (int e = a.rpf[u] + lane; e < a.rpf[u + 1]; e += 32) c += a.dS[a.cif[e]] >= 3;
+    c = warp_sum(c);
+    if (lane == 0) a.q0[u] = c;
+  }
+  const long long G3 = block_sum(x3, s_ll);  // its barriers also publish q0
+  for (int v = o + wid; v < o + n; v += nw) {
+    if (a.ub[v] < 0) continue;  // a member (warp-uniform)
+    const long long s = warp_two_hop(a, a.dS, a.q0, v) + G3;
+    if (lane == 0 && s < a.ub[v]) a.ub[v] = s;
+  }
+  cta_sync();
+}
+
+static __device__ bool grid_refresh_graph(const BatchArgs &a, int g) {
+  __shared__ long long s_ll[32];
+  const int tid = threadIdx.x, lane = tid & 31, b = blockIdx.x, G = gridDim.x, T = blockDim.x;
+  const int gw = (b * T + tid) >> 5, nw = (G * T) >> 5;
+  const int o = a.off[g], n = a.ng[g];
+  long long *g3 = a.g3 + a.count + g;
+  if (b == 0 && tid == 0) *g3 = 0;
+  if (!bsync(a)) return false;
+  long long x3 = 0;
+  for (int i = b * T + tid; i < n; i += G * T) x3 += max(a.dS[o + i] - 3, 0);
+  x3 = block_sum(x3, s_ll);
+  if (tid == 0 && x3) atomicAdd((unsigned long long *)g3, (unsigned long long)x3);
+  for (int u = o + gw; u < o + n; u += nw) {
+    int c = 0;
+    for (int e = a.rpf[u] + lane; e < a.rpf[u + 1]; e += 32) c += a.dS[a.cif[e]] >= 3;
+    c = warp_sum(c);
+    if (lane == 0) a.q0[u] = c;
+  }
+  if (!bsync(a)) return false;
+  const long long G3 = *(volatile long long *)g3;
+  for (int v = o + gw; v < o + n; v += nw) {
+    if (a.ub[v] < 0) continue;  // a member (warp-uniform)
+    const long long s = warp_two_hop(a, a.dS, a.q0, v) + G3;
+    if (lane == 0 && s < a.ub[v]) a.ub[v] = s;
+  }
+  return bsync(a);
+}
+
 // Two CTAs per SM (64 registers, no spills): the CTA-local phases are latency
 // bound and gain from the second resident CTA.
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArgs a) {
@@ -293,7 +701,6 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   __shared__ int s_task;
   __shared__ int s_scan[33];
   __shared__ unsigned long long s_red[32];
-  __shared__ long long s_ll[32];
   const int tid = threadIdx.x, lane = tid & 31, b = blockIdx.x, G = gridDim.x, T = blockDim.x;
   GainCounters cnt;
   const unsigned long long t_start = global_ns();
@@ -325,6 +732,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       }
     }
   }
+  for (int g = b * T + tid; g < 2 * a.count; g += G * T) a.g3[g] = 0;
   if (!bsync(a)) return;
   // ---- P1: BFS from all v_a ----
   for (int g = b * T + tid; g < a.count; g += G * T) a.seeds[g] = a.off[g] + (int)(a.packed[g] & 0xffffffffull);
@@ -348,7 +756,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       a.f0[va] = fa;
       a.key[va] = LLONG_MIN;
     }
-    __syncthreads();
+    cta_sync();
     int carry = 0;
     for (int base = 0; base < n; base += T) {
       const int i = base + tid;
@@ -363,7 +771,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       carry += total;
     }
     if (tid == 0) a.scount[g] = carry;
-    __syncthreads();
+    cta_sync();
   }
   if (!bsync(a)) return;
   // P2b: task prefix over graphs (64 survivors per task)
@@ -383,9 +791,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     const LaneGraphs lg{a.gid, a.ng, a.bestf};
     for (;;) {
       if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
-      __syncthreads();
+      cta_sync();
       const int t = s_task;
-      __syncthreads();
+      cta_sync();
       if (t >= n_tasks) break;
       int lo = 0, hi = a.count - 1;  // graph with tstart[g] <= t < tstart[g+1] (non-empty)
       while (lo < hi) {
@@ -398,7 +806,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       cta_gain_batch<kModeFarness, true, false>(a.rp, a.ci, a.N, a.dS, a.slist + o + first, nl, s_out, myws, a.gctl, nullptr,
                                    lg, cnt, o);
       if (tid < nl) a.f0[a.slist[o + first + tid]] = s_out[tid];
-      __syncthreads();
+      cta_sync();
     }
   }
   if (!bsync(a)) return;
@@ -406,7 +814,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   for (int g = b; g < a.count; g += G) {
     const int s0 = cta_argmin_f0(a, g);
     if (tid == 0) a.seeds[g] = a.off[g] + (s0 >= 0 ? s0 : 0);
-    __syncthreads();
+    cta_sync();
   }
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) a.ctl->ns_ph[0] = global_ns() - t_start;
@@ -447,12 +855,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   }
   // ---- P4: round 1 (graph-aligned batches from a dynamic counter) ----
   if (b == 0 && tid == 0) a.ctl->ns_ph[4] = global_ns() - t_start;
-  const int n_tasks = a.bstart[a.count];
+  if (a.bounded) {
+    if (!bsync(a)) return;  // the pruned adjacency's c3 and the picks above are in place
+    if (!batch_round1_bounded(a, myws, cnt, s_out)) return;
+  }
+  const int n_tasks = a.bounded ? 0 : a.bstart[a.count];
   for (;;) {
     if (tid == 0) s_task = atomicAdd(&a.ctl->task, 1);
-    __syncthreads();
+    cta_sync();
     const int t = s_task;
-    __syncthreads();
+    cta_sync();
     if (t >= n_tasks) break;
     int lo = 0, hi = a.count - 1;  // graph with bstart[g] <= t < bstart[g+1]
     while (lo < hi) {
@@ -469,7 +881,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
   }
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) a.ctl->ns_ph[5] = global_ns() - t_start;
-  for (int v = b * T + tid; v < a.N; v += G * T) a.stamp[v] = 1;
+  if (!a.bounded)  // every candidate was evaluated in round 1
+    for (int v = b * T + tid; v < a.N; v += G * T) a.stamp[v] = 1;
   for (int g = b * T + tid; g < a.count; g += G * T) a.ub[a.seeds[g]] = -1;  // s0 is a member
   if (!bsync(a)) return;
   // per-graph argmax (gain desc, id asc) of round 1
@@ -480,7 +893,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     if (v < a.N) {
       g = a.gid[v];
       const long long u = a.ub[v];
-      if (u >= 0 && a.kk[g] >= 2) {
+      if (u >= 0 && a.kk[g] >= 2 && a.stamp[v] == 1) {  // exact round-1 gains only
         if (u >= (1ll << 31)) atomicExch(&a.ctl->err, GC_ERANGE);
         key = ((unsigned long long)u << 32) | (0xffffffffull - (unsigned long long)(v - a.off[g]));
       }
@@ -501,7 +914,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       a.ctl->nseeds = 0;
       a.ctl->remaining = 0;
     }
-    __syncthreads();
+    cta_sync();
     for (int g = tid; g < a.count; g += T) {
       if (a.kk[g] < 2) {
         a.lc[g].round = a.kk[g];  // nothing after round 0
@@ -533,56 +946,12 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
     a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;
     a.ctl->nseeds = 0;
   }
+  if (a.bounded && !batch_bound_refresh(a)) return;
   // ---- P5: active lists (one CTA per graph) ----
   for (int g = b; g < a.count; g += G) {
     if (a.kk[g] <= 2) continue;
-    const int o = a.off[g], n = a.ng[g];
-    long long umin = LLONG_MAX, umax = LLONG_MIN, c = 0;
-    for (int i = tid; i < n; i += T) {
-      const long long u = a.ub[o + i];
-      if (u < 0) continue;
-      umin = min(umin, u);
-      umax = max(umax, u);
-      ++c;
-    }
-    umin = block_min_ll(umin, s_ll);
-    umax = block_max_ll(umax, s_ll);
-    c = block_sum(c, s_ll);
-    int32_t *act = a.act + (size_t)g * a.A;
-    // list = {ub >= thr} with thr the smallest value whose list fits in A
-    // (thr = umin when everything fits); every dropped candidate has ub < thr
-    long long thr = umin;
-    if (c > a.A) {
-      long long lo2 = umin, hi2 = umax + 1;  // count(>= lo2) > A, count(>= hi2) <= A
-      while (hi2 - lo2 > 1) {
-        const long long mid = lo2 + (hi2 - lo2) / 2;
-        long long cc = 0;
-        for (int i = tid; i < n; i += T) cc += a.ub[o + i] >= mid;
-        cc = block_sum(cc, s_ll);
-        if (cc <= a.A) hi2 = mid;
-        else lo2 = mid;
-      }
-      thr = hi2;
-    }
-    int carry = 0;
-    for (int base = 0; base < n; base += T) {
-      const int i = base + tid;
-      const int f = i < n && a.ub[o + i] >= 0 && a.ub[o + i] >= thr;
-      int total;
-      const int pos = block_excl_scan(f, s_scan, &total);
-      if (f && carry + pos < a.A) act[carry + pos] = o + i;
-      carry += total;
-    }
-    if (carry > a.A) {  // cannot happen (count(ub >= thr) <= A); never write past the list
-      if (tid == 0) check_fail(a.ctl, 5, g, a.A, carry);
-      carry = a.A;
-    }
-    if (tid == 0) {
-      a.act_n[g] = carry;
-      a.lc[g].theta = c > a.A ? thr : LLONG_MIN;
-    }
+    cta_build_list(a, g);
     if (tid == 0) a.full[g] = 0;
-    __syncthreads();
   }
   if (!bsync(a)) return;
   if (b == 0 && tid == 0) a.ctl->ns_ph[1] = global_ns() - t_start;
@@ -597,27 +966,36 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       if (a.ng[g] >= a.grid_min_n) continue;  // done in P6a
       LazyCtl *lc = &a.lc[g];
       const int o = a.off[g];
+      unsigned long long t_ph[3] = {0, 0, 0}, t_mark = global_ns();  // thread 0's phase clocks
       for (;;) {
         if (tid == 0) s_stop = (lc->round >= a.kk[g]) || (*(volatile int32_t *)&a.ctl->err != 0);
-        __syncthreads();
+        cta_sync();
         if (s_stop) break;
-        const bool full = a.full[g] != 0;
+        const bool full = a.full[g] == 1;  // 0: list, 2 + r: list rebuilt in round r, 1: every candidate
         const int32_t *act = full ? a.iota + o : a.act + (size_t)g * a.A;
         const int m = full ? a.ng[g] : a.act_n[g];
         if (full && tid == 0) lc->theta = LLONG_MIN;
-        __syncthreads();
+        cta_sync();
         lazy_cta0_step(act, m, a.ub, a.stamp, lc, nullptr, lc->pad != 0, nullptr, 0);
-        __syncthreads();
+        cta_sync();
         const int dec = *(volatile int32_t *)&lc->dec;
+        if (tid == 0) {
+          const unsigned long long now = global_ns();
+          t_ph[0] += now - t_mark;
+          t_mark = now;
+        }
+        int ph = 0;  // the rest of the step: 0 list rebuild, 1 gain batch, 2 d_S update
         if (dec == 0) {  // evaluate the selected batch
           cta_gain_batch<kModeGain, true, false>(a.rpf, a.cif, a.N, a.dS, lc->sel, lc->n_sel, lc->gsel, myws,
                                                  a.gctl, a.mx, LaneGraphs(), cnt, o, a.c3);
           if (tid == 0) lc->pad = 1;  // fold it next step
+          ph = 1;
         } else if (dec == 1) {  // accept: record, then update d_S from the pick
+          ph = 2;
           const int pick = lc->best_id;
           const long long gain = lc->best_gain;
           const int r = lc->round;
-          __syncthreads();
+          cta_sync();
           const long long decr = cta_relabel_bfs(a.rpf, a.cif, a.dS, pick, myws.qv0, myws.qv1);
           if (tid == 0) {
             if (decr != gain) check_fail(a.ctl, 6, g, gain, decr);
@@ -631,16 +1009,31 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
             lc->round = r + 1;
             lc->steps += 0;
           }
-        } else {  // the list cannot certify: use every candidate of the graph
+        } else {  // the list cannot certify: refresh the bounds and rebuild it
+          const int r = lc->round;
+          const bool again = a.full[g] == 2 + r;
+          cta_sync();
+          if (!again) {
+            cta_refresh_graph(a, g);
+            cta_build_list(a, g);
+          }
           if (tid == 0) {
-            a.full[g] = 1;
+            a.full[g] = again ? 1 : 2 + r;  // a second failure in one round: every candidate
             lc->pad = 0;
           }
         }
-        if (tid == 0 && global_ns() - t_start > 6ull * a.tns) atomicExch(&a.ctl->err, GC_ETIMEOUT);
-        __syncthreads();
+        if (tid == 0) {
+          const unsigned long long now = global_ns();
+          t_ph[ph] += now - t_mark;
+          t_mark = now;
+          if (now - t_start > 6ull * a.tns) atomicExch(&a.ctl->err, GC_ETIMEOUT);
+        }
+        cta_sync();
       }
-      if (tid == 0) atomicAdd((unsigned long long *)&a.ctl->iterations, (unsigned long long)lc->steps);
+      if (tid == 0) {
+        atomicAdd((unsigned long long *)&a.ctl->iterations, (unsigned long long)lc->steps);
+        for (int q = 0; q < 3; ++q) atomicAdd(&a.ctl->ns_lazy[q], t_ph[q]);
+      }
     }
   }
   if (!bsync(a)) return;
@@ -652,7 +1045,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_solve(const BatchArg
       a.ctl->nseeds = 0;
       a.ctl->pk[0] = a.ctl->pk[1] = a.ctl->pk[2] = 0;  // the grid lazy rounds leave them set
     }
-    __syncthreads();
+    cta_sync();
     for (int g = tid; g < a.count; g += T) {
       long long f = a.pgain[(size_t)g * a.kmax];
       for (int r = 1; r < a.kk[g]; ++r) f -= a.pgain[(size_t)g * a.kmax + r];
@@ -745,7 +1138,7 @@ struct gc_batch {
   unsigned char *ws = nullptr;
   size_t ws_stride = 0;
   unsigned long long *packed = nullptr;
-  long long *fa = nullptr, *farness = nullptr, *bestf = nullptr;
+  long long *fa = nullptr, *farness = nullptr, *bestf = nullptr, *g3 = nullptr;
   LazyCtl *lc = nullptr;
   int32_t *act = nullptr, *act_n = nullptr, *full = nullptr, *kk = nullptr, *bstart = nullptr;
   int32_t A = 0, act_cap = 0;
@@ -763,6 +1156,7 @@ struct gc_batch {
   cudaStream_t cap_stream = nullptr;  // private stream the sequence is captured on
   std::vector<int32_t> cap_k;
   int32_t cap_A = 0, cap_lanes = 0, cap_grid_min_n = 0;
+  uint32_t cap_flags = 0;
   std::vector<int32_t> h_picks;
   std::vector<long long> h_pgain, h_far;
   int32_t *h_picks_pinned = nullptr;
@@ -778,7 +1172,7 @@ static void batch_release(gc_batch *b) {
   void *dev[] = {b->rp, b->ci, b->gid, b->off, b->ng, b->iota, b->dS, b->mx, b->stamp, b->q0, b->q1, b->goff, b->st1,
                  b->ub, b->key, b->f0, b->ws, b->packed, b->fa, b->farness, b->bestf, b->lc, b->act, b->act_n,
                  b->full, b->kk, b->bstart, b->picks, b->pgain, b->seeds, b->ctl, b->gctl, b->slist,
-                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg, b->gsel, b->dS1};
+                 b->scount, b->tstart, b->rpf, b->cif, b->c3, b->gx, b->gg, b->gsel, b->dS1, b->g3};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -862,7 +1256,7 @@ static int batch_load_impl(int32_t count, const int32_t *const *row_ptrs, const 
             balloc(&b->kk, (size_t)count) && balloc(&b->bstart, (size_t)count + 1) && balloc(&b->ctl, 1) &&
             balloc(&b->slist, Nn) && balloc(&b->scount, (size_t)count) && balloc(&b->tstart, (size_t)count + 1) &&
             balloc(&b->rpf, Nn + 1) && balloc(&b->cif, std::max<size_t>(1, (size_t)E)) && balloc(&b->c3, Nn) &&
-            balloc(&b->dS1, Nn) &&
+            balloc(&b->dS1, Nn) && balloc(&b->g3, 2 * (size_t)count) &&
             balloc(&b->gx, 3 * (size_t)std::max<int32_t>(1, b->max_n)) && balloc(&b->gg, 1) && balloc(&b->gsel, 1) &&
             balloc(&b->gctl, 1) && cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl)) == cudaSuccess &&
             cudaMallocHost((void **)&b->h_gctl, sizeof(GainCtl)) == cudaSuccess;
@@ -1001,7 +1395,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   }
   std::vector<int32_t> bstart(b->count + 1, 0);
   for (int32_t g = 0; g < b->count; ++g) bstart[g + 1] = bstart[g] + (b->h_n[g] + lanes1 - 1) / lanes1;
-  const bool same = b->exec && !resized && b->cap_k == std::vector<int32_t>(ks, ks + b->count) && b->cap_A == A && b->cap_grid_min_n == opts.batch_grid_min_n &&
+  const bool same = b->exec && !resized && b->cap_k == std::vector<int32_t>(ks, ks + b->count) && b->cap_A == A && b->cap_grid_min_n == opts.batch_grid_min_n && b->cap_flags == opts.flags &&
                     b->cap_lanes == lanes1;
   BatchArgs a;
   a.rp = b->rp;
@@ -1030,6 +1424,8 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
   a.gg = b->gg;
   a.gsel = b->gsel;
   a.gx = b->gx;
+  a.bounded = (opts.flags & GC_OPT_NO_ROUND1_BOUND) ? 0 : 1;
+  a.g3 = b->g3;
   a.grid_min_n = opts.batch_grid_min_n == 0 ? kBatchGridMinN
                  : (opts.batch_grid_min_n < 0 ? INT32_MAX : opts.batch_grid_min_n);
   a.ub = b->ub;
@@ -1105,6 +1501,7 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     b->cap_A = A;
     b->cap_lanes = lanes1;
     b->cap_grid_min_n = opts.batch_grid_min_n;
+    b->cap_flags = opts.flags;
     // capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the graph is then launched on the caller's stream
     cudaError_t e = cudaSuccess;
@@ -1169,8 +1566,10 @@ int gc_batch_greedy(gc_batch *b, const int32_t *ks, const gc_opts *opts_in, int3
     const unsigned long long *ph = b->h_ctl->ns_ph;
     stats->ms_round0 = ph[0] * 1e-6;
     stats->ms_round1 = (ph[1] - ph[0]) * 1e-6;
-    stats->ms_lazy_gain = (ph[2] - ph[1]) * 1e-6;
-    stats->ms_lazy_update = (ph[3] - ph[2]) * 1e-6;
+    stats->ms_lazy_kernel = (ph[2] - ph[1]) * 1e-6;  // the lazy rounds of every graph (P6)
+    stats->ms_lazy_select = b->h_ctl->ns_lazy[0] * 1e-6;  // their phases, summed over graphs
+    stats->ms_lazy_gain = b->h_ctl->ns_lazy[1] * 1e-6;
+    stats->ms_lazy_update = b->h_ctl->ns_lazy[2] * 1e-6;
     stats->ms_gain_kernel = (ph[5] - ph[4]) * 1e-6;  // round-1 gains of every graph (P4)
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }

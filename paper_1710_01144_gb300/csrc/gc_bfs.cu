@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_dist(const int32_t *__restr
     __threadfence();
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
+  cta_sync();
   if (!last) return;
   __threadfence();
   s = 0;
@@ -176,35 +176,35 @@ __global__ void __launch_bounds__(1024) k_level_prefix(unsigned long long *cnt, 
     carry_c = 0;
     carry_m = 0;
   }
-  __syncthreads();
+  cta_sync();
   for (int base = 0; base <= D; base += 1024) {
     const int l = base + threadIdx.x;
     const unsigned long long c = l <= D ? cnt[l] : 0ull;
     s_c[threadIdx.x] = c;
     s_m[threadIdx.x] = c * (unsigned long long)(l <= D ? l : 0);
-    __syncthreads();
+    cta_sync();
     for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
       unsigned long long a = 0, b = 0;
       if (threadIdx.x >= o) {
         a = s_c[threadIdx.x - o];
         b = s_m[threadIdx.x - o];
       }
-      __syncthreads();
+      cta_sync();
       s_c[threadIdx.x] += a;
       s_m[threadIdx.x] += b;
-      __syncthreads();
+      cta_sync();
     }
     if (l <= D) {
       C[l + 1] = carry_c + s_c[threadIdx.x];
       M[l + 1] = carry_m + s_m[threadIdx.x];
       cnt[l] = 0;
     }
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 1023) {
       carry_c += s_c[1023];
       carry_m += s_m[1023];
     }
-    __syncthreads();
+    cta_sync();
   }
   if (threadIdx.x == 0) {
     C[0] = 0;
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(1024) k_scan_tops(long long *tile_sum, int32_t
     const int ex = block_excl_scan((int)v, s_scan, &tot);
     if (i < tiles) tile_sum[i] = carry + ex;
     carry += tot;
-    __syncthreads();
+    cta_sync();
   }
 }
 
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const int32_t *__restrict__
     if (i < n) out[i] = (int32_t)(carry + ex);
     if (i == n - 1) out[n] = (int32_t)(carry + ex + v);
     carry += tot;
-    __syncthreads();
+    cta_sync();
   }
 }
 
@@ -426,9 +426,9 @@ __global__ void __launch_bounds__(1024) k_max_nbr_heavy(const int32_t *__restric
     for (int e = rp[v] + threadIdx.x; e < rp[v + 1]; e += 1024) m = max(m, dS[ci[e]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __syncthreads();
+    cta_sync();
     if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x < 32) {
       m = s_m[threadIdx.x];
 #pragma unroll

@@ -35,8 +35,8 @@ struct GainCounters {
 // adjacency entries overlap freely, three times faster on hub-heavy batches.
 template <int MODE, bool RO_GRAPH = true, bool RO_DS = true>
 __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                               int32_t n, const int32_t *__restrict__ dS,
-                                               const int32_t *__restrict__ cand, int nl,
+                                               int32_t n, const int32_t *dS,
+                                               const int32_t *cand, int nl,
                                                long long *__restrict__ out, const GainWs &ws, GainCtl *ctl,
                                                const int32_t *__restrict__ mx, const LaneGraphs lg,
                                                GainCounters &cnt, int voff = 0,
@@ -71,7 +71,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
     s_touched = 0;
     s_alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
   }
-  __syncthreads();
+  cta_sync();
   int32_t *qcur_v = ws.qv0, *qnxt_v = ws.qv1;
 
   // level 0: lane j reaches its candidate
@@ -99,11 +99,11 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       if (on == 0) qcur_v[atomicAdd(&s_qn, 1)] = c;
     }
   }
-  __syncthreads();
+  cta_sync();
   int F = s_qn;
-  __syncthreads();
+  cta_sync();
   if (tid == 0) s_qn = 0;
-  __syncthreads();
+  cta_sync();
 
   int L = 0;
   for (; F > 0; ++L) {
@@ -139,7 +139,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       s_rs[tid] = rs;
       s_m[tid] = m;
       if (tid == T - 1) s_off[T] = total;
-      __syncthreads();
+      cta_sync();
       // kEdgeIlp adjacency entries per thread are in flight at once: the
       // column, d_S, visited-word loads and the claiming atomics of
       // independent entries are issued before any result is used.
@@ -192,7 +192,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
           } while (won);
         }
       }
-      __syncthreads();
+      cta_sync();
     }
     const int Fn = s_qn;
     if (MODE == kModeFarness && tid < kLanes && ((s_alive >> tid) & 1ull)) {
@@ -201,11 +201,11 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       const long long best = lg.gid ? s_best[tid] : *(volatile long long *)&ctl->best_f;
       if (Fn > 0 && lb > best) atomicAnd(&s_alive, ~(1ull << tid));
     }
-    __syncthreads();
+    cta_sync();
     if (tid == 0) s_qn = 0;
     { int32_t *t = qcur_v; qcur_v = qnxt_v; qnxt_v = t; }
     F = Fn;
-    __syncthreads();
+    cta_sync();
     if (MODE == kModeFarness && s_alive == 0) {
       // every lane is cut: clear the claims of the frontier that is not expanded
       for (int i = tid; i < F; i += T) nxt[qcur_v[i] - voff] = 0;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
   }
   const int nt = s_touched;
   for (int i = tid; i < nt; i += T) ws.vis[ws.touched[i] - voff] = 0;
-  __syncthreads();
+  cta_sync();
 }
 
 // CTA-local pruned relabel BFS from seed s (the pruned SSSP of Sec. 4.1 that
@@ -269,7 +269,7 @@ static __device__ __noinline__ long long cta_relabel_bfs(const int32_t *__restri
       s_F = 1;
     }
   }
-  __syncthreads();
+  cta_sync();
   int32_t *qc = q0, *qn = q1;
   for (int L = 0; s_F > 0; ++L) {
     const int F = s_F;
@@ -287,7 +287,7 @@ static __device__ __noinline__ long long cta_relabel_bfs(const int32_t *__restri
       s_off[tid] = off;
       s_rs[tid] = rs;
       if (tid == T - 1) s_off[T] = total;
-      __syncthreads();
+      cta_sync();
       for (int e = tid; e < total; e += T) {
         int lo = 0, hi = T - 1;
         while (lo < hi) {
@@ -304,13 +304,13 @@ static __device__ __noinline__ long long cta_relabel_bfs(const int32_t *__restri
           }
         }
       }
-      __syncthreads();
+      cta_sync();
     }
     if (tid == 0) {
       s_F = s_qn;
       s_qn = 0;
     }
-    __syncthreads();
+    cta_sync();
     int32_t *t = qc;
     qc = qn;
     qn = t;

@@ -15,6 +15,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// CTA barrier.  __syncthreads() is an aligned barrier: it counts a warp
+// correctly only if the warp arrives converged.  A warp still split by an
+// earlier single-thread branch (thread 0's bookkeeping, a poll) could be
+// counted at the wrong barrier, after which its warps run one barrier apart;
+// __syncwarp() first reconverges it.  Every CTA barrier of the library goes
+// through here.
+__device__ __forceinline__ void cta_sync() {
+  __syncwarp();
+  __syncthreads();
+}
+
 // Grid barrier for cooperative launches (all CTAs co-resident).  One 32-bit
 // word per barrier: in every episode CTA 0 adds 2^31 - (G - 1) and each other
 // CTA adds 1 (G = gridDim.x), so the episode adds exactly 2^31: bit 31 of the
@@ -29,7 +40,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
                                           unsigned long long timeout_ns) {
   __shared__ int s_ok;
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
@@ -50,12 +61,16 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int32_t *err,
     }
     s_ok = ok && (*(volatile int32_t *)err == 0);
   }
-  __syncthreads();
+  cta_sync();
   return s_ok != 0;
 }
 
 // A load through the read-only data path when RO (the data must not change
-// while the kernel can still read it), else a plain load.
+// while the kernel can still read it), else a plain load.  For the same reason
+// no pointer to data that a persistent kernel rewrites (d_S, bounds, stamps,
+// selected candidates, active lists) is declared const __restrict__: the
+// compiler may then load it through the non-coherent read-only path, which a
+// grid barrier does not refresh.
 template <bool RO>
 __device__ __forceinline__ int32_t ld_ro(const int32_t *p) {
   if (RO) return __ldg(p);
@@ -74,16 +89,16 @@ template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   v = warp_sum(v);
-  __syncthreads();
+  cta_sync();
   if (lane == 0) sh[wid] = v;
-  __syncthreads();
+  cta_sync();
   const int nw = (blockDim.x + 31) >> 5;
   T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
   if (wid == 0) r = warp_sum(r);
   if (threadIdx.x == 0) sh[0] = r;
-  __syncthreads();
+  cta_sync();
   r = sh[0];
-  __syncthreads();
+  cta_sync();
   return r;
 }
 
@@ -97,9 +112,9 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  __syncthreads();
+  cta_sync();
   if (lane == 31) sh[wid] = x;
-  __syncthreads();
+  cta_sync();
   if (wid == 0) {
     const int nw = (blockDim.x + 31) >> 5;
     int s = (lane < nw) ? sh[lane] : 0;
@@ -111,11 +126,11 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     if (lane < nw) sh[lane] = s;  // inclusive prefix of warp totals
     if (lane == nw - 1) sh[32] = s;
   }
-  __syncthreads();
+  cta_sync();
   const int warp_off = wid ? sh[wid - 1] : 0;
   *total = sh[32];
   const int r = warp_off + x - v;
-  __syncthreads();
+  cta_sync();
   return r;
 }
 

@@ -52,9 +52,9 @@ __global__ void __launch_bounds__(kGainThreads, 2)
   GainCounters cnt;
   for (;;) {
     if (tid == 0) s_batch = (int)atomicAdd(&ctl->batch_next, 1u);
-    __syncthreads();
+    cta_sync();
     const int b = s_batch;
-    __syncthreads();
+    cta_sync();
     if (b >= n_batches) break;
     const int base = b * lanes;
     cta_gain_batch<MODE, true, true>(rp, ci, n, dS, cand + base, min(lanes, n_cand - base), out + base, ws, ctl, mx,

@@ -29,8 +29,9 @@ static __device__ __forceinline__ int row_len(const int32_t *__restrict__ rp, co
 // Largest x in [0, F) with start[x] <= e, for one warp; start is
 // non-decreasing and start[0] <= e.  A 32-ary search: about log32(F) rounds
 // of one coalesced probe each.
-static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict__ start, int F, long long e) {
+static __device__ __forceinline__ int warp_find_start(const int32_t *start, int F, long long e) {
   const int lane = threadIdx.x & 31;
+  __syncwarp();  // callers reach it right after thread 0's bookkeeping: reconverge first
   int lo = 0, hi = F - 1;
   while (hi - lo >= 32) {
     const int step = (hi - lo + 32) / 32;  // 32 probes cover [lo, hi]
@@ -77,7 +78,7 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *__restrict_
 constexpr int kBatchAll = 0, kBatchLevel0 = 1, kBatchRest = 2;
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                int32_t n, const int32_t *__restrict__ dS, const int32_t *cand, int32_t nl_arg,
+                                int32_t n, const int32_t *dS, const int32_t *cand, int32_t nl_arg,
                                 const int32_t *nl_dev, long long *out, unsigned char *ws_base, int32_t *gx,
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
@@ -146,6 +147,9 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   if (MODE != kModeGain) phase = kBatchAll;
   // ---- level 0 (warp 0 of CTA 0, or of the calling CTA): lanes reach their candidates ----
   if (phase != kBatchRest && (b == 0 || phase == kBatchLevel0) && tid < 32) {
+    // the caller may arrive with the warp split by a single-thread branch: the
+    // warp-synchronous enqueue below needs it converged
+    __syncwarp();
     // lane t handles lanes t and t + 32 of the batch, one after the other
     for (int h = 0; h < 2; ++h) {
       const int j = lane + 32 * h;
@@ -181,7 +185,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   }
   if (phase == kBatchLevel0) return true;
   bool ok = true;
-  if (phase == kBatchRest) __syncthreads();  // s_gain and s_cnt are zero
+  if (phase == kBatchRest) cta_sync();  // s_gain and s_cnt are zero
   else ok = grid_sync(bar, err, timeout_ns);
   // invalid candidate ids leave their lanes empty
   if (ok && MODE == kModeFarness) {
@@ -189,7 +193,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       s_tg[tid] = 0;
       s_tc[tid] = tid < nl ? ((volatile u64 *)ctl->dcnt[0])[tid] : 0ull;
     }
-    __syncthreads();
+    cta_sync();
     for (int j = 0; j < nl; ++j)
       if (s_tc[j] == 0) alive &= ~(1ull << j);
   }
@@ -222,7 +226,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         const int x = warp_find_start(qstart, F, es);
         if (tid == 0) s_x0 = x;
       }
-      __syncthreads();
+      cta_sync();
       int x = s_x0;
       while (x < F) {
         // stage up to T entries from x: range starts, row starts, lane masks
@@ -243,7 +247,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           }
         }
         if (tid == 0) s_go[cntx] = (x + cntx < F) ? qstart[x + cntx] : (int)E;
-        __syncthreads();
+        cta_sync();
         const long long a0 = max((long long)s_go[0], es), a1 = min((long long)s_go[cntx], ee);
         for (long long e0 = a0 + (long long)(tid & ~31) * kGridIlp; e0 < a1; e0 += (long long)T * kGridIlp) {
           // kGridIlp entries per thread: loads of all are issued before any claim
@@ -324,13 +328,13 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
           }
         }
         const int done_end = s_go[cntx];
-        __syncthreads();  // the staged arrays are reused
+        cta_sync();  // the staged arrays are reused
         if ((long long)done_end >= ee) break;
         x += cntx;
       }
     }
     if (MODE == kModeFarness) {
-      __syncthreads();
+      cta_sync();
       if (tid < kLanes) {  // the vertices claimed at distance L + 1
         if (s_gain[tid]) atomicAdd(&ctl->dgain[(L + 1) % 3][tid], s_gain[tid]);
         if (s_cnt[tid]) atomicAdd(&ctl->dcnt[(L + 1) % 3][tid], (u64)s_cnt[tid]);
@@ -353,7 +357,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
         s_tg[tid] += ((volatile u64 *)ctl->dgain[(L + 1) % 3])[tid];
         s_tc[tid] += ((volatile u64 *)ctl->dcnt[(L + 1) % 3])[tid];
       }
-      __syncthreads();
+      cta_sync();
       for (int j = 0; j < nl; ++j) {
         if (!((alive >> j) & 1ull)) continue;
         const long long s = (long long)s_tg[j];
@@ -376,7 +380,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   // L = levels expanded
   // ---- results ----
   if (MODE == kModeGain) {
-    __syncthreads();
+    cta_sync();
     if (tid < kLanes && s_gain[tid]) atomicAdd(&ctl->gain[tid], s_gain[tid]);
   }
   // leave the workspace zero: the touched list is complete once the last
@@ -516,7 +520,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
         const int x = warp_find_start(qs, F, es);
         if (tid == 0) s_x0 = x;
       }
-      __syncthreads();
+      cta_sync();
       int x = s_x0;
       while (x < F) {
         const int xi = x + tid;
@@ -526,7 +530,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
           s_rs[tid] = __ldg(rp + qc[xi]);
         }
         if (tid == 0) s_go[cntx] = (x + cntx < F) ? qs[x + cntx] : (int)E;
-        __syncthreads();
+        cta_sync();
         const long long a0 = max((long long)s_go[0], es), a1 = min((long long)s_go[cntx], ee);
         for (long long e0 = a0 + (tid & ~31); e0 < a1; e0 += T) {  // warp-uniform trip count
           const long long e = e0 + lane;
@@ -554,7 +558,7 @@ static __device__ __forceinline__ bool grid_relabel_bfs(
           enqueue(q, w, nl, lw);
         }
         const int done_end = s_go[cntx];
-        __syncthreads();  // the staged arrays are reused
+        cta_sync();  // the staged arrays are reused
         if ((long long)done_end >= ee) break;
         x += cntx;
       }

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         lazy_cta0_step(lact, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
                        lkey, lst, wsel, wgain, wpos, wide ? wcap : 0);
         if (lean) {
-          __syncthreads();  // lc->dec, lc->sel and the reset batch control block
+          cta_sync();  // lc->dec, lc->sel and the reset batch control block
           const int d = *(volatile int32_t *)&lc->dec;
           if (d == 0) {
             grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     ++r;
     // the other CTAs read none of the bookkeeping before the next step's
     // barrier unless they select or score too; CTA 0's own threads do
-    if (lean) __syncthreads();
+    if (lean) cta_sync();
     else if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     if (timer) {
       t1 = global_ns();

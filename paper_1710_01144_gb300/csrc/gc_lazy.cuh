@@ -17,16 +17,16 @@ static __device__ __forceinline__ long long block_min_ll(long long v, long long 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
+  cta_sync();
   if (lane == 0) sh[wid] = v;
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0) {
     for (int w = 1; w < nw; ++w) v = min(v, sh[w]);
     sh[0] = v;
   }
-  __syncthreads();
+  cta_sync();
   v = sh[0];
-  __syncthreads();
+  cta_sync();
   return v;
 }
 
@@ -34,16 +34,16 @@ static __device__ __forceinline__ long long block_max_ll(long long v, long long 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
+  cta_sync();
   if (lane == 0) sh[wid] = v;
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0) {
     for (int w = 1; w < nw; ++w) v = max(v, sh[w]);
     sh[0] = v;
   }
-  __syncthreads();
+  cta_sync();
   v = sh[0];
-  __syncthreads();
+  cta_sync();
   return v;
 }
 
@@ -59,12 +59,12 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
       id = oid;
     }
   }
-  __syncthreads();
+  cta_sync();
   if (lane == 0) {
     sv[wid] = v;
     sid[wid] = id;
   }
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0) {
     for (int w = 1; w < nw; ++w)
       if (better_max(sv[w], sid[w], v, id)) {
@@ -74,10 +74,10 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
     sv[0] = v;
     sid[0] = id;
   }
-  __syncthreads();
+  cta_sync();
   v = sv[0];
   id = sid[0];
-  __syncthreads();
+  cta_sync();
 }
 
 // Exact top-`need` of the list entries by key (larger first; ties by list
@@ -87,7 +87,7 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
 // Histogram passes over [kmin, kmax] fix the threshold value; every key above it
 // is taken, then keys equal to it in list order.  Returns the number taken.
 template <class KeyFn>
-static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn key, long long kmin, long long kmax,
+static __device__ int cta_topk(const int32_t *act, int32_t m, KeyFn key, long long kmin, long long kmax,
                         long long cnt, int need, int32_t *sel, int base, unsigned int *s_hist,
                         int32_t *selpos = nullptr, unsigned long long *scanned = nullptr, int cap = kLanes) {
   __shared__ int s_scan[33];
@@ -105,7 +105,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
       const unsigned long long width = span / kLazyBins + ((span % kLazyBins) ? 1ull : 0ull);
       for (int i = tid; i < kLazyBins; i += T) s_hist[i] = 0;
       if (scanned && tid == 0) *scanned += (unsigned long long)m;
-      __syncthreads();
+      cta_sync();
       for (int i = tid; i < m; i += T) {
         const long long k = key(i, act[i]);
         if (k == LLONG_MIN) continue;
@@ -113,7 +113,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
         if (uu - lo > hi - lo) continue;  // outside [lo, hi] (unsigned wrap)
         atomicAdd(&s_hist[(uu - lo) / width], 1u);
       }
-      __syncthreads();
+      cta_sync();
       // walk down from the top bin: thread t owns bins 1023-2t and 1022-2t
       const int b0 = kLazyBins - 1 - 2 * tid, b1 = b0 - 1;
       const int h0 = tid < kLazyBins / 2 ? (int)s_hist[b0] : 0;
@@ -133,7 +133,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
           s_ab = a0 + h0;
         }
       }
-      __syncthreads();
+      cta_sync();
       const int bb = s_b;
       const long long ab = s_ab;
       const unsigned long long bin_lo = lo + width * (unsigned long long)bb;
@@ -147,7 +147,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
       const unsigned long long room = hi - bin_lo;
       lo = bin_lo;
       hi = bin_lo + (width - 1ull < room ? width - 1ull : room);
-      __syncthreads();
+      cta_sync();
     }
   }
   // Selection in list order.  Thread t owns the contiguous entries [t C, t C + C):
@@ -185,7 +185,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
       eq_before += eq;
     }
   }
-  __syncthreads();
+  cta_sync();
   const int taken = tot_gt + min(tot_eq, eq_take);
   return taken < need ? taken : need;
 }
@@ -200,7 +200,7 @@ static __device__ int cta_topk(const int32_t *__restrict__ act, int32_t m, KeyFn
 // proposal network (score != nullptr), `fill` of the 64 lanes go to the
 // unevaluated candidates whose bound most exceeds the network's predicted
 // gain: evaluating them tightens the bounds later rounds must beat.
-static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *ub, int32_t *stamp,
                                LazyCtl *lc, GridGainCtl *gg, bool fold, const float *score, int fill,
                                long long *akey = nullptr, int32_t *ast = nullptr, int32_t *wsel = nullptr,
                                long long *wgain = nullptr, int32_t *wpos = nullptr, int wcap = 0) {
@@ -238,7 +238,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
     const int mine = bid;
     block_argmax_all(bv, bid, s_v, s_id);
     if (mine >= 0 && mine == bid) s_bpos = mypos;
-    __syncthreads();
+    cta_sync();
     if (tid == 0) {
       if (bid >= 0 && better_max(bv, bid, lc->best_gain, lc->best_id)) {
         lc->best_gain = bv;
@@ -248,7 +248,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
       lc->steps += 1;
       lc->evals += ns;
     }
-    __syncthreads();
+    cta_sync();
   }
   const long long gb = *(volatile long long *)&lc->best_gain;
   const int vb = *(volatile int32_t *)&lc->best_id;
@@ -304,7 +304,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
       stamp[lc->sel[tid]] = r;
       if (akey) ast[lc->selpos[tid]] = r;
     }
-    __syncthreads();
+    cta_sync();
     auto by_slack = [=] __device__(int i, int v) -> long long {
       const long long u = akey ? akey[i] : ub[v];
       if (u < 0 || (akey ? ast[i] : stamp[v]) == r) return LLONG_MIN;
@@ -359,7 +359,7 @@ static __device__ void lazy_cta0_step(const int32_t *__restrict__ act, int32_t m
 //   5. selection: entries above it and, in list order, enough equal to it.
 // Returns false if a barrier gave up; *dec_out gets the decision.  The caller
 // synchronises the grid before using the selection.
-static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m, long long *ub, int32_t *stamp,
+static __device__ bool grid_lazy_step(const int32_t *act, int32_t m, long long *ub, int32_t *stamp,
                                       long long *akey, int32_t *ast, LazyCtl *lc, GridGainCtl *gg, bool fold,
                                       int32_t *sel, int32_t *selpos, const long long *gsel, int cap,
                                       GridSelScratch *sc, GridBar *bar, int32_t *err, unsigned long long tns,
@@ -410,7 +410,7 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
     const int mine = fid;
     block_argmax_all(fv, fid, s_v, s_id);
     if (mine >= 0 && mine == fid) s_b = fpos;
-    __syncthreads();
+    cta_sync();
     if (fid >= 0 && better_max(fv, fid, gb, vb)) {
       gb = fv;
       vb = fid;
@@ -423,7 +423,7 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
       lc->steps += 1;
       lc->evals += ns;
     }
-    __syncthreads();
+    cta_sync();
   }
   // ---- 2. scan of this CTA's slice ----
   long long umax = LLONG_MIN, umin = LLONG_MAX, cnt = 0;
@@ -492,7 +492,7 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
       for (int i = tid; i < kSelBins; i += T) s_hist[i] = 0;
       if (b == 0)  // the next pass's buffer (read two passes ago by everyone)
         for (int i = tid; i < kSelBins; i += T) sc->hist[(pass + 1) % 3][i] = 0;
-      __syncthreads();
+      cta_sync();
       for (int i = lo + tid; i < hi; i += T) {
         const long long k = key_of(i);
         if (k == LLONG_MIN) continue;
@@ -500,7 +500,7 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
         if (uu - lo2 > hi2 - lo2) continue;  // outside [lo2, hi2]
         atomicAdd(&s_hist[(uu - lo2) / width], 1u);
       }
-      __syncthreads();
+      cta_sync();
       for (int i = tid; i < kSelBins; i += T)
         if (s_hist[i]) atomicAdd(&gh[i], s_hist[i]);
       if (!grid_sync(bar, err, tns)) return false;
@@ -524,10 +524,10 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
           s_ab = a0 + h0;
         }
       }
-      __syncthreads();
+      cta_sync();
       const int bb = s_b;
       const long long ab = s_ab;
-      __syncthreads();
+      cta_sync();
       const unsigned long long bin_lo = lo2 + width * (unsigned long long)bb;
       if (width == 1ull) {
         tau = (long long)bin_lo;
@@ -615,15 +615,15 @@ static __device__ bool grid_lazy_step(const int32_t *__restrict__ act, int32_t m
 
 // Proposal scores of the active list for this round (every CTA, one warp per
 // candidate): score[i] = network output on the candidate's features.
-static __device__ void lazy_score(const int32_t *__restrict__ act, int32_t m, const float *__restrict__ prop,
-                           const int32_t *__restrict__ rp, const int32_t *__restrict__ dS,
-                           const long long *__restrict__ ub, const int32_t *__restrict__ stamp,
+static __device__ void lazy_score(const int32_t *act, int32_t m, const float *__restrict__ prop,
+                           const int32_t *__restrict__ rp, const int32_t *dS,
+                           const long long *ub, const int32_t *stamp,
                            const long long *__restrict__ two_hop, const int32_t *__restrict__ mx, int32_t round,
                            long long prev_gain, float *score) {
   __shared__ float sw[kMlpParams];
   __shared__ float sh[kGridGainThreads / 32][kMlpHidden];
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = prop[i];
-  __syncthreads();
+  cta_sync();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid, nw = gridDim.x * (blockDim.x >> 5);
   for (int i = gw; i < m; i += nw) {
@@ -632,7 +632,7 @@ static __device__ void lazy_score(const int32_t *__restrict__ act, int32_t m, co
     const float o = mlp_forward_warp(sw, f, sh[wid]);
     if (lane == 0) score[i] = o;
   }
-  __syncthreads();
+  cta_sync();
 }
 
 }  // namespace gc

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "gc_device.cuh"
 #include "gc_internal.cuh"
 #include "gc_mlp.cuh"
 
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_forward(const float *__rest
   __shared__ float sw[kMlpParams];
   __shared__ float sh[kMlpThreads / 32][kMlpHidden];
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = W[i];
-  __syncthreads();
+  cta_sync();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid, nw = gridDim.x * (blockDim.x >> 5);
   for (int s = gw; s < m; s += nw) {
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwdbwd(const float *__restr
   __shared__ float sh1[kMlpThreads / 32][kMlpHidden];
   __shared__ float sd2[kMlpThreads / 32][kMlpHidden];
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = W[i];
-  __syncthreads();
+  cta_sync();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid, nw = gridDim.x * (blockDim.x >> 5);
   double lsum = 0;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(1024) k_round1_propose(int32_t *list, int32_t 
     s_ub[i] = i < m ? ub[s_id[i]] : LLONG_MIN;
     s_key[i] = -INFINITY;
   }
-  __syncthreads();
+  cta_sync();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = wid; i < m; i += blockDim.x >> 5) {
     float f[kMlpIn];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(1024) k_round1_propose(int32_t *list, int32_t 
     const float o = mlp_forward_warp(sw, f, sh[wid]);
     if (lane == 0) s_key[i] = o;
   }
-  __syncthreads();
+  cta_sync();
   // bitonic sort of (key desc, ub desc, id asc) over kProposeMax entries
   for (int size = 2; size <= kProposeMax; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(1024) k_round1_propose(int32_t *list, int32_t 
           const int ti = s_id[i]; s_id[i] = s_id[j]; s_id[j] = ti;
         }
       }
-      __syncthreads();
+      cta_sync();
     }
   }
   if (threadIdx.x < kLanes && threadIdx.x < m) list[threadIdx.x] = s_id[threadIdx.x];

@@ -24,8 +24,8 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpIn * kMlpHidden, kOffW2 = kOffB1
 //   0 log1p(deg)  1 d_S  2 log1p(max(ub,0))  3 round - stamp  4 log1p(two_hop)
 //   5 mx - d_S    6 log1p(prev_gain)          7 f2 - f6
 __device__ __forceinline__ void cand_features(int v, const int32_t *__restrict__ rp,
-                                              const int32_t *__restrict__ dS, const long long *__restrict__ ub,
-                                              const int32_t *__restrict__ stamp,
+                                              const int32_t *dS, const long long *ub,
+                                              const int32_t *stamp,
                                               const long long *__restrict__ two_hop,
                                               const int32_t *__restrict__ mx, int32_t round, long long prev_gain,
                                               float *f) {

@@ -116,12 +116,12 @@ __device__ __forceinline__ long long r0_block_min(long long v, long long *sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
+  cta_sync();
   if (lane == 0) sh[wid] = v;
-  __syncthreads();
+  cta_sync();
   v = LLONG_MAX;
   for (int w = 0; w < nw; ++w) v = min(v, sh[w]);
-  __syncthreads();
+  cta_sync();
   return v;
 }
 
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
       const int lo = 64 * tid;
       s_alive[tid] = nb >= lo + 64 ? ~0ull : (nb > lo ? ((1ull << (nb - lo)) - 1ull) : 0ull);
     }
-    __syncthreads();
+    cta_sync();
     // ---------- distance 1: the candidates' rows, top-down ----------
     {
       const int j = tid;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
       const int ex = block_excl_scan(j < B ? deg : 0, s_scan, &total);
       if (j < B) s_eoff[j] = ex;
       if (j == 0) s_eoff[B] = total;
-      __syncthreads();
+      cta_sync();
       if (b == 0 && j < nb) {  // level 0: each lane reaches its candidate
         const int c = s_cand[j];
         atomicOr(&vis[(size_t)c * W + (j >> 6)], 1ull << (j & 63));
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
           atomicAdd(&s_lc[lo], 1u);
         }
       }
-      __syncthreads();
+      cta_sync();
       for (int j2 = tid; j2 < nb; j2 += T)
         if (s_lc[j2]) {
           atomicAdd(&ctl->tot[1][j2], (u64)s_lc[j2]);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         if (drop) atomicAnd(&s_alive[j >> 6], ~(1ull << (j & 63)));
         if (write && b == 0) lgain[s_pos[j]] = out;
       }
-      __syncthreads();
+      cta_sync();
       if (b == 0)  // the next level's totals (read two folds ago by every CTA)
         for (int j = tid; j < B; j += T) ctl->tot[(d + 1) % 3][j] = 0;
       int alive_cnt = 0;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         alive_cnt = 0;
       }
       if (co && d == 2 && b == 0 && tid == 0) ctl->co_lanes += (unsigned long long)nb;
-      __syncthreads();
+      cta_sync();
       if (alive_cnt == 0) {
         any_alive = false;
         break;
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         }
       }
       w_claim += l_claim;
-      __syncthreads();
+      cta_sync();
       for (int j = tid; j < nb; j += T)
         if (s_lc[j]) {
           atomicAdd(&ctl->tot[(d + 1) % 3][j], (u64)s_lc[j]);
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
           st_words<W>(vis + (size_t)s_cand[j] * W, z);
         }
       clear_frontier<W>(vis, fbs[1], nbw, false);
-      __syncthreads();
+      cta_sync();
       if (!grid_sync(&ctl->bar, err, tns)) break;
     }
     clear_frontier<W>(bufs[d % 3], fbs[d % 3], nbw);

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sel_range(int32_t n, const long
     __threadfence();
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
+  cta_sync();
   if (!last) return;
   __threadfence();
   mx = LLONG_MIN;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sel_range(int32_t n, const long
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
   }
-  __syncthreads();
+  cta_sync();
   if (lane == 0) {
     smx[wid] = mx;
     smn[wid] = mn;
@@ -124,14 +124,14 @@ __global__ void __launch_bounds__(kRedThreads) k_sel_hist(int32_t n, const long 
   const unsigned long long span = (unsigned long long)hi - (unsigned long long)lo + 1ull;
   const unsigned long long width = span / kHistBins + ((span % kHistBins) ? 1ull : 0ull);
   for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
+  cta_sync();
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const long long k = sel_key<MODE>(v, ub, stamp, round, key);
     if (k == LLONG_MIN || k < lo || k > hi) continue;
     const unsigned long long b = ((unsigned long long)k - (unsigned long long)lo) / width;
     atomicAdd(&sh[b], 1u);
   }
-  __syncthreads();
+  cta_sync();
   for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(1024) k_sel_pick(unsigned int *hist, SelCtl *c
       s_above = total - (long long)hist[0];
       s_here = hist[0];
     }
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) {
       const unsigned long long lo = (unsigned long long)ctl->lo, hi = (unsigned long long)ctl->hi;
       const unsigned long long span = hi - lo + 1ull;
@@ -267,12 +267,12 @@ __device__ __forceinline__ void block_arg(long long &v, int &id, long long *sv, 
       id = oid;
     }
   }
-  __syncthreads();
+  cta_sync();
   if (lane == 0) {
     sv[wid] = v;
     sid[wid] = id;
   }
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0)
     for (int w = 1; w < nw; ++w)
       if (MAX ? better_max(sv[w], sid[w], v, id) : better_min(sv[w], sid[w], v, id)) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kRedThreads) k_after_eval_lazy(const int32_t *
     __threadfence();
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
+  cta_sync();
   if (!last) return;
   __threadfence();
   bv = ctl->best_gain;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kRedThreads) k_unevaluated_best(int32_t n, con
     __threadfence();
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
+  cta_sync();
   if (!last) return;
   __threadfence();
   bv = LLONG_MIN;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kRedThreads) k_argmin(int32_t n, const long lo
     __threadfence();
     last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
+  cta_sync();
   if (!last) return;
   __threadfence();
   bv = LLONG_MAX;

@@ -374,13 +374,13 @@ class Batch:
         self.close()
 
     def greedy(self, ks, active_target: int = 0, lanes: int = 0, capture: bool = False, timeout_ms: int = 0,
-               grid_min_n: int = 0):
+               grid_min_n: int = 0, round1_bound: bool = True):
         ks = np.ascontiguousarray(ks, dtype=np.int32)
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.active_target, o.step_lanes = active_target, lanes
         o.batch_grid_min_n = grid_min_n
-        o.flags = GC_OPT_CAPTURE if capture else 0
+        o.flags = (GC_OPT_CAPTURE if capture else 0) | (0 if round1_bound else GC_OPT_NO_ROUND1_BOUND)
         if timeout_ms:
             o.timeout_ms = timeout_ms
         groups = np.zeros(max(int(ks.sum()), 1), dtype=np.int32)

@@ -46,11 +46,14 @@ def test_batch_matches_oracle(gcm):
     graphs, ks = mixed_batch()
     ref = oracle_groups(graphs, ks)
     with gcm.Batch(graphs) as B:
-        # grid_min_n: 1 = every graph's lazy rounds grid-wide, -1 = all CTA-local
-        for act, lanes, gmin in ((0, 0, 0), (2, 16, 1), (64, 64, -1), (0, 0, 1)):
-            groups, far, st = B.greedy(ks, active_target=act, lanes=lanes, grid_min_n=gmin)
+        # grid_min_n: 1 = every graph's lazy rounds grid-wide, -1 = all CTA-local;
+        # bound: round 1 from two-hop bounds (default) or over every vertex
+        for act, lanes, gmin, bound in ((0, 0, 0, True), (2, 16, 1, True), (64, 64, -1, True), (0, 0, 1, True),
+                                        (0, 0, 0, False), (2, 16, 1, False)):
+            groups, far, st = B.greedy(ks, active_target=act, lanes=lanes, grid_min_n=gmin, round1_bound=bound)
             for i, ((g, f), got) in enumerate(zip(ref, groups)):
-                np.testing.assert_array_equal(got, g, err_msg="graph %d (act %d, gmin %d)" % (i, act, gmin))
+                np.testing.assert_array_equal(got, g, err_msg="graph %d (act %d, gmin %d, bound %s)"
+                                              % (i, act, gmin, bound))
                 assert far[i] == f
 
 
