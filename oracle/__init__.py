@@ -65,6 +65,8 @@ def _load():
             lib.or_gains_bitparallel.argtypes = [i32, vp, vp, vp, i32, vp]
             lib.or_top1_closeness.restype = ctypes.c_int
             lib.or_top1_closeness.argtypes = [i32, vp, vp, i32, vp, vp, vp]
+            lib.or_topk_closeness.restype = ctypes.c_int
+            lib.or_topk_closeness.argtypes = [i32, vp, vp, i32, i32, vp, vp, vp]
             lib.or_greedypp.restype = ctypes.c_int
             lib.or_greedypp.argtypes = [i32, vp, vp, i32, vp, vp, vp, i32, ctypes.POINTER(_GppStats)]
             lib.or_greedypp_cost_sample.restype = ctypes.c_int
@@ -172,6 +174,21 @@ def top1_closeness(row_ptr, col_idx, threads: int | None = None):
     if rc:
         raise ValueError("disconnected graph")
     return s0.value, f0.value, full.value
+
+
+def topk_closeness(row_ptr, col_idx, k: int, threads: int | None = None):
+    """Top-k closeness (Sec. 3.1, Algorithm 3): (ids, farness values) of the k
+    vertices of smallest farness, ordered by (farness, id); plus the number of
+    BFSs that ran to completion."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    ids = np.zeros(k, dtype=np.int32)
+    f = np.zeros(k, dtype=np.int64)
+    full = ctypes.c_int64()
+    rc = _load().or_topk_closeness(n, rp.ctypes.data, ci.ctypes.data, k, threads or default_threads(),
+                                   ids.ctypes.data, f.ctypes.data, ctypes.addressof(full))
+    if rc:
+        raise ValueError("disconnected graph or k outside [1, n]" if rc == -1 else "allocation failed")
+    return ids, f, full.value
 
 
 def greedypp(row_ptr, col_idx, k: int, threads: int | None = None):

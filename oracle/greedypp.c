@@ -199,6 +199,92 @@ int or_top1_closeness(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
   return 0;
 }
 
+/* Top-k closeness (Sec. 3.1, Algorithm 3 with general k): the k vertices of
+ * smallest farness f({v}), ordered by (farness, id).  Vertices are searched in
+ * decreasing degree order (ties: smaller id first).  While fewer than k
+ * searches have completed nothing is cut; afterwards a BFS is cut once its
+ * bound exceeds the k-th best (farness, id) pair found so far, lexicographically
+ * (tie-safe, as in the top-1 search).  A completed search replaces the k-th best
+ * when it is smaller.  ids_out / f_out receive the k results in order.
+ * Returns 0, -1 (disconnected or k outside [1, n]) or -2 (allocation). */
+int or_topk_closeness(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t k, int32_t nthreads,
+                      int32_t *ids_out, int64_t *f_out, int64_t *n_full) {
+  if (k < 1 || k > n) return -1;
+  int nt = nthreads > 0 ? nthreads : 1;
+  int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int64_t *top_f = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+  int32_t *top_id = (int32_t *)malloc((size_t)k * sizeof(int32_t));
+  if (!order || !top_f || !top_id) { free(order); free(top_f); free(top_id); return -2; }
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d > maxd) maxd = d;
+  }
+  int64_t *cnt = (int64_t *)calloc((size_t)maxd + 2, sizeof(int64_t));
+  if (!cnt) { free(order); free(top_f); free(top_id); return -2; }
+  for (int32_t v = 0; v < n; ++v) cnt[maxd - (row_ptr[v + 1] - row_ptr[v]) + 1]++;
+  for (int32_t d = 1; d <= maxd + 1; ++d) cnt[d] += cnt[d - 1];
+  for (int32_t v = 0; v < n; ++v) order[cnt[maxd - (row_ptr[v + 1] - row_ptr[v])]++] = v;
+  free(cnt);
+
+  int32_t have = 0;  /* results so far, kept sorted by (farness, id) in top_f / top_id */
+  int64_t full = 0;
+  int err = 0;
+#pragma omp parallel num_threads(nt)
+  {
+    bfs_ws w;
+    int ok = ws_init(&w, n) == 0;
+    if (!ok) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = 0; i < n; ++i) {
+      if (!ok) continue;
+      int32_t v = order[i];
+      int64_t bf = -1;  /* no cut until k searches have completed */
+      int32_t bi = -1;
+#pragma omp critical(gpp_topk)
+      {
+        if (have == k) { bf = top_f[k - 1]; bi = top_id[k - 1]; }
+      }
+      int64_t f = bfscut(n, row_ptr, col_idx, v, bf, bi, &w);
+      if (f == -2) {
+#pragma omp atomic write
+        err = 2;
+      }
+      if (f >= 0) {
+#pragma omp atomic
+        full++;
+#pragma omp critical(gpp_topk)
+        {
+          /* insert (f, v) if the list is short or it beats the k-th entry */
+          if (have < k || f < top_f[k - 1] || (f == top_f[k - 1] && v < top_id[k - 1])) {
+            int32_t j = have < k ? have++ : k - 1;
+            while (j > 0 && (top_f[j - 1] > f || (top_f[j - 1] == f && top_id[j - 1] > v))) {
+              top_f[j] = top_f[j - 1];
+              top_id[j] = top_id[j - 1];
+              --j;
+            }
+            top_f[j] = f;
+            top_id[j] = v;
+          }
+        }
+      }
+    }
+    if (ok) ws_free(&w);
+  }
+  free(order);
+  if (!err) {
+    for (int32_t j = 0; j < k; ++j) { ids_out[j] = top_id[j]; f_out[j] = top_f[j]; }
+    if (n_full) *n_full = full;
+  }
+  free(top_f);
+  free(top_id);
+  if (err) return err == 1 ? -2 : -1;
+  return 0;
+}
+
 /* Greedy++ (pruned SSSPs + supermodular lazy bounds), farness form.
  * Outputs as or_greedy_plain; stats may be NULL.  Returns 0 / -1 / -2. */
 int or_greedypp(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t k,

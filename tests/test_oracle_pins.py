@@ -276,6 +276,63 @@ def test_top1_closeness(name, g):
     assert s0 == int(np.argmin(f)) and f0 == min(f)
 
 
+# --------------------------- top-k closeness (Sec. 3.1, Algorithm 3, k > 1) ---
+def topk_by_definition(f, k):
+    """The k smallest (farness, id) pairs of a list of single-vertex farness values."""
+    order = sorted(range(len(f)), key=lambda v: (f[v], v))[:k]
+    return np.array(order, dtype=np.int32), np.array([f[v] for v in order], dtype=np.int64)
+
+
+@pytest.mark.parametrize("name,g", o2_cases())
+def test_topk_closeness_equals_sorted_farness(name, g):
+    rp, ci = g
+    n = rp.size - 1
+    if n <= 500:  # farness from Floyd-Warshall row sums: no BFS code involved
+        f = [int(x) for x in apsp_fw(rp, ci).sum(axis=1)]
+    else:         # the plain BFS farness, itself pinned to Floyd-Warshall above
+        f = [oracle.farness(rp, ci, [v]) for v in range(n)]
+    for k in sorted({1, 2, 5, 17, n // 3 or 1, n}):
+        if k > n:
+            continue
+        ids, fk, _ = oracle.topk_closeness(rp, ci, k)
+        want_ids, want_f = topk_by_definition(f, k)
+        np.testing.assert_array_equal(ids, want_ids, err_msg="%s k=%d" % (name, k))
+        np.testing.assert_array_equal(fk, want_f, err_msg="%s k=%d" % (name, k))
+
+
+@pytest.mark.parametrize("n", [9, 20, 33])
+def test_topk_closeness_closed_forms(n):
+    # path: f(v) = v(v+1)/2 + (n-1-v)(n-v)/2, smallest around the middle
+    rp, ci = sg.path(n)
+    f = [v * (v + 1) // 2 + (n - 1 - v) * (n - v) // 2 for v in range(n)]
+    ids, fk, _ = oracle.topk_closeness(rp, ci, 5)
+    np.testing.assert_array_equal(ids, topk_by_definition(f, 5)[0])
+    np.testing.assert_array_equal(fk, topk_by_definition(f, 5)[1])
+    # cycle: every vertex has floor(n^2/4), so the k smallest ids
+    rp, ci = sg.cycle(n)
+    ids, fk, _ = oracle.topk_closeness(rp, ci, 4)
+    assert ids.tolist() == [0, 1, 2, 3] and (fk == n * n // 4).all()
+    # star with centre 0: n-1, then leaves at 2n-3 in id order
+    rp, ci = sg.star(n)
+    ids, fk, _ = oracle.topk_closeness(rp, ci, 3)
+    assert ids.tolist() == [0, 1, 2] and fk.tolist() == [n - 1, 2 * n - 3, 2 * n - 3]
+
+
+def test_topk_closeness_k1_and_threads():
+    rp, ci = graphgen.rmat(12, 8.0, seed=5)
+    s0, f0, _ = oracle.top1_closeness(rp, ci)
+    ids, fk, _ = oracle.topk_closeness(rp, ci, 1)
+    assert ids.tolist() == [s0] and fk.tolist() == [f0]
+    a = oracle.topk_closeness(rp, ci, 40, threads=1)
+    b = oracle.topk_closeness(rp, ci, 40, threads=4)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    with pytest.raises(ValueError):
+        oracle.topk_closeness(rp, ci, 0)
+    with pytest.raises(ValueError):
+        oracle.topk_closeness(rp, ci, rp.size)
+
+
 def test_errors():
     rp, ci = sg.disjoint_union(sg.path(3), sg.path(4))
     with pytest.raises(ValueError):
