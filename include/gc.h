@@ -307,6 +307,23 @@ int gc_gain_upper_bounds(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *
 int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group,
               int64_t *out_farness, gc_stats *stats);
 
+/* gc_top_closeness -- top-k closeness (Sec. 3.1, Algorithm 3 with general k):
+ * the k vertices of smallest single-vertex farness f({v}) = sum_u d(v, u), in
+ * increasing order of (farness, id).  Bit-parallel BFScut searches as in round
+ * 0 of gc_greedy, with the cut fixed at an upper bound of the k-th smallest
+ * farness (the k-th best of at least k exact probe searches), so no vertex of
+ * the result is ever cut.  k = 1 gives s0 of gc_greedy.
+ * k          : 1 <= k <= n.
+ * opts       : NULL = defaults (round0_lanes, max_ctas, timeout, flags
+ *              GC_OPT_R0_FULL_LEVELS are used).
+ * out_ids    : host int32[k], the vertices in order.
+ * out_farness: host int64[k], their farness values.
+ * stats      : optional; round0_evals = vertices searched (probes and
+ *              survivors of the bound), ms_total, kernel_launches.
+ * Errors   : GC_EINVAL, GC_EDISCONNECTED, GC_ETIMEOUT, GC_ENOMEM, GC_ECUDA. */
+int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_ids, int64_t *out_farness,
+                     gc_stats *stats);
+
 /* ------------------------------------------------- learned proposal ---- */
 /* A small network that only ORDERS exact evaluations (not part of the paper;
  * the acceptance rule of Sec. 4.2 is unchanged, so the group is identical with

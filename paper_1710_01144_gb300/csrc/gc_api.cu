@@ -413,6 +413,146 @@ int gc_gain_upper_bounds(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *
   return GC_OK;
 }
 
+// Top-k closeness (Sec. 3.1, Algorithm 3 with general k): the k vertices of
+// smallest farness f({v}), ordered by (farness, id).  The round-0 machinery of
+// gc_greedy with one change: the BFScut threshold is fixed at an upper bound
+// T of the k-th smallest farness instead of following the best farness found.
+//   1. lower bounds LB(v) (the round-0 keys); one BFS from the vertex of
+//      smallest bound, whose depth picks the search path and whose levels
+//      tighten the bounds of deep graphs (pivot bound);
+//   2. probes: at least k vertices of smallest bound, searched to the end;
+//      T = the k-th smallest of their farness values (>= the true k-th);
+//   3. every other vertex with LB(v) <= T, searched with the cut fixed at T:
+//      a vertex of the true top k has LB <= f <= T, so it is never cut;
+//   4. the k smallest (farness, id) among the vertices searched exactly.
+int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_ids, int64_t *out_farness,
+                     gc_stats *stats) {
+  if (!g || !out_ids || !out_farness || k < 1 || k > g->n)
+    return fail(GC_EINVAL, "bad argument to gc_top_closeness (need 1 <= k <= n)");
+  gc_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gc_opts_default(&opts);
+  const int64_t tns = timeout_ns(&opts);
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = g->launches;
+  g->mx = nullptr;
+  GC_CUDA(cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), g->stream));
+  GC_CUDA(cudaMemsetAsync(g->gctl, 0, sizeof(GainCtl), g->stream));
+  GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+  GC_TRY(launch_fill_i64(g, g->f0, -1, g->n));
+  GC_TRY(launch_round0_keys(g));
+  GC_TRY(launch_argmin_lb(g));
+  GC_TRY(distances_from(g, &g->sctl->arg_id, 1, tns, nullptr));
+  const int32_t ecc = g->h_bctl->levels;
+  if (ecc > kShallowLevels) GC_TRY(launch_pivot_bound(g));
+  // 2. probes, searched with no cut (threshold +infinity, kept fixed)
+  struct {
+    long long best_f;
+    int32_t fixed;
+  } thr = {LLONG_MAX, 1};
+  GC_CUDA(cudaMemcpyAsync(&g->gctl->best_f, &thr.best_f, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
+  GC_CUDA(cudaMemcpyAsync(&g->gctl->fixed_best, &thr.fixed, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_select(g, kSelKey, 0, k, kTauHistogram, 0));
+  GC_TRY(read_ctl(g));
+  const int32_t n_probe = std::min<int32_t>(g->h_sctl->n_sel, (k + kLanes - 1) / kLanes * kLanes);
+  if (n_probe < k) return fail(GC_EINTERNAL, "top-k closeness: fewer probes than k");
+  GC_TRY(launch_clamp_nsel(g, n_probe));
+  if (n_probe <= kRound0GridMax) {
+    for (int32_t off = 0; off < n_probe; off += kLanes)
+      GC_TRY(launch_gains_grid(g, kModeFarness, g->list + off, std::min<int32_t>(kLanes, n_probe - off), nullptr,
+                               g->lgain + off, tns, false));
+  } else {
+    GC_TRY(launch_gains(g, kModeFarness, g->list, n_probe, nullptr, g->lgain, opts.max_ctas, kLanes, false));
+  }
+  GC_TRY(launch_after_eval(g, 0, 0));
+  std::vector<long long> pf(n_probe);
+  GC_CUDA(cudaMemcpyAsync(pf.data(), g->lgain, (size_t)n_probe * sizeof(long long), cudaMemcpyDeviceToHost,
+                          g->stream));
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  std::sort(pf.begin(), pf.end());
+  if (pf[0] < 0) return fail(GC_EINTERNAL, "top-k closeness: a probe search did not complete");
+  const long long T = pf[k - 1];
+  // 3. every vertex whose bound reaches at most T, cut at T (fixed)
+  thr.best_f = T;
+  GC_CUDA(cudaMemcpyAsync(&g->gctl->best_f, &thr.best_f, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_select(g, kSelKey, 0, 0, kTauHost, -T));
+  GC_TRY(read_ctl(g));
+  const int32_t n_surv = g->h_sctl->n_sel;
+  int r0_w = 0;
+  if (n_surv > 0 && opts.round0_lanes >= 0 && ecc <= kShallowLevels) {
+    const int want = opts.round0_lanes > 0 ? opts.round0_lanes : (n_surv > 128 ? 256 : n_surv > 64 ? 128 : 64);
+    r0_w = want >= 512 ? 8 : want >= 256 ? 4 : want >= 128 ? 2 : 1;
+    if (opts.round0_lanes == 0) {  // the same choice as round 0 of gc_greedy
+      GC_TRY(launch_sum_two_hop(g, (unsigned long long *)g->g3));
+      unsigned long long two_hop_sum = 0;
+      GC_CUDA(cudaMemcpyAsync(&two_hop_sum, g->g3, sizeof(two_hop_sum), cudaMemcpyDeviceToHost, g->stream));
+      GC_TRY(sync(g));
+      const double passes = std::ceil((double)n_surv / (64.0 * r0_w));
+      if ((double)two_hop_sum < passes * (double)g->nnz) r0_w = 0;
+    }
+  }
+  float ms_wide = 0.f;
+  if (n_surv > 0) {
+    if (r0_w > 0) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      GC_TRY(gain_event(g, 0, &e0));
+      GC_TRY(gain_event(g, 1, &e1));
+      GC_CUDA(cudaEventRecord(e0, g->stream));
+      GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w,
+                                !(opts.flags & GC_OPT_R0_FULL_LEVELS), tns));
+      GC_CUDA(cudaEventRecord(e1, g->stream));
+      GC_TRY(sync(g));
+      GC_CUDA(cudaEventElapsedTime(&ms_wide, e0, e1));
+    } else if (n_surv <= kRound0GridMax) {
+      for (int32_t off = 0; off < n_surv; off += kLanes)
+        GC_TRY(launch_gains_grid(g, kModeFarness, g->list + off, std::min<int32_t>(kLanes, n_surv - off), nullptr,
+                                 g->lgain + off, tns, false));
+    } else {
+      GC_TRY(launch_gains(g, kModeFarness, g->list, n_surv, nullptr, g->lgain, opts.max_ctas, kLanes, false));
+    }
+    GC_TRY(launch_after_eval(g, 0, 0));
+  }
+  GC_TRY(read_ctl(g));
+  GC_TRY(device_errors(g));
+  // 4. the k smallest (farness, id): every vertex at or below the selection
+  // threshold, then sorted here (ties at the threshold add a few entries)
+  GC_TRY(launch_topk_keys(g));
+  GC_TRY(launch_select(g, kSelKey, 0, k, kTauHistogram, 0));
+  GC_TRY(launch_gather_f0(g));
+  GC_TRY(read_ctl(g));
+  const int32_t m = g->h_sctl->n_sel;
+  if (m < k) return fail(GC_EINTERNAL, "top-k closeness: fewer exact results than k");
+  std::vector<int32_t> ids(m);
+  std::vector<long long> fs(m);
+  GC_CUDA(cudaMemcpyAsync(ids.data(), g->list, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+  GC_CUDA(cudaMemcpyAsync(fs.data(), g->lgain, (size_t)m * sizeof(long long), cudaMemcpyDeviceToHost, g->stream));
+  GC_TRY(sync(g));
+  std::vector<int32_t> ord(m);
+  for (int32_t i = 0; i < m; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+    return fs[a] < fs[b] || (fs[a] == fs[b] && ids[a] < ids[b]);
+  });
+  for (int32_t i = 0; i < k; ++i) {
+    out_ids[i] = ids[ord[i]];
+    out_farness[i] = fs[ord[i]];
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->round0_evals = (int64_t)n_probe + n_surv;
+    stats->batches = (int64_t)g->h_gctl->batches;
+    stats->edges_union = (int64_t)g->h_gctl->edges_union;
+    stats->levels = (int64_t)g->h_gctl->levels;
+    stats->lanes = (int64_t)g->h_gctl->lanes;
+    stats->ms_round0_wide = ms_wide;
+    stats->r0_width = r0_w * 64;
+    stats->kernel_launches = g->launches - launches0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->ms_round0 = stats->ms_total;
+  }
+  return GC_OK;
+}
+
 int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
               gc_stats *stats) {
   if (!g || !out_group || !out_farness || k < 1 || k > g->n)

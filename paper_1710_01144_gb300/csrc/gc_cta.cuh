@@ -234,7 +234,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
     } else {
       r = (long long)s_gain[tid];
       if (lg.gid) atomicMin(&lg.best_f[lg.gid[c]], r);
-      else atomicMin(&ctl->best_f, r);
+      else if (!ctl->fixed_best) atomicMin(&ctl->best_f, r);
     }
     out[tid] = r;
   }

@@ -421,7 +421,7 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       atomicExch(&gctl->err, GC_EDISCONNECTED);
     } else {
       r = (long long)s_tg[tid];
-      atomicMin(&gctl->best_f, r);
+      if (!gctl->fixed_best) atomicMin(&gctl->best_f, r);
     }
     out[tid] = r;
   }

@@ -119,6 +119,10 @@ struct GainCtl {
   // farness mode, GC_EDISCONNECTED: a candidate whose search ended short and
   // the vertices it reached (for the error message)
   long long short_vertex, short_count;
+  // farness mode: nonzero keeps best_f fixed (top-k closeness cuts at the
+  // k-th best, not at the best farness a search completes with)
+  int32_t fixed_best;
+  int32_t pad;
 };
 
 // Grid-wide gain kernel control block (zeroed before each launch).
@@ -374,6 +378,9 @@ int launch_unevaluated_best(gc_graph *g, int32_t round);
 int launch_argmin_f0(gc_graph *g);
 int launch_argmin_lb(gc_graph *g);
 int launch_round0_seed(gc_graph *g);
+// top-k closeness: key <- -f0 for searched vertices; lgain[i] <- f0[list[i]]
+int launch_topk_keys(gc_graph *g);
+int launch_gather_f0(gc_graph *g);
 int launch_round_begin(gc_graph *g);
 int launch_round_end(gc_graph *g);
 int launch_clamp_nsel(gc_graph *g, int32_t cap);

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
   const int gw = b * (T / 32) + (tid >> 5), nwarps = G * (T / 32);
   const int nbw = (n + 31) >> 5;
   int32_t *err = &gctl->err;
+  const bool fixed_best = *(volatile int32_t *)&gctl->fixed_best != 0;  // top-k: the cut stays at its start
   u64 *bufs[3] = {buf_a, buf_b, buf_c};
   uint32_t *fbs[3] = {fb_a, fb_b, fb_c};
   const int C = nh > 0 ? hcp[nh] : 0;  // heavy-row chunks
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         }
       }
       fmin = r0_block_min(fmin, s_red);
-      bf = min(bf, fmin);
+      if (!fixed_best) bf = min(bf, fmin);
       for (int j = tid; j < nb; j += T) {
         if (!((s_alive[j >> 6] >> (j & 63)) & 1ull)) continue;
         bool drop = false;

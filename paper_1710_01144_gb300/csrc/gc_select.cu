@@ -463,6 +463,20 @@ __global__ void k_round0_pivot(long long *f0, long long *key, SelCtl *ctl, GainC
   ctl->tau = -gctl->best_f;
 }
 
+// Top-k closeness: the selection key of every exactly searched vertex is its
+// negated farness (the k largest keys are the k smallest farness values);
+// vertices never searched, or cut, are not selectable.
+__global__ void k_topk_keys(const long long *f0, int32_t n, long long *key) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    key[v] = f0[v] >= 0 ? -f0[v] : LLONG_MIN;
+}
+
+// lgain[i] <- f0[list[i]] for the selected list
+__global__ void k_gather_f0(const int32_t *list, const long long *f0, long long *lgain, const SelCtl *ctl) {
+  const int m = ctl->n_sel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) lgain[i] = f0[list[i]];
+}
+
 // Start of a lazy round: clear the round's best and the acceptance flag.
 __global__ void k_round_begin(SelCtl *ctl) {
   ctl->best_gain = -1;
@@ -564,6 +578,20 @@ int launch_argmin_f0(gc_graph *g) {
 int launch_argmin_lb(gc_graph *g) {
   ++g->launches;
   k_argmin<1><<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->n, g->key, g->partial, g->sctl);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_topk_keys(gc_graph *g) {
+  ++g->launches;
+  k_topk_keys<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->f0, g->n, g->key);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int launch_gather_f0(gc_graph *g) {
+  ++g->launches;
+  k_gather_f0<<<g->red_blocks, kRedThreads, 0, g->stream>>>(g->list, g->f0, g->lgain, g->sctl);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }

@@ -39,7 +39,8 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_last_error", "gc_marginal_gains_static", "gc_mlp_create", "gc_mlp_free", "gc_mlp_set_params",
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
-           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch")
+           "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch",
+           "gc_top_closeness")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -129,6 +130,7 @@ def load(path: str = LIB_PATH):
         lib.gc_batch_vertices.restype = i64
         lib.gc_batch_greedy.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_greedy_batch.argtypes = [vp, vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_top_closeness.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded",
@@ -269,6 +271,20 @@ class Graph:
         _check(load().gc_greedy(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
                                 ctypes.byref(st)))
         return grp[:k], f.value, st.as_dict()
+
+    def top_closeness(self, k: int, round0_lanes: int = 0, max_ctas: int = 0, r0_full_levels: bool = False):
+        """gc_top_closeness: (ids, farness values, stats) of the k vertices of
+        smallest farness, ordered by (farness, id)."""
+        o = Opts()
+        load().gc_opts_default(ctypes.byref(o))
+        o.round0_lanes, o.max_ctas = round0_lanes, max_ctas
+        o.flags = GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0
+        ids = np.zeros(max(int(k), 1), dtype=np.int32)
+        f = np.zeros(max(int(k), 1), dtype=np.int64)
+        st = Stats()
+        _check(load().gc_top_closeness(self._h, int(k), ctypes.byref(o), ids.ctypes.data, f.ctypes.data,
+                                       ctypes.byref(st)))
+        return ids[:k], f[:k], st.as_dict()
 
 
 def gains_static(row_ptr_dev, col_idx_dev, S_dev, cand_dev, out_dev, stream=None):
