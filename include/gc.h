@@ -324,6 +324,22 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group,
 int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_ids, int64_t *out_farness,
                      gc_stats *stats);
 
+/* gc_greedy_bits -- bitGreedy++ (Sec. 4.3, Theorem 1): the same group as
+ * gc_greedy, with every round scoring EVERY vertex by bit vectors: b^i_u (the
+ * vertices within distance i of u) built level by level by ORs over the
+ * neighbours, the gain of u being sum_i |b^i_u AND NOT b^i_S| and, in round 0,
+ * the farness of u being sum_i (n - |b^i_u|).  The vectors are held for 64 W
+ * target vertices at a time (W <= 32 words per vertex, two buffers of n x W
+ * words: the memory limit), and a target's bit is dropped once d_S of the
+ * target is reached (pruning).  No lazy bounds: every round is a full sweep.
+ * For small graphs: n <= 65536.
+ * k, opts, out_group, out_farness, stats: as gc_greedy (stats: rounds, levels
+ * swept, evals = n k, ms_total, kernel_launches).
+ * Errors   : GC_EINVAL, GC_ERANGE (n > 65536), GC_EDISCONNECTED, GC_ETIMEOUT,
+ *            GC_ENOMEM, GC_ECUDA. */
+int gc_greedy_bits(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group, int64_t *out_farness,
+                   gc_stats *stats);
+
 /* ------------------------------------------------- learned proposal ---- */
 /* A small network that only ORDERS exact evaluations (not part of the paper;
  * the acceptance rule of Sec. 4.2 is unchanged, so the group is identical with

@@ -553,6 +553,90 @@ int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *ou
   return GC_OK;
 }
 
+// bitGreedy++ (Sec. 4.3, Theorem 1): every round scores every vertex by the
+// bit-vector sweep of gc_bits.cu (round 0: the farness of every vertex; later
+// rounds: every marginal gain against d_S), takes the best (ties: smaller id)
+// and updates d_S by the pruned relabel BFS, whose decrease must equal the
+// pick's gain.  The group equals gc_greedy's.
+int gc_greedy_bits(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
+                   gc_stats *stats) {
+  if (!g || !out_group || !out_farness || k < 1 || k > g->n)
+    return fail(GC_EINVAL, "bad argument to gc_greedy_bits (need 1 <= k <= n)");
+  if (g->n > kBitsMaxN)
+    return fail(GC_ERANGE, "gc_greedy_bits: n above " + std::to_string(kBitsMaxN) +
+                               " (the bit-vector variant is for small graphs)");
+  gc_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gc_opts_default(&opts);
+  const int64_t tns = timeout_ns(&opts);
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = g->launches;
+  const int32_t n = g->n;
+  const int W = std::min(32, (n + 63) / 64);  // 64 W targets per chunk
+  const size_t bytes_B = 2 * (size_t)n * W * sizeof(unsigned long long) + 2 * (size_t)n;  // words, row flags
+  const size_t bytes = ws_align(bytes_B) + ws_align((size_t)n * sizeof(long long)) + ws_align(sizeof(BitsCtl));
+  unsigned char *mem = nullptr;
+  if (cudaMalloc((void **)&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GC_ENOMEM, "gc_greedy_bits: device allocation failed");
+  }
+  unsigned long long *B = (unsigned long long *)mem;
+  long long *out = (long long *)(mem + ws_align(bytes_B));
+  BitsCtl *ctl = (BitsCtl *)(mem + ws_align(bytes_B) + ws_align((size_t)n * sizeof(long long)));
+  BitsCtl h;
+  auto done = [&](int rc) {
+    cudaStreamSynchronize(g->stream);
+    cudaFree(mem);
+    return rc;
+  };
+  auto sweep = [&](int mode) -> int {
+    GC_TRY(launch_bits_round(g, mode, B, out, ctl, W, tns));
+    GC_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(BitsCtl), cudaMemcpyDeviceToHost, g->stream));
+    GC_TRY(sync(g));
+    if (h.err) return fail(h.err, h.err == GC_ETIMEOUT ? "device-side wait timed out" : "bit-vector sweep failed");
+    if (h.best == 0ull) return fail(GC_EINTERNAL, "gc_greedy_bits: no vertex to pick");
+    return GC_OK;
+  };
+  int64_t levels = 0;
+  int rc = sweep(0);  // round 0: s0 = argmin (farness, id)
+  if (rc != GC_OK) return done(rc);
+  levels += (int64_t)h.levels;
+  const int32_t s0 = (int32_t)(0xffffffffu - (unsigned)(h.best & 0xffffffffull));
+  const long long f_s0 = 0x7fffffffll - (long long)(h.best >> 32);
+  GC_CUDA(cudaMemcpyAsync(g->io_a, &s0, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_CUDA(cudaMemsetAsync(g->bctl, 0, sizeof(BfsCtl), g->stream));
+  int64_t f = 0;
+  if ((rc = distances_from(g, g->io_a, 1, tns, &f)) != GC_OK) return done(rc);
+  if (f != f_s0) return done(fail(GC_EINTERNAL, "gc_greedy_bits: farness of s0 disagrees between the sweep and the BFS"));
+  out_group[0] = s0;
+  for (int32_t r = 1; r < k; ++r) {
+    if ((rc = sweep(1)) != GC_OK) return done(rc);
+    levels += (int64_t)h.levels;
+    const int32_t pick = (int32_t)(0xffffffffu - (unsigned)(h.best & 0xffffffffull));
+    const long long gain = (long long)(h.best >> 32);
+    // d_S <- min(d_S, d(pick, .)) by the pruned relabel BFS; its decrease is the gain
+    GC_CUDA(cudaMemcpyAsync(g->io_a, &pick, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+    if ((rc = launch_bfs_relabel(g, g->dS, g->io_a, 1, tns)) != GC_OK) return done(rc);
+    if ((rc = read_ctl(g)) != GC_OK) return done(rc);
+    if (g->h_bctl->err) return done(device_errors(g));
+    if ((long long)g->h_bctl->decrease != gain)
+      return done(fail(GC_EINTERNAL, "gc_greedy_bits: gain of the pick disagrees with the d_S update (round " +
+                                         std::to_string(r) + ")"));
+    f -= gain;
+    out_group[r] = pick;
+  }
+  *out_farness = f;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->rounds = k;
+    stats->levels = levels;
+    stats->evals = (int64_t)n * k;
+    stats->kernel_launches = g->launches - launches0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return done(GC_OK);
+}
+
 int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
               gc_stats *stats) {
   if (!g || !out_group || !out_farness || k < 1 || k > g->n)

@@ -146,6 +146,18 @@ struct GridGainCtl {
   unsigned long long dcnt[3][kLanes];
 };
 
+// Control block of the bit-vector sweep (gc_bits.cu), zeroed before each launch.
+struct BitsCtl {
+  GridBar bar;
+  int32_t err;
+  int32_t pad;
+  unsigned int changed[3];  // farness sweep: some word changed at level i (by i mod 3)
+  int32_t pad2;
+  unsigned long long best;    // packed arg-best of the round
+  unsigned long long levels;  // levels swept, summed over the target chunks
+};
+constexpr int32_t kBitsMaxN = 65536;  // bit-vector variant: packed 32-bit values (farness < 2^31)
+
 // Persistent lazy-rounds kernel control block (gc_lazy.cu).
 struct LazyCtl {
   GridBar bar;
@@ -380,6 +392,12 @@ int launch_argmin_lb(gc_graph *g);
 int launch_round0_seed(gc_graph *g);
 // top-k closeness: key <- -f0 for searched vertices; lgain[i] <- f0[list[i]]
 int launch_topk_keys(gc_graph *g);
+// bitGreedy++ sweep (gc_bits.cu): mode 0 farness of every vertex, mode 1 gain
+// of every vertex against d_S; B holds 2 n W words and then 2 n bytes (row
+// flags), out n int64; ctl->best
+// gets the packed arg-best (see k_bits_argbest)
+int launch_bits_round(gc_graph *g, int mode, unsigned long long *B, long long *out, BitsCtl *ctl, int W,
+                      int64_t tns);
 int launch_gather_f0(gc_graph *g);
 int launch_round_begin(gc_graph *g);
 int launch_round_end(gc_graph *g);

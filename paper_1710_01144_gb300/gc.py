@@ -40,7 +40,7 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
            "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch",
-           "gc_top_closeness")
+           "gc_top_closeness", "gc_greedy_bits")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
         lib.gc_batch_greedy.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_greedy_batch.argtypes = [vp, vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_top_closeness.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_greedy_bits.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded",
@@ -270,6 +271,19 @@ class Graph:
         st = Stats()
         _check(load().gc_greedy(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
                                 ctypes.byref(st)))
+        return grp[:k], f.value, st.as_dict()
+
+    def greedy_bits(self, k: int, timeout_us: int = 0):
+        """gc_greedy_bits (bitGreedy++, every vertex scored every round):
+        (group, farness, stats)."""
+        o = Opts()
+        load().gc_opts_default(ctypes.byref(o))
+        o.timeout_us = timeout_us
+        grp = np.zeros(max(int(k), 1), dtype=np.int32)
+        f = ctypes.c_int64()
+        st = Stats()
+        _check(load().gc_greedy_bits(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
+                                     ctypes.byref(st)))
         return grp[:k], f.value, st.as_dict()
 
     def top_closeness(self, k: int, round0_lanes: int = 0, max_ctas: int = 0, r0_full_levels: bool = False):
