@@ -59,6 +59,14 @@ def _load():
             lib.or_gains.argtypes = [i32, vp, vp, vp, i32, vp, i32, vp, i32]
             lib.or_greedy_plain.restype = ctypes.c_int
             lib.or_greedy_plain.argtypes = [i32, vp, vp, i32, vp, vp, vp, i32]
+            lib.or_dijkstra_multi.restype = i64
+            lib.or_dijkstra_multi.argtypes = [i32, vp, vp, vp, vp, i32, vp]
+            lib.or_wfarness.restype = i64
+            lib.or_wfarness.argtypes = [i32, vp, vp, vp, vp, i32]
+            lib.or_wgains.restype = ctypes.c_int
+            lib.or_wgains.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, vp, i32]
+            lib.or_wgreedy_plain.restype = ctypes.c_int
+            lib.or_wgreedy_plain.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp, i32]
             lib.or_opt_bruteforce.restype = i64
             lib.or_opt_bruteforce.argtypes = [i32, vp, vp, i32, vp]
             lib.or_gains_bitparallel.restype = ctypes.c_int
@@ -138,6 +146,58 @@ def greedy_plain(row_ptr, col_idx, k: int, threads: int | None = None):
     gt = np.empty(k, dtype=np.int64)
     rc = _load().or_greedy_plain(n, rp.ctypes.data, ci.ctypes.data, k, g.ctypes.data,
                                  ft.ctypes.data, gt.ctypes.data, threads or default_threads())
+    if rc:
+        raise ValueError("bad k or disconnected graph")
+    return g, ft, gt
+
+
+def dijkstra(row_ptr, col_idx, weights, src):
+    """Weighted distances from the sources (int64 array, -1 where unreachable)."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    w = _i32(np.asarray(weights, dtype=np.int32))
+    s = np.atleast_1d(np.asarray(src, dtype=np.int32))
+    d = np.zeros(max(n, 1), dtype=np.int64)
+    r = _load().or_dijkstra_multi(n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data, _i32(s).ctypes.data, s.size,
+                                  d.ctypes.data)
+    if r < 0:
+        raise ValueError("bad source id or a weight below 1")
+    return d[:n]
+
+
+def wfarness(row_ptr, col_idx, weights, S) -> int:
+    """Weighted f(S) = sum_u d_w(u, S) (int); raises if undefined."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    w = _i32(np.asarray(weights, dtype=np.int32))
+    s = np.asarray(S, dtype=np.int32)
+    f = _load().or_wfarness(n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data, _i32(s).ctypes.data, s.size)
+    if f < 0:
+        raise ValueError("weighted farness undefined (empty group, bad id, bad weight or disconnected graph)")
+    return int(f)
+
+
+def wgains(row_ptr, col_idx, weights, S, cand, threads: int | None = None):
+    """Weighted Delta(v|S) for each candidate by a full Dijkstra from v."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    w = _i32(np.asarray(weights, dtype=np.int32))
+    s = np.asarray(S, dtype=np.int32)
+    c = np.asarray(cand, dtype=np.int32)
+    out = np.zeros(max(c.size, 1), dtype=np.int64)
+    rc = _load().or_wgains(n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data, _i32(s).ctypes.data, s.size,
+                           _i32(c).ctypes.data, c.size, out.ctypes.data, threads or default_threads())
+    if rc:
+        raise ValueError("bad group or candidate")
+    return out[:c.size]
+
+
+def wgreedy_plain(row_ptr, col_idx, weights, k: int, threads: int | None = None):
+    """Plain weighted greedy (Dijkstra for every SSSP): (group, farness_trace, gain_trace)."""
+    rp, ci, n = _csr(row_ptr, col_idx)
+    w = _i32(np.asarray(weights, dtype=np.int32))
+    g = np.empty(k, dtype=np.int32)
+    ft = np.empty(k, dtype=np.int64)
+    gt = np.empty(k, dtype=np.int64)
+    rc = _load().or_wgreedy_plain(n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data, k, g.ctypes.data,
+                                  ft.ctypes.data, gt.ctypes.data, threads or default_threads())
     if rc:
         raise ValueError("bad k or disconnected graph")
     return g, ft, gt

@@ -282,3 +282,187 @@ int or_gains_bitparallel(int32_t n, const int32_t *row_ptr, const int32_t *col_i
   free(prev); free(cur); free(bS); free(in_S);
   return 0;
 }
+
+/* ------------------------------------------------------ weighted graphs ---- */
+/* The paper's weighted case (Sec. 3.2: every SSSP becomes a Dijkstra search,
+ * O(kn(m + n log n)) for the greedy): positive integer edge weights w[e] >= 1
+ * aligned with col_idx (the same weight in both rows of an edge), distances in
+ * int64, unreachable -1.  Farness, gain and plain greedy are the definitions
+ * above with d the weighted distance. */
+
+typedef struct { int64_t d; int32_t v; } wh_item;
+
+/* binary min-heap on (d, v) */
+static void wh_push(wh_item *h, int64_t *size, int64_t d, int32_t v) {
+  int64_t i = (*size)++;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d < d || (h[p].d == d && h[p].v <= v)) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i].d = d; h[i].v = v;
+}
+
+static wh_item wh_pop(wh_item *h, int64_t *size) {
+  wh_item top = h[0], last = h[--(*size)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= *size) break;
+    if (c + 1 < *size && (h[c + 1].d < h[c].d || (h[c + 1].d == h[c].d && h[c + 1].v < h[c].v))) ++c;
+    if (last.d < h[c].d || (last.d == h[c].d && last.v <= h[c].v)) break;
+    h[i] = h[c];
+    i = c;
+  }
+  h[i] = last;
+  return top;
+}
+
+/* Multi-source Dijkstra: dist[u] = min_{s in src} d(s,u), -1 where
+ * unreachable.  Returns the number of reached vertices, -1 on a bad source
+ * id, -3 on a weight below 1, -2 on allocation failure. */
+int64_t or_dijkstra_multi(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w,
+                          const int32_t *src, int32_t n_src, int64_t *dist) {
+  int64_t nnz = row_ptr[n];
+  wh_item *heap = (wh_item *)malloc((size_t)(nnz + n_src + 1) * sizeof(wh_item));
+  char *done = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!heap || !done) { free(heap); free(done); return -2; }
+  for (int32_t u = 0; u < n; ++u) dist[u] = -1;
+  int64_t size = 0, reached = 0;
+  for (int32_t i = 0; i < n_src; ++i) {
+    int32_t s = src[i];
+    if (s < 0 || s >= n) { free(heap); free(done); return -1; }
+    if (dist[s] != 0) { dist[s] = 0; wh_push(heap, &size, 0, s); }
+  }
+  while (size > 0) {
+    wh_item it = wh_pop(heap, &size);
+    if (done[it.v]) continue;  /* a stale entry */
+    done[it.v] = 1;
+    ++reached;
+    for (int32_t e = row_ptr[it.v]; e < row_ptr[it.v + 1]; ++e) {
+      if (w[e] < 1) { free(heap); free(done); return -3; }
+      int32_t x = col_idx[e];
+      int64_t nd = it.d + w[e];
+      if (!done[x] && (dist[x] < 0 || nd < dist[x])) { dist[x] = nd; wh_push(heap, &size, nd, x); }
+    }
+  }
+  free(heap); free(done);
+  return reached;
+}
+
+/* f(S) = sum_u d(u,S) with weighted distances; -1 if unreachable / bad S. */
+int64_t or_wfarness(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w,
+                    const int32_t *S, int32_t s_len) {
+  if (s_len <= 0) return -1;
+  int64_t *d = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  if (!d) return -2;
+  int64_t reached = or_dijkstra_multi(n, row_ptr, col_idx, w, S, s_len, d);
+  int64_t f = 0;
+  if (reached != n) f = -1;
+  else for (int32_t u = 0; u < n; ++u) f += d[u];
+  free(d);
+  return f;
+}
+
+/* Delta(v|S) = sum_u max(0, dS[u] - d(v,u)) from a FULL Dijkstra out of v. */
+static int64_t wgain_full(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w,
+                          const int64_t *dS, int32_t v, int64_t *dist) {
+  or_dijkstra_multi(n, row_ptr, col_idx, w, &v, 1, dist);
+  int64_t g = 0;
+  for (int32_t u = 0; u < n; ++u)
+    if (dist[u] >= 0 && dS[u] > dist[u]) g += dS[u] - dist[u];
+  return g;
+}
+
+/* gains[i] = Delta(cand[i] | S), weighted.  Returns 0, -1 on bad input. */
+int or_wgains(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, const int32_t *S,
+              int32_t s_len, const int32_t *cand, int32_t n_cand, int64_t *gains, int32_t nthreads) {
+  if (s_len <= 0) return -1;
+  int64_t *dS = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  if (!dS) return -2;
+  if (or_dijkstra_multi(n, row_ptr, col_idx, w, S, s_len, dS) < 0) { free(dS); return -1; }
+  for (int32_t i = 0; i < n_cand; ++i)
+    if (cand[i] < 0 || cand[i] >= n) { free(dS); return -1; }
+  int bad = 0;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+  {
+    int64_t *dist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!dist) {
+#pragma omp atomic write
+      bad = 1;
+    }
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = 0; i < n_cand; ++i)
+      if (dist) gains[i] = wgain_full(n, row_ptr, col_idx, w, dS, cand[i], dist);
+    free(dist);
+  }
+  free(dS);
+  return bad ? -2 : 0;
+}
+
+/* Plain weighted greedy: or_greedy_plain with Dijkstra for every SSSP.
+ * Outputs as or_greedy_plain.  Returns 0, -1 (bad input / disconnected). */
+int or_wgreedy_plain(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *w, int32_t k,
+                     int32_t *group, int64_t *farness_trace, int64_t *gain_trace, int32_t nthreads) {
+  if (k < 1 || k > n) return -1;
+  int nt = nthreads > 0 ? nthreads : 1;
+  int64_t *score = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *dS = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *dnew = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  char *in_S = (char *)calloc((size_t)n, 1);
+  if (!score || !dS || !dnew || !in_S) { free(score); free(dS); free(dnew); free(in_S); return -2; }
+  int rc = 0;
+  /* round 0: s0 = argmin_v f({v}) by n full Dijkstra searches, ties -> smallest id */
+#pragma omp parallel num_threads(nt)
+  {
+    int64_t *dist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 4)
+    for (int32_t v = 0; v < n; ++v) {
+      if (!dist) { score[v] = -2; continue; }
+      int64_t reached = or_dijkstra_multi(n, row_ptr, col_idx, w, &v, 1, dist);
+      int64_t f = 0;
+      for (int32_t u = 0; u < n; ++u) f += dist[u];
+      score[v] = (reached == n) ? f : -1;
+    }
+    free(dist);
+  }
+  int32_t s0 = -1;
+  for (int32_t v = 0; v < n; ++v) {
+    if (score[v] < 0) { rc = -1; break; }
+    if (s0 < 0 || score[v] < score[s0]) s0 = v;
+  }
+  if (s0 < 0) rc = -1;
+  if (rc == 0) {
+    group[0] = s0; in_S[s0] = 1;
+    or_dijkstra_multi(n, row_ptr, col_idx, w, &s0, 1, dS);
+    int64_t f = 0;
+    for (int32_t u = 0; u < n; ++u) f += dS[u];
+    farness_trace[0] = f;
+    gain_trace[0] = f;
+    for (int32_t r = 1; r < k; ++r) {
+#pragma omp parallel num_threads(nt)
+      {
+        int64_t *dist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 4)
+        for (int32_t v = 0; v < n; ++v)
+          score[v] = (in_S[v] || !dist) ? -1 : wgain_full(n, row_ptr, col_idx, w, dS, v, dist);
+        free(dist);
+      }
+      int32_t best = -1;
+      for (int32_t v = 0; v < n; ++v)
+        if (!in_S[v] && (best < 0 || score[v] > score[best])) best = v;
+      if (best < 0 || score[best] < 0) { rc = -2; break; }
+      group[r] = best; in_S[best] = 1;
+      or_dijkstra_multi(n, row_ptr, col_idx, w, &best, 1, dnew);
+      for (int32_t u = 0; u < n; ++u)
+        if (dnew[u] < dS[u]) dS[u] = dnew[u];
+      f = 0;
+      for (int32_t u = 0; u < n; ++u) f += dS[u];
+      gain_trace[r] = farness_trace[r - 1] - f;
+      farness_trace[r] = f;
+    }
+  }
+  free(score); free(dS); free(dnew); free(in_S);
+  return rc;
+}

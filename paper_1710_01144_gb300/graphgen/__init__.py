@@ -140,6 +140,22 @@ def batch_graph(item: BatchItem):
 
 
 # Named workloads (the five evaluation configurations, by what they are).
+def edge_weights(row_ptr, col_idx, w_max: int = 16, seed: int = 1):
+    """Seeded positive integer weights in [1, w_max] for every adjacency entry,
+    the same in both rows of an edge: a splitmix64 hash of (min(u, w),
+    max(u, w), seed).  int32 array aligned with col_idx."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    u = np.repeat(np.arange(rp.size - 1, dtype=np.int64), np.diff(rp))
+    a, b = np.minimum(u, ci).astype(np.uint64), np.maximum(u, ci).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        x = (a * np.uint64(0x9E3779B97F4A7C15)) ^ (b + np.uint64(seed) * np.uint64(0xD1B54A32D192ED03))
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    return (x % np.uint64(w_max)).astype(np.int32) + np.int32(1)
+
+
 def ba_n2000_m5(seed: int = 1):
     return barabasi_albert(2000, 5, seed)
 

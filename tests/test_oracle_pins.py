@@ -333,6 +333,91 @@ def test_topk_closeness_k1_and_threads():
         oracle.topk_closeness(rp, ci, rp.size)
 
 
+# ------------------------------------- weighted graphs (Sec. 3.2, Dijkstra) ---
+def apsp_fw_weighted(rp, ci, w):
+    """All-pairs weighted distances by Floyd-Warshall on the weight matrix."""
+    n = rp.size - 1
+    D = np.full((n, n), 10**15, dtype=np.int64)
+    np.fill_diagonal(D, 0)
+    for u in range(n):
+        for e in range(rp[u], rp[u + 1]):
+            D[u, ci[e]] = min(D[u, ci[e]], int(w[e]))
+    for m in range(n):
+        D = np.minimum(D, D[:, m:m + 1] + D[m:m + 1, :])
+    return D
+
+
+@pytest.mark.parametrize("name,g", o2_cases())
+def test_weighted_with_unit_weights_is_unweighted(name, g):
+    rp, ci = g
+    n = rp.size - 1
+    w = np.ones(ci.size, np.int32)
+    k = min(8, n)
+    a = oracle.greedy_plain(rp, ci, k)
+    b = oracle.wgreedy_plain(rp, ci, w, k)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y, err_msg=name)
+    S = [0, n - 1] if n > 1 else [0]
+    cand = list(range(0, n, max(1, n // 40)))
+    np.testing.assert_array_equal(oracle.wgains(rp, ci, w, S, cand), oracle.gains(rp, ci, S, cand))
+
+
+@pytest.mark.parametrize("name,g", tiny_graphs())
+def test_weighted_matches_floyd_warshall(name, g):
+    rp, ci = g
+    n = rp.size - 1
+    for seed in (1, 2):
+        w = graphgen.edge_weights(rp, ci, 9, seed)
+        D = apsp_fw_weighted(rp, ci, w)
+        for v in range(n):
+            np.testing.assert_array_equal(oracle.dijkstra(rp, ci, w, v), D[v], err_msg=name)
+        S = [v for v in range(0, n, 3)][:3]
+        dS = D[S].min(axis=0)
+        assert oracle.wfarness(rp, ci, w, S) == int(dS.sum())
+        want = [int(np.maximum(0, dS - D[v]).sum()) for v in range(n)]
+        np.testing.assert_array_equal(oracle.wgains(rp, ci, w, S, list(range(n))), want)
+        k = min(5, n)
+        grp, tr = greedy_by_definition(D, k)
+        g2, ft, _ = oracle.wgreedy_plain(rp, ci, w, k)
+        assert g2.tolist() == grp and ft.tolist() == tr, name
+
+
+@pytest.mark.parametrize("n", [5, 12, 30])
+def test_weighted_path_closed_form(n):
+    rp, ci = sg.path(n)
+    w = graphgen.edge_weights(rp, ci, 7, n)
+    P = np.zeros(n, np.int64)  # P[i] = distance from vertex 0 along the path
+    for i in range(1, n):
+        e = next(e for e in range(rp[i], rp[i + 1]) if ci[e] == i - 1)
+        P[i] = P[i - 1] + int(w[e])
+    for v in (0, n // 2, n - 1):
+        assert oracle.wfarness(rp, ci, w, [v]) == int(np.abs(P - P[v]).sum())
+    f = [int(np.abs(P - P[v]).sum()) for v in range(n)]
+    g, ft, _ = oracle.wgreedy_plain(rp, ci, w, 1)
+    assert g[0] == int(np.argmin(f)) and ft[0] == min(f)
+
+
+def test_weighted_scaling_and_supermodularity():
+    rp, ci = graphgen.rmat(9, 6.0, seed=3)
+    n = rp.size - 1
+    w = graphgen.edge_weights(rp, ci, 12, 5)
+    g1, f1, t1 = oracle.wgreedy_plain(rp, ci, w, 6)
+    g3, f3, t3 = oracle.wgreedy_plain(rp, ci, 3 * w, 6)
+    np.testing.assert_array_equal(g1, g3)
+    np.testing.assert_array_equal(3 * f1, f3)
+    rng = np.random.default_rng(7)
+    checks = 0
+    for _ in range(60):
+        T = rng.choice(n, size=6, replace=False)
+        S = T[:3]
+        v = rng.integers(0, n, size=20)
+        a = oracle.wgains(rp, ci, w, S, v)
+        b = oracle.wgains(rp, ci, w, T, v)
+        assert (b <= a).all()
+        checks += v.size
+    assert checks >= 1000
+
+
 def test_errors():
     rp, ci = sg.disjoint_union(sg.path(3), sg.path(4))
     with pytest.raises(ValueError):
