@@ -324,6 +324,29 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group,
 int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_ids, int64_t *out_farness,
                      gc_stats *stats);
 
+/* gc_set_weights -- attach positive integer edge weights to a handle, for the
+ * weighted entry points (the paper's weighted case: every SSSP a
+ * shortest-path search, Sec. 3.2).
+ * weights : int32[nnz] aligned with col_idx, host (copied) or device
+ *           (flags & GC_DEVICE_PTRS, copied); every weight >= 1 and the same
+ *           in both rows of an edge.
+ * flags   : GC_DEVICE_PTRS | GC_VALIDATE (also check the two rows agree).
+ * Errors  : GC_EINVAL (a weight below 1, or rows that disagree under
+ *           GC_VALIDATE), GC_ERANGE ((n - 1) x max weight >= 2^30: path
+ *           lengths could overflow the int32 distances), GC_ENOMEM, GC_ECUDA. */
+int gc_set_weights(gc_graph *g, const int32_t *weights, uint32_t flags);
+
+/* gc_greedy_weighted -- Greedy on the weighted graph: Algorithm 2 with weighted
+ * distances, the pruned searches of Sec. 4.1 (valid for positive weights) and
+ * the lazy bounds of Sec. 4.2; s0 = argmin f({v}) by a full search from every
+ * vertex; ties to the smallest id.  Farness = sum of weighted distances (int64).
+ * Requires gc_set_weights.  k, opts, out_group, out_farness, stats: as
+ * gc_greedy (stats: rounds, steps, evals, round0_evals, ms_total, launches).
+ * Errors   : GC_EINVAL (no weights, bad k), GC_EDISCONNECTED, GC_ENOMEM,
+ *            GC_ECUDA. */
+int gc_greedy_weighted(gc_graph *g, int32_t k, const gc_opts *opts, int32_t *out_group, int64_t *out_farness,
+                       gc_stats *stats);
+
 /* gc_greedy_bits -- bitGreedy++ (Sec. 4.3, Theorem 1): the same group as
  * gc_greedy, with every round scoring EVERY vertex by bit vectors: b^i_u (the
  * vertices within distance i of u) built level by level by ORs over the

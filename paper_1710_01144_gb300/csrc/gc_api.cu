@@ -66,7 +66,7 @@ static void release(gc_graph *g) {
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
                  g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
-                 g->g3, g->c3s, g->r0_vis};
+                 g->g3, g->c3s, g->r0_vis, g->wt, g->w_ws};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -549,6 +549,143 @@ int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *ou
     stats->kernel_launches = g->launches - launches0;
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     stats->ms_round0 = stats->ms_total;
+  }
+  return GC_OK;
+}
+
+// Edge weights for the weighted entry points (gc_weighted.cu).  Checked on the
+// device: every weight >= 1, the same in both rows of an edge (with
+// GC_VALIDATE), and (n - 1) * max weight below kInf, so that no path length
+// can overflow the int32 distances.
+int gc_set_weights(gc_graph *g, const int32_t *weights, uint32_t flags) {
+  if (!g || (g->nnz > 0 && !weights)) return fail(GC_EINVAL, "bad argument to gc_set_weights");
+  if (!g->wt && g->nnz > 0) {
+    int rc = dalloc(&g->wt, (size_t)g->nnz);
+    if (rc) return rc;
+  }
+  if (g->nnz == 0) return GC_OK;
+  const cudaMemcpyKind kind = (flags & GC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  GC_CUDA(cudaMemcpyAsync(g->wt, weights, (size_t)g->nnz * sizeof(int32_t), kind, g->stream));
+  int32_t zero2[2] = {0, 0}, h[2] = {0, 0};
+  GC_CUDA(cudaMemcpyAsync(g->io_b, zero2, sizeof(zero2), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_wcheck(g, (flags & GC_VALIDATE) != 0, g->io_b, g->io_b + 1));
+  GC_CUDA(cudaMemcpyAsync(h, g->io_b, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+  GC_TRY(sync(g));
+  g->w_ok = false;
+  if (h[0]) return fail(GC_EINVAL, (flags & GC_VALIDATE) ? "a weight is below 1 or differs between the two rows of an edge"
+                                                         : "a weight is below 1");
+  if ((int64_t)(g->n - 1) * (int64_t)h[1] >= (int64_t)kInf)
+    return fail(GC_ERANGE, "(n - 1) * max weight reaches 2^30: path lengths could overflow");
+  g->w_ok = true;
+  return GC_OK;
+}
+
+// Weighted Greedy: Algorithm 2 with every SSSP a shortest-path search (the
+// paper's weighted case) and the pruning of Sec. 4.1 and the lazy bounds of
+// Sec. 4.2 unchanged.  Round 0 evaluates f({v}) of every vertex by a full
+// search (a label-correcting search has no distance order to cut on);
+// later rounds take host-driven lazy steps, one candidate per CTA; d_S is
+// updated in place from each pick and its decrease must equal the pick's gain.
+int gc_greedy_weighted(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group, int64_t *out_farness,
+                       gc_stats *stats) {
+  if (!g || !out_group || !out_farness || k < 1 || k > g->n)
+    return fail(GC_EINVAL, "bad argument to gc_greedy_weighted (need 1 <= k <= n)");
+  if (!g->w_ok) return fail(GC_EINVAL, "gc_greedy_weighted: no weights set (gc_set_weights)");
+  gc_opts opts;
+  if (opts_in) opts = *opts_in;
+  else gc_opts_default(&opts);
+  (void)opts;
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = g->launches;
+  const int32_t n = g->n;
+  if (!g->w_ws) {  // per-CTA search workspaces: within 40% of free memory and 16 GB
+    int occ = 0;
+    GC_TRY(wsssp_occupancy(&occ));
+    g->w_stride = wws_stride(n);
+    size_t free_b = 0, total_b = 0;
+    GC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = std::min<size_t>(free_b / 10 * 4, (size_t)16 << 30);
+    int want = std::max(1, occ) * g->num_sms;
+    if ((size_t)want * g->w_stride > budget) want = (int)std::max<size_t>(1, budget / g->w_stride);
+    const size_t bytes = (size_t)want * g->w_stride + 256;
+    if (cudaMalloc((void **)&g->w_ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      g->w_ws = nullptr;
+      return fail(GC_ENOMEM, "gc_greedy_weighted: workspace allocation failed");
+    }
+    g->w_ctas = want;
+    g->w_task = (unsigned int *)(g->w_ws + (size_t)want * g->w_stride);
+    // queue flags 0, then every workspace's dist = kInf
+    for (int c = 0; c < want; ++c) {
+      unsigned char *p = g->w_ws + (size_t)c * g->w_stride;
+      GC_CUDA(cudaMemsetAsync(p, 0, g->w_stride, g->stream));
+    }
+    for (int c = 0; c < want; ++c)
+      GC_TRY(launch_fill_i32(g, (int32_t *)(g->w_ws + (size_t)c * g->w_stride), kInf, n));
+  }
+  GC_CUDA(cudaMemsetAsync(g->sctl, 0, sizeof(SelCtl), g->stream));
+  // ---- round 0: f({v}) of every vertex, s0 = argmin (f, id) ----
+  GC_TRY(launch_iota(g, g->list, n));
+  GC_CUDA(cudaMemcpyAsync(&g->sctl->n_sel, &n, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_wsssp(g, kWFarness, g->list, &g->sctl->n_sel, g->f0, g->w_task));
+  GC_TRY(launch_argmin_f0(g));
+  GC_TRY(read_ctl(g));
+  if (g->h_sctl->err) return fail(g->h_sctl->err, g->h_sctl->err == GC_EDISCONNECTED ? "graph is disconnected"
+                                                                                      : "weighted search failed");
+  const int32_t s0 = g->h_sctl->arg_id;
+  const long long f_s0 = g->h_sctl->arg_val;
+  if (s0 < 0 || s0 >= n) return fail(GC_EINTERNAL, "gc_greedy_weighted: round 0 produced no vertex");
+  // d_S = d(s0, .) by the in-place search from s0; its sum must equal f_s0
+  GC_TRY(launch_fill_i32(g, g->dS, kInf, n));
+  GC_CUDA(cudaMemcpyAsync(g->io_a, &s0, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  GC_TRY(launch_wrelabel(g, g->io_a, &g->bctl->decrease));
+  GC_TRY(launch_sum_dist(g, g->dS));
+  GC_TRY(read_ctl(g));
+  if (g->h_sctl->count != 0 || (long long)g->h_sctl->sum != f_s0)
+    return fail(GC_EINTERNAL, "gc_greedy_weighted: farness of s0 disagrees between round 0 and d_S");
+  long long f = f_s0;
+  out_group[0] = s0;
+  // ---- rounds 1..k-1: host-driven lazy steps, one candidate per CTA ----
+  GC_TRY(launch_fill_i64(g, g->ub, LLONG_MAX, n));
+  GC_TRY(launch_fill_i64(g, g->ub + s0, -1, 1));
+  GC_TRY(launch_fill_i32(g, g->stamp, 0, n));
+  const int32_t step_want = g->w_ctas;
+  int64_t steps = 0, evals = 0;
+  for (int32_t r = 1; r < k; ++r) {
+    GC_TRY(launch_round_begin(g));
+    for (;;) {
+      GC_TRY(launch_select(g, kSelLazy, r, step_want, kTauHistogram, 0));
+      GC_TRY(launch_wsssp(g, kWGain, g->list, &g->sctl->n_sel, g->lgain, g->w_task));
+      GC_TRY(launch_after_eval(g, r, 0));
+      GC_TRY(launch_unevaluated_best(g, r));
+      GC_TRY(read_ctl(g));
+      if (g->h_sctl->err) return fail(g->h_sctl->err, "weighted search failed");
+      ++steps;
+      evals += g->h_sctl->n_sel;
+      if (g->h_sctl->accepted) break;
+      if (g->h_sctl->n_sel == 0) return fail(GC_EINTERNAL, "gc_greedy_weighted: lazy step selected no candidate");
+    }
+    const int32_t pick = g->h_sctl->best_id;
+    const long long gain = g->h_sctl->best_gain;
+    GC_TRY(launch_round_end(g));
+    GC_CUDA(cudaMemcpyAsync(g->io_a, &pick, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+    GC_TRY(launch_wrelabel(g, g->io_a, &g->bctl->decrease));
+    GC_TRY(read_ctl(g));
+    if ((long long)g->h_bctl->decrease != gain)
+      return fail(GC_EINTERNAL, "gc_greedy_weighted: gain of the pick disagrees with the d_S update (round " +
+                                    std::to_string(r) + ")");
+    f -= gain;
+    out_group[r] = pick;
+  }
+  *out_farness = f;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->rounds = k;
+    stats->steps = steps;
+    stats->evals = evals;
+    stats->round0_evals = n;
+    stats->kernel_launches = g->launches - launches0;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return GC_OK;
 }

@@ -259,6 +259,14 @@ struct gc_graph {
   int32_t *mx = nullptr;  // mx[u] >= max over neighbours w of d_S[w] (or nullptr: no pruning)
   int32_t *mx_buf = nullptr;
   long long *two_hop = nullptr;            // sum over neighbours of (deg - 1), feature input
+  // weighted graphs (gc_set_weights, gc_weighted.cu): weights aligned with ci,
+  // the per-CTA search workspaces (allocated on first use) and their task counter
+  int32_t *wt = nullptr;
+  bool w_ok = false;  // weights set and checked
+  unsigned char *w_ws = nullptr;
+  size_t w_stride = 0;
+  int w_ctas = 0;
+  unsigned int *w_task = nullptr;
   float *score = nullptr;                  // proposal scores of the active list [n]
   // learned proposal (caller-owned weights) and training-data recorder
   const float *prop_params = nullptr;
@@ -392,6 +400,17 @@ int launch_argmin_lb(gc_graph *g);
 int launch_round0_seed(gc_graph *g);
 // top-k closeness: key <- -f0 for searched vertices; lgain[i] <- f0[list[i]]
 int launch_topk_keys(gc_graph *g);
+// weighted searches (gc_weighted.cu): kWFarness f({v}) of each listed source,
+// kWGain Delta(v|S) of each listed candidate (one CTA per search, out[i] per
+// list entry); kWRelabel d_S <- min(d_S, d(s, .)) in place (one CTA)
+enum WMode { kWFarness = 0, kWGain = 1, kWRelabel = 2 };
+size_t wws_stride(int32_t n);
+int wsssp_occupancy(int *blocks_per_sm);
+int launch_wsssp(gc_graph *g, int mode, const int32_t *list, const int32_t *m_dev, long long *out,
+                 unsigned int *task);
+int launch_wrelabel(gc_graph *g, const int32_t *src, unsigned long long *decrease);
+int launch_wcheck(gc_graph *g, bool mirror, int32_t *bad, int32_t *max_w);
+int launch_iota(gc_graph *g, int32_t *p, int32_t n);
 // bitGreedy++ sweep (gc_bits.cu): mode 0 farness of every vertex, mode 1 gain
 // of every vertex against d_S; B holds 2 n W words and then 2 n bytes (row
 // flags), out n int64; ctl->best

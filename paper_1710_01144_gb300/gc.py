@@ -40,7 +40,7 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
            "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch",
-           "gc_top_closeness", "gc_greedy_bits")
+           "gc_top_closeness", "gc_greedy_bits", "gc_set_weights", "gc_greedy_weighted")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -132,6 +132,8 @@ def load(path: str = LIB_PATH):
         lib.gc_greedy_batch.argtypes = [vp, vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_top_closeness.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_greedy_bits.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
+        lib.gc_set_weights.argtypes = [vp, vp, ctypes.c_uint32]
+        lib.gc_greedy_weighted.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("gc_num_vertices", "gc_num_entries", "gc_last_error", "gc_recorded",
@@ -271,6 +273,27 @@ class Graph:
         st = Stats()
         _check(load().gc_greedy(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
                                 ctypes.byref(st)))
+        return grp[:k], f.value, st.as_dict()
+
+    def set_weights(self, weights, validate: bool = False):
+        """gc_set_weights: positive int32 edge weights aligned with col_idx
+        (numpy, copied; or an int32 CUDA tensor)."""
+        flags = GC_VALIDATE if validate else 0
+        if hasattr(weights, "data_ptr"):
+            _check(load().gc_set_weights(self._h, weights.data_ptr(), flags | GC_DEVICE_PTRS))
+        else:
+            w = _i32(np.asarray(weights, dtype=np.int32))
+            _check(load().gc_set_weights(self._h, w.ctypes.data, flags))
+
+    def greedy_weighted(self, k: int):
+        """gc_greedy_weighted: (group, farness, stats) with weighted distances."""
+        o = Opts()
+        load().gc_opts_default(ctypes.byref(o))
+        grp = np.zeros(max(int(k), 1), dtype=np.int32)
+        f = ctypes.c_int64()
+        st = Stats()
+        _check(load().gc_greedy_weighted(self._h, int(k), ctypes.byref(o), grp.ctypes.data, ctypes.byref(f),
+                                         ctypes.byref(st)))
         return grp[:k], f.value, st.as_dict()
 
     def greedy_bits(self, k: int, timeout_us: int = 0):
