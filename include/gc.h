@@ -78,6 +78,11 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
                                vertex in round 1 instead of only those whose
                                two-hop upper bound reaches the best exact
                                gain, and skip the bound refresh; work only */
+#define GC_OPT_NO_CLAIM_LOG 0x20u /* gc_greedy, persistent lazy rounds: update d_S
+                               by the relabel BFS from each pick (Sec. 4.1)
+                               instead of from the claim log of the pick's
+                               gain batch (the same vertices at the same
+                               distances); work only */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
@@ -130,6 +135,11 @@ typedef struct gc_opts {
                               microseconds, overriding timeout_ms (a limit
                               that short makes the waits give up with
                               GC_ETIMEOUT; the handle stays usable) */
+  int32_t claim_log_cap;   /* if > 0: at most this many claim-log entries per
+                              round of the persistent lazy kernel (default: the
+                              log allocated at load, 2n entries clamped to
+                              [2^20, 2^24]); a round whose log outgrows it
+                              updates d_S by the relabel BFS; work only */
 } gc_opts;
 
 /* Work counters of the last gc_greedy / gc_marginal_gains call. */
@@ -191,6 +201,10 @@ typedef struct gc_stats {
   int64_t r0_bu_gathers;     /* bottom-up: frontier lane words gathered */
   int64_t r0_width;          /* its candidates per batch (0: not used) */
   int64_t r0_dense_clears;   /* its batches that cleared every visited word */
+  /* gc_greedy: d_S updates of the persistent lazy kernel taken from the claim
+   * log (the rest ran the relabel BFS) */
+  int64_t lazy_log_picks;    /* picks updated from the log */
+  int64_t lazy_upd_log;      /* log entries those updates read */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -66,7 +66,7 @@ static void release(gc_graph *g) {
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
                  g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
-                 g->g3, g->c3s, g->r0_vis, g->wt, g->w_ws};
+                 g->g3, g->c3s, g->r0_vis, g->wt, g->w_ws, g->clog};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -269,6 +269,11 @@ int gc_load_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, uint3
       (rc = dalloc(&g->wgain, (size_t)g->wcap)) ||
       (rc = dalloc(&g->rec_count, 1)))
     return bail(rc);
+  // claim log of the persistent lazy kernel: 2n entries (16 bytes each),
+  // at least 2^20 and at most 2^24; a round that outgrows it falls back to the
+  // relabel BFS for its d_S update
+  g->clog_cap = std::min<long long>(1ll << 24, std::max<long long>(1ll << 20, 2ll * n));
+  if ((rc = dalloc(&g->clog, (size_t)g->clog_cap))) return bail(rc);
   if (cudaMallocHost((void **)&g->h_sctl, sizeof(SelCtl)) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_gctl, sizeof(GainCtl)) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_bctl, sizeof(BfsCtl)) != cudaSuccess ||
@@ -785,6 +790,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   const int64_t tns = timeout_ns(&opts);
   auto t0 = std::chrono::steady_clock::now();
   const int64_t launches0 = g->launches;
+  memset(g->h_lctl, 0, sizeof(LazyCtl));  // the stats read it whether or not the lazy kernel runs
   size_t ev_used = 0;
   int64_t r0_stats[3] = {0, 0, 0};  // wide round-0 kernel: batches, bottom-up levels, top-down entries
   double r0_ms[4] = {0, 0, 0, 0};     // and its phases: selection, top-down, bottom-up, clears
@@ -978,6 +984,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
       init.best_id = -1;
       init.best_pos = -1;
       init.best_gain = -1;
+      init.best_lane = -1;
       init.last_gain = gains_picked[r - 1];
       init.scored_round = -1;
       *g->h_lctl = init;
@@ -1003,7 +1010,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
         GC_CUDA(cudaEventRecord(le0, g->stream));
         GC_TRY(launch_lazy_rounds(g, k, tns, opts.use_proposal && g->prop_fill > 0 ? g->prop_params : nullptr,
                                   g->prop_fill,
-                                  step_form == 2, local_max, opts.lazy_ctas, pruned));
+                                  step_form == 2, local_max, opts.lazy_ctas, pruned,
+                                  !(opts.flags & GC_OPT_NO_CLAIM_LOG), opts.claim_log_cap));
         GC_CUDA(cudaEventRecord(le1, g->stream));
         ++lazy_launches;
         GC_CUDA(cudaMemcpyAsync(g->h_lctl, g->lctl, sizeof(LazyCtl), cudaMemcpyDeviceToHost, g->stream));
@@ -1178,6 +1186,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lazy_upd_edges = (int64_t)g->h_lctl->upd_work[1];
     stats->lazy_upd_relabels = (int64_t)g->h_lctl->upd_relabels;
     stats->lazy_sel_scanned = (int64_t)g->h_lctl->sel_scanned;
+    stats->lazy_log_picks = (int64_t)g->h_lctl->log_picks;
+    stats->lazy_upd_log = (int64_t)g->h_lctl->upd_log;
     stats->r0_batches = r0_stats[0];
     stats->r0_levels = r0_stats[1];
     stats->r0_td_edges = r0_stats[2];

@@ -75,6 +75,9 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *start, int 
 // persistent kernel's selecting CTA does it right after choosing the batch);
 // kBatchRest then runs the rest in every CTA, after a grid barrier the caller
 // placed between the two.  kBatchAll does both with a barrier of its own.
+// With `log` (gain mode), every claim that wins lanes at level L >= 1 appends
+// {w, L, lanes won} at *log_n (one warp-aggregated slot per claim round); slots
+// at or past log_cap are counted in *log_n but not written.
 constexpr int kBatchAll = 0, kBatchLevel0 = 1, kBatchRest = 2;
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -83,7 +86,8 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                                 int32_t *__restrict__ goff, GridGainCtl *ctl, GainCtl *gctl, GridBar *bar,
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
                                 const int32_t *__restrict__ c3 = nullptr, int voff = 0, int ws_n = -1,
-                                int phase = kBatchAll) {
+                                int phase = kBatchAll, ClaimRec *log = nullptr,
+                                unsigned long long *log_n = nullptr, unsigned long long log_cap = 0) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
@@ -307,6 +311,18 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             u64 won = nb[k] & ~ov[k];
             const bool fresh = won && ov[k] == 0;
             const bool q = on[k] == 0ull;
+            if (MODE == kModeGain && log) {
+              const unsigned lm = __ballot_sync(0xffffffffu, won != 0ull);
+              if (lm) {
+                const int leader = __ffs(lm) - 1;
+                unsigned long long at = 0;
+                if (lane == leader) at = atomicAdd(log_n, (unsigned long long)__popc(lm));
+                at = __shfl_sync(0xffffffffu, at, leader) + (unsigned long long)__popc(lm & ((1u << lane) - 1u));
+                if (won && at < log_cap)
+                  *reinterpret_cast<int4 *>(log + at) =
+                      make_int4(w[k], nlev, (int)(unsigned)won, (int)(unsigned)(won >> 32));
+              }
+            }
             if (won) {
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
               do {

@@ -158,6 +158,16 @@ struct BitsCtl {
 };
 constexpr int32_t kBitsMaxN = 65536;  // bit-vector variant: packed 32-bit values (farness < 2^31)
 
+// One entry of the claim log of the persistent lazy kernel: at BFS level
+// `lev` of a 64-lane gain batch, the lanes `won` reached vertex w for the first
+// time.  A lane's entries are its whole pruned search (Sec. 4.1): the vertices
+// with d(candidate, w) < d_S[w], each once, at that distance.
+struct __align__(16) ClaimRec {
+  int32_t w;
+  int32_t lev;
+  unsigned long long won;
+};
+
 // Persistent lazy-rounds kernel control block (gc_lazy.cu).
 struct LazyCtl {
   GridBar bar;
@@ -185,6 +195,15 @@ struct LazyCtl {
   unsigned long long upd_work[2];  // relabel BFS: frontier entries, adjacency entries
   unsigned long long upd_relabels; // relabel BFS: vertices whose d_S decreased
   unsigned long long sel_scanned;  // selection: active-list entries read
+  // claim log of the current round (entries [0, log_n); past the capacity
+  // nothing is written but log_n still counts): the entries of the batches
+  // folded so far end at log_mark; the round's best came from lane best_lane
+  // of the batch whose entries are [best_seg0, best_seg1) (-1: no log)
+  unsigned long long log_n, log_mark, best_seg0, best_seg1;
+  int32_t best_lane;
+  int32_t pad4;
+  unsigned long long upd_log;    // d_S updates from the log: entries read
+  unsigned long long log_picks;  // picks whose d_S update came from the log
 };
 
 // Control block of the wide round-0 kernel (gc_round0.cu), zeroed before each
@@ -289,6 +308,8 @@ struct gc_graph {
   unsigned long long *g3 = nullptr;  // round-1 bounds: sum over u of (d_S[u] - 3)^+
   int32_t *c3s = nullptr;            // bound refresh: neighbours with the current d_S >= 3 [n]
   gc::GridSelScratch *gsel = nullptr;  // grid-wide lazy selection scratch (histograms zero at rest)
+  gc::ClaimRec *clog = nullptr;  // persistent lazy kernel: claim log [clog_cap]
+  long long clog_cap = 0;
   int32_t *wsel = nullptr;     // wide lazy steps: candidates, list positions, gains [wcap]
   int32_t *wpos = nullptr;
   long long *wgain = nullptr;
@@ -452,7 +473,8 @@ int launch_active_theta(gc_graph *g);
 // local_max: largest pick gain whose d_S update runs on one CTA (above it,
 // grid-wide)
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       bool wide, long long local_max, int ctas, bool pruned);
+                       bool wide, long long local_max, int ctas, bool pruned, bool use_log,
+                       long long log_cap);
 int lazy_occupancy(int *blocks_per_sm);
 // round 0 on shallow graphs: f({v}) or -1 (cut / bound above the best) into
 // lgain[i] for list[0..m), B = 64 W lanes per batch (W in {1, 2, 4, 8}); a batch

@@ -17,8 +17,13 @@
 //     candidates: histogram passes over the bounds fix the threshold value,
 //     ties at the threshold go to the smallest ids (list order).
 // Then every CTA runs the 64-lane pruned BFS on that batch (grid_gain_batch).
-// On acceptance every CTA runs the relabel BFS from the pick (the pruned SSSP
-// that turns d_S into min(d_S, d(pick, .)), Sec. 4.1) and the round advances.
+// On acceptance d_S becomes min(d_S, d(pick, .)) and the round advances.  The
+// vertices whose label drops are exactly those the pick's lane reached in its
+// pruned search, at the distances it reached them (Sec. 4.1), so the update
+// reads them from the claim log the batches of the round wrote: one pass over
+// the batch's entries by every CTA, no BFS levels.  If the log ran out of room
+// (or in wide steps, which keep none) every CTA runs the relabel BFS from the
+// pick instead (the pruned SSSP of Sec. 4.1).
 #include <algorithm>
 
 #include "gc_cta.cuh"
@@ -36,7 +41,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                   int32_t fill, const long long *__restrict__ two_hop, float *score, size_t ws_stride,
                   int32_t wide, long long local_max, long long *akey, int32_t *ast,
                   int32_t *gx, int32_t *wsel, long long *wgain, int32_t *wpos, int32_t wcap,
-                  const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3, GridSelScratch *gsel) {
+                  const int32_t *__restrict__ rp_full, const int32_t *__restrict__ c3, GridSelScratch *gsel,
+                  ClaimRec *clog, unsigned long long clog_cap) {
   __shared__ unsigned long long s_red[32];
   extern __shared__ __align__(16) unsigned char s_list[];  // kLazyListSmem bytes
   const int m = *m_dev;
@@ -104,7 +110,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
           const int d = *(volatile int32_t *)&lc->dec;
           if (d == 0) {
             grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
-                                       &lc->bar, &lc->err, tns, mx, c3, 0, -1, kBatchLevel0);
+                                       &lc->bar, &lc->err, tns, mx, c3, 0, -1, kBatchLevel0, clog, &lc->log_n,
+                                       clog_cap);
           } else if (d == 1 && threadIdx.x == 0) {
             picks[r] = lc->best_id;
             pgain[r] = lc->best_gain;
@@ -140,7 +147,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
         ok = grid_sync(&lc->bar, &lc->err, tns);  // gains visible to CTA 0
       } else {
         ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
-                                        &lc->bar, &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll);
+                                        &lc->bar, &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll, clog,
+                                        &lc->log_n, clog_cap);
         // the gains are in lc->gsel, written by CTA 0: only a grid-wide fold
         // needs them published
         if (!lean) ok = ok && grid_sync(&lc->bar, &lc->err, tns);
@@ -166,7 +174,40 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       if (!grid_sync(&lc->bar, &lc->err, tns)) break;
     }
     bool ok = true;
-    if (*(volatile long long *)&lc->best_gain <= local_max) {  // small region: CTA 0 alone
+    const int blane = *(volatile int32_t *)&lc->best_lane;
+    const unsigned long long s0 = *(volatile unsigned long long *)&lc->best_seg0;
+    const unsigned long long s1 = *(volatile unsigned long long *)&lc->best_seg1;
+    if (clog && !wide && blane >= 0 && blane < kLanes && s0 <= s1 && s1 <= clog_cap) {
+      // from the claim log: the pick's lane, in the entries of its batch
+      const u64 bit = 1ull << blane;
+      u64 dec = 0, rel = 0;
+      for (unsigned long long i = s0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < s1;
+           i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int4 e = *reinterpret_cast<const int4 *>(clog + i);
+        const u64 won = (u64)(unsigned)e.z | ((u64)(unsigned)e.w << 32);
+        if (!(won & bit)) continue;
+        const int old = atomicMin(&dS[e.x], e.y);  // each vertex once per lane
+        if (old > e.y) {
+          if (old < kInf) dec += (u64)(old - e.y);
+          ++rel;
+        }
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {  // the pick itself (level 0)
+        const int old = atomicMin(&dS[*(volatile int32_t *)&lc->best_id], 0);
+        if (old > 0) {
+          if (old < kInf) dec += (u64)old;
+          ++rel;
+        }
+        lc->upd_log += s1 - s0;
+        lc->log_picks += 1;
+      }
+      dec = block_sum(dec, s_red);
+      rel = block_sum(rel, s_red);
+      if (threadIdx.x == 0) {
+        if (dec) atomicAdd(&lc->decrease, dec);
+        if (rel) atomicAdd(&lc->upd_relabels, rel);
+      }
+    } else if (*(volatile long long *)&lc->best_gain <= local_max) {  // small region: CTA 0 alone
       if (blockIdx.x == 0) {
         const long long d = cta_relabel_bfs(rp, ci, dS, *(volatile int32_t *)&lc->best_id, myws.qv0, myws.qv1);
         if (threadIdx.x == 0) lc->decrease = (unsigned long long)d;
@@ -185,6 +226,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       if (bp >= 0 && bp < m && lact[bp] == lc->best_id) lkey[bp] = -1;
       lc->best_id = -1;
       lc->best_gain = -1;
+      lc->best_lane = -1;
+      lc->log_n = 0;  // the next round's log (its first batch starts after a barrier)
+      lc->log_mark = 0;
       lc->rounds_done += 1;
       lc->round = r + 1;
     }
@@ -238,7 +282,8 @@ int launch_active_theta(gc_graph *g) {
 }
 
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
-                       bool wide_steps, long long local_max, int ctas, bool pruned) {
+                       bool wide_steps, long long local_max, int ctas, bool pruned, bool use_log,
+                       long long log_cap) {
   int grid = std::min(g->lazy_ctas, g->ws_count);
   if (ctas > 0 && ctas < grid) grid = ctas;
   int32_t wide = wide_steps ? 1 : 0;
@@ -270,6 +315,9 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
   long long *akey = g->akey;
   int32_t *ast = g->ast;
   int32_t *gx = g->gx;
+  ClaimRec *clog = use_log ? g->clog : nullptr;
+  unsigned long long clog_cap =
+      use_log ? (unsigned long long)(log_cap > 0 ? std::min(log_cap, g->clog_cap) : g->clog_cap) : 0ull;
   void *args[] = {(void *)&rp,    (void *)&ci,    (void *)&n,    (void *)&dS,   (void *)&ub,
                   (void *)&stamp, (void *)&act,   (void *)&m_dev, (void *)&k,   (void *)&picks,
                   (void *)&pgain, (void *)&pdec,  (void *)&ws,   (void *)&goff, (void *)&gg,
@@ -277,7 +325,7 @@ int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *
                   (void *)&mx,    (void *)&prop,  (void *)&fill, (void *)&two_hop, (void *)&score,
                   (void *)&ws_stride, (void *)&wide, (void *)&local_max, (void *)&akey,
                   (void *)&ast, (void *)&gx, (void *)&wsel, (void *)&wgain, (void *)&wpos, (void *)&wcap,
-                  (void *)&rp_full, (void *)&c3, (void *)&gsel};
+                  (void *)&rp_full, (void *)&c3, (void *)&gsel, (void *)&clog, (void *)&clog_cap};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel((const void *)k_lazy_rounds, dim3(grid), dim3(kGridGainThreads), args,
                                       kLazyListSmem, g->stream));

@@ -208,7 +208,7 @@ static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *
   __shared__ int s_id[32];
   __shared__ long long s_ll[32];
   __shared__ unsigned int s_hist[kLazyBins];
-  __shared__ int s_bpos;
+  __shared__ int s_bpos, s_blane;
   const int tid = threadIdx.x;
   const int T = blockDim.x;
   const int r = lc->round;
@@ -218,7 +218,7 @@ static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *
     const int32_t *fsel = wcap ? wsel : lc->sel, *fpos = wcap ? wpos : lc->selpos;
     const long long *fgain = wcap ? wgain : lc->gsel;
     long long bv = -1;
-    int bid = -1, mypos = -1;
+    int bid = -1, mypos = -1, mylane = -1;
     for (int i = tid; i < ns; i += T) {
       const int v = fsel[i];
       const long long gv = fgain[i];
@@ -233,18 +233,28 @@ static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *
         bv = gv;
         bid = v;
         mypos = p;
+        mylane = i;
       }
     }
     const int mine = bid;
     block_argmax_all(bv, bid, s_v, s_id);
-    if (mine >= 0 && mine == bid) s_bpos = mypos;
+    if (mine >= 0 && mine == bid) {
+      s_bpos = mypos;
+      s_blane = mylane;
+    }
     cta_sync();
     if (tid == 0) {
+      // the batch's claim-log entries: [log_mark, log_n)
+      const unsigned long long l1 = *(volatile unsigned long long *)&lc->log_n;
       if (bid >= 0 && better_max(bv, bid, lc->best_gain, lc->best_id)) {
         lc->best_gain = bv;
         lc->best_id = bid;
         lc->best_pos = s_bpos;
+        lc->best_lane = wcap ? -1 : s_blane;  // wide steps keep no log
+        lc->best_seg0 = lc->log_mark;
+        lc->best_seg1 = l1;
       }
+      lc->log_mark = l1;
       lc->steps += 1;
       lc->evals += ns;
     }
@@ -369,7 +379,7 @@ static __device__ bool grid_lazy_step(const int32_t *act, int32_t m, long long *
   __shared__ long long s_ll[32];
   __shared__ unsigned int s_hist[kSelBins];
   __shared__ int s_scan[33];
-  __shared__ int s_b;
+  __shared__ int s_b, s_lane;
   __shared__ long long s_ab;
   const int tid = threadIdx.x, T = blockDim.x, G = gridDim.x, b = blockIdx.x;
   const int r = *(volatile int32_t *)&lc->round;
@@ -389,7 +399,7 @@ static __device__ bool grid_lazy_step(const int32_t *act, int32_t m, long long *
   if (fold) {
     const int ns = *(volatile int32_t *)&lc->n_sel;
     long long fv = -1;
-    int fid = -1, fpos = -1;
+    int fid = -1, fpos = -1, flane = -1;
     for (int j = tid; j < ns; j += T) {
       const int v = sel[j], p = selpos[j];
       const long long gv = gsel[j];
@@ -405,18 +415,32 @@ static __device__ bool grid_lazy_step(const int32_t *act, int32_t m, long long *
         fv = gv;
         fid = v;
         fpos = p;
+        flane = j;
       }
     }
     const int mine = fid;
     block_argmax_all(fv, fid, s_v, s_id);
-    if (mine >= 0 && mine == fid) s_b = fpos;
+    if (mine >= 0 && mine == fid) {
+      s_b = fpos;
+      s_lane = flane;
+    }
     cta_sync();
+    bool improved = false;
     if (fid >= 0 && better_max(fv, fid, gb, vb)) {
       gb = fv;
       vb = fid;
       bpos = s_b;
+      improved = true;
     }
     if (b == 0 && tid == 0) {
+      // the batch's claim-log entries: [log_mark, log_n)
+      const unsigned long long l1 = *(volatile unsigned long long *)&lc->log_n;
+      if (improved) {
+        lc->best_lane = s_lane;
+        lc->best_seg0 = lc->log_mark;
+        lc->best_seg1 = l1;
+      }
+      lc->log_mark = l1;
       lc->best_gain = gb;
       lc->best_id = vb;
       lc->best_pos = bpos;

@@ -32,6 +32,7 @@ GC_OPT_CAPTURE = 0x2
 GC_OPT_FULL_ADJACENCY = 0x4
 GC_OPT_NO_ROUND1_BOUND = 0x8
 GC_OPT_R0_FULL_LEVELS = 0x10
+GC_OPT_NO_CLAIM_LOG = 0x20
 
 # every entry point declared in include/gc.h
 EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_num_entries",
@@ -58,7 +59,7 @@ class Opts(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("step_form", ctypes.c_int32),
                 ("local_update_max_gain", ctypes.c_int32), ("lazy_ctas", ctypes.c_int32),
                 ("batch_grid_min_n", ctypes.c_int32), ("round0_lanes", ctypes.c_int32),
-                ("timeout_us", ctypes.c_int32)]
+                ("timeout_us", ctypes.c_int32), ("claim_log_cap", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -77,7 +78,7 @@ class Stats(ctypes.Structure):
         ("r0_td_edges", ctypes.c_int64), ("ms_r0_select", ctypes.c_double), ("ms_r0_topdown", ctypes.c_double),
         ("ms_r0_bottomup", ctypes.c_double), ("ms_r0_clear", ctypes.c_double), ("r0_bu_rows", ctypes.c_int64),
         ("r0_bu_scanned", ctypes.c_int64), ("r0_bu_gathers", ctypes.c_int64), ("r0_width", ctypes.c_int64),
-        ("r0_dense_clears", ctypes.c_int64)]
+        ("r0_dense_clears", ctypes.c_int64), ("lazy_log_picks", ctypes.c_int64), ("lazy_upd_log", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -254,20 +255,23 @@ class Graph:
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
                step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0,
                pruned_adjacency: bool = True, round1_bound: bool = True, timeout_us: int = 0,
-               round0_lanes: int = 0, r0_full_levels: bool = False):
+               round0_lanes: int = 0, r0_full_levels: bool = False, claim_log: bool = True,
+               claim_log_cap: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.eval_per_step, o.max_ctas, o.use_proposal = eval_per_step, max_ctas, int(use_proposal)
         o.step_lanes, o.step_mode, o.active_target = step_lanes, step_mode, active_target
         o.round1_heavy = round1_heavy
         o.flags = ((0 if expand_bound else GC_OPT_NO_EXPAND_BOUND) | (0 if pruned_adjacency else GC_OPT_FULL_ADJACENCY)
-                   | (0 if round1_bound else GC_OPT_NO_ROUND1_BOUND) | (GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0))
+                   | (0 if round1_bound else GC_OPT_NO_ROUND1_BOUND) | (GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0)
+                   | (0 if claim_log else GC_OPT_NO_CLAIM_LOG))
         o.step_form, o.local_update_max_gain = step_form, local_update_max_gain
         o.lazy_ctas = lazy_ctas
         if timeout_ms:
             o.timeout_ms = timeout_ms
         o.timeout_us = timeout_us
         o.round0_lanes = round0_lanes
+        o.claim_log_cap = claim_log_cap
         grp = np.zeros(max(int(k), 1), dtype=np.int32)
         f = ctypes.c_int64()
         st = Stats()

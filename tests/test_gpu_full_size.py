@@ -113,9 +113,11 @@ def test_greedy_rmat24_k50_full_size(gcm):
     ft = np.array([int(x) for x in gold["farness"]], dtype=np.int64)
     with gcm.Graph(rp, ci) as G:
         for kw in ({}, {"step_mode": 1, "eval_per_step": 128}, {"round0_lanes": -1}):
-            got, f, _ = G.greedy(50, **kw)
+            got, f, st = G.greedy(50, **kw)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
+            if not kw:  # the persistent rounds' d_S updates come from the claim log (up to overflow)
+                assert 0 < st["lazy_log_picks"] <= 48
         # the farness of the first ten picks, recomputed by one oracle BFS
         assert G.farness(grp[:10]) == ft[9] == oracle.farness(rp, ci, grp[:10])
 

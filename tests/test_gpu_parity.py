@@ -146,6 +146,39 @@ def test_greedy_step_forms(gcm, name, g):
             assert f == ft[-1]
 
 
+@pytest.mark.parametrize("name,g", small_cases() + [("rmat13", graphgen.rmat(13, 16.0, seed=4))])
+def test_greedy_claim_log(gcm, name, g):
+    """d_S updates of the persistent rounds from the claim log of the pick's
+    gain batch, against the relabel BFS from the pick: the oracle's group and
+    farness, and the same number of lowered labels (the same vertices).  With
+    grid-wide steps every pick of rounds >= 2 comes from the log, also across
+    the relaunches that rebuild a tiny active list; a log capped at 16 entries
+    mixes both updates; wide steps (the automatic form on deep graphs) keep no
+    log.  The host checks every update's decrease against the pick's gain."""
+    rp, ci = g
+    k = min(12, rp.size - 1)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, k)
+    relabels = set()
+    with gcm.Graph(rp, ci) as G:
+        for form, act, log, cap in ((1, 0, False, 0), (1, 0, True, 0), (1, 64, True, 0), (1, 1, True, 0),
+                                    (1, 0, True, 16), (2, 0, True, 0), (0, 0, True, 0)):
+            got, f, st = G.greedy(k, step_form=form, active_target=act, step_mode=3 if act else 0,
+                                  claim_log=log, claim_log_cap=cap)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+            relabels.add(st["lazy_upd_relabels"])
+            picks = st["lazy_log_picks"]
+            if not log or form == 2:
+                assert picks == 0, (form, act, log, cap, picks)
+            elif form == 1 and cap == 0:
+                assert picks == max(0, k - 2), (form, act, log, cap, picks)
+            else:  # a capped log, or the automatic form (wide steps on deep graphs)
+                assert picks in range(max(0, k - 2) + 1), (form, act, log, cap, picks)
+            if picks == max(0, k - 2) and k > 2:
+                assert st["lazy_upd_frontier"] == 0  # no relabel BFS ran
+    assert len(relabels) == 1
+
+
 @pytest.mark.parametrize("name,g", small_cases())
 def test_greedy_bound_off(gcm, name, g):
     rp, ci = g
@@ -190,6 +223,11 @@ def test_greedy_rmat20_k100_full_size(gcm):
         got, f, st = G.greedy(100)
         np.testing.assert_array_equal(got, grp)
         assert f == ft[-1]
+        assert st["lazy_log_picks"] == 98  # every d_S update of rounds 2..99 from the claim log
+        g1, f1, s1 = G.greedy(100, claim_log=False)
+        np.testing.assert_array_equal(g1, grp)
+        assert f1 == ft[-1] and s1["lazy_log_picks"] == 0
+        assert s1["lazy_upd_relabels"] == st["lazy_upd_relabels"]
         for mode, heavy, bound, form, local, pruned in ((1, -1, False, 0, 0, True), (2, 64, True, 0, 0, False),
                                                         (3, 4096, True, 1, -1, True), (3, 0, False, 2, 1 << 30, False)):
             g2, f2, _ = G.greedy(100, step_mode=mode, round1_heavy=heavy, expand_bound=bound,
