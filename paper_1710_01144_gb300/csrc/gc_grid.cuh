@@ -78,7 +78,13 @@ static __device__ __forceinline__ int warp_find_start(const int32_t *start, int 
 // With `log` (gain mode), every claim that wins lanes at level L >= 1 appends
 // {w, L, lanes won} at *log_n (one warp-aggregated slot per claim round); slots
 // at or past log_cap are counted in *log_n but not written.
+// With `acc`, each thread adds its work counts (scalar and union adjacency
+// entries, frontier entries, pushes) to *acc instead of the batch summing them
+// over the CTA and into gctl (a persistent caller sums them once at its end).
 constexpr int kBatchAll = 0, kBatchLevel0 = 1, kBatchRest = 2;
+struct GridCounts {
+  u64 scalar = 0, uni = 0, front = 0, push = 0;
+};
 template <int MODE>
 static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t n, const int32_t *dS, const int32_t *cand, int32_t nl_arg,
@@ -87,7 +93,8 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                                 int32_t *err, unsigned long long timeout_ns, const int32_t *__restrict__ mx,
                                 const int32_t *__restrict__ c3 = nullptr, int voff = 0, int ws_n = -1,
                                 int phase = kBatchAll, ClaimRec *log = nullptr,
-                                unsigned long long *log_n = nullptr, unsigned long long log_cap = 0) {
+                                unsigned long long *log_n = nullptr, unsigned long long log_cap = 0,
+                                GridCounts *acc = nullptr) {
   constexpr int T = kGridGainThreads;
   __shared__ u64 s_gain[kLanes];
   __shared__ unsigned int s_cnt[kLanes];
@@ -120,13 +127,36 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
   }
   u64 alive = nl >= kLanes ? ~0ull : ((1ull << nl) - 1ull);
 
-  // Queue w for level lev (its lanes are already in claim word lev mod 3):
-  // warp-aggregated slot and range start.  Every lane of the warp calls it.
-  // deg: the row length w will scan at level lev (loaded by the caller with
-  // its other per-neighbour data, so that no load waits here)
-  auto enqueue = [&](bool q, int w, int lev, int deg) {
-    const unsigned qm = __ballot_sync(0xffffffffu, q);
-    if (!qm) return;
+  if (MODE != kModeGain) phase = kBatchAll;
+  // ---- level 0 (warps 0 and 1 of CTA 0, or of the calling CTA): lanes reach
+  // their candidates; thread j takes lane j.  Per warp three rounds of memory
+  // traffic: the candidates' labels, bounds and rows; the visited and claim
+  // words; the touched-list and frontier slots. ----
+  if (phase != kBatchRest && (b == 0 || phase == kBatchLevel0) && tid < kLanes) {
+    // the caller may arrive with the warp split by a single-thread branch: the
+    // warp-synchronous code below needs it converged
+    __syncwarp();
+    const int j = tid;
+    const int c = j < nl ? cand[j] : -1;
+    const bool valid = j < nl && c >= 0 && c < n && c - voff >= 0 && c - voff < ws_n;
+    if (j < nl && !valid) atomicExch(&ctl->err, GC_EINVAL);  // outside the graph
+    int dc = 1, mxc = INT_MAX, deg = 0;
+    if (valid) {
+      if (MODE == kModeGain) dc = dS[c];
+      if (MODE == kModeGain && mx) mxc = __ldg(mx + c);
+      deg = row_len(rp, c3, c, 0);
+    }
+    const bool reach = valid && dc > 0;
+    if (reach) {
+      if (MODE == kModeGain) ctl->gain[j] = (u64)dc;
+      else ctl->dcnt[0][j] = 1;
+    }
+    const u64 bit = 1ull << j;
+    const bool expand = reach && (MODE != kModeGain || mxc > 1);
+    const u64 ov = reach ? atomicOr(&ws.vis[c - voff], bit) : ~0ull;
+    const u64 on = expand ? atomicOr(&ws.nx[0][c - voff], bit) : ~0ull;
+    const bool fresh = ov == 0ull, q = on == 0ull;
+    const unsigned fm = __ballot_sync(0xffffffffu, fresh), qm = __ballot_sync(0xffffffffu, q);
     if (!q) deg = 0;
     int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
 #pragma unroll
@@ -135,53 +165,22 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
       if (lane >= o) incl += y;
     }
     const int sum = __shfl_sync(0xffffffffu, incl, 31);
-    const int leader = __ffs(qm) - 1;
-    unsigned long long base = 0;
-    if (lane == leader)
-      base = atomicAdd(&ctl->pk[lev % 3], ((unsigned long long)__popc(qm) << 32) | (unsigned long long)sum);
-    base = __shfl_sync(0xffffffffu, base, leader);
+    unsigned long long bq = 0;
+    int bf = 0;
+    if (lane == 0) {
+      if (qm) bq = atomicAdd(&ctl->pk[0], ((unsigned long long)__popc(qm) << 32) | (unsigned long long)sum);
+      if (fm) bf = atomicAdd(&ctl->touched, __popc(fm));
+    }
+    const unsigned below = (1u << lane) - 1u;
+    bq = __shfl_sync(0xffffffffu, bq, 0);
+    bf = __shfl_sync(0xffffffffu, bf, 0);
+    if (fresh) ws.touched[bf + __popc(fm & below)] = c;
     if (q) {
-      const int slot = (int)(base >> 32) + __popc(qm & ((1u << lane) - 1u));
-      list_of(lev % 3)[slot] = w;
-      starts_of(lev & 1)[slot] = (int)(base & 0xffffffffull) + incl - deg;
+      const int slot = (int)(bq >> 32) + __popc(qm & below);
+      list_of(0)[slot] = c;
+      starts_of(0)[slot] = (int)(bq & 0xffffffffull) + incl - deg;
     }
-    c_push += (lane == leader) ? (u64)__popc(qm) : 0ull;
-  };
-
-  if (MODE != kModeGain) phase = kBatchAll;
-  // ---- level 0 (warp 0 of CTA 0, or of the calling CTA): lanes reach their candidates ----
-  if (phase != kBatchRest && (b == 0 || phase == kBatchLevel0) && tid < 32) {
-    // the caller may arrive with the warp split by a single-thread branch: the
-    // warp-synchronous enqueue below needs it converged
-    __syncwarp();
-    // lane t handles lanes t and t + 32 of the batch, one after the other
-    for (int h = 0; h < 2; ++h) {
-      const int j = lane + 32 * h;
-      const int c = j < nl ? cand[j] : -1;
-      bool q = false;
-      if (j < nl) {
-        const u64 bit = 1ull << j;
-        bool reach = false;
-        if (c < 0 || c >= n || c - voff < 0 || c - voff >= ws_n) {  // outside the graph
-          atomicExch(&ctl->err, GC_EINVAL);
-        } else if (MODE == kModeGain) {
-          const int dc = dS[c];
-          if (dc > 0) {
-            ctl->gain[j] = (u64)dc;
-            reach = true;
-          }
-        } else {
-          ctl->dcnt[0][j] = 1;
-          reach = true;
-        }
-        if (reach) {
-          if (atomicOr(&ws.vis[c - voff], bit) == 0) ws.touched[atomicAdd(&ctl->touched, 1)] = c;
-          const bool expand = MODE != kModeGain || !mx || __ldg(mx + c) > 1;
-          if (expand) q = atomicOr(&ws.nx[0][c - voff], bit) == 0;
-        }
-      }
-      enqueue(q, c, 0, q ? row_len(rp, c3, c, 0) : 0);
-    }
+    c_push += lane == 0 ? (u64)__popc(qm) : 0ull;
     if (phase == kBatchLevel0) {
       if (c_push) atomicAdd(&gctl->pushes, c_push);
       return true;
@@ -311,17 +310,47 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
             u64 won = nb[k] & ~ov[k];
             const bool fresh = won && ov[k] == 0;
             const bool q = on[k] == 0ull;
-            if (MODE == kModeGain && log) {
-              const unsigned lm = __ballot_sync(0xffffffffu, won != 0ull);
-              if (lm) {
-                const int leader = __ffs(lm) - 1;
-                unsigned long long at = 0;
-                if (lane == leader) at = atomicAdd(log_n, (unsigned long long)__popc(lm));
-                at = __shfl_sync(0xffffffffu, at, leader) + (unsigned long long)__popc(lm & ((1u << lane) - 1u));
-                if (won && at < log_cap)
-                  *reinterpret_cast<int4 *>(log + at) =
-                      make_int4(w[k], nlev, (int)(unsigned)won, (int)(unsigned)(won >> 32));
+            // the warp's appends -- next frontier (slot and range start),
+            // touched list, claim log -- take their slots by atomics that lane
+            // 0 issues together, so that their round trips overlap
+            const unsigned qm = __ballot_sync(0xffffffffu, q), fm = __ballot_sync(0xffffffffu, fresh);
+            const unsigned lm = (MODE == kModeGain && log) ? __ballot_sync(0xffffffffu, won != 0ull) : 0u;
+            const int deg = q ? lw[k] : 0;
+            int incl = deg;  // inclusive prefix of the degrees over the queueing lanes
+            if (qm) {
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
               }
+            }
+            const int sum = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long bq = 0, bl = 0;
+            int bf = 0;
+            if (lane == 0) {
+              if (qm) bq = atomicAdd(&ctl->pk[nlev % 3], ((unsigned long long)__popc(qm) << 32) | (unsigned long long)sum);
+              if (fm) bf = atomicAdd(&ctl->touched, __popc(fm));
+              if (lm) bl = atomicAdd(log_n, (unsigned long long)__popc(lm));
+              c_push += (u64)__popc(qm);
+            }
+            const unsigned below = (1u << lane) - 1u;
+            if (qm) {
+              bq = __shfl_sync(0xffffffffu, bq, 0);
+              if (q) {
+                const int slot = (int)(bq >> 32) + __popc(qm & below);
+                list_of(nlev % 3)[slot] = w[k];
+                starts_of(nlev & 1)[slot] = (int)(bq & 0xffffffffull) + incl - deg;
+              }
+            }
+            if (fm) {
+              bf = __shfl_sync(0xffffffffu, bf, 0);
+              if (fresh) ws.touched[bf + __popc(fm & below)] = w[k];
+            }
+            if (lm) {
+              bl = __shfl_sync(0xffffffffu, bl, 0) + (unsigned long long)__popc(lm & below);
+              if (won && bl < log_cap)
+                *reinterpret_cast<int4 *>(log + bl) =
+                    make_int4(w[k], nlev, (int)(unsigned)won, (int)(unsigned)(won >> 32));
             }
             if (won) {
               const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
@@ -331,15 +360,6 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 atomicAdd(&s_gain[j], wt);
                 if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1u);
               } while (won);
-            }
-            enqueue(q, w[k], nlev, lw[k]);
-            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-            if (fm) {
-              const int leader = __ffs(fm) - 1;
-              int pos = 0;
-              if (lane == leader) pos = atomicAdd(&ctl->touched, __popc(fm));
-              pos = __shfl_sync(0xffffffffu, pos, leader);
-              if (fresh) ws.touched[pos + __popc(fm & ((1u << lane) - 1u))] = w[k];
             }
           }
         }
@@ -405,15 +425,24 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     const int nt = *(volatile int32_t *)&ctl->touched;
     for (int i = b * T + tid; i < nt; i += G * T) ws.vis[ws.touched[i] - voff] = 0;
   }
-  c_scalar = block_sum(c_scalar, s_red);
-  c_union = block_sum(c_union, s_red);
-  c_front = block_sum(c_front, s_red);
-  c_push = block_sum(c_push, s_red);
+  if (acc) {
+    acc->scalar += c_scalar;
+    acc->uni += c_union;
+    acc->front += c_front;
+    acc->push += c_push;
+  } else {
+    c_scalar = block_sum(c_scalar, s_red);
+    c_union = block_sum(c_union, s_red);
+    c_front = block_sum(c_front, s_red);
+    c_push = block_sum(c_push, s_red);
+  }
   if (tid == 0) {
-    atomicAdd(&gctl->edges_scalar, c_scalar);
-    atomicAdd(&gctl->edges_union, c_union);
-    atomicAdd(&gctl->frontier, c_front);
-    atomicAdd(&gctl->pushes, c_push);
+    if (!acc) {
+      atomicAdd(&gctl->edges_scalar, c_scalar);
+      atomicAdd(&gctl->edges_union, c_union);
+      atomicAdd(&gctl->frontier, c_front);
+      atomicAdd(&gctl->pushes, c_push);
+    }
     if (b == 0) {
       atomicAdd(&gctl->levels, (u64)L);
       atomicAdd(&gctl->batches, 1ull);

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const GainWs myws = gain_ws(ws, ws_stride, n, blockIdx.x);  // this CTA's own workspace
   GainCounters cnt;
+  GridCounts gcnt;  // this thread's work counts of the grid-wide batches
   unsigned long long t0 = timer ? global_ns() : 0, t1;
   bool fold = false;
   // CTA 0 selects for short lists (a few scans of m entries cost less than the
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       } else {
         ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
                                         &lc->bar, &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll, clog,
-                                        &lc->log_n, clog_cap);
+                                        &lc->log_n, clog_cap, &gcnt);
         // the gains are in lc->gsel, written by CTA 0: only a grid-wide fold
         // needs them published
         if (!lean) ok = ok && grid_sync(&lc->bar, &lc->err, tns);
@@ -243,17 +244,20 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       t0 = t1;
     }
   }
-  // work counters of the spread evaluations
-  const u64 c_scalar = block_sum(cnt.scalar, s_red), c_union = block_sum(cnt.uni, s_red);
-  const u64 c_front = block_sum(cnt.front, s_red), c_push = block_sum(cnt.push, s_red);
-  if (threadIdx.x == 0 && cnt.batches) {
-    atomicAdd(&gctl->edges_scalar, c_scalar);
-    atomicAdd(&gctl->edges_union, c_union);
-    atomicAdd(&gctl->frontier, c_front);
-    atomicAdd(&gctl->pushes, c_push);
-    atomicAdd(&gctl->levels, cnt.levels);
-    atomicAdd(&gctl->batches, cnt.batches);
-    atomicAdd(&gctl->lanes, cnt.lanes);
+  // work counters: the wide steps' (per CTA) and the grid-wide batches' (per
+  // thread, summed here once instead of after every batch)
+  const u64 c_scalar = block_sum(cnt.scalar + gcnt.scalar, s_red), c_union = block_sum(cnt.uni + gcnt.uni, s_red);
+  const u64 c_front = block_sum(cnt.front + gcnt.front, s_red), c_push = block_sum(cnt.push + gcnt.push, s_red);
+  if (threadIdx.x == 0) {
+    if (c_scalar) atomicAdd(&gctl->edges_scalar, c_scalar);
+    if (c_union) atomicAdd(&gctl->edges_union, c_union);
+    if (c_front) atomicAdd(&gctl->frontier, c_front);
+    if (c_push) atomicAdd(&gctl->pushes, c_push);
+    if (cnt.batches) {
+      atomicAdd(&gctl->levels, cnt.levels);
+      atomicAdd(&gctl->batches, cnt.batches);
+      atomicAdd(&gctl->lanes, cnt.lanes);
+    }
   }
 }
 

@@ -80,6 +80,48 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
   cta_sync();
 }
 
+// The per-step statistics of CTA 0's list scan in one exchange: the best
+// (value, id) pair, the smallest value and the count, each reduced over the
+// warp by shuffles, then over the warps by every thread from shared memory.
+// One CTA barrier: the arrays are this function's own, and a caller runs other
+// barriers between two calls.
+static __device__ __forceinline__ void block_scan_stats(long long &umax, int &vmax, long long &umin,
+                                                        long long &cnt) {
+  __shared__ long long s_mx[32], s_mn[32], s_ct[32];
+  __shared__ int s_id[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, umax, o);
+    const int oid = __shfl_xor_sync(0xffffffffu, vmax, o);
+    if (better_max(ov, oid, umax, vmax)) {
+      umax = ov;
+      vmax = oid;
+    }
+    umin = min(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if (lane == 0) {
+    s_mx[wid] = umax;
+    s_id[wid] = vmax;
+    s_mn[wid] = umin;
+    s_ct[wid] = cnt;
+  }
+  cta_sync();
+  umax = s_mx[0];
+  vmax = s_id[0];
+  umin = s_mn[0];
+  cnt = s_ct[0];
+  for (int w = 1; w < nw; ++w) {
+    if (better_max(s_mx[w], s_id[w], umax, vmax)) {
+      umax = s_mx[w];
+      vmax = s_id[w];
+    }
+    umin = min(umin, s_mn[w]);
+    cnt += s_ct[w];
+  }
+}
+
 // Exact top-`need` of the list entries by key (larger first; ties by list
 // order, i.e. smaller id), written to sel[base..cap) and, when selpos is
 // given, their list positions to selpos[base..cap).  key(i, v) returns LLONG_MIN
@@ -279,9 +321,7 @@ static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *
     ++cnt;
   }
   if (akey && tid == 0) lc->sel_scanned += (unsigned long long)m;
-  block_argmax_all(umax, vmax, s_v, s_id);
-  umin = block_min_ll(umin, s_ll);
-  cnt = block_sum(cnt, s_ll);
+  block_scan_stats(umax, vmax, umin, cnt);
   int dec;
   if (vb >= 0 && (cnt == 0 || better_max(gb, vb, umax, vmax))) dec = gb >= theta ? 1 : 2;
   else if (cnt == 0) dec = 2;
