@@ -352,8 +352,23 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
                 *reinterpret_cast<int4 *>(log + bl) =
                     make_int4(w[k], nlev, (int)(unsigned)won, (int)(unsigned)(won >> 32));
             }
-            if (won) {
-              const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
+            // per-lane sums: claims that won one lane (the common case: a
+            // row's entries all carry the lane of the vertex being expanded)
+            // are summed over the threads of the warp that won the same lane,
+            // and one thread adds the sum; claims of several lanes add each
+            const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
+            const bool one = won != 0ull && (won & (won - 1ull)) == 0ull;
+            const int j1 = one ? __ffsll((long long)won) - 1 : -1;  // (the -1 group adds nothing here)
+            const unsigned grp = __match_any_sync(0xffffffffu, j1);
+            if (one) {
+              // wt < 2^31: two 16-bit halves keep the 32-lane sums exact
+              const unsigned lo = __reduce_add_sync(grp, (unsigned)(wt & 0xffffu));
+              const unsigned hi = __reduce_add_sync(grp, (unsigned)(wt >> 16));
+              if (lane == __ffs(grp) - 1) {
+                atomicAdd(&s_gain[j1], (u64)lo + ((u64)hi << 16));
+                if (MODE == kModeFarness) atomicAdd(&s_cnt[j1], (unsigned)__popc(grp));
+              }
+            } else if (won) {
               do {
                 const int j = __ffsll((long long)won) - 1;
                 won &= won - 1;
