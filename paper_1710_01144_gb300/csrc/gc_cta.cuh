@@ -54,7 +54,7 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
   __shared__ int s_qn, s_touched;
   __shared__ u64 s_alive;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid < kLanes) {
     s_gain[tid] = 0;
     s_cnt[tid] = 0;
@@ -143,7 +143,9 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
       // kEdgeIlp adjacency entries per thread are in flight at once: the
       // column, d_S, visited-word loads and the claiming atomics of
       // independent entries are issued before any result is used.
-      for (int e0 = tid; e0 < total; e0 += kEdgeIlp * T) {
+      // (the trip count is the same for the 32 threads of a warp: the
+      // warp-wide sums and appends below need them converged)
+      for (int e0 = tid; e0 - (tid & 31) < total; e0 += kEdgeIlp * T) {
         int w[kEdgeIlp], sl[kEdgeIlp];
 #pragma unroll
         for (int k = 0; k < kEdgeIlp; ++k) {
@@ -174,22 +176,55 @@ __device__ __forceinline__ void cta_gain_batch(const int32_t *__restrict__ rp, c
         u64 ov[kEdgeIlp];
 #pragma unroll
         for (int k = 0; k < kEdgeIlp; ++k) ov[k] = nb[k] ? atomicOr(&ws.vis[w[k] - voff], nb[k]) : ~0ull;
+        u64 on[kEdgeIlp];
+#pragma unroll
+        for (int k = 0; k < kEdgeIlp; ++k) {
+          const u64 won = nb[k] & ~ov[k];
+          on[k] = won ? atomicOr(&nxt[w[k] - voff], won) : ~0ull;
+        }
 #pragma unroll
         for (int k = 0; k < kEdgeIlp; ++k) {
           u64 won = nb[k] & ~ov[k];
-          if (!won) continue;
-          if (ov[k] == 0) ws.touched[atomicAdd(&s_touched, 1)] = w[k];
-          if (atomicOr(&nxt[w[k] - voff], won) == 0) {
-            qnxt_v[atomicAdd(&s_qn, 1)] = w[k];
+          // touched list and next frontier: one shared-memory slot reservation
+          // per warp for each
+          const bool fresh = won && ov[k] == 0, q = won && on[k] == 0;
+          const unsigned fm = __ballot_sync(0xffffffffu, fresh), qm = __ballot_sync(0xffffffffu, q);
+          int bt = 0, bq = 0;
+          if (lane == 0) {
+            if (fm) bt = atomicAdd(&s_touched, __popc(fm));
+            if (qm) bq = atomicAdd(&s_qn, __popc(qm));
+          }
+          const unsigned below = (1u << lane) - 1u;
+          bt = __shfl_sync(0xffffffffu, bt, 0);
+          bq = __shfl_sync(0xffffffffu, bq, 0);
+          if (fresh) ws.touched[bt + __popc(fm & below)] = w[k];
+          if (q) {
+            qnxt_v[bq + __popc(qm & below)] = w[k];
             ++cnt.push;
           }
+          // per-lane sums: a claim of one lane (the common case: a row's
+          // entries carry the lane of the vertex being expanded) is summed over
+          // the warp's threads that won the same lane, one thread adds the sum
           const u64 wt = MODE == kModeGain ? (u64)(dw[k] - nlev) : (u64)nlev;
-          do {
-            const int j = __ffsll((long long)won) - 1;
-            won &= won - 1;
-            atomicAdd(&s_gain[j], wt);
-            if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
-          } while (won);
+          const bool one = won != 0ull && (won & (won - 1ull)) == 0ull;
+          const int j1 = one ? __ffsll((long long)won) - 1 : -1;  // (the -1 group adds nothing here)
+          const unsigned grp = __match_any_sync(0xffffffffu, j1);
+          if (one) {
+            // wt < 2^31: two 16-bit halves keep the 32-lane sums exact
+            const unsigned lo = __reduce_add_sync(grp, (unsigned)(wt & 0xffffu));
+            const unsigned hi = __reduce_add_sync(grp, (unsigned)(wt >> 16));
+            if (lane == __ffs(grp) - 1) {
+              atomicAdd(&s_gain[j1], (u64)lo + ((u64)hi << 16));
+              if (MODE == kModeFarness) atomicAdd(&s_cnt[j1], __popc(grp));
+            }
+          } else if (won) {
+            do {
+              const int j = __ffsll((long long)won) - 1;
+              won &= won - 1;
+              atomicAdd(&s_gain[j], wt);
+              if (MODE == kModeFarness) atomicAdd(&s_cnt[j], 1);
+            } while (won);
+          }
         }
       }
       cta_sync();
