@@ -288,7 +288,10 @@ int launch_active_theta(gc_graph *g) {
 int launch_lazy_rounds(gc_graph *g, int32_t k, int64_t timeout_ns, const float *prop, int32_t fill,
                        bool wide_steps, long long local_max, int ctas, bool pruned, bool use_log,
                        long long log_cap) {
-  int grid = std::min(g->lazy_ctas, g->ws_count);
+  // one CTA per SM; wide steps give every CTA a gain workspace of its own, so
+  // there the grid is also capped by the workspaces allocated (on large graphs
+  // fewer than the SMs); grid-wide steps use workspace 0 and CTA 0's only
+  int grid = wide_steps ? std::min(g->lazy_ctas, g->ws_count) : g->lazy_ctas;
   if (ctas > 0 && ctas < grid) grid = ctas;
   int32_t wide = wide_steps ? 1 : 0;
   int32_t wcap = std::min(g->wcap, grid * kLanes);
