@@ -16,8 +16,9 @@ constexpr int32_t kInf = 0x3fffffff;  // "unreached" distance (d + 1 cannot over
 constexpr int kLanes = 64;            // candidates per bit-parallel batch (one uint64 word)
 constexpr int kGainThreads = 512;     // threads per CTA of the gain kernel
 constexpr int kCta0SelectMax = 4096;  // lazy selection by CTA 0 up to this list length, grid-wide above
-// CTA 0's shared-memory copy of such a list: bound (int64), id and stamp (int32)
-constexpr int kLazyListSmem = kCta0SelectMax * 16;
+// CTA 0's shared-memory copy of such a list: bound (int64), id and stamp
+// (int32); its sorted view: two position arrays (uint16) and a mark byte
+constexpr int kLazyListSmem = kCta0SelectMax * 16 + kCta0SelectMax * 5;
 constexpr int kWideLevels = 16;       // lazy steps go wide above this many BFS levels per batch
 constexpr int kEdgeIlp = 4;           // adjacency entries in flight per thread (CTA gain batch)
 constexpr int kBfsThreads = 256;      // threads per CTA of the grid-wide BFS

@@ -54,18 +54,24 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
   const int32_t *lact = act;
   long long *lkey = akey;
   int32_t *lst = ast;
+  __shared__ Cta0State s_st;  // CTA 0's step state in lean steps
   {  // the copies of the bounds of the (new) active list, and best_id's position
     const int b0 = *(volatile int32_t *)&lc->best_id;
     if (local) {
       if (blockIdx.x == 0) {
         long long *sk = reinterpret_cast<long long *>(s_list);
         int32_t *sa = reinterpret_cast<int32_t *>(sk + kCta0SelectMax), *ss = sa + kCta0SelectMax;
+        if (threadIdx.x == 0) s_st.bpos = -1;
+        cta_sync();
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
           const int v = act[i];
           sa[i] = v;
           sk[i] = ub[v];
           ss[i] = stamp[v];
-          if (v == b0) lc->best_pos = i;
+          if (v == b0) {
+            lc->best_pos = i;
+            s_st.bpos = i;
+          }
         }
         lact = sa;
         lkey = sk;
@@ -80,6 +86,25 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       }
     }
   }
+  // CTA 0's sorted view of a shared-memory list (lean steps)
+  __shared__ int s_nord;
+  SortedView view;
+  view.ord = reinterpret_cast<uint16_t *>(s_list + (size_t)kCta0SelectMax * 16);
+  view.tmp = view.ord + kCta0SelectMax;
+  view.mark = reinterpret_cast<unsigned char *>(view.tmp + kCta0SelectMax);
+  view.nord = &s_nord;
+  const bool use_view = local && !prop && !wide;
+  if (use_view && blockIdx.x == 0) {
+    if (threadIdx.x == 0) {  // the lean state, carried over from an earlier launch of the round
+      s_st.bid = *(volatile int32_t *)&lc->best_id;
+      s_st.bgain = *(volatile long long *)&lc->best_gain;
+      s_st.theta = *(volatile long long *)&lc->theta;
+      s_st.log_mark = *(volatile unsigned long long *)&lc->log_mark;
+      s_st.nsel = 0;
+      s_st.dec = 0;
+    }
+    sv_build(lkey, m, view);
+  }
   if (!grid_sync(&lc->bar, &lc->err, tns)) return;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const GainWs myws = gain_ws(ws, ws_stride, n, blockIdx.x);  // this CTA's own workspace
@@ -93,7 +118,12 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
   // batches it also runs level 0 of the batch and the accept bookkeeping before
   // the step's barrier, and fewer barriers are needed per step and per round.
   const bool cta0_sel = prop || wide || m <= kCta0SelectMax;
-  const bool lean = cta0_sel && !prop && !wide;
+  const bool lean = cta0_sel && !prop && !wide;  // (then also use_view: the list is local)
+  // the batch as CTA 0 sees it in lean steps (shared memory) and as the others do
+  const bool st0 = lean && blockIdx.x == 0;
+  const int32_t *bsel = st0 ? s_st.sel : lc->sel;
+  const int32_t *bnsel = st0 ? &s_st.nsel : &lc->n_sel;
+  long long *bout = st0 ? s_st.gout : lc->gsel;
   int r = *(volatile int32_t *)&lc->round;  // every CTA counts the rounds itself
   for (;;) {
     if (r >= k) break;
@@ -104,21 +134,23 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     }
     if (cta0_sel) {
       if (blockIdx.x == 0) {
-        lazy_cta0_step(lact, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
-                       lkey, lst, wsel, wgain, wpos, wide ? wcap : 0);
         if (lean) {
-          cta_sync();  // lc->dec, lc->sel and the reset batch control block
-          const int d = *(volatile int32_t *)&lc->dec;
+          lean_step(lact, ub, stamp, lc, gg, fold, r, lkey, lst, view, s_st);
+          cta_sync();  // s_st.dec, the batch and the reset batch control block
+          const int d = s_st.dec;
           if (d == 0) {
-            grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
+            grid_gain_batch<kModeGain>(rp, ci, n, dS, s_st.sel, 0, &s_st.nsel, s_st.gout, ws, gx, goff, gg, gctl,
                                        &lc->bar, &lc->err, tns, mx, c3, 0, -1, kBatchLevel0, clog, &lc->log_n,
                                        clog_cap);
           } else if (d == 1 && threadIdx.x == 0) {
-            picks[r] = lc->best_id;
-            pgain[r] = lc->best_gain;
+            picks[r] = s_st.bid;
+            pgain[r] = s_st.bgain;
             lc->pk[0] = lc->pk[1] = lc->pk[2] = 0;
             lc->decrease = 0;
           }
+        } else {
+          lazy_cta0_step(lact, m, ub, stamp, lc, wide ? nullptr : gg, fold, (prop && !wide) ? score : nullptr, fill,
+                         lkey, lst, wsel, wgain, wpos, wide ? wcap : 0);
         }
       }
     } else {  // every CTA takes part in the selection
@@ -147,8 +179,8 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
                                     wgain + bi * kLanes, myws, gctl, mx, LaneGraphs(), cnt, 0, c3);
         ok = grid_sync(&lc->bar, &lc->err, tns);  // gains visible to CTA 0
       } else {
-        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, lc->sel, 0, &lc->n_sel, lc->gsel, ws, gx, goff, gg, gctl,
-                                        &lc->bar, &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll, clog,
+        ok = grid_gain_batch<kModeGain>(rp, ci, n, dS, bsel, 0, bnsel, bout, ws, gx, goff, gg, gctl, &lc->bar,
+                                        &lc->err, tns, mx, c3, 0, -1, lean ? kBatchRest : kBatchAll, clog,
                                         &lc->log_n, clog_cap, &gcnt);
         // the gains are in lc->gsel, written by CTA 0: only a grid-wide fold
         // needs them published
@@ -220,17 +252,25 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
     ok = ok && grid_sync(&lc->bar, &lc->err, tns);
     if (!ok) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      pdec[r] = (long long)lc->decrease;
-      lc->last_gain = lc->best_gain;
-      ub[lc->best_id] = -1;  // a member: never a candidate again
-      const int bp = lc->best_pos;
-      if (bp >= 0 && bp < m && lact[bp] == lc->best_id) lkey[bp] = -1;
+      const int bid = lean ? s_st.bid : lc->best_id;
+      const long long bgain = lean ? s_st.bgain : lc->best_gain;
+      const int bp = lean ? s_st.bpos : lc->best_pos;
+      pdec[r] = (long long)*(volatile unsigned long long *)&lc->decrease;
+      lc->last_gain = bgain;
+      ub[bid] = -1;  // a member: never a candidate again
+      if (bp >= 0 && bp < m && lact[bp] == bid) lkey[bp] = -1;
       lc->best_id = -1;
       lc->best_gain = -1;
       lc->best_lane = -1;
       lc->log_n = 0;  // the next round's log (its first batch starts after a barrier)
       lc->log_mark = 0;
-      lc->rounds_done += 1;
+      if (lean) {
+        s_st.bid = -1;
+        s_st.bgain = -1;
+        s_st.bpos = -1;
+        s_st.log_mark = 0;
+      }
+      atomicAdd(&lc->rounds_done, 1);
       lc->round = r + 1;
     }
     ++r;

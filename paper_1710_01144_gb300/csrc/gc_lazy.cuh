@@ -80,6 +80,164 @@ static __device__ __forceinline__ void block_argmax_all(long long &v, int &id, l
   cta_sync();
 }
 
+// CTA 0's sorted view of its shared-memory list (lean steps): the positions
+// of the entries with a bound >= 0 in the order (bound desc, position asc) --
+// position order is id order, so this is the selection's order, ties to the
+// smaller id.  A step's batch is then the first 64 entries not evaluated in
+// the round, the same set the histogram selection finds.  A fold changes the
+// bounds of its batch only (exact gains), so the view is kept by one merge of
+// the re-sorted batch into the other entries; members (bound -1) leave it at
+// the next fold.  ord and tmp hold kCta0SelectMax entries, mark as many bytes
+// (zero between folds), *nord the view's length.
+struct SortedView {
+  uint16_t *ord, *tmp;
+  unsigned char *mark;
+  int *nord;
+};
+
+// a precedes b in the view
+static __device__ __forceinline__ bool sv_before(const long long *sk, int a, int b) {
+  const long long ka = sk[a], kb = sk[b];
+  return ka > kb || (ka == kb && a < b);
+}
+
+// The view of sk[0..m): the positions with sk >= 0, bitonic-sorted (padding
+// positions 0xffff go last).  Whole CTA.
+static __device__ void sv_build(const long long *sk, int m, const SortedView &v) {
+  __shared__ int s_scan[33];
+  const int tid = threadIdx.x, T = blockDim.x;
+  int nv = 0;
+  for (int base = 0; base < m; base += T) {
+    const int i = base + tid;
+    const int e = (i < m && sk[i] >= 0) ? 1 : 0;
+    if (i < m) v.mark[i] = 0;
+    int tot;
+    const int off = block_excl_scan(e, s_scan, &tot);
+    if (e) v.ord[nv + off] = (uint16_t)i;
+    nv += tot;
+  }
+  int N = 1;
+  while (N < nv) N <<= 1;
+  for (int i = nv + tid; i < N; i += T) v.ord[i] = 0xffffu;
+  cta_sync();
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < N; i += T) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int a = v.ord[i], b = v.ord[ixj];
+          const bool b_first = b != 0xffff && (a == 0xffff || sv_before(sk, b, a));
+          const bool a_first = a != 0xffff && (b == 0xffff || sv_before(sk, a, b));
+          if ((i & k) == 0 ? b_first : a_first) {
+            v.ord[i] = (uint16_t)b;
+            v.ord[ixj] = (uint16_t)a;
+          }
+        }
+      }
+      cta_sync();
+    }
+  if (tid == 0) *v.nord = nv;
+  cta_sync();
+}
+
+// After a fold: the batch's entries (list positions pos[0..ns), their bounds
+// in sk already the exact gains) leave the view, entries with sk < 0 are
+// dropped, and the batch, sorted by rank counting, is merged back.  Whole CTA.
+static __device__ void sv_refold(const long long *sk, const int32_t *pos, int ns, const SortedView &v) {
+  __shared__ uint16_t s_nb[kLanes];
+  __shared__ int s_scan[33];
+  const int tid = threadIdx.x, T = blockDim.x;
+  if (tid < ns) v.mark[pos[tid]] = 1;
+  cta_sync();
+  const int nord = *v.nord;
+  // the kept entries, in order, to tmp: contiguous chunks per thread
+  const int C = (nord + T - 1) / T;
+  const int i0 = min(nord, tid * C), i1 = min(nord, i0 + C);
+  int keep = 0;
+  for (int i = i0; i < i1; ++i) {
+    const int p = v.ord[i];
+    keep += (!v.mark[p] && sk[p] >= 0) ? 1 : 0;
+  }
+  int nkeep;
+  int at = block_excl_scan(keep, s_scan, &nkeep);
+  for (int i = i0; i < i1; ++i) {
+    const int p = v.ord[i];
+    if (!v.mark[p] && sk[p] >= 0) v.tmp[at++] = (uint16_t)p;
+  }
+  if (tid < ns) {  // the batch in view order
+    const int p = pos[tid];
+    int rk = 0;
+    for (int j = 0; j < ns; ++j) rk += sv_before(sk, pos[j], p) ? 1 : 0;
+    s_nb[rk] = (uint16_t)p;
+  }
+  cta_sync();
+  if (tid < ns) v.mark[pos[tid]] = 0;
+  // merge: each entry's rank is its index plus the entries of the other run
+  // before it (binary search)
+  for (int i = tid; i < nkeep; i += T) {
+    const int p = v.tmp[i];
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sv_before(sk, s_nb[mid], p)) lo = mid + 1;
+      else hi = mid;
+    }
+    v.ord[i + lo] = (uint16_t)p;
+  }
+  if (tid < ns) {
+    const int p = s_nb[tid];
+    int lo = 0, hi = nkeep;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sv_before(sk, v.tmp[mid], p)) lo = mid + 1;
+      else hi = mid;
+    }
+    v.ord[tid + lo] = (uint16_t)p;
+  }
+  if (tid == 0) *v.nord = nkeep + ns;
+  cta_sync();
+}
+
+// The first `need` entries of the view not evaluated in round r (and with a
+// bound >= 0) to sel/selpos, in view order; *umax/*vmax get the first one's
+// bound and id (LLONG_MIN / -1 if none).  Returns how many were taken.
+// Whole CTA; *scanned counts the view entries read.
+static __device__ int sv_select(const long long *sk, const int32_t *sa, const int32_t *ss, int r,
+                                const SortedView &v, int need, int32_t *sel, int32_t *selpos, long long *umax,
+                                int *vmax, unsigned long long *scanned) {
+  __shared__ int s_scan[33];
+  __shared__ long long s_u;
+  __shared__ int s_v;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int nord = *v.nord;
+  if (tid == 0) {
+    s_u = LLONG_MIN;
+    s_v = -1;
+  }
+  int taken = 0, base = 0;
+  for (; base < nord && taken < need; base += T) {
+    const int i = base + tid;
+    const int p = i < nord ? v.ord[i] : 0;
+    const bool e = i < nord && sk[p] >= 0 && ss[p] != r;
+    int tot;
+    const int off = block_excl_scan(e ? 1 : 0, s_scan, &tot);
+    if (e && taken + off < need) {
+      sel[taken + off] = sa[p];
+      selpos[taken + off] = p;
+      if (taken + off == 0) {
+        s_u = sk[p];
+        s_v = sa[p];
+      }
+    }
+    taken += tot;
+  }
+  cta_sync();
+  *umax = s_u;
+  *vmax = s_v;
+  if (tid == 0 && scanned) atomicAdd(scanned, (unsigned long long)min(base, nord));
+  return taken < need ? taken : need;
+}
+
 // The per-step statistics of CTA 0's list scan in one exchange: the best
 // (value, id) pair, the smallest value and the count, each reduced over the
 // warp by shuffles, then over the warps by every thread from shared memory.
@@ -385,6 +543,122 @@ static __device__ void lazy_cta0_step(const int32_t *act, int32_t m, long long *
     lc->n_sel = taken < kLanes ? taken : kLanes;
     lc->dec = 0;
     if (gg) {
+      gg->pk[0] = 0;
+      gg->pk[1] = 0;
+      gg->pk[2] = 0;
+      gg->touched = 0;
+    }
+  }
+}
+
+// CTA 0's state in lean steps, in its shared memory: CTA 0 alone selects,
+// runs level 0, reads the batch's gains and folds them, so it keeps the batch
+// (ids, list positions, gains), the decision and the round's best here and
+// publishes to LazyCtl only what the other CTAs read (dec, n_sel, best_*,
+// log_mark).  Every read on CTA 0's path of a step is then a shared-memory
+// read but one (the claim log's length).
+struct Cta0State {
+  int32_t sel[kLanes], selpos[kLanes];
+  long long gout[kLanes];
+  int nsel, dec, bid, bpos;
+  long long bgain, theta;
+  unsigned long long log_mark;
+};
+
+// One lean step of CTA 0 (list in shared memory: ids act, bounds akey, stamps
+// ast, all at list positions; its sorted view): fold the batch just evaluated
+// (exact gains become bounds, the round's best is updated), then decide --
+// accept the best, ask for a longer list, or evaluate the head of the view --
+// exactly as lazy_cta0_step does with its histogram selection.
+static __device__ void lean_step(const int32_t *act, long long *ub, int32_t *stamp, LazyCtl *lc,
+                                 GridGainCtl *gg, bool fold, int r, long long *akey, int32_t *ast,
+                                 const SortedView &view, Cta0State &st) {
+  __shared__ long long s_bv[2];
+  __shared__ int s_bid[2], s_bpos[2], s_blane[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (fold) {
+    const int ns = st.nsel;
+    long long bv = -1;
+    int bid = -1, bpos = -1, blane = -1;
+    if (tid < ns) {
+      const int v = st.sel[tid], p = st.selpos[tid];
+      const long long gv = st.gout[tid];
+      ub[v] = gv;
+      stamp[v] = r;
+      akey[p] = gv;
+      ast[p] = r;
+      bv = gv;
+      bid = v;
+      bpos = p;
+      blane = tid;
+    }
+    if (tid < kLanes) {  // arg-best of the batch: warps 0 and 1, then thread 0
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bpos, o), ol = __shfl_xor_sync(0xffffffffu, blane, o);
+        if (oid >= 0 && (bid < 0 || better_max(ov, oid, bv, bid))) {
+          bv = ov;
+          bid = oid;
+          bpos = op;
+          blane = ol;
+        }
+      }
+      if (lane == 0) {
+        s_bv[tid >> 5] = bv;
+        s_bid[tid >> 5] = bid;
+        s_bpos[tid >> 5] = bpos;
+        s_blane[tid >> 5] = blane;
+      }
+    }
+    cta_sync();
+    if (tid == 0) {
+      if (s_bid[1] >= 0 && (bid < 0 || better_max(s_bv[1], s_bid[1], bv, bid))) {
+        bv = s_bv[1];
+        bid = s_bid[1];
+        bpos = s_bpos[1];
+        blane = s_blane[1];
+      }
+      // the batch's claim-log entries: [log_mark, log_n)
+      const unsigned long long l1 = *(volatile unsigned long long *)&lc->log_n;
+      if (bid >= 0 && better_max(bv, bid, st.bgain, st.bid)) {
+        st.bgain = bv;
+        st.bid = bid;
+        st.bpos = bpos;
+        lc->best_gain = bv;
+        lc->best_id = bid;
+        lc->best_pos = bpos;
+        lc->best_lane = blane;
+        lc->best_seg0 = st.log_mark;
+        lc->best_seg1 = l1;
+      }
+      st.log_mark = l1;
+      lc->log_mark = l1;
+      atomicAdd(reinterpret_cast<unsigned long long *>(&lc->steps), 1ull);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&lc->evals), (unsigned long long)ns);
+    }
+    sv_refold(akey, st.selpos, ns, view);
+  }
+  long long vmx;
+  int vid;
+  const int taken = sv_select(akey, act, ast, r, view, kLanes, st.sel, st.selpos, &vmx, &vid, &lc->sel_scanned);
+  const long long gb = st.bgain;
+  const int vb = st.bid;
+  int dec;
+  if (vb >= 0 && (taken == 0 || better_max(gb, vb, vmx, vid))) dec = gb >= st.theta ? 1 : 2;
+  else if (taken == 0) dec = 2;
+  else dec = 0;
+  if (dec == 0 && tid < kLanes) {  // a fresh grid-batch control block
+    gg->gain[tid] = 0;
+    gg->cnt[tid] = 0;
+  }
+  if (tid == 0) {
+    st.dec = dec;
+    lc->dec = dec;
+    if (dec == 0) {
+      st.nsel = taken;
+      lc->n_sel = taken;
       gg->pk[0] = 0;
       gg->pk[1] = 0;
       gg->pk[2] = 0;
