@@ -225,12 +225,14 @@ static __device__ __forceinline__ bool grid_gain_batch(const int32_t *__restrict
     const int nlev = L + 1;
     const long long es = E * b / G, ee = E * (b + 1) / G;
     if (es < ee) {
-      if (tid < 32) {
+      // the first entry whose range holds edge es: a warp-wide search, unless
+      // one staging pass covers the whole frontier (then it starts at 0)
+      if (F > T && tid < 32) {
         const int x = warp_find_start(qstart, F, es);
         if (tid == 0) s_x0 = x;
       }
       cta_sync();
-      int x = s_x0;
+      int x = F > T ? s_x0 : 0;
       while (x < F) {
         // stage up to T entries from x: range starts, row starts, lane masks
         const int xi = x + tid;
