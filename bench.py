@@ -214,10 +214,13 @@ def profiled_traffic(kernel: str, workload: str):
 
 def lazy_kernel_bytes(t) -> float:
     """Algorithmic bytes of the persistent lazy kernel: its gain phases (the
-    model below), its d_S updates (row pointers 8 B per frontier entry, 4 B
-    per adjacency entry, 4 B per lowered label) and its selection passes
-    (list id, bound and stamp: 16 B per active-list entry read)."""
+    model below), the claim log (16 B per entry written by the gain phases and
+    per entry read by a d_S update), its relabel-BFS d_S updates (row pointers
+    8 B per frontier entry, 4 B per adjacency entry) and every update's lowered
+    labels (4 B each), and its selection passes (list id, bound and stamp: 16 B
+    per active-list entry read)."""
     return (algorithmic_bytes(t["lazy_frontier"], t["lazy_edges"], t["lazy_pushes"], t["lazy_lanes"]) +
+            16.0 * t.get("lazy_log_entries", 0) + 16.0 * t.get("lazy_upd_log", 0) +
             8.0 * t["lazy_upd_frontier"] + 4.0 * t["lazy_upd_edges"] + 4.0 * t["lazy_upd_relabels"] +
             16.0 * t["lazy_sel_scanned"])
 

@@ -205,6 +205,7 @@ typedef struct gc_stats {
    * log (the rest ran the relabel BFS) */
   int64_t lazy_log_picks;    /* picks updated from the log */
   int64_t lazy_upd_log;      /* log entries those updates read */
+  int64_t lazy_log_entries;  /* log entries the gain phases wrote (16 bytes each) */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

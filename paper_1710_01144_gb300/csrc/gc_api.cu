@@ -1188,6 +1188,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->lazy_sel_scanned = (int64_t)g->h_lctl->sel_scanned;
     stats->lazy_log_picks = (int64_t)g->h_lctl->log_picks;
     stats->lazy_upd_log = (int64_t)g->h_lctl->upd_log;
+    stats->lazy_log_entries = (int64_t)g->h_lctl->log_written;
     stats->r0_batches = r0_stats[0];
     stats->r0_levels = r0_stats[1];
     stats->r0_td_edges = r0_stats[2];

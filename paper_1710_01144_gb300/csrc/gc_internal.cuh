@@ -205,6 +205,7 @@ struct LazyCtl {
   int32_t pad4;
   unsigned long long upd_log;    // d_S updates from the log: entries read
   unsigned long long log_picks;  // picks whose d_S update came from the log
+  unsigned long long log_written;  // log entries written (summed over rounds)
 };
 
 // Control block of the wide round-0 kernel (gc_round0.cu), zeroed before each

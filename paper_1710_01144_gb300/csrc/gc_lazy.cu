@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(kGridGainThreads, 1)
       const int bid = lean ? s_st.bid : lc->best_id;
       const long long bgain = lean ? s_st.bgain : lc->best_gain;
       const int bp = lean ? s_st.bpos : lc->best_pos;
+      const unsigned long long ln = *(volatile unsigned long long *)&lc->log_n;
       pdec[r] = (long long)*(volatile unsigned long long *)&lc->decrease;
+      lc->log_written += ln < clog_cap ? ln : clog_cap;
       lc->last_gain = bgain;
       ub[bid] = -1;  // a member: never a candidate again
       if (bp >= 0 && bp < m && lact[bp] == bid) lkey[bp] = -1;
