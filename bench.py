@@ -450,15 +450,47 @@ def comparison_legs(gc, rp, ci, args, grp0, f0):
         G.set_proposal(None)
         net.close()
     out["speedup_learned_vs_plain"] = out["plain_gpu_lazy_ms"] / out["learned_ms"]
-    if args.scale != 20 or args.k != 100:
-        rp20, ci20 = graphgen.rmat_s20_ef16()
-        with gc.Graph(rp20, ci20) as G20:
-            G20.greedy(100)
-            ms, _ = _best_ms(lambda: G20.greedy(100), 5)
+    rp20, ci20 = graphgen.rmat_s20_ef16() if (args.scale != 20) else (rp, ci)
+    with gc.Graph(rp20, ci20) as G20:
+        g20, _, _ = G20.greedy(100)
+        ms, _ = _best_ms(lambda: G20.greedy(100), 5)
         out["rmat_s20_ef16_lcc_k100_ms"] = ms
+        out["gain_lanes_rmat_s20"] = gain_lanes_leg(G20, int(g20[0]))
     if args.batch_graphs > 0:
         out["mixed_batch"] = mixed_batch_leg(gc, args.batch_graphs)
     return out
+
+
+def gain_lanes_leg(G, s0):
+    """Round 1 without bounds as one gc_marginal_gains call: the gain of every
+    vertex for S = {s0}, at 64, 128 and 256 candidates per CTA batch (identical
+    results), with the kernel's device time and its byte model per width."""
+    n = G.n
+    allv = np.arange(n, dtype=np.int32)
+    res, ref = {}, None
+    for lanes in (64, 128, 256):
+        G.set_gain_lanes(lanes)
+        G.gains([s0], allv)  # warm-up (and the wide kernel's workspace)
+        best = None
+        for _ in range(3):
+            g, st = G.gains([s0], allv, stats=True)
+            if best is None or st["ms_gain_kernel"] < best["ms_gain_kernel"]:
+                best = st
+        if ref is None:
+            ref = g
+        assert np.array_equal(g, ref), "gains differ between lane widths"
+        w = lanes // 64
+        # per frontier entry: row pointers and its W claim words; per adjacency
+        # entry 4 B; per push: d_S, visited and claim words; 8 B per gain
+        bytes_alg = ((8.0 + 8.0 * w) * best["frontier"] + 4.0 * best["edges_union"]
+                     + (4.0 + 16.0 * w) * best["pushes"] + 8.0 * n)
+        res[str(lanes)] = {"ms_gain_kernel": best["ms_gain_kernel"], "batches": best["batches"],
+                           "edges_union": best["edges_union"], "edges_scalar": best["edges_scalar"],
+                           "gteps_scalar": best["edges_scalar"] / (best["ms_gain_kernel"] * 1e6),
+                           "achieved_gbs": bytes_alg / (best["ms_gain_kernel"] * 1e6)}
+    G.set_gain_lanes(64)
+    res["fastest"] = min((k for k in res), key=lambda k: res[k]["ms_gain_kernel"])
+    return res
 
 
 def mixed_batch_leg(gc, count):

@@ -241,8 +241,8 @@ int64_t gc_num_entries(const gc_graph *g);
 int gc_group_farness(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_farness);
 
 /* gc_marginal_gains -- Delta(v | S) for each candidate v (Sec. 4.1 pruned SSSP,
- * evaluated 64 candidates at a time by a bit-parallel multi-source BFS in the
- * form of Theorem 1, Sec. 4.3).
+ * evaluated 64 candidates at a time (128 or 256 after gc_set_gain_lanes) by
+ * a bit-parallel multi-source BFS in the form of Theorem 1, Sec. 4.3).
  * S        : host int32[s_len], s_len >= 1 (d(., empty set) is undefined).
  * cand     : host int32[n_cand], any ids in [0, n), repeats allowed, n_cand >= 0.
  * out_gain : host int64[n_cand]; 0 for candidates in S.
@@ -250,6 +250,22 @@ int gc_group_farness(gc_graph *g, const int32_t *S, int32_t s_len, int64_t *out_
  * Errors   : GC_EINVAL, GC_EDISCONNECTED. */
 int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_t *cand,
                       int32_t n_cand, int64_t *out_gain, gc_stats *stats);
+
+/* gc_set_gain_lanes -- candidates per batch of the CTA-batched gain kernel:
+ * the width of the lane words of the bit-parallel pruned BFS (Sec. 4.1 with
+ * the bit vectors of Theorem 1, Sec. 4.3; one bit per candidate, one scan of
+ * a frontier vertex's row for every candidate that reached it at that level).
+ * lanes    : 64 (default: one uint64 word per vertex), 128 or 256 (two or four
+ *            words per vertex, 64 or 128 bytes of lane words and flags per
+ *            vertex in each CTA's workspace, allocated on the first call that
+ *            uses it and kept until gc_free).
+ * Applies to every later gain evaluation of the handle that runs whole batches
+ * one per CTA: gc_marginal_gains, gc_marginal_gains_device, and gc_greedy's
+ * round-1 sweep and host-driven lazy steps (step_mode 1 with step_lanes 64).
+ * Batches of fewer lanes, grid-wide batches
+ * and the persistent lazy kernel keep 64 lanes.  Results never depend on it.
+ * Errors   : GC_EINVAL (NULL handle, lanes not 64, 128 or 256). */
+int gc_set_gain_lanes(gc_graph *g, int32_t lanes);
 
 /* gc_marginal_gains_device -- as gc_marginal_gains with device pointers for
  * S, cand and out_gain; asynchronous on the handle's stream (no sync, no

@@ -11,6 +11,9 @@ Batched solver (`gc_batch_greedy`):
 Single-graph solver (`gc_greedy`):
     active_target -- candidate-list size of the persistent lazy kernel
     round1_heavy  -- highest-degree round-1 candidates evaluated grid-wide
+Gain evaluation (`gc_marginal_gains`):
+    gain_lanes    -- candidates per CTA batch of the bit-parallel pruned BFS
+                     (64, 128 or 256: one, two or four 64-bit words per vertex)
 """
 from __future__ import annotations
 
@@ -25,6 +28,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gcgb300", "auto
 
 BATCH_SPACE = [{"lanes": l, "A": a} for l in (16, 32, 64) for a in (256, 1024, 4096)]
 SINGLE_SPACE = [{"active_target": a, "round1_heavy": h} for a in (512, 2048, 8192) for h in (256, 1024, 4096)]
+GAIN_LANES_SPACE = (64, 128, 256)
 
 
 def _load(path):
@@ -111,3 +115,34 @@ def tune_single(graph, k: int, reps: int = 2, cache: str | None = DEFAULT_CACHE,
         data[key] = entry
         _store(cache, data)
     return entry["best"], entry
+
+
+def tune_gain_lanes(graph, S, cand, reps: int = 3, cache: str | None = DEFAULT_CACHE, space=None, log=None):
+    """Best candidates-per-batch width for gc_marginal_gains of this many
+    candidates against a group of this size on this graph (cached), by the
+    gain kernel's device time; every width must return the same gains.  The
+    handle is left at the winning width."""
+    key = signature("gains", [graph.n, graph.nnz], [int(np.size(S)), int(np.size(cand))])
+    data = _load(cache) if cache else {}
+    if key not in data:
+        results, ref = [], None
+        for lanes in space or GAIN_LANES_SPACE:
+            graph.set_gain_lanes(lanes)
+            graph.gains(S, cand)  # warm-up (allocates a wide kernel's workspace)
+            best, got = float("inf"), None
+            for _ in range(reps):
+                got, st = graph.gains(S, cand, stats=True)
+                best = min(best, st["ms_gain_kernel"])
+            if ref is None:
+                ref = got
+            elif not np.array_equal(got, ref):
+                raise RuntimeError("autotune: gain_lanes %d changed a gain" % lanes)
+            results.append({"gain_lanes": lanes, "ms": best})
+            if log:
+                log("gains lanes %d: %.2f ms" % (lanes, best))
+        win = min(results, key=lambda r: r["ms"])
+        data[key] = {"best": {"gain_lanes": win["gain_lanes"]}, "trials": results}
+        if cache:
+            _store(cache, data)
+    graph.set_gain_lanes(data[key]["best"]["gain_lanes"])
+    return data[key]["best"], data[key]

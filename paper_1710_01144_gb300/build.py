@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgc.so")
-SOURCES = ["gc_api.cu", "gc_bfs.cu", "gc_gain.cu", "gc_gain_grid.cu", "gc_select.cu", "gc_static.cu", "gc_lazy.cu", "gc_mlp.cu", "gc_batch.cu", "gc_round0.cu", "gc_bits.cu", "gc_weighted.cu"]
+SOURCES = ["gc_api.cu", "gc_bfs.cu", "gc_gain.cu", "gc_gain_wide.cu", "gc_gain_grid.cu", "gc_select.cu", "gc_static.cu", "gc_lazy.cu", "gc_mlp.cu", "gc_batch.cu", "gc_round0.cu", "gc_bits.cu", "gc_weighted.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

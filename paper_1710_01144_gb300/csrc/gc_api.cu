@@ -66,7 +66,7 @@ static void release(gc_graph *g) {
                  g->ws, g->dec, g->ggctl, g->goff, g->lctl, g->picks, g->pgain, g->pdec, g->mx_buf,
                  g->two_hop, g->score, g->rec_count, g->akey, g->ast, g->gx, g->wsel, g->wpos, g->wgain,
                  g->lev_cnt, g->lev_C, g->lev_M, g->lev_max, g->rpf, g->cif, g->c3, g->gsel, g->heavy, g->n_heavy,
-                 g->g3, g->c3s, g->r0_vis, g->wt, g->w_ws, g->clog};
+                 g->g3, g->c3s, g->r0_vis, g->wt, g->w_ws, g->clog, g->x_ws};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (g->h_sctl) cudaFreeHost(g->h_sctl);
@@ -386,6 +386,13 @@ int gc_marginal_gains(gc_graph *g, const int32_t *S, int32_t s_len, const int32_
     stats->ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
+  return GC_OK;
+}
+
+int gc_set_gain_lanes(gc_graph *g, int32_t lanes) {
+  if (!g || (lanes != 64 && lanes != 128 && lanes != 256))
+    return fail(GC_EINVAL, "gc_set_gain_lanes: lanes must be 64, 128 or 256");
+  g->gain_lanes = lanes;
   return GC_OK;
 }
 

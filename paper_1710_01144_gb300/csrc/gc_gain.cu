@@ -93,6 +93,9 @@ int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
                  const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes, bool pruned) {
   if (!n_cand_dev && n_cand <= 0) return GC_OK;
   if (lanes < 1 || lanes > kLanes) lanes = kLanes;
+  // full batches of gains at the handle's width above 64: the wide kernel
+  if (mode == kModeGain && lanes == kLanes && g->gain_lanes > kLanes)
+    return launch_gains_wide(g, cand, n_cand, n_cand_dev, out, max_ctas, pruned);
   GC_CUDA(cudaMemsetAsync(&g->gctl->batch_next, 0, sizeof(unsigned int), g->stream));
   int ctas = g->gain_ctas;
   if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;

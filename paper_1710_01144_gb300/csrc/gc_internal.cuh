@@ -288,6 +288,13 @@ struct gc_graph {
   size_t w_stride = 0;
   int w_ctas = 0;
   unsigned int *w_task = nullptr;
+  // candidates per batch of the CTA-batched gain kernel (gc_set_gain_lanes):
+  // 64, or 128 / 256 for the wide kernel (gc_gain_wide.cu), whose per-CTA
+  // workspaces are allocated on first use
+  int32_t gain_lanes = 64;
+  unsigned char *x_ws = nullptr;
+  size_t x_stride = 0;
+  int x_ctas = 0, x_w = 0;
   float *score = nullptr;                  // proposal scores of the active list [n]
   // learned proposal (caller-owned weights) and training-data recorder
   const float *prop_params = nullptr;
@@ -401,6 +408,11 @@ int launch_gains(gc_graph *g, int mode, const int32_t *cand, int32_t n_cand,
                  const int32_t *n_cand_dev, long long *out, int max_ctas, int lanes = kLanes,
                  bool pruned = false);
 size_t gain_ws_stride(int32_t n);
+// Gain mode with 128 or 256 candidates per batch (g->gain_lanes), one CTA per
+// batch; the same contract as launch_gains at 64 lanes.
+int launch_gains_wide(gc_graph *g, const int32_t *cand, int32_t n_cand, const int32_t *n_cand_dev,
+                      long long *out, int max_ctas, bool pruned);
+size_t gain_wide_ws_stride(int32_t n, int W);
 // One batch of nl <= 64 candidates with every CTA (cooperative launch);
 // nl_dev (optional) gives min(64, *nl_dev) instead.
 int launch_gains_grid(gc_graph *g, int mode, const int32_t *cand, int32_t nl, const int32_t *nl_dev,

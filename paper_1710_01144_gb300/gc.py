@@ -41,7 +41,7 @@ EXPORTS = ("gc_opts_default", "gc_load_csr", "gc_free", "gc_num_vertices", "gc_n
            "gc_mlp_get_params", "gc_mlp_forward", "gc_mlp_grad", "gc_mlp_adam_step", "gc_mlp_train",
            "gc_candidate_features", "gc_set_proposal", "gc_set_recorder", "gc_recorded", "gc_batch_load",
            "gc_batch_free", "gc_batch_vertices", "gc_batch_greedy", "gc_gain_upper_bounds", "gc_greedy_batch",
-           "gc_top_closeness", "gc_greedy_bits", "gc_set_weights", "gc_greedy_weighted")
+           "gc_top_closeness", "gc_greedy_bits", "gc_set_weights", "gc_greedy_weighted", "gc_set_gain_lanes")
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         lib.gc_group_farness.argtypes = [vp, vp, i32, vp]
         lib.gc_marginal_gains.argtypes = [vp, vp, i32, vp, i32, vp, ctypes.POINTER(Stats)]
         lib.gc_marginal_gains_device.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.gc_set_gain_lanes.argtypes = [vp, i32]
         lib.gc_greedy.argtypes = [vp, i32, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]
         lib.gc_gain_upper_bounds.argtypes = [vp, vp, i32, vp]
         lib.gc_marginal_gains_static.argtypes = [i32, vp, vp, vp, i32, vp, i32, vp, vp]
@@ -220,6 +221,10 @@ class Graph:
         _check(load().gc_marginal_gains(self._h, s.ctypes.data, int(np.size(S)), _i32(c).ctypes.data,
                                         c.size, out.ctypes.data, ctypes.byref(st)))
         return (out[:c.size], st.as_dict()) if stats else out[:c.size]
+
+    def set_gain_lanes(self, lanes: int):
+        """Candidates per batch (64, 128 or 256) of the CTA-batched gain kernel."""
+        _check(load().gc_set_gain_lanes(self._h, int(lanes)))
 
     def gains_device(self, S_dev, cand_dev, out_dev):
         """Asynchronous gains on the handle's stream; all three are CUDA tensors."""

@@ -366,3 +366,102 @@ def test_round0_wide_lane_widths(gcm, name, g, lanes):
             assert st["r0_batches"] >= 2
         got1, f1, _ = G.greedy(1, round0_lanes=lanes)
         assert got1[0] == s0 and f1 == f0
+
+
+# ---- gain kernel at 128 and 256 candidates per batch (gc_set_gain_lanes) ----
+
+@pytest.mark.parametrize("lanes", [128, 256])
+@pytest.mark.parametrize("name,g", small_cases())
+def test_gains_wide_lanes(gcm, name, g, lanes):
+    """Two or four lane words per vertex: the same exact gains as the oracle's
+    full BFS for every candidate, groups of 1, 3 and 8 vertices."""
+    rp, ci = g
+    n = rp.size - 1
+    rng = np.random.default_rng(2)
+    with gcm.Graph(rp, ci) as G:
+        G.set_gain_lanes(lanes)
+        for size in (1, 3, 8):
+            S = rng.choice(n, size=min(size, n), replace=False)
+            cand = np.arange(n, dtype=np.int32)
+            np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+
+
+@pytest.mark.parametrize("lanes", [128, 256])
+def test_gains_wide_ragged_repeats_members(gcm, lanes):
+    """Partial last batches, members of S, a repeated candidate inside one
+    batch, more candidates than vertices, and the width switched back and
+    forth on one handle."""
+    rp, ci = graphgen.barabasi_albert(3000, 4, 11)
+    n = rp.size - 1
+    rng = np.random.default_rng(3)
+    S = rng.choice(n, size=6, replace=False)
+    with gcm.Graph(rp, ci) as G:
+        for m in (0, 1, 127, 128, 129, 255, 256, 257, 1000, 4097):
+            G.set_gain_lanes(lanes)
+            cand = rng.integers(0, n, size=m).astype(np.int32)
+            if m > 3:
+                cand[:3] = S[:3]
+                cand[3] = cand[4]
+            ref = oracle.gains(rp, ci, S, cand)
+            np.testing.assert_array_equal(G.gains(S, cand), ref)
+            G.set_gain_lanes(64)
+            np.testing.assert_array_equal(G.gains(S, cand), ref)
+        G.set_gain_lanes(lanes)
+        cand = rng.integers(0, n, size=2 * n + 5).astype(np.int32)
+        np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+        with pytest.raises(gcm.GcError):
+            G.set_gain_lanes(96)
+
+
+@pytest.mark.parametrize("lanes", [128, 256])
+def test_gains_wide_rmat14_sampled(gcm, lanes):
+    """R-MAT scale 14 (hub rows much longer than a CTA's 512 threads): 3000
+    seeded candidates, several batches and a ragged tail, against the oracle;
+    every vertex against the 64-lane kernel."""
+    rp, ci = graphgen.rmat(14, 16.0, seed=6)
+    n = rp.size - 1
+    rng = np.random.default_rng(8)
+    S = rng.choice(n, size=4, replace=False)
+    cand = rng.choice(n, size=3000, replace=False).astype(np.int32)
+    with gcm.Graph(rp, ci) as G:
+        G.set_gain_lanes(lanes)
+        np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+        allv = np.arange(n, dtype=np.int32)
+        wide = G.gains(S, allv)
+        G.set_gain_lanes(64)
+        np.testing.assert_array_equal(wide, G.gains(S, allv))
+
+
+@pytest.mark.parametrize("lanes", [128, 256])
+@pytest.mark.parametrize("name,g", small_cases() + [("rmat13", graphgen.rmat(13, 16.0, seed=4))])
+def test_greedy_wide_lanes(gcm, name, g, lanes):
+    """Greedy whose round 1 (every vertex, no bounds) and host-driven lazy
+    steps run on the wide kernel: the oracle's group and farness."""
+    rp, ci = g
+    k = min(12, rp.size - 1)
+    grp, ft, _ = oracle.greedy_plain(rp, ci, k)
+    with gcm.Graph(rp, ci) as G:
+        G.set_gain_lanes(lanes)
+        for kw in ({"round1_bound": False, "step_mode": 1, "eval_per_step": 256, "step_lanes": 64},
+                   {"step_mode": 1, "eval_per_step": 512, "step_lanes": 64}, {}):
+            got, f, st = G.greedy(k, **kw)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+
+
+def test_autotune_gain_lanes(gcm, tmp_path):
+    """The width tuner times 64, 128 and 256 lanes, checks that they agree,
+    caches the winner and leaves the handle at it; the oracle's gains."""
+    from paper_1710_01144_gb300 import autotune
+
+    rp, ci = graphgen.barabasi_albert(3000, 4, 11)
+    n = rp.size - 1
+    S = np.array([5, 77, 1234], dtype=np.int32)
+    cand = np.arange(n, dtype=np.int32)
+    cache = str(tmp_path / "tune.json")
+    with gcm.Graph(rp, ci) as G:
+        best, entry = autotune.tune_gain_lanes(G, S, cand, reps=1, cache=cache)
+        assert best["gain_lanes"] in (64, 128, 256) and len(entry["trials"]) == 3
+        np.testing.assert_array_equal(G.gains(S, cand), oracle.gains(rp, ci, S, cand))
+        again, _ = autotune.tune_gain_lanes(G, S, cand, cache=cache)
+        assert again == best
