@@ -320,14 +320,18 @@ def run_gc(args):
     with gc.Graph(hrp, hci) as Gw:  # warm the allocator path once
         Gw.greedy(args.k)
     barrier()
-    e2e_t = []
+    e2e_t, e2e_parts = [], []
     for _ in range(e2e_steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with gc.Graph(hrp, hci) as Ge:
+            t1 = time.perf_counter()
             g_e, f_e, _ = Ge.greedy(args.k)
-        e2e_t.append((time.perf_counter() - t0) * 1e3)
+            t2 = time.perf_counter()
+        t3 = time.perf_counter()
+        e2e_t.append((t3 - t0) * 1e3)
+        e2e_parts.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3))
         assert np.array_equal(g_e, grp0) and f_e == f0
     barrier()
     t_e2e = max_over_ranks(sum(e2e_t) / len(e2e_t), "cuda")
@@ -391,7 +395,8 @@ def run_gc(args):
             "e2e": {"value": job_value(ws, t_e2e), "unit": "size-%d groups/s" % args.k,
                     "ms_per_step": t_e2e,
                     "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
-                    "d2h_bytes_per_step": int(4 * args.k + 8)},
+                    "d2h_bytes_per_step": int(4 * args.k + 8),
+                    "ms_load_greedy_free": [round(float(np.mean([p[i] for p in e2e_parts])), 2) for i in range(3)]},
             "gpu_launches": int(tot["kernel_launches"]),
             "clocks": clocks,
         }
