@@ -83,6 +83,13 @@ typedef struct gc_graph gc_graph; /* opaque: device CSR + distance/bound arrays 
                                instead of from the claim log of the pick's
                                gain batch (the same vertices at the same
                                distances); work only */
+#define GC_OPT_R0_NO_PROBE 0x40u /* gc_greedy, gc_top_closeness round 0 (wide
+                               batches): no far-vertex probe before the
+                               count-only distance-2 pass (the probe reads the
+                               short rows of every 8th window of 32 vertices
+                               first and cuts every lane whose BFScut bound,
+                               with the vertices proven at distance >= 3,
+                               already exceeds the best farness); work only */
 
 /* Options of gc_greedy; zero-initialise and set what you need
  * (gc_opts_default fills the defaults). */
@@ -206,6 +213,8 @@ typedef struct gc_stats {
   int64_t lazy_log_picks;    /* picks updated from the log */
   int64_t lazy_upd_log;      /* log entries those updates read */
   int64_t lazy_log_entries;  /* log entries the gain phases wrote (16 bytes each) */
+  int64_t r0_probes;         /* round 0, wide batches: far-vertex probes run */
+  int64_t r0_probe_cut;      /* and the lanes they cut */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

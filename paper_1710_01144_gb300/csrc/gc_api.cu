@@ -512,7 +512,8 @@ int gc_top_closeness(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *ou
       GC_TRY(gain_event(g, 1, &e1));
       GC_CUDA(cudaEventRecord(e0, g->stream));
       GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w,
-                                !(opts.flags & GC_OPT_R0_FULL_LEVELS), tns));
+                                !(opts.flags & GC_OPT_R0_FULL_LEVELS), tns,
+                                (opts.flags & GC_OPT_R0_NO_PROBE) ? 0 : kR0ProbeStride));
       GC_CUDA(cudaEventRecord(e1, g->stream));
       GC_TRY(sync(g));
       GC_CUDA(cudaEventElapsedTime(&ms_wide, e0, e1));
@@ -802,6 +803,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   int64_t r0_stats[3] = {0, 0, 0};  // wide round-0 kernel: batches, bottom-up levels, top-down entries
   double r0_ms[4] = {0, 0, 0, 0};     // and its phases: selection, top-down, bottom-up, clears
   int64_t r0_bu[4] = {0, 0, 0, 0};    // its bottom-up claiming rows, entries read, words gathered, dense clears
+  int64_t r0_probe[2] = {0, 0};       // its probe passes and the lanes they cut
   bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
@@ -899,10 +901,10 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     ev_k64.push_back(3);
     GC_CUDA(cudaEventRecord(e0, g->stream));
     GC_TRY(launch_round0_wide(g, g->list, n_surv, g->lgain, r0_w, 8 * r0_w, !(opts.flags & GC_OPT_R0_FULL_LEVELS),
-                              tns));
+                              tns, (opts.flags & GC_OPT_R0_NO_PROBE) ? 0 : kR0ProbeStride));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     R0Ctl r0c;
-    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 14 * sizeof(unsigned long long),
+    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 16 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, g->stream));
     GC_TRY(sync(g));
     r0_wide_lanes = (int64_t)r0c.lanes;
@@ -914,6 +916,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     r0_bu[1] = (int64_t)r0c.bu_scanned;
     r0_bu[2] = (int64_t)r0c.bu_gathers;
     r0_bu[3] = (int64_t)r0c.dense_clears;
+    r0_probe[0] = (int64_t)r0c.probe_levels;
+    r0_probe[1] = (int64_t)r0c.probe_cut;
   } else if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)
@@ -1208,6 +1212,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->r0_bu_gathers = r0_bu[2];
     stats->r0_width = r0_w * kLanes;
     stats->r0_dense_clears = r0_bu[3];
+    stats->r0_probes = r0_probe[0];
+    stats->r0_probe_cut = r0_probe[1];
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

@@ -222,12 +222,14 @@ struct R0Ctl {
   int32_t cand[kR0MaxLanes];  // the batch: candidate ids and their list positions
   int32_t pos[kR0MaxLanes];
   unsigned long long tot[3][kR0MaxLanes];  // claims per lane at distance d, in tot[d mod 3]
+  unsigned long long far[kR0MaxLanes];     // probe: vertices proven at distance >= 3, per lane
   unsigned long long batches, levels, lanes;  // work counters
   unsigned long long td_edges;                 // adjacency entries of the top-down levels
   unsigned long long ns[4];  // CTA 0's clock: selection, top-down level, bottom-up levels with folds, clears
   unsigned long long bu_rows, bu_scanned, bu_gathers;  // bottom-up: vertices that claimed lanes, entries read, frontier words gathered
   unsigned long long co_lanes, co_surv;  // lanes of count-only batches, and those of them deferred
   unsigned long long dense_clears;       // batches that cleared every visited word
+  unsigned long long probe_levels, probe_cut;  // probe passes run, and lanes they cut
 };
 
 // Selection / reduction control block (lives across a whole greedy call).
@@ -493,9 +495,12 @@ int lazy_occupancy(int *blocks_per_sm);
 // round 0 on shallow graphs: f({v}) or -1 (cut / bound above the best) into
 // lgain[i] for list[0..m), B = 64 W lanes per batch (W in {1, 2, 4, 8}); a batch
 // whose live lanes drop below defer_below after distance 2 defers them;
-// count_only lets first-pass batches count distance 2 without writing it
+// count_only lets first-pass batches count distance 2 without writing it;
+// probe_stride > 0: those batches first probe the short rows of every
+// probe_stride-th window for vertices at distance >= 3 (0 = no probe)
+constexpr int32_t kR0ProbeStride = 8;
 int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
-                       bool count_only, int64_t timeout_ns);
+                       bool count_only, int64_t timeout_ns, int32_t probe_stride = kR0ProbeStride);
 int bfs_kernel_occupancy(int *blocks_per_sm);
 
 }  // namespace gc

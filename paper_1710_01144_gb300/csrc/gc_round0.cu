@@ -145,6 +145,9 @@ __device__ __forceinline__ void clear_frontier(u64 *buf, uint32_t *fb, int nbw, 
   }
 }
 
+template <int W>
+__device__ __forceinline__ void count_lanes(bool has, const u64 (&xw)[W], int lane, unsigned int (&lc)[2 * W]);
+
 // The end of a vertex chunk in a bottom-up pass: lane w (if `want`) has found
 // the missing lanes `nw` among its frontier neighbours; record them in its
 // visited and next-frontier words and the next bitmap, and add them to this
@@ -168,9 +171,17 @@ __device__ __forceinline__ void claim_words(int w, int base, int lane, bool want
   }
   const unsigned hm = __ballot_sync(0xffffffffu, has);
   if (write && lane == 0 && hm) atomicOr(&fbn[base >> 5], hm);  // both passes may mark this word
+  count_lanes<W>(has, nw, lane, lc);
+}
+
+// Per-lane counts of the bits of x over the warp (only where `has`):
+// lc[2k + h] += the number of threads whose word k holds bit 32h + (this
+// thread's lane), one warp ballot per lane bit.
+template <int W>
+__device__ __forceinline__ void count_lanes(bool has, const u64 (&xw)[W], int lane, unsigned int (&lc)[2 * W]) {
 #pragma unroll
   for (int k = 0; k < W; ++k) {
-    const u64 x = has ? nw[k] : 0ull;
+    const u64 x = has ? xw[k] : 0ull;
     if (!__any_sync(0xffffffffu, x != 0)) continue;
     unsigned c0 = 0, c1 = 0;
 #pragma unroll
@@ -194,12 +205,12 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
                   int32_t *defer, R0Ctl *ctl, GainCtl *gctl, u64 *vis, u64 *buf_a, u64 *buf_b, u64 *buf_c,
                   uint32_t *fb_a, uint32_t *fb_b, uint32_t *fb_c, const int32_t *__restrict__ heavy, int32_t nh,
                   const int32_t *__restrict__ hcp, u64 *hacc, int32_t defer_below, int32_t allow_count_only,
-                  unsigned long long tns) {
+                  int32_t probe_stride, unsigned long long tns) {
   constexpr int B = 64 * W;
   constexpr int T = kR0Threads;
   __shared__ int s_cand[B], s_pos[B];
   __shared__ long long s_sum[B], s_cnt[B], s_fin[B];
-  __shared__ unsigned int s_lc[B];
+  __shared__ unsigned int s_lc[B], s_fc[B];
   __shared__ int s_eoff[B + 1];
   __shared__ u64 s_alive[W];
   __shared__ int s_scan[33];
@@ -282,6 +293,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         ctl->count_only = allow_count_only && phase == 0 && 4 * ctl->co_surv <= ctl->co_lanes + 64;
       }
       for (int i = lane; i < 3 * B; i += 32) ctl->tot[i / B][i % B] = 0;  // rows are kR0MaxLanes apart
+      for (int i = lane; i < B; i += 32) ctl->far[i] = 0;
     }
     if (!grid_sync(&ctl->bar, err, tns)) break;
     lap(0);
@@ -300,6 +312,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
       s_cnt[j] = 1;  // the candidate itself
       s_fin[j] = -1;
       s_lc[j] = 0;
+      s_fc[j] = 0;
     }
     if (tid < W) {
       const int lo = 64 * tid;
@@ -440,10 +453,12 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
 #pragma unroll
       for (int k = 0; k < 2 * W; ++k) lc[k] = 0;
       unsigned int l_scan = 0, l_gath = 0, l_claim = 0;
-      // Pass A: rows of at most 32 entries, one thread each, kR0Ilp entries in
-      // flight; a lane word is loaded only while some of its missing lanes are
-      // unfound, and the scan stops once none is left.
-      for (int base = gw * 32; base < n; base += nwarps * 32) {
+      // One window of 32 vertices, its rows of at most 32 entries: one thread
+      // each, kR0Ilp entries in flight; a lane word is loaded only while some
+      // of its missing lanes are unfound, and the scan stops once none is
+      // left.  With fc, also counts per lane the vertices whose whole row held
+      // none of their missing lanes: those are at distance >= d + 2.
+      auto short_window = [&](int base, bool with_far, unsigned int(&fc)[2 * W]) {
         const int w = base + lane;
         int r0 = 0, r1 = 0;
         u64 miss[W];
@@ -460,7 +475,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
             want |= miss[k] != 0;
           }
         }
-        if (!__any_sync(0xffffffffu, want)) continue;
+        if (!__any_sync(0xffffffffu, want)) return;
         u64 acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[k] = 0;
@@ -490,10 +505,89 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
           for (int k = 0; k < W; ++k) acc[k] &= miss[k];
         }
         claim_words<W>(w, base, lane, want, acc, vis, nxt, fbn, lc, l_claim, write_lv);
+        if (with_far) {
+          u64 far[W];
+#pragma unroll
+          for (int k = 0; k < W; ++k) far[k] = miss[k] & ~acc[k];
+          count_lanes<W>(want, far, lane, fc);
+        }
+      };
+      // Pass A, the short rows, in probe_stride stages at distance 2 (the
+      // first bottom-up level): stage s takes the windows i with
+      // i mod probe_stride == s.  A vertex whose whole row held none of a
+      // lane's missing bits is at distance >= 3 from that lane's candidate,
+      // so after each stage, with far_j such vertices counted over the grid,
+      //   f({v_j}) >= sum_j + (d + 1) (n - cnt_j - far_j) + (d + 2) far_j,
+      // and a lane whose bound exceeds the best farness is cut (BFScut,
+      // Sec. 3.1) before the remaining windows, the longer rows and the hub
+      // chunks are read.  On R-MAT most vertices are at distance >= 3 from
+      // every round-0 survivor, so the first stage or two usually cut the
+      // whole batch.  A count-only batch then defers what is left (those
+      // lanes rerun in full batches) instead of reading the longer rows.
+      const bool probe = d == 1 && probe_stride > 0;
+      const int S = probe ? probe_stride : 1;
+      bool live = true;
+      for (int st = 0; st < S && live; ++st) {
+        unsigned int fc[2 * W];
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k) fc[k] = 0;
+        for (int base = (gw * S + st) * 32; base < n; base += nwarps * S * 32) short_window(base, probe, fc);
+        if (!probe) break;
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k)
+          if (fc[k]) atomicAdd(&s_fc[64 * (k >> 1) + 32 * (k & 1) + lane], fc[k]);
+        cta_sync();
+        for (int j = tid; j < nb; j += T)
+          if (s_fc[j]) {
+            atomicAdd(&ctl->far[j], (u64)s_fc[j]);
+            s_fc[j] = 0;
+          }
+        ok = grid_sync(&ctl->bar, err, tns);
+        if (!ok) break;
+        const volatile u64 *farc = ctl->far;
+        for (int j = tid; j < nb; j += T) {
+          if (!((s_alive[j >> 6] >> (j & 63)) & 1ull)) continue;
+          const long long fj = (long long)farc[j];
+          const long long lb =
+              s_sum[j] + (long long)(d + 1) * ((long long)n - s_cnt[j] - fj) + (long long)(d + 2) * fj;
+          if (lb > bf) {
+            atomicAnd(&s_alive[j >> 6], ~(1ull << (j & 63)));
+            if (b == 0) {
+              lgain[s_pos[j]] = -1;  // cut: cannot beat the best farness
+              atomicAdd(&ctl->probe_cut, 1ull);
+            }
+          }
+        }
+        if (b == 0 && tid == 0) ++ctl->probe_levels;
+        cta_sync();
+        live = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) live |= s_alive[k] != 0;
+      }
+      if (!ok) break;
+      if (probe && co && live) {
+        // count-only: the lanes the short rows could not cut run later in
+        // full batches of their own
+        if (b == 0 && tid == 0) {
+          int at = ctl->n_defer, cnt = 0;
+          for (int j = 0; j < nb; ++j)
+            if ((s_alive[j >> 6] >> (j & 63)) & 1ull) {
+              defer[2 * at] = s_cand[j];
+              defer[2 * at + 1] = s_pos[j];
+              ++at;
+              ++cnt;
+            }
+          ctl->n_defer = at;
+          ctl->co_surv += (unsigned long long)cnt;
+        }
+        cta_sync();
+        if (tid < W) s_alive[tid] = 0ull;
+        cta_sync();
+        live = false;
       }
       // Pass B: rows of 33 .. kHeavyRow entries, the whole warp on one vertex
       // at a time (coalesced column loads, kR0Ilp per lane in flight).
-      for (int base = gw * 32; base < n; base += nwarps * 32) {
+      for (int base = gw * 32; live && base < n; base += nwarps * 32) {
         const int w = base + lane;
         int r0 = 0, r1 = 0;
         u64 miss[W];
@@ -564,7 +658,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
 #pragma unroll
       for (int k = 0; k < W; ++k) al[k] = s_alive[k];
       // heavy rows: chunks of kHeavyRow entries, partial ORs into hacc
-      for (int c = gw; c < C; c += nwarps) {
+      for (int c = gw; live && c < C; c += nwarps) {
         int lo = 0, hi = nh - 1;  // heavy row holding chunk c
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -812,7 +906,7 @@ static int round0_workspace(gc_graph *g, int W) {
 }
 
 int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *lgain, int W, int32_t defer_below,
-                       bool count_only, int64_t timeout_ns) {
+                       bool count_only, int64_t timeout_ns, int32_t probe_stride) {
   if (m <= 0) return GC_OK;
   if (W != 1 && W != 2 && W != 4 && W != 8) return GC_EINVAL;
   int rc = round0_workspace(g, W);
@@ -843,7 +937,7 @@ int launch_round0_wide(gc_graph *g, const int32_t *list, int32_t m, long long *l
                   (void *)&lgain, (void *)&defer, (void *)&ctl, (void *)&gctl,     (void *)&vis,   (void *)&b0,
                   (void *)&b1,   (void *)&b2,   (void *)&f0,   (void *)&f1,       (void *)&f2,    (void *)&heavy,
                   (void *)&nh,   (void *)&hcp,  (void *)&hacc, (void *)&defer_below, (void *)&allow_co,
-                  (void *)&tns};
+                  (void *)&probe_stride, (void *)&tns};
   ++g->launches;
   GC_CUDA(cudaLaunchCooperativeKernel(round0_fn(W), dim3(grid), dim3(kR0Threads), args, round0_dyn_smem(W),
                                       g->stream));

@@ -32,6 +32,7 @@ GC_OPT_CAPTURE = 0x2
 GC_OPT_FULL_ADJACENCY = 0x4
 GC_OPT_NO_ROUND1_BOUND = 0x8
 GC_OPT_R0_FULL_LEVELS = 0x10
+GC_OPT_R0_NO_PROBE = 0x40
 GC_OPT_NO_CLAIM_LOG = 0x20
 
 # every entry point declared in include/gc.h
@@ -79,7 +80,7 @@ class Stats(ctypes.Structure):
         ("ms_r0_bottomup", ctypes.c_double), ("ms_r0_clear", ctypes.c_double), ("r0_bu_rows", ctypes.c_int64),
         ("r0_bu_scanned", ctypes.c_int64), ("r0_bu_gathers", ctypes.c_int64), ("r0_width", ctypes.c_int64),
         ("r0_dense_clears", ctypes.c_int64), ("lazy_log_picks", ctypes.c_int64), ("lazy_upd_log", ctypes.c_int64),
-        ("lazy_log_entries", ctypes.c_int64)]
+        ("lazy_log_entries", ctypes.c_int64), ("r0_probes", ctypes.c_int64), ("r0_probe_cut", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -261,7 +262,7 @@ class Graph:
                active_target: int = 0, round1_heavy: int = 0, expand_bound: bool = True,
                step_form: int = 0, local_update_max_gain: int = 0, lazy_ctas: int = 0,
                pruned_adjacency: bool = True, round1_bound: bool = True, timeout_us: int = 0,
-               round0_lanes: int = 0, r0_full_levels: bool = False, claim_log: bool = True,
+               round0_lanes: int = 0, r0_full_levels: bool = False, r0_probe: bool = True, claim_log: bool = True,
                claim_log_cap: int = 0):
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
@@ -270,6 +271,7 @@ class Graph:
         o.round1_heavy = round1_heavy
         o.flags = ((0 if expand_bound else GC_OPT_NO_EXPAND_BOUND) | (0 if pruned_adjacency else GC_OPT_FULL_ADJACENCY)
                    | (0 if round1_bound else GC_OPT_NO_ROUND1_BOUND) | (GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0)
+                   | (0 if r0_probe else GC_OPT_R0_NO_PROBE)
                    | (0 if claim_log else GC_OPT_NO_CLAIM_LOG))
         o.step_form, o.local_update_max_gain = step_form, local_update_max_gain
         o.lazy_ctas = lazy_ctas
@@ -319,13 +321,14 @@ class Graph:
                                      ctypes.byref(st)))
         return grp[:k], f.value, st.as_dict()
 
-    def top_closeness(self, k: int, round0_lanes: int = 0, max_ctas: int = 0, r0_full_levels: bool = False):
+    def top_closeness(self, k: int, round0_lanes: int = 0, max_ctas: int = 0, r0_full_levels: bool = False,
+                      r0_probe: bool = True):
         """gc_top_closeness: (ids, farness values, stats) of the k vertices of
         smallest farness, ordered by (farness, id)."""
         o = Opts()
         load().gc_opts_default(ctypes.byref(o))
         o.round0_lanes, o.max_ctas = round0_lanes, max_ctas
-        o.flags = GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0
+        o.flags = (GC_OPT_R0_FULL_LEVELS if r0_full_levels else 0) | (0 if r0_probe else GC_OPT_R0_NO_PROBE)
         ids = np.zeros(max(int(k), 1), dtype=np.int32)
         f = np.zeros(max(int(k), 1), dtype=np.int64)
         st = Stats()

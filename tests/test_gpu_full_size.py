@@ -112,12 +112,13 @@ def test_greedy_rmat24_k50_full_size(gcm):
     grp = np.array([int(x) for x in gold["group"]], dtype=np.int32)
     ft = np.array([int(x) for x in gold["farness"]], dtype=np.int64)
     with gcm.Graph(rp, ci) as G:
-        for kw in ({}, {"step_mode": 1, "eval_per_step": 128}, {"round0_lanes": -1}):
+        for kw in ({}, {"step_mode": 1, "eval_per_step": 128}, {"round0_lanes": -1}, {"r0_probe": False}):
             got, f, st = G.greedy(50, **kw)
             np.testing.assert_array_equal(got, grp)
             assert f == ft[-1]
             if not kw:  # the persistent rounds' d_S updates come from the claim log (up to overflow)
                 assert 0 < st["lazy_log_picks"] <= 48
+                assert st["r0_probe_cut"] > 0  # the far-vertex probe cut round-0 lanes
         # the farness of the first ten picks, recomputed by one oracle BFS
         assert G.farness(grp[:10]) == ft[9] == oracle.farness(rp, ci, grp[:10])
 

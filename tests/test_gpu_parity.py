@@ -346,6 +346,33 @@ def round0_cases():
             ("rmat12", graphgen.rmat(12, 16.0, seed=1)), ("star70", sg.star(70)), ("k9", sg.complete(9))]
 
 
+@pytest.mark.parametrize("name,g", round0_cases() + [("rmat14", graphgen.rmat(14, 16.0, seed=2)),
+                                                     ("rmat15", graphgen.rmat(15, 16.0, seed=3))])
+@pytest.mark.parametrize("lanes", [64, 256])
+def test_round0_probe_on_off(gcm, name, g, lanes):
+    """Round 0 with and without the far-vertex probe before the count-only
+    distance-2 pass (vertices proven at distance >= 3 raise the BFScut bound
+    and cut lanes early): the oracle's s0 and farness, its top-5 closeness,
+    and the same group."""
+    rp, ci = g
+    s0, f0, _ = oracle.top1_closeness(rp, ci)
+    k = 3
+    grp, ft, _, _ = oracle.greedypp(rp, ci, k)
+    ids, fs, _ = oracle.topk_closeness(rp, ci, 5)
+    with gcm.Graph(rp, ci) as G:
+        for probe in (True, False):
+            got, f, st = G.greedy(k, round0_lanes=lanes, r0_probe=probe)
+            np.testing.assert_array_equal(got, grp)
+            assert f == ft[-1]
+            if not probe:
+                assert st["r0_probes"] == 0
+            got1, f1, _ = G.greedy(1, round0_lanes=lanes, r0_probe=probe)
+            assert got1[0] == s0 and f1 == f0
+            ti, tf = G.top_closeness(5, round0_lanes=lanes, r0_probe=probe)[:2]
+            np.testing.assert_array_equal(ti, ids)
+            np.testing.assert_array_equal(tf, fs)
+
+
 @pytest.mark.parametrize("name,g", round0_cases())
 @pytest.mark.parametrize("lanes", [64, 128, 256, 512, -1])
 def test_round0_wide_lane_widths(gcm, name, g, lanes):
