@@ -235,17 +235,19 @@ def algorithmic_bytes(frontier, edges, pushes, lanes) -> float:
 
 def round0_kernel_bytes(t, n) -> float:
     """Algorithmic bytes of the wide round-0 kernel (bottom-up bit-parallel
-    BFScut, B = r0_width lanes, B/8 bytes per lane word): per bottom-up level,
-    every vertex's row pointers (8 B) and visited word (B/8 B); 4 B per
-    adjacency entry read; per vertex whose claim is written, its visited and
-    claim words (2 B/8 B) and the later clear of the claim word (B/8 B); per
-    top-down adjacency entry 4 B plus the two 8-byte words it sets and their
-    later clear (32 B); per batch that wrote bottom-up levels the dense clear
-    of the visited words (n B/8 B).  Gathered frontier words are not counted:
-    each re-reads a word already counted when it was written (most hit L2)."""
+    BFScut, B = r0_width lanes, B/8 bytes per lane word): in the bottom-up
+    passes, the row pointers (8 B) of every vertex they visit and the visited
+    word (B/8 B) of every vertex whose row they consider (the far-vertex probe
+    stages visit only part of the vertices); 4 B per adjacency entry read; per
+    vertex whose claim is written, its visited and claim words (2 B/8 B) and
+    the later clear of the claim word (B/8 B); per top-down adjacency entry 4 B
+    plus the two 8-byte words it sets and their later clear (32 B); per batch
+    that wrote bottom-up levels the dense clear of the visited words (n B/8 B).
+    Gathered frontier words are not counted: each re-reads a word already
+    counted when it was written (most hit L2)."""
     wb = t["r0_width"] / 8.0 if t["r0_width"] else 0.0
-    return (t["r0_levels"] * n * (8.0 + wb) + 4.0 * t["r0_bu_scanned"] + 3.0 * wb * t["r0_bu_rows"] +
-            36.0 * t["r0_td_edges"] + t["r0_dense_clears"] * n * wb)
+    return (8.0 * t["r0_bu_vertices"] + wb * t["r0_bu_visreads"] + 4.0 * t["r0_bu_scanned"] +
+            3.0 * wb * t["r0_bu_rows"] + 36.0 * t["r0_td_edges"] + t["r0_dense_clears"] * n * wb)
 
 
 def golden_for(scale: int, k: int):
@@ -380,10 +382,11 @@ def run_gc(args):
             "config": config_dict(args, n, nnz, "flushed between steps (512 MiB write outside the timed window)"),
             "gteps_scalar": tot["edges_scalar"] / (sum(times) * 1e-3) / 1e9,
             "gteps_union": tot["edges_union"] / (sum(times) * 1e-3) / 1e9,
-            "work_per_step": {k: tot[k] // args.steps for k in
-                              ("evals", "steps", "batches", "edges_scalar", "edges_union", "levels",
-                               "round0_evals", "gain_launches", "kernel_launches", "r0_batches", "r0_levels",
-                               "r0_width", "r0_bu_scanned", "r0_bu_gathers", "r0_td_edges")},
+            "work_per_step": dict({k: tot[k] // args.steps for k in
+                                   ("evals", "steps", "batches", "edges_scalar", "edges_union", "levels",
+                                    "round0_evals", "gain_launches", "kernel_launches", "r0_batches", "r0_levels",
+                                    "r0_bu_scanned", "r0_bu_gathers", "r0_td_edges", "r0_probes", "r0_probe_cut",
+                                    "r0_bu_vertices", "r0_bu_visreads")}, r0_width=tot["r0_width"]),
             "ms_round0": per("ms_round0"),
             "ms_round1": per("ms_round1"),
             "ms_phases": {k: per(k) for k in ("ms_round0_wide", "ms_r0_topdown", "ms_r0_bottomup", "ms_r0_clear",

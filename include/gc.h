@@ -213,8 +213,10 @@ typedef struct gc_stats {
   int64_t lazy_log_picks;    /* picks updated from the log */
   int64_t lazy_upd_log;      /* log entries those updates read */
   int64_t lazy_log_entries;  /* log entries the gain phases wrote (16 bytes each) */
-  int64_t r0_probes;         /* round 0, wide batches: far-vertex probes run */
+  int64_t r0_probes;         /* round 0, wide batches: far-vertex probe stages run */
   int64_t r0_probe_cut;      /* and the lanes they cut */
+  int64_t r0_bu_vertices;    /* bottom-up: vertices whose row pointers were read */
+  int64_t r0_bu_visreads;    /* bottom-up: visited lane words read (per vertex) */
 } gc_stats;
 
 /* gc_opts_default: fill *opts with the defaults.  Returns GC_OK or GC_EINVAL. */

@@ -803,7 +803,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
   int64_t r0_stats[3] = {0, 0, 0};  // wide round-0 kernel: batches, bottom-up levels, top-down entries
   double r0_ms[4] = {0, 0, 0, 0};     // and its phases: selection, top-down, bottom-up, clears
   int64_t r0_bu[4] = {0, 0, 0, 0};    // its bottom-up claiming rows, entries read, words gathered, dense clears
-  int64_t r0_probe[2] = {0, 0};       // its probe passes and the lanes they cut
+  int64_t r0_probe[4] = {0, 0, 0, 0};  // its probe stages, the lanes they cut, row-pointer pairs and visited words read
   bool pruned = false;  // the pruned adjacency is built after round 0
   std::vector<char> ev_k64;  // per event pair: 1 = CTA-batched gain kernel, 0 = grid-wide, 2 = persistent
   auto gains_timed = [&](int mode, const int32_t *cand, int32_t n_cand, const int32_t *n_dev,
@@ -904,7 +904,7 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
                               tns, (opts.flags & GC_OPT_R0_NO_PROBE) ? 0 : kR0ProbeStride));
     GC_CUDA(cudaEventRecord(e1, g->stream));
     R0Ctl r0c;
-    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 16 * sizeof(unsigned long long),
+    GC_CUDA(cudaMemcpyAsync(&r0c.batches, &g->r0_ctl->batches, 18 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, g->stream));
     GC_TRY(sync(g));
     r0_wide_lanes = (int64_t)r0c.lanes;
@@ -918,6 +918,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     r0_bu[3] = (int64_t)r0c.dense_clears;
     r0_probe[0] = (int64_t)r0c.probe_levels;
     r0_probe[1] = (int64_t)r0c.probe_cut;
+    r0_probe[2] = (int64_t)r0c.bu_vertices;
+    r0_probe[3] = (int64_t)r0c.bu_visreads;
   } else if (n_surv <= kRound0GridMax) {
     // few survivors (hubs with large searches): one grid-wide batch per 64
     for (int32_t off = 0; off < n_surv; off += kLanes)
@@ -1214,6 +1216,8 @@ int gc_greedy(gc_graph *g, int32_t k, const gc_opts *opts_in, int32_t *out_group
     stats->r0_dense_clears = r0_bu[3];
     stats->r0_probes = r0_probe[0];
     stats->r0_probe_cut = r0_probe[1];
+    stats->r0_bu_vertices = r0_probe[2];
+    stats->r0_bu_visreads = r0_probe[3];
     stats->ms_lazy_select = lazy_ms[0];
     stats->ms_lazy_gain = lazy_ms[1];
     stats->ms_lazy_update = lazy_ms[2];

@@ -229,7 +229,8 @@ struct R0Ctl {
   unsigned long long bu_rows, bu_scanned, bu_gathers;  // bottom-up: vertices that claimed lanes, entries read, frontier words gathered
   unsigned long long co_lanes, co_surv;  // lanes of count-only batches, and those of them deferred
   unsigned long long dense_clears;       // batches that cleared every visited word
-  unsigned long long probe_levels, probe_cut;  // probe passes run, and lanes they cut
+  unsigned long long probe_levels, probe_cut;  // probe stages run, and lanes they cut
+  unsigned long long bu_vertices, bu_visreads;  // bottom-up: row-pointer pairs and visited words read
 };
 
 // Selection / reduction control block (lives across a whole greedy call).

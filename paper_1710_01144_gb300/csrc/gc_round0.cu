@@ -35,6 +35,14 @@
 //   sum sum_j):  f({v_j}) >= sum_j + (d + 1) (n - cnt_j);  cut if > best.
 // best only decreases (completed lanes), so every CTA keeps the same copy.
 //
+// The first bottom-up level (distance 2) reads the short rows in stages (the
+// far-vertex probe): a vertex whose whole row holds none of a lane's missing
+// bits is at distance >= 3 from that lane's candidate, and counting such
+// vertices raises the lane's bound above the usual "every unvisited vertex at
+// d + 1" form.  Most round-0 survivors of R-MAT graphs are at distance >= 3
+// from most vertices, so a stage or two cut a whole batch before its longer
+// rows and hub chunks are read.
+//
 // Survivors are taken in list order while their lower bound is at most the
 // best farness so far.  A batch whose live lanes fall below `defer_below`
 // after the distance-2 cut hands them to a deferred list and ends, so that a
@@ -224,6 +232,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
   uint32_t *fbs[3] = {fb_a, fb_b, fb_c};
   const int C = nh > 0 ? hcp[nh] : 0;  // heavy-row chunks
   u64 w_batches = 0, w_levels = 0, w_lanes = 0, w_td = 0, w_scan = 0, w_gath = 0, w_claim = 0;
+  u64 w_vert = 0, w_visr = 0;  // bottom-up: row-pointer pairs and visited words read
   const bool timer = b == 0 && tid == 0;
   u64 t_prev = timer ? global_ns() : 0, t_ph[4] = {0, 0, 0, 0};
   auto lap = [&](int i) {
@@ -452,7 +461,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
       unsigned int lc[2 * W];
 #pragma unroll
       for (int k = 0; k < 2 * W; ++k) lc[k] = 0;
-      unsigned int l_scan = 0, l_gath = 0, l_claim = 0;
+      unsigned int l_scan = 0, l_gath = 0, l_claim = 0, l_vert = 0, l_visr = 0;
       // One window of 32 vertices, its rows of at most 32 entries: one thread
       // each, kR0Ilp entries in flight; a lane word is loaded only while some
       // of its missing lanes are unfound, and the scan stops once none is
@@ -466,8 +475,10 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         if (w < n) {
           r0 = __ldg(rp + w);
           r1 = __ldg(rp + w + 1);
+          ++l_vert;
         }
         if (r1 - r0 <= 32 && r1 > r0) {
+          ++l_visr;
           ld_words<W>(vis + (size_t)w * W, miss);
 #pragma unroll
           for (int k = 0; k < W; ++k) {
@@ -595,8 +606,10 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         if (w < n) {
           r0 = __ldg(rp + w);
           r1 = __ldg(rp + w + 1);
+          ++l_vert;
         }
         if (r1 - r0 > 32 && r1 - r0 <= kHeavyRow) {
+          ++l_visr;
           ld_words<W>(vis + (size_t)w * W, miss);
 #pragma unroll
           for (int k = 0; k < W; ++k) {
@@ -670,6 +683,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         const int a1 = min(__ldg(rp + h + 1), a0 + kHeavyRow);
         u64 vh[W], ms[W], ac[W];
         ld_words<W>(vis + (size_t)h * W, vh);
+        ++l_visr;
         bool any = false;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -721,6 +735,8 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         if (lc[k]) atomicAdd(&s_lc[64 * (k >> 1) + 32 * (k & 1) + lane], lc[k]);
       w_scan += l_scan;
       w_gath += l_gath;
+      w_vert += l_vert;
+      w_visr += l_visr;
       ok = grid_sync(&ctl->bar, err, tns);
       if (!ok) break;
       // heavy rows: apply the accumulated lanes
@@ -804,7 +820,11 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
   w_scan = block_sum(w_scan, (u64 *)s_red);
   w_gath = block_sum(w_gath, (u64 *)s_red);
   w_claim = block_sum(w_claim, (u64 *)s_red);
+  w_vert = block_sum(w_vert, (u64 *)s_red);
+  w_visr = block_sum(w_visr, (u64 *)s_red);
   if (tid == 0) {
+    atomicAdd(&ctl->bu_vertices, w_vert);
+    atomicAdd(&ctl->bu_visreads, w_visr);
     atomicAdd(&ctl->bu_scanned, w_scan);
     atomicAdd(&ctl->bu_gathers, w_gath);
     atomicAdd(&ctl->bu_rows, w_claim);

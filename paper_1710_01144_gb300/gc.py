@@ -80,7 +80,8 @@ class Stats(ctypes.Structure):
         ("ms_r0_bottomup", ctypes.c_double), ("ms_r0_clear", ctypes.c_double), ("r0_bu_rows", ctypes.c_int64),
         ("r0_bu_scanned", ctypes.c_int64), ("r0_bu_gathers", ctypes.c_int64), ("r0_width", ctypes.c_int64),
         ("r0_dense_clears", ctypes.c_int64), ("lazy_log_picks", ctypes.c_int64), ("lazy_upd_log", ctypes.c_int64),
-        ("lazy_log_entries", ctypes.c_int64), ("r0_probes", ctypes.c_int64), ("r0_probe_cut", ctypes.c_int64)]
+        ("lazy_log_entries", ctypes.c_int64), ("r0_probes", ctypes.c_int64), ("r0_probe_cut", ctypes.c_int64),
+        ("r0_bu_vertices", ctypes.c_int64), ("r0_bu_visreads", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
