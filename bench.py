@@ -178,7 +178,7 @@ KERNEL_SOURCES = {
 TRAFFIC_FILES = {
     "k_round0_wide": os.path.join(ROOT, "profiles", "dram_traffic_round0_wide_rmat.txt"),
     "k_gains64": os.path.join(ROOT, "profiles", "dram_traffic_rmat_s20_k100.txt"),
-    "k_lazy_rounds": os.path.join(ROOT, "profiles", "dram_traffic_rmat_s20_k100.txt"),
+    "k_lazy_rounds": os.path.join(ROOT, "profiles", "dram_traffic_lazy_rounds_rmat_s24.txt"),
 }
 
 
