@@ -241,13 +241,16 @@ def round0_kernel_bytes(t, n) -> float:
     stages visit only part of the vertices); 4 B per adjacency entry read; per
     vertex whose claim is written, its visited and claim words (2 B/8 B) and
     the later clear of the claim word (B/8 B); per top-down adjacency entry 4 B
-    plus the two 8-byte words it sets and their later clear (32 B); per batch
-    that wrote bottom-up levels the dense clear of the visited words (n B/8 B).
+    plus the 8-byte visited word it sets and its later clear (20 B: a
+    count-only batch sets no distance-1 claim word; the first-pass batches,
+    where nearly every top-down entry lies, are count-only, and the second word
+    that full batches set is not counted); per batch that wrote bottom-up
+    levels the dense clear of the visited words (n B/8 B).
     Gathered frontier words are not counted: each re-reads a word already
     counted when it was written (most hit L2)."""
     wb = t["r0_width"] / 8.0 if t["r0_width"] else 0.0
     return (8.0 * t["r0_bu_vertices"] + wb * t["r0_bu_visreads"] + 4.0 * t["r0_bu_scanned"] +
-            3.0 * wb * t["r0_bu_rows"] + 36.0 * t["r0_td_edges"] + t["r0_dense_clears"] * n * wb)
+            3.0 * wb * t["r0_bu_rows"] + 20.0 * t["r0_td_edges"] + t["r0_dense_clears"] * n * wb)
 
 
 def golden_for(scale: int, k: int):

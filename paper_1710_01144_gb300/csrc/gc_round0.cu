@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
         const size_t at = (size_t)w * W + (lo >> 6);
         const u64 old = atomicOr(&vis[at], bit);
         if (!(old & bit)) {
-          atomicOr(&nx1[at], bit);
+          if (!co) atomicOr(&nx1[at], bit);  // (a count-only pass reads vis instead, see below)
           atomicOr(&fb1[w >> 5], 1u << (w & 31));
           atomicAdd(&s_lc[lo], 1u);
         }
@@ -453,7 +453,13 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
       // end or are deferred at the next fold)
       const bool write_lv = !(co && d == 1);
       wrote |= write_lv;
-      const u64 *cur = bufs[d % 3];
+      // The frontier words of distance d.  A count-only pass writes no visited
+      // word, so at distance 1 it reads vis (lanes within distance 1) for the
+      // frontier's words: a lane j that vis adds beyond the distance-1 claims
+      // has the frontier vertex as its candidate, so every neighbour u of it
+      // is within distance 1 of v_j and lane j is not missing at u.  The
+      // top-down level then skips the claim words of distance 1.
+      const u64 *cur = (co && d == 1) ? vis : bufs[d % 3];
       const uint32_t *fbc = fbs[d % 3];
       u64 *nxt = bufs[(d + 1) % 3];
       uint32_t *fbn = fbs[(d + 1) % 3];
@@ -799,7 +805,7 @@ __global__ void __launch_bounds__(kR0Threads, W <= 4 ? 2 : 1)
           const u64 z[W] = {};
           st_words<W>(vis + (size_t)s_cand[j] * W, z);
         }
-      clear_frontier<W>(vis, fbs[1], nbw, false);
+      clear_frontier<W>(vis, fbs[1], nbw, co);  // (count-only: no distance-1 claim words to clear)
       cta_sync();
       if (!grid_sync(&ctl->bar, err, tns)) break;
     }
