@@ -353,11 +353,6 @@ __global__ void __launch_bounds__(kGainThreads, W <= 2 ? 2 : 1)
   }
 }
 
-template <int W>
-const void *wide_fn() {
-  return reinterpret_cast<const void *>(k_gains_wide<W>);
-}
-
 }  // namespace
 
 size_t gain_wide_ws_stride(int32_t n, int W) {
@@ -368,7 +363,8 @@ size_t gain_wide_ws_stride(int32_t n, int W) {
 // when W changes), one per resident CTA within 40% of free memory and 16 GB.
 static int wide_workspace(gc_graph *g, int W) {
   if (g->x_ws && g->x_w == W) return GC_OK;
-  if (g->x_ws) {
+  if (g->x_ws) {  // (an earlier launch on the handle's stream may still use it)
+    GC_CUDA(cudaStreamSynchronize(g->stream));
     cudaFree(g->x_ws);
     g->x_ws = nullptr;
     g->x_w = 0;
